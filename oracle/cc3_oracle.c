@@ -1,0 +1,611 @@
+/*
+ * Plain FP64 CPU oracle for the closed-shell CC3 triples hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library may link, load or
+ * call this file; only the test-suite, the smoke check and the CPU-baseline leg
+ * of the benchmark use it.  It shares no code with the GPU path.
+ *
+ * What it computes (Paul, Myhre, Koch, "A new and efficient implementation of
+ * CC3", arXiv 2007.01088, section "Implementation"):
+ *
+ *   oracle_omega      Algorithm 1 (CC3 ground-state triples residual): the
+ *                     restricted loop i >= j >= k, the permutation operator
+ *                     P^{abc}_{ijk} (eq. "permutation"), the orbital-energy
+ *                     denominator, the contravariant combination of Algorithm 1,
+ *                     the four contractions for every distinct permutation of
+ *                     (i,j,k), and the back-transform (1/3) P^{ab}_{ij}(2X+X^{ba}).
+ *   oracle_prep       Algorithm 2 (Z^v and Z^o intermediates).
+ *   oracle_jacobian   The right CC3 Jacobian transformation of trial vectors,
+ *                     reconstructed from eq. "jcc3": R3 = (w - eps)^{-1}
+ *                     <mu3|[H,R2] + [[H,R1],T2]>, rho = <mu1|[H,R3]> and
+ *                     <mu2|[H,R3]> + <mu2|[[H,R1],T3]>, with the R1-dressed
+ *                     integrals from the first-order T1 transformation.
+ *
+ * The integrals enter in the general five-block form, so that the same code
+ * serves T1-transformed (non-symmetric) integrals:
+ *   vvvo[b][d][c][k] = g_{bdck}     oovo[l][j][c][k] = g_{ljck}
+ *   ooov[j][l][k][c] = g_{jlkc}     ovov[j][b][k][c] = g_{jbkc}
+ *   vvov[d][b][k][c] = g_{dbkc}     F_ov[k][c]
+ * and t2[i][j][a][b] = t^{ab}_{ij}, omega1[i][a], omega2[i][j][a][b].
+ *
+ * Readings of the paper taken here (the paper is silent or garbled there):
+ *  - The contravariant amplitudes permute the virtual indices with i,j,k fixed
+ *    (Algorithm 1 form); eq. "contra_t" as printed permutes both index sets.
+ *  - "For permutations of i,j,k" runs over the DISTINCT ordered triples
+ *    (6, 3 or 0 of them); for (p,q,r) = (ijk[s0], ijk[s1], ijk[s2]) the
+ *    amplitude tau^{xyz}_{pqr} is the element of tau_{ijk} that holds x in slot
+ *    s0, y in slot s1 and z in slot s2 (each virtual index travels with its
+ *    occupied partner, by the six-fold symmetry).
+ *  - P^{ab}_{ij} X^{ab}_{ij} = X^{ab}_{ij} + X^{ba}_{ji} in the back-transform.
+ *  - The triples energy is E_T = sum_{ijab} t^{ab}_{ij} Omega~^{ab}_{ij}.
+ *  - tau = -W / eps with eps^{abc}_{ijk} = e_a+e_b+e_c-e_i-e_j-e_k (plain
+ *    orbital energies); the R3 denominator is (w - eps)^{-1}.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+  int no, nv;
+  const double *eps_o, *eps_v, *t2;
+  const double *vvvo, *oovo, *ooov, *ovov, *vvov, *F_ov;
+} blocks_t;
+
+#define T2(B, i, j, a, b) (B)->t2[(((size_t)(i) * (B)->no + (j)) * (B)->nv + (a)) * (B)->nv + (b)]
+#define VVVO(B, b, d, c, k) (B)->vvvo[(((size_t)(b) * (B)->nv + (d)) * (B)->nv + (c)) * (B)->no + (k)]
+#define OOVO(B, l, j, c, k) (B)->oovo[(((size_t)(l) * (B)->no + (j)) * (B)->nv + (c)) * (B)->no + (k)]
+#define OOOV(B, j, l, k, c) (B)->ooov[(((size_t)(j) * (B)->no + (l)) * (B)->no + (k)) * (B)->nv + (c)]
+#define OVOV(B, j, b, k, c) (B)->ovov[(((size_t)(j) * (B)->nv + (b)) * (B)->no + (k)) * (B)->nv + (c)]
+#define VVOV(B, d, b, k, c) (B)->vvov[(((size_t)(d) * (B)->nv + (b)) * (B)->no + (k)) * (B)->nv + (c)]
+
+/* The six terms of the permutation operator P^{abc}_{ijk}: term s puts the
+ * ordered occupied triple (ijk[s0], ijk[s1], ijk[s2]) with virtual indices
+ * (v[s0], v[s1], v[s2]), v = (a,b,c).  Order as in eq. "permutation":
+ * B^{abc}_{ijk} + B^{bac}_{jik} + B^{cba}_{kji} + B^{acb}_{ikj} + B^{bca}_{jki}
+ * + B^{cab}_{kij}. */
+static const int PERM6[6][3] = {{0, 1, 2}, {1, 0, 2}, {2, 1, 0},
+                                {0, 2, 1}, {1, 2, 0}, {2, 0, 1}};
+
+/* B_{pqr}[x][y][z] = sum_d t^{xd}_{pq} g_{ydzr} - sum_l t^{xy}_{pl} g_{lqzr}
+ * (the bracket of the tau line of Algorithms 1 and 2 for one ordered triple).
+ * t and the two integral blocks are passed separately so that the Jacobian can
+ * call the same builder with (R2, g) and (t2, g-hat). */
+static void build_B(int no, int nv, const double *t, const double *gvvvo,
+                    const double *goovo, int p, int q, int r, double *Bout,
+                    long long *flops) {
+  size_t nv2 = (size_t)nv * nv;
+  for (int x = 0; x < nv; ++x)
+    for (int y = 0; y < nv; ++y)
+      for (int z = 0; z < nv; ++z) {
+        double s = 0.0;
+        const double *tr = t + (((size_t)p * no + q) * nv + x) * nv;
+        for (int d = 0; d < nv; ++d)
+          s += tr[d] * gvvvo[(((size_t)y * nv + d) * nv + z) * no + r];
+        for (int l = 0; l < no; ++l)
+          s -= t[(((size_t)p * no + l) * nv + x) * nv + y] *
+               goovo[(((size_t)l * no + q) * nv + z) * no + r];
+        Bout[(size_t)x * nv2 + (size_t)y * nv + z] = s;
+      }
+  /* dominant term only: the d-sum is one nv x nv^2 x nv contraction */
+  if (flops) *flops += 2LL * nv * nv * nv * nv;
+}
+
+/* W = P^{abc}_{ijk} B for one unique triple; each distinct ordered triple's B
+ * is built once and placed in every slot arrangement P asks for. */
+static void build_W(int no, int nv, const double *t, const double *gvvvo,
+                    const double *goovo, const int ijk[3], double *W,
+                    double *Bscratch, long long *flops) {
+  size_t nv2 = (size_t)nv * nv, nv3 = nv2 * nv;
+  memset(W, 0, nv3 * sizeof(double));
+  int done[6] = {0, 0, 0, 0, 0, 0};
+  for (int s = 0; s < 6; ++s) {
+    if (done[s]) continue;
+    int p = ijk[PERM6[s][0]], q = ijk[PERM6[s][1]], r = ijk[PERM6[s][2]];
+    build_B(no, nv, t, gvvvo, goovo, p, q, r, Bscratch, flops);
+    for (int s2 = s; s2 < 6; ++s2) {
+      if (ijk[PERM6[s2][0]] != p || ijk[PERM6[s2][1]] != q ||
+          ijk[PERM6[s2][2]] != r)
+        continue;
+      done[s2] = 1;
+      const int *m = PERM6[s2];
+      int v[3];
+      for (v[0] = 0; v[0] < nv; ++v[0])
+        for (v[1] = 0; v[1] < nv; ++v[1])
+          for (v[2] = 0; v[2] < nv; ++v[2]) {
+            size_t src = (size_t)v[m[0]] * nv2 + (size_t)v[m[1]] * nv + v[m[2]];
+            W[(size_t)v[0] * nv2 + (size_t)v[1] * nv + v[2]] += Bscratch[src];
+          }
+    }
+  }
+}
+
+/* tau~^{abc} = 4 tau^{abc} - 2 tau^{acb} - 2 tau^{cba} - 2 tau^{bac}
+ *              + tau^{bca} + tau^{cab}      (Algorithm 1, i,j,k fixed) */
+static void contravariant(int nv, const double *tau, double *tt) {
+  size_t nv2 = (size_t)nv * nv;
+#define TAU(a, b, c) tau[(size_t)(a) * nv2 + (size_t)(b) * nv + (c)]
+  for (int a = 0; a < nv; ++a)
+    for (int b = 0; b < nv; ++b)
+      for (int c = 0; c < nv; ++c)
+        tt[(size_t)a * nv2 + (size_t)b * nv + c] =
+            4.0 * TAU(a, b, c) - 2.0 * TAU(a, c, b) - 2.0 * TAU(c, b, a) -
+            2.0 * TAU(b, a, c) + TAU(b, c, a) + TAU(c, a, b);
+#undef TAU
+}
+
+/* The distinct ordered permutations of (i,j,k): returns how many (6, 3 or 0)
+ * and, for each, the slot map s (p,q,r) = (ijk[s0], ijk[s1], ijk[s2]). */
+static int distinct_perms(const int ijk[3], int maps[6][3]) {
+  int n = 0;
+  if (ijk[0] == ijk[1] && ijk[1] == ijk[2]) return 0;
+  for (int s = 0; s < 6; ++s) {
+    int p = ijk[PERM6[s][0]], q = ijk[PERM6[s][1]], r = ijk[PERM6[s][2]];
+    int seen = 0;
+    for (int u = 0; u < n; ++u)
+      if (ijk[maps[u][0]] == p && ijk[maps[u][1]] == q && ijk[maps[u][2]] == r)
+        seen = 1;
+    if (!seen) {
+      maps[n][0] = PERM6[s][0];
+      maps[n][1] = PERM6[s][1];
+      maps[n][2] = PERM6[s][2];
+      ++n;
+    }
+  }
+  return n;
+}
+
+/* View V[x][y][z] = tau~^{xyz}_{pqr} taken from tau~_{ijk}: x sits in slot
+ * m[0], y in slot m[1], z in slot m[2]. */
+static void permuted_view(int nv, const double *tt, const int m[3], double *V) {
+  size_t nv2 = (size_t)nv * nv;
+  int s[3];
+  for (int x = 0; x < nv; ++x)
+    for (int y = 0; y < nv; ++y)
+      for (int z = 0; z < nv; ++z) {
+        s[m[0]] = x;
+        s[m[1]] = y;
+        s[m[2]] = z;
+        V[(size_t)x * nv2 + (size_t)y * nv + z] =
+            tt[(size_t)s[0] * nv2 + (size_t)s[1] * nv + s[2]];
+      }
+}
+
+/* The four contractions of Algorithm 1 for one ordered triple (p,q,r):
+ *   Om1^a_p      += sum_{bc} V^{abc} g_{qbrc}
+ *   Om~^{ab}_{pq} += sum_c  V^{abc} F_{rc}
+ *   Om~^{ab}_{pl} -= sum_c  V^{abc} g_{qlrc}
+ *   Om~^{ad}_{pq} += sum_bc V^{abc} g_{dbrc}                                  */
+static void contract_omega(const blocks_t *B, const double *V, int p, int q,
+                           int r, double *om1, double *omt, long long *flops) {
+  int no = B->no, nv = B->nv;
+  size_t nv2 = (size_t)nv * nv;
+  for (int a = 0; a < nv; ++a) {
+    double s1 = 0.0;
+    for (int b = 0; b < nv; ++b)
+      for (int c = 0; c < nv; ++c)
+        s1 += V[(size_t)a * nv2 + (size_t)b * nv + c] * OVOV(B, q, b, r, c);
+    om1[(size_t)p * nv + a] += s1;
+  }
+  for (int a = 0; a < nv; ++a)
+    for (int b = 0; b < nv; ++b) {
+      const double *vr = V + (size_t)a * nv2 + (size_t)b * nv;
+      double sF = 0.0;
+      for (int c = 0; c < nv; ++c) sF += vr[c] * B->F_ov[(size_t)r * nv + c];
+      omt[(((size_t)p * no + q) * nv + a) * nv + b] += sF;
+      for (int l = 0; l < no; ++l) {
+        double so = 0.0;
+        for (int c = 0; c < nv; ++c) so += vr[c] * OOOV(B, q, l, r, c);
+        omt[(((size_t)p * no + l) * nv + a) * nv + b] -= so;
+      }
+    }
+  for (int a = 0; a < nv; ++a)
+    for (int d = 0; d < nv; ++d) {
+      double s = 0.0;
+      for (int b = 0; b < nv; ++b)
+        for (int c = 0; c < nv; ++c)
+          s += V[(size_t)a * nv2 + (size_t)b * nv + c] * VVOV(B, d, b, r, c);
+      omt[(((size_t)p * no + q) * nv + a) * nv + d] += s;
+    }
+  if (flops) *flops += 2LL * nv * nv * nv * nv;
+}
+
+/* Denominator (w - eps^{abc}_{ijk}); tau = W / (w - eps), so w = 0 gives the
+ * tau line of Algorithm 1, tau = -W / eps. */
+static void divide_denominator(const blocks_t *B, const int ijk[3], double w,
+                               const double *W, double *tau) {
+  int nv = B->nv;
+  size_t nv2 = (size_t)nv * nv;
+  double eo = B->eps_o[ijk[0]] + B->eps_o[ijk[1]] + B->eps_o[ijk[2]];
+  for (int a = 0; a < nv; ++a)
+    for (int b = 0; b < nv; ++b)
+      for (int c = 0; c < nv; ++c) {
+        double e = B->eps_v[a] + B->eps_v[b] + B->eps_v[c] - eo;
+        size_t x = (size_t)a * nv2 + (size_t)b * nv + c;
+        tau[x] = W[x] / (w - e);
+      }
+}
+
+/* Omega2 = (1/3) P^{ab}_{ij} (2 Om~^{ab}_{ij} + Om~^{ba}_{ij}) */
+static void back_transform(int no, int nv, const double *omt, double *om2) {
+#define OT(i, j, a, b) omt[(((size_t)(i) * no + (j)) * nv + (a)) * nv + (b)]
+  for (int i = 0; i < no; ++i)
+    for (int j = 0; j < no; ++j)
+      for (int a = 0; a < nv; ++a)
+        for (int b = 0; b < nv; ++b)
+          om2[(((size_t)i * no + j) * nv + a) * nv + b] =
+              (2.0 * OT(i, j, a, b) + OT(i, j, b, a) + 2.0 * OT(j, i, b, a) +
+               OT(j, i, a, b)) / 3.0;
+#undef OT
+}
+
+static int list_triples(int no, int ntri, const int *tri, int **out) {
+  if (tri) {
+    *out = (int *)malloc(sizeof(int) * 3 * (size_t)(ntri > 0 ? ntri : 1));
+    if (!*out) return -1;
+    memcpy(*out, tri, sizeof(int) * 3 * (size_t)ntri);
+    return ntri;
+  }
+  int n = 0;
+  *out = (int *)malloc(sizeof(int) * 3 * ((size_t)no * no * no + 1));
+  if (!*out) return -1;
+  for (int i = 0; i < no; ++i)
+    for (int j = 0; j <= i; ++j)
+      for (int k = 0; k <= j; ++k) {
+        if (i == j && j == k) continue;
+        (*out)[3 * n] = i;
+        (*out)[3 * n + 1] = j;
+        (*out)[3 * n + 2] = k;
+        ++n;
+      }
+  return n;
+}
+
+static int set_threads(int nthreads) {
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+  return omp_get_max_threads();
+#else
+  (void)nthreads;
+  return 1;
+#endif
+}
+
+/* Algorithm 1.  tri = NULL runs every triple i >= j >= k; otherwise the ntri
+ * triples listed (each i >= j >= k) -- the same restriction the GPU library
+ * takes.  omega1[no][nv], omega2[no][no][nv][nv], omega2_tilde (may be NULL),
+ * E_T (may be NULL).  flops counts the dominant contractions only (the d-sum
+ * of each distinct B and the vvov contraction of each distinct permutation).  Returns threads used. */
+int oracle_omega(int no, int nv, const double *eps_o, const double *eps_v,
+                 const double *t2, const double *vvvo, const double *oovo,
+                 const double *ooov, const double *ovov, const double *vvov,
+                 const double *F_ov, int ntri, const int *tri, double *omega1,
+                 double *omega2, double *omega2_tilde, double *E_T,
+                 long long *flops, int nthreads) {
+  blocks_t B = {no, nv, eps_o, eps_v, t2, vvvo, oovo, ooov, ovov, vvov, F_ov};
+  size_t nv3 = (size_t)nv * nv * nv, n1 = (size_t)no * nv,
+         n2 = (size_t)no * no * nv * nv;
+  int *T = NULL;
+  int nt = list_triples(no, ntri, tri, &T);
+  if (nt < 0) return -1;
+  int used = set_threads(nthreads);
+  double *om1 = (double *)calloc(n1 ? n1 : 1, sizeof(double));
+  double *omt = (double *)calloc(n2 ? n2 : 1, sizeof(double));
+  long long fl = 0;
+#pragma omp parallel reduction(+ : fl)
+  {
+    double *W = (double *)malloc(nv3 * sizeof(double));
+    double *S = (double *)malloc(nv3 * sizeof(double));
+    double *tau = (double *)malloc(nv3 * sizeof(double));
+    double *V = (double *)malloc(nv3 * sizeof(double));
+    double *m1 = (double *)calloc(n1 ? n1 : 1, sizeof(double));
+    double *mt = (double *)calloc(n2 ? n2 : 1, sizeof(double));
+#pragma omp for schedule(dynamic, 1)
+    for (int t = 0; t < nt; ++t) {
+      const int *ijk = T + 3 * t;
+      int maps[6][3];
+      int np = distinct_perms(ijk, maps);
+      if (np == 0) continue;
+      build_W(no, nv, t2, vvvo, oovo, ijk, W, S, &fl);
+      divide_denominator(&B, ijk, 0.0, W, tau);
+      contravariant(nv, tau, S); /* S = tau~ */
+      for (int u = 0; u < np; ++u) {
+        permuted_view(nv, S, maps[u], V);
+        contract_omega(&B, V, ijk[maps[u][0]], ijk[maps[u][1]],
+                       ijk[maps[u][2]], m1, mt, &fl);
+      }
+    }
+#pragma omp critical
+    {
+      for (size_t x = 0; x < n1; ++x) om1[x] += m1[x];
+      for (size_t x = 0; x < n2; ++x) omt[x] += mt[x];
+    }
+    free(W); free(S); free(tau); free(V); free(m1); free(mt);
+  }
+  if (omega1) memcpy(omega1, om1, n1 * sizeof(double));
+  if (omega2) back_transform(no, nv, omt, omega2);
+  if (omega2_tilde) memcpy(omega2_tilde, omt, n2 * sizeof(double));
+  if (E_T) {
+    double e = 0.0;
+    for (size_t x = 0; x < n2; ++x) e += t2[x] * omt[x];
+    *E_T = e;
+  }
+  if (flops) *flops = fl;
+  free(om1); free(omt); free(T);
+  return used;
+}
+
+/* Algorithm 2: Z~v[a][b][i][d] -= sum_c tau~^{abc}_{ijk} g_{jdkc} and
+ * Z~o[a][j][i][l] += sum_bc tau~^{abc}_{ijk} g_{lbkc}, over every distinct
+ * permutation of each triple (ooov here is g_{jdkc} read as ovov[j][d][k][c],
+ * the same integrals as the ground state's singles contraction).
+ * Zv[nv][nv][no][nv], Zo[nv][no][no][no].  Returns threads used. */
+int oracle_prep(int no, int nv, const double *eps_o, const double *eps_v,
+                const double *t2, const double *vvvo, const double *oovo,
+                const double *ovov, int ntri, const int *tri, double *Zv,
+                double *Zo, long long *flops, int nthreads) {
+  blocks_t B = {no, nv, eps_o, eps_v, t2, vvvo, oovo, NULL, ovov, NULL, NULL};
+  size_t nv3 = (size_t)nv * nv * nv;
+  size_t nzv = nv3 * no, nzo = (size_t)nv * no * no * no;
+  int *T = NULL;
+  int nt = list_triples(no, ntri, tri, &T);
+  if (nt < 0) return -1;
+  int used = set_threads(nthreads);
+  memset(Zv, 0, nzv * sizeof(double));
+  memset(Zo, 0, nzo * sizeof(double));
+  long long fl = 0;
+#pragma omp parallel reduction(+ : fl)
+  {
+    double *W = (double *)malloc(nv3 * sizeof(double));
+    double *S = (double *)malloc(nv3 * sizeof(double));
+    double *tau = (double *)malloc(nv3 * sizeof(double));
+    double *V = (double *)malloc(nv3 * sizeof(double));
+    double *zv = (double *)calloc(nzv ? nzv : 1, sizeof(double));
+    double *zo = (double *)calloc(nzo ? nzo : 1, sizeof(double));
+    size_t nv2 = (size_t)nv * nv;
+#pragma omp for schedule(dynamic, 1)
+    for (int t = 0; t < nt; ++t) {
+      const int *ijk = T + 3 * t;
+      int maps[6][3];
+      int np = distinct_perms(ijk, maps);
+      if (np == 0) continue;
+      build_W(no, nv, t2, vvvo, oovo, ijk, W, S, &fl);
+      divide_denominator(&B, ijk, 0.0, W, tau);
+      contravariant(nv, tau, S);
+      for (int u = 0; u < np; ++u) {
+        int p = ijk[maps[u][0]], q = ijk[maps[u][1]], r = ijk[maps[u][2]];
+        permuted_view(nv, S, maps[u], V);
+        for (int a = 0; a < nv; ++a)
+          for (int b = 0; b < nv; ++b)
+            for (int d = 0; d < nv; ++d) {
+              double s = 0.0;
+              for (int c = 0; c < nv; ++c)
+                s += V[(size_t)a * nv2 + (size_t)b * nv + c] * OVOV(&B, q, d, r, c);
+              zv[(((size_t)a * nv + b) * no + p) * nv + d] -= s;
+            }
+        for (int a = 0; a < nv; ++a)
+          for (int l = 0; l < no; ++l) {
+            double s = 0.0;
+            for (int b = 0; b < nv; ++b)
+              for (int c = 0; c < nv; ++c)
+                s += V[(size_t)a * nv2 + (size_t)b * nv + c] * OVOV(&B, l, b, r, c);
+            zo[(((size_t)a * no + q) * no + p) * no + l] += s;
+          }
+        fl += 2LL * nv * nv * nv * nv;
+      }
+    }
+#pragma omp critical
+    {
+      for (size_t x = 0; x < nzv; ++x) Zv[x] += zv[x];
+      for (size_t x = 0; x < nzo; ++x) Zo[x] += zo[x];
+    }
+    free(W); free(S); free(tau); free(V); free(zv); free(zo);
+  }
+  if (flops) *flops = fl;
+  free(T);
+  return used;
+}
+
+/* (pq|rs) = sum_J L[J][p][q] L[J][r][s] over the n = no+nv active orbitals
+ * (occupied first). */
+static double eri(const double *L, int naux, int n, int p, int q, int r, int s) {
+  double v = 0.0;
+  size_t n2 = (size_t)n * n;
+  for (int J = 0; J < naux; ++J)
+    v += L[J * n2 + (size_t)p * n + q] * L[J * n2 + (size_t)r * n + s];
+  return v;
+}
+
+/* R1-dressed blocks from the first-order T1 transformation
+ * g^_{pqrs} = -[p in v] sum_l R^p_l g_{lqrs} + [q in o] sum_e R^e_q g_{pers}
+ *             -[r in v] sum_l R^r_l g_{pqls} + [s in o] sum_e R^e_s g_{pqre}
+ * (H = exp(-T1) H exp(T1), differentiated along T1 = R1):
+ *   g^_{bdck} = -sum_l R^b_l (ld|ck) - sum_l R^c_l (bd|lk) + sum_e R^e_k (bd|ce)
+ *   g^_{ljck} =  sum_d R^d_j (ld|ck) - sum_m R^c_m (lj|mk) + sum_d R^d_k (lj|cd)
+ *   g^_{jlkc} =  sum_d R^d_l (jd|kc)        g^_{dbkc} = -sum_l R^d_l (lb|kc)
+ *   g^_{jbkc} = 0                           F^_{kc} = sum_ld [2(kc|ld)-(kd|lc)] R^d_l
+ * The vvvv integrals of the first line are contracted through the Cholesky
+ * vectors: sum_e R^e_k (bd|ce) = sum_J L^J_bd (sum_e L^J_ce R^e_k). */
+static void dressed_blocks(int no, int nv, const double *L, int naux,
+                           const double *R1, double *hvvvo, double *hoovo,
+                           double *hooov, double *hvvov, double *hF) {
+  int n = no + nv;
+  size_t n2 = (size_t)n * n;
+#define R(i, a) R1[(size_t)(i) * nv + (a)]
+#define V(p) (no + (p))
+  double *M = (double *)calloc((size_t)naux * nv * no + 1, sizeof(double));
+  for (int J = 0; J < naux; ++J)
+    for (int c = 0; c < nv; ++c)
+      for (int k = 0; k < no; ++k) {
+        double s = 0.0;
+        for (int e = 0; e < nv; ++e)
+          s += L[J * n2 + (size_t)V(c) * n + V(e)] * R(k, e);
+        M[((size_t)J * nv + c) * no + k] = s;
+      }
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int b = 0; b < nv; ++b)
+    for (int d = 0; d < nv; ++d)
+      for (int c = 0; c < nv; ++c)
+        for (int k = 0; k < no; ++k) {
+          double s = 0.0;
+          for (int l = 0; l < no; ++l)
+            s -= R(l, b) * eri(L, naux, n, l, V(d), V(c), k);
+          for (int l = 0; l < no; ++l)
+            s -= R(l, c) * eri(L, naux, n, V(b), V(d), l, k);
+          for (int J = 0; J < naux; ++J)
+            s += L[J * n2 + (size_t)V(b) * n + V(d)] *
+                 M[((size_t)J * nv + c) * no + k];
+          hvvvo[(((size_t)b * nv + d) * nv + c) * no + k] = s;
+        }
+  for (int l = 0; l < no; ++l)
+    for (int j = 0; j < no; ++j)
+      for (int c = 0; c < nv; ++c)
+        for (int k = 0; k < no; ++k) {
+          double s = 0.0;
+          for (int d = 0; d < nv; ++d)
+            s += R(j, d) * eri(L, naux, n, l, V(d), V(c), k);
+          for (int m = 0; m < no; ++m)
+            s -= R(m, c) * eri(L, naux, n, l, j, m, k);
+          for (int d = 0; d < nv; ++d)
+            s += R(k, d) * eri(L, naux, n, l, j, V(c), V(d));
+          hoovo[(((size_t)l * no + j) * nv + c) * no + k] = s;
+        }
+  for (int j = 0; j < no; ++j)
+    for (int l = 0; l < no; ++l)
+      for (int k = 0; k < no; ++k)
+        for (int c = 0; c < nv; ++c) {
+          double s = 0.0;
+          for (int d = 0; d < nv; ++d)
+            s += R(l, d) * eri(L, naux, n, j, V(d), k, V(c));
+          hooov[(((size_t)j * no + l) * no + k) * nv + c] = s;
+        }
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int d = 0; d < nv; ++d)
+    for (int b = 0; b < nv; ++b)
+      for (int k = 0; k < no; ++k)
+        for (int c = 0; c < nv; ++c) {
+          double s = 0.0;
+          for (int l = 0; l < no; ++l)
+            s -= R(l, d) * eri(L, naux, n, l, V(b), k, V(c));
+          hvvov[(((size_t)d * nv + b) * no + k) * nv + c] = s;
+        }
+  for (int k = 0; k < no; ++k)
+    for (int c = 0; c < nv; ++c) {
+      double s = 0.0;
+      for (int l = 0; l < no; ++l)
+        for (int d = 0; d < nv; ++d)
+          s += (2.0 * eri(L, naux, n, k, V(c), l, V(d)) -
+                eri(L, naux, n, k, V(d), l, V(c))) * R(l, d);
+      hF[(size_t)k * nv + c] = s;
+    }
+  free(M);
+#undef R
+#undef V
+}
+
+/* Right Jacobian transformation of nvec trial vectors (R1[n][i][a],
+ * R2[n][i][j][a][b], frequency w[n]):
+ *   W_R  = P[ sum_d R^{ad}_{ij} g_{bdck} - sum_l R^{ab}_{il} g_{ljck} ]
+ *        + P[ sum_d t^{ad}_{ij} g^_{bdck} - sum_l t^{ab}_{il} g^_{ljck} ]
+ *   R3   = W_R / (w - eps);  R~3 its contravariant form
+ *   rho~ = contractions(R~3; g, F) + contractions(tau~3; g^, F^)
+ *   rho2 = (1/3) P^{ab}_{ij}(2 rho~ + rho~^{ba});  rho1 = rho~1.
+ * The integrals are symmetric (T1 = 0), given as the five blocks plus the
+ * Cholesky vectors chol_L[naux][n][n] for the dressed blocks.
+ * The tau~3 . g^ contractions are done directly here (Algorithm 2's
+ * intermediates are the GPU library's way to the same sums).
+ * Returns threads used. */
+int oracle_jacobian(int no, int nv, const double *eps_o, const double *eps_v,
+                    const double *t2, const double *vvvo, const double *oovo,
+                    const double *ooov, const double *ovov, const double *vvov,
+                    const double *F_ov, const double *chol_L, int naux,
+                    int nvec, const double *w, const double *R1,
+                    const double *R2, int ntri, const int *tri, double *rho1,
+                    double *rho2, long long *flops, int nthreads) {
+  size_t nv3 = (size_t)nv * nv * nv, n1 = (size_t)no * nv,
+         n2 = (size_t)no * no * nv * nv;
+  size_t nvvvo = nv3 * no, noovo = (size_t)no * no * nv * no,
+         nooov = (size_t)no * no * no * nv, nvvov = nv3 * no;
+  int *T = NULL;
+  int nt = list_triples(no, ntri, tri, &T);
+  if (nt < 0) return -1;
+  int used = set_threads(nthreads);
+  long long fl_total = 0;
+  for (int vec = 0; vec < nvec; ++vec) {
+    const double *r1 = R1 + vec * n1, *r2 = R2 + vec * n2;
+    double *hvvvo = (double *)malloc(nvvvo * sizeof(double));
+    double *hoovo = (double *)malloc(noovo * sizeof(double) + 8);
+    double *hooov = (double *)malloc(nooov * sizeof(double) + 8);
+    double *hvvov = (double *)malloc(nvvov * sizeof(double));
+    double *hF = (double *)malloc(n1 * sizeof(double) + 8);
+    double *zero_ovov = (double *)calloc(n2 + 1, sizeof(double));
+    dressed_blocks(no, nv, chol_L, naux, r1, hvvvo, hoovo, hooov, hvvov, hF);
+    blocks_t Bg = {no, nv, eps_o, eps_v, t2, vvvo, oovo, ooov, ovov, vvov, F_ov};
+    blocks_t Bh = {no, nv, eps_o, eps_v, t2, hvvvo, hoovo, hooov, zero_ovov,
+                   hvvov, hF};
+    double *om1 = (double *)calloc(n1 + 1, sizeof(double));
+    double *omt = (double *)calloc(n2 + 1, sizeof(double));
+    long long fl = 0;
+#pragma omp parallel reduction(+ : fl)
+    {
+      double *W = (double *)malloc(nv3 * sizeof(double));
+      double *W2 = (double *)malloc(nv3 * sizeof(double));
+      double *S = (double *)malloc(nv3 * sizeof(double));
+      double *tau = (double *)malloc(nv3 * sizeof(double));
+      double *V = (double *)malloc(nv3 * sizeof(double));
+      double *m1 = (double *)calloc(n1 + 1, sizeof(double));
+      double *mt = (double *)calloc(n2 + 1, sizeof(double));
+#pragma omp for schedule(dynamic, 1)
+      for (int t = 0; t < nt; ++t) {
+        const int *ijk = T + 3 * t;
+        int maps[6][3];
+        int np = distinct_perms(ijk, maps);
+        if (np == 0) continue;
+        /* R3 and its contractions with the undressed integrals */
+        build_W(no, nv, r2, vvvo, oovo, ijk, W, S, &fl);
+        build_W(no, nv, t2, hvvvo, hoovo, ijk, W2, S, &fl);
+        for (size_t x = 0; x < nv3; ++x) W[x] += W2[x];
+        divide_denominator(&Bg, ijk, w[vec], W, tau);
+        contravariant(nv, tau, S);
+        for (int u = 0; u < np; ++u) {
+          permuted_view(nv, S, maps[u], V);
+          contract_omega(&Bg, V, ijk[maps[u][0]], ijk[maps[u][1]],
+                         ijk[maps[u][2]], m1, mt, &fl);
+        }
+        /* tau3 and its contractions with the dressed integrals */
+        build_W(no, nv, t2, vvvo, oovo, ijk, W, S, &fl);
+        divide_denominator(&Bg, ijk, 0.0, W, tau);
+        contravariant(nv, tau, S);
+        for (int u = 0; u < np; ++u) {
+          permuted_view(nv, S, maps[u], V);
+          contract_omega(&Bh, V, ijk[maps[u][0]], ijk[maps[u][1]],
+                         ijk[maps[u][2]], m1, mt, &fl);
+        }
+      }
+#pragma omp critical
+      {
+        for (size_t x = 0; x < n1; ++x) om1[x] += m1[x];
+        for (size_t x = 0; x < n2; ++x) omt[x] += mt[x];
+      }
+      free(W); free(W2); free(S); free(tau); free(V); free(m1); free(mt);
+    }
+    memcpy(rho1 + vec * n1, om1, n1 * sizeof(double));
+    back_transform(no, nv, omt, rho2 + vec * n2);
+    fl_total += fl;
+    free(om1); free(omt); free(hvvvo); free(hoovo); free(hooov); free(hvvov);
+    free(hF); free(zero_ovov);
+  }
+  if (flops) *flops = fl_total;
+  free(T);
+  return used;
+}
+
+/* Only the dressed blocks (for tests that pin them on their own). */
+void oracle_dressed_blocks(int no, int nv, const double *chol_L, int naux,
+                           const double *R1, double *hvvvo, double *hoovo,
+                           double *hooov, double *hvvov, double *hF) {
+  dressed_blocks(no, nv, chol_L, naux, R1, hvvvo, hoovo, hooov, hvvov, hF);
+}
