@@ -1,0 +1,270 @@
+"""Benchmark of the CC3 triples hot path on GB300.
+
+One step = one CC3 triples residual evaluation (paper, Algorithm 1: every
+occupied triple i >= j >= k, W build, denominators, contravariant amplitudes,
+the four contractions, back-transform and energy) on the seeded synthetic
+no = 16, nv = 160 problem, inputs resident in HBM.  The metric is nominal
+TFLOP/s with 4 nv^4 no^3 FLOP per evaluation (the paper's convention).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec split|fp64]
+  python bench.py --impl reference ...    (the FP64 CPU oracle, bounded sample)
+
+Multi-GPU (torchrun): every rank evaluates its own independent problem of the
+same size (weak scaling, no collective on the data path); rank 0 prints the
+aggregate over ranks with the max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CC3 triples TFLOP/s (4 nv^4 no^3 per Omega) vs FP64 at dE<=1e-8 Eh; p99 lat"
+NO, NV = 16, 160
+WORKLOAD = "CC3 triples residual, no=16 nv=160, seeded synthetic (Cholesky-like integrals, MP2 t2)"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(p)), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed
+    region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace('.', '').isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace('.', '').isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.rows)}
+
+
+def oracle_sample(inp, seconds_target=15.0, nthreads=0):
+    """Time the FP64 oracle on a bounded, seeded sample of triples."""
+    import oracle
+    from cc3_inputs import unique_triples
+    tr = unique_triples(inp.no)
+    rng = np.random.default_rng(11)
+    order = rng.permutation(len(tr))
+    # calibrate on one triple, then size the sample to ~seconds_target
+    t0 = time.perf_counter()
+    r = oracle.omega_inputs(inp, triples=[tr[order[0]][:3]], nthreads=nthreads)
+    dt1 = time.perf_counter() - t0
+    threads = r["threads"]
+    n = int(max(1, min(len(tr), seconds_target / max(dt1, 1e-3) * min(threads, 8))))
+    sel = [tr[x][:3] for x in order[:n]]
+    w = sum(tr[x][3] for x in order[:n])
+    t0 = time.perf_counter()
+    r = oracle.omega_inputs(inp, triples=sel, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    flop = 4.0 * inp.nv ** 4 * w
+    return dict(value=flop / dt / 1e12, unit="TFLOP/s", cores=r["threads"],
+                kind="oracle", seconds=dt,
+                sample=f"{n} of {len(tr)} triples (weight {w} of {inp.no**3 - inp.no}) "
+                       f"of the no={inp.no} nv={inp.nv} residual, FP64 C oracle, "
+                       f"{r['threads']} OpenMP threads")
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from cc3_inputs import make_inputs
+    inp = make_inputs(NO, NV, seed=0)
+    vals = []
+    per_step = max(5.0, 60.0 / max(1, args.steps + args.warmup))
+    for s in range(args.warmup + args.steps):
+        r = oracle_sample(inp, seconds_target=per_step)
+        if s >= args.warmup:
+            vals.append(r)
+    v = statistics.median([x["value"] for x in vals])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.median([x["seconds"] for x in vals]),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "no": NO, "nv": NV, "prec": "fp64-cpu-oracle"},
+            "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": vals[-1]["cores"],
+                             "kind": "oracle", "sample": vals[-1]["sample"]},
+            "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native")
+    ap.add_argument("--prec", default="fp64", choices=["split", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 3 if args.prec == "fp64" else 10
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    import paper_2007_01088_gb300 as g
+    from cc3_inputs import make_inputs
+    prec = g.CC3_SPLIT_BF16 if args.prec == "split" else g.CC3_FP64
+    inp = make_inputs(NO, NV, seed=rank)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        ctx = g.Context(inp, device=True, stream=stream)
+        g.lib.cc3_ctx_set_tracing(ctx.ctx, 1) if hasattr(g.lib, "cc3_ctx_set_tracing") else None
+        out = (torch.empty((NO, NV), dtype=torch.float64, device=dev),
+               torch.empty((NO, NO, NV, NV), dtype=torch.float64, device=dev),
+               torch.empty((1,), dtype=torch.float64, device=dev))
+        for _ in range(args.warmup):
+            ctx.omega(prec, out=out)
+        stream.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        clocks = ClockSampler(local)
+        clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        launches = 0
+        for _ in range(args.steps):
+            ctx.omega(prec, out=out)
+            launches += ctx.counters()["launches"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    cnt = ctx.counters()
+    flop = cnt["nominal_flop"]
+    tmax = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(tmax.item())
+    value = ws * flop / (ms_max * 1e-3) / 1e12
+
+    # end to end through the public API with host buffers: upload of the
+    # inputs, the evaluation and the download of Omega1, Omega2, E_T
+    h2d = sum(getattr(inp, n).nbytes for n in
+              ["eps_o", "eps_v", "t2", "g_vvvo", "g_ooov", "g_ovov", "F_ov"])
+    d2h = 8 * (NO * NV + NO * NO * NV * NV + 1)
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        hc = g.Context(inp, device=False)
+        hc.omega(prec)
+        hc.close()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+
+    pk, src = peaks()
+    ratio = 1.25 / 2250.0  # nominal FP64 / dense BF16 of GB300
+    if prec == g.CC3_FP64:
+        peak = pk["bf16_tflops"] * ratio
+        roof = {"bound": "tensor", "achieved": flop / (ms * 1e-3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "frac": None, "traffic": None,
+                "peak_source": f"{src} bf16 burst x nominal FP64/BF16 ratio (1.25/2250)"}
+    else:
+        peak = pk["bf16_tflops"]
+        roof = {"bound": "tensor", "achieved": None, "peak": peak, "unit": "TFLOP/s",
+                "frac": None, "traffic": None, "peak_source": f"{src} bf16 burst"}
+    kt = getattr(ctx, "kernel_times", None)
+    if callable(kt):
+        info = kt()
+        if info:
+            roof.update(info)
+    if roof.get("achieved") is not None:
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == g.CC3_FP64 else "bf16",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "no": NO, "nv": NV,
+                       "prec": args.prec, "parallelism": f"replicas{ws}",
+                       "l2": "inputs larger than L2 (g_vvvo 524 MB)"},
+            "roofline": roof,
+            "e2e": {"value": ws * flop / e2e_s / 1e12, "unit": "TFLOP/s",
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches), "clocks": clk,
+            "executed_flop_per_step": cnt["executed_flop"]}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = {k: v for k, v in oracle_sample(inp).items()
+                                if k in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,180 @@
+/*
+ * cc3.h -- C ABI of the GB300 CC3 triples library (libcc3.so).
+ *
+ * The library computes the closed-shell CC3 triples contribution to the
+ * coupled-cluster residual and to the right Jacobian transformation, following
+ * Paul, Myhre and Koch, "A new and efficient implementation of CC3"
+ * (arXiv 2007.01088), section "Implementation", Algorithms 1 and 2 and
+ * eq. "jcc3".  Everything runs in CUDA kernels on one GPU (sm_103a).
+ *
+ * Index conventions (row-major, float64, indices in the order written):
+ *   no occupied (active) and nv virtual orbitals
+ *   eps_o[no], eps_v[nv]                orbital energies (Eh)
+ *   t2[i][j][a][b]  = t^{ab}_{ij}        doubles amplitudes
+ *   g_vvvo[b][d][c][k] = (bd|ck)         two-electron integrals (chemists'
+ *   g_ooov[l][j][k][c] = (lj|kc)         notation, real orbitals, full 8-fold
+ *   g_ovov[j][b][k][c] = (jb|kc)         permutational symmetry, T1 = 0)
+ *   F_ov[k][c]                           occupied-virtual Fock block
+ *   chol_L[J][p][q]                      Cholesky vectors over the no+nv
+ *                                        orbitals (occupied first), optional
+ *   R1[n][i][a], R2[n][i][j][a][b]       trial vectors
+ *   Omega1[i][a], Omega2[i][j][a][b], rho1[n][i][a], rho2[n][i][j][a][b]
+ *
+ * Ownership: the caller owns every buffer it passes.  cc3_ctx_create copies
+ * its inputs into device memory owned by the context (device-to-device with
+ * CC3_DEVICE_PTRS); the context frees them in cc3_ctx_destroy.  Outputs are
+ * overwritten with the triples contribution only (the caller adds it to its
+ * CCSD residual).  With CC3_DEVICE_PTRS every pointer argument of every call
+ * on that context (inputs and outputs) is a device pointer; otherwise all are
+ * host pointers and the call copies and synchronises.
+ *
+ * Threading: calls on one context are serialised by the caller; distinct
+ * contexts may be used from different threads.  cuda_stream may be NULL (the
+ * legacy default stream) or a cudaStream_t.
+ *
+ * Errors: every call returns a status (CC3_OK = 0, negative on error) and
+ * never aborts the process; cc3_strerror names it.  A device-side failure is
+ * reported through a device status word and surfaces as CC3_ERR_TIMEOUT or
+ * CC3_ERR_CUDA.
+ */
+#ifndef CC3_H
+#define CC3_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cc3_ctx cc3_ctx;
+typedef struct cc3_server cc3_server;
+
+/* Arithmetic of the bulk contractions.
+ * CC3_FP64       native FP64 (DMMA/DFMA) everywhere.
+ * CC3_SPLIT_BF16 the dominant contractions run as exact products of
+ *                integer-valued BF16 slices of the FP64 operands on the
+ *                tensor cores (FP32 accumulation of exact integer sums),
+ *                recombined in extended precision; denominators,
+ *                cross-triple accumulation and the energy stay in FP64 or
+ *                in double-float arithmetic of equal or better accuracy.
+ * CC3_SPLIT_INT8 reserved (the INT8 tensor rate of this GPU is far below its
+ *                BF16 rate); returns CC3_ERR_UNSUPPORTED. */
+typedef enum { CC3_FP64 = 0, CC3_SPLIT_BF16 = 1, CC3_SPLIT_INT8 = 2 } cc3_prec;
+
+enum {
+  CC3_OK = 0,
+  CC3_ERR_ARG = -1,         /* invalid argument (size, pointer, flag)        */
+  CC3_ERR_OOM = -2,         /* device or host allocation failed               */
+  CC3_ERR_CUDA = -3,        /* a CUDA call or kernel launch failed            */
+  CC3_ERR_TIMEOUT = -4,     /* a bounded device wait gave up                  */
+  CC3_ERR_DENOM = -5,       /* |w - eps| too small or eps <= 0 somewhere      */
+  CC3_ERR_BUSY = -6,        /* server full / request rejected at admission    */
+  CC3_ERR_UNSUPPORTED = -7, /* option not available in this build             */
+  CC3_ERR_NOT_FOUND = -8,   /* unknown ticket                                  */
+  CC3_ERR_CANCELLED = -9    /* request cancelled / server stopped              */
+};
+
+/* flags of cc3_ctx_create */
+#define CC3_DEVICE_PTRS 1u   /* all pointers of this context are device pointers */
+#define CC3_DETERMINISTIC 2u /* fixed-order cross-triple reductions (bitwise    */
+                             /* reproducible results, somewhat slower)          */
+
+/* Create a context for one problem (no >= 1, 1 <= nv <= 1024).  Uploads and
+ * reorders the inputs (paper: integrals are reordered before the triple loop,
+ * "Implementation" section).  chol_L may be NULL (naux = 0): then the
+ * Jacobian is unavailable (CC3_ERR_ARG).  On success *out owns device memory
+ * of about (5 nv^3 no + 4 no^2 nv^2) * 8 bytes plus per-call workspace. */
+int cc3_ctx_create(cc3_ctx **out, int no, int nv, const double *eps_o,
+                   const double *eps_v, const double *t2, const double *g_vvvo,
+                   const double *g_ooov, const double *g_ovov,
+                   const double *F_ov, const double *chol_L, int naux,
+                   unsigned flags, void *cuda_stream);
+
+void cc3_ctx_destroy(cc3_ctx *ctx);
+
+/* Restrict the triple loop to ntri unique occupied triples ijk[3*t..3*t+2]
+ * with i >= j >= k (host pointer, copied).  ntri = 0 or ijk = NULL restores the
+ * full loop (all i >= j >= k, paper Algorithm 1).  The results are then the
+ * contributions of exactly those triples (used for sampled checks and for
+ * task filters such as core-valence separation). */
+int cc3_ctx_set_triples(cc3_ctx *ctx, int ntri, const int *ijk);
+
+/* CC3 triples contribution to the ground-state residual (Algorithm 1):
+ * Omega1[no][nv], Omega2[no][no][nv][nv] (covariant, pair symmetric) and
+ * E_T = sum_{ijab} t^{ab}_{ij} Omega~^{ab}_{ij} (the contravariant residual
+ * paired with the amplitudes).  Any output pointer may be NULL. */
+int cc3_omega_triples(cc3_ctx *ctx, cc3_prec prec, double *Omega1,
+                      double *Omega2, double *E_T, void *cuda_stream);
+
+/* Right CC3 Jacobian transformation (triples part) of nvec trial vectors at
+ * frequencies omega[nvec] (host array always):
+ *   R3 = (w - eps)^{-1} <mu3| [H,R2] + [[H,R1],T2] >,
+ *   rho = <mu1|[H,R3]> (+) <mu2|[H,R3]> + <mu2|[[H,R1],T3]>   (eq. "jcc3")
+ * with H the T1-transformed Hamiltonian; the R1 dressing of the integrals
+ * needs the Cholesky vectors.  The tau3-dependent intermediates of
+ * Algorithm 2 are built on first use and cached in the context.
+ * rho1[nvec][no][nv], rho2[nvec][no][no][nv][nv]. */
+int cc3_jacobian_triples(cc3_ctx *ctx, cc3_prec prec, int nvec,
+                         const double *omega, const double *R1,
+                         const double *R2, double *rho1, double *rho2,
+                         void *cuda_stream);
+
+/* Counters of the last call on ctx: nominal FLOP (4 nv^4 no^3 per residual,
+ * 8 nv^4 no^3 per trial vector, over the triples in the loop), FLOP executed
+ * by the FP64 or slice products, and the number of kernel launches. */
+typedef struct {
+  double nominal_flop;
+  double executed_flop;
+  long long launches;
+  int slices;              /* BF16 slices per operand (split path), else 0 */
+} cc3_counters;
+int cc3_ctx_counters(const cc3_ctx *ctx, cc3_counters *out);
+
+/* Set the number of BF16 slices per FP64 operand of the split path
+ * (3 <= s <= 8; default chosen from the tolerances, see DESIGN).  */
+int cc3_ctx_set_slices(cc3_ctx *ctx, int slices);
+
+const char *cc3_strerror(int status);
+
+/* ---------------------------------------------------------------------
+ * Serving: a request loop with continuous batching.  Requests (residual or
+ * Jacobian evaluations of problems of different size) are admitted while
+ * others run, as slots and device memory free up; admitted requests keep
+ * their inputs resident and their triple work interleaves on the GPU.
+ * ------------------------------------------------------------------- */
+typedef struct {
+  int kind;               /* 0 = residual (Omega), 1 = Jacobian             */
+  cc3_prec prec;
+  int no, nv, naux;       /* sizes; naux may be 0 for kind 0                */
+  const double *eps_o, *eps_v, *t2, *g_vvvo, *g_ooov, *g_ovov, *F_ov, *chol_L;
+  int nvec;               /* kind 1: trial vectors                           */
+  const double *omega, *R1, *R2;
+  /* outputs (host pointers; filled by cc3_serve_wait) */
+  double *Omega1, *Omega2, *E_T;  /* kind 0 */
+  double *rho1, *rho2;            /* kind 1 */
+} cc3_request;
+
+typedef struct {
+  long long submitted, admitted, completed, rejected, cancelled;
+  double p50_ms, p99_ms, mean_ms;    /* submit -> completion latency        */
+  double busy_s, wall_s;             /* device busy time, server wall time  */
+  double nominal_flop;               /* over completed requests             */
+  size_t hbm_in_use, hbm_peak;
+} cc3_stats;
+
+int cc3_serve_start(cc3_server **out, size_t hbm_budget_bytes, int max_slots);
+/* Copies the request's inputs (host pointers) at submit; returns a ticket. */
+int cc3_serve_submit(cc3_server *srv, const cc3_request *req, uint64_t *ticket);
+int cc3_serve_poll(cc3_server *srv, uint64_t ticket, int *done);
+/* Waits up to timeout_s (< 0: forever); writes the outputs into the pointers
+ * given at submit and returns the request's status. */
+int cc3_serve_wait(cc3_server *srv, uint64_t ticket, double timeout_s);
+int cc3_serve_cancel(cc3_server *srv, uint64_t ticket);
+int cc3_serve_stats(cc3_server *srv, cc3_stats *out);
+int cc3_serve_stop(cc3_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CC3_H */

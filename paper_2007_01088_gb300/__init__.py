@@ -1,0 +1,232 @@
+"""GB300 (sm_103a) CC3 triples library: Python binding of libcc3.so.
+
+The functions here carry the names of the C ABI in ``include/cc3.h`` and only
+marshal arguments; every step of the computation runs in the library's CUDA
+kernels.  There is no CPU fallback: if the shared library cannot be loaded,
+importing the binding raises.
+
+Arrays may be numpy float64 arrays (host; the library copies and synchronises)
+or CUDA torch float64 tensors (device; the context is then created with
+CC3_DEVICE_PTRS and every call takes device tensors).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB, build as _build
+
+__all__ = ["CC3_FP64", "CC3_SPLIT_BF16", "CC3_SPLIT_INT8", "CC3_DEVICE_PTRS",
+           "CC3_DETERMINISTIC", "CC3Error", "lib", "cc3_ctx_create",
+           "cc3_ctx_destroy", "cc3_ctx_set_triples", "cc3_omega_triples",
+           "cc3_jacobian_triples", "cc3_ctx_counters", "cc3_ctx_set_slices",
+           "cc3_strerror", "Context", "EXPORTED"]
+
+CC3_FP64, CC3_SPLIT_BF16, CC3_SPLIT_INT8 = 0, 1, 2
+CC3_DEVICE_PTRS, CC3_DETERMINISTIC = 1, 2
+
+# every symbol include/cc3.h declares
+EXPORTED = ["cc3_ctx_create", "cc3_ctx_destroy", "cc3_ctx_set_triples",
+            "cc3_omega_triples", "cc3_jacobian_triples", "cc3_ctx_counters",
+            "cc3_ctx_set_slices", "cc3_strerror", "cc3_serve_start",
+            "cc3_serve_submit", "cc3_serve_poll", "cc3_serve_wait",
+            "cc3_serve_cancel", "cc3_serve_stats", "cc3_serve_stop"]
+
+
+class CC3Error(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {cc3_strerror(status)} ({status})")
+        self.status = status
+
+
+class Counters(ctypes.Structure):
+    _fields_ = [("nominal_flop", ctypes.c_double), ("executed_flop", ctypes.c_double),
+                ("launches", ctypes.c_longlong), ("slices", ctypes.c_int)]
+
+
+def _load():
+    path = LIB
+    if not os.path.exists(path):
+        path = _build()
+    L = ctypes.CDLL(path)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.cc3_ctx_create.argtypes = [ctypes.POINTER(P), I, I] + [P] * 8 + [I, ctypes.c_uint, P]
+    L.cc3_ctx_create.restype = I
+    L.cc3_ctx_destroy.argtypes = [P]
+    L.cc3_ctx_destroy.restype = None
+    L.cc3_ctx_set_triples.argtypes = [P, I, P]
+    L.cc3_ctx_set_triples.restype = I
+    L.cc3_omega_triples.argtypes = [P, I, P, P, P, P]
+    L.cc3_omega_triples.restype = I
+    L.cc3_jacobian_triples.argtypes = [P, I, I, P, P, P, P, P, P]
+    L.cc3_jacobian_triples.restype = I
+    L.cc3_ctx_counters.argtypes = [P, ctypes.POINTER(Counters)]
+    L.cc3_ctx_counters.restype = I
+    L.cc3_ctx_set_slices.argtypes = [P, I]
+    L.cc3_ctx_set_slices.restype = I
+    L.cc3_strerror.argtypes = [I]
+    L.cc3_strerror.restype = ctypes.c_char_p
+    return L
+
+
+lib = _load()
+
+
+def cc3_strerror(status: int) -> str:
+    return lib.cc3_strerror(int(status)).decode()
+
+
+def _check(status, where):
+    if status != 0:
+        raise CC3Error(status, where)
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """Pointer of a numpy array or torch tensor (None for None)."""
+    if x is None:
+        return None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return ctypes.c_void_p(x.data_ptr())
+    if not (isinstance(x, np.ndarray) and x.flags["C_CONTIGUOUS"]):
+        raise ValueError("arrays must be C-contiguous")
+    return x.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return ctypes.c_void_p(s.cuda_stream)
+    return ctypes.c_void_p(int(s))
+
+
+# ---- C ABI, same names -----------------------------------------------------
+def cc3_ctx_create(no, nv, eps_o, eps_v, t2, g_vvvo, g_ooov, g_ovov, F_ov,
+                   chol_L=None, naux=0, flags=0, stream=None):
+    ctx = ctypes.c_void_p()
+    st = lib.cc3_ctx_create(ctypes.byref(ctx), int(no), int(nv), _ptr(eps_o),
+                            _ptr(eps_v), _ptr(t2), _ptr(g_vvvo), _ptr(g_ooov),
+                            _ptr(g_ovov), _ptr(F_ov), _ptr(chol_L), int(naux),
+                            int(flags), _stream(stream))
+    _check(st, "cc3_ctx_create")
+    return ctx
+
+
+def cc3_ctx_destroy(ctx):
+    lib.cc3_ctx_destroy(ctx)
+
+
+def cc3_ctx_set_triples(ctx, triples=None):
+    if triples is None or len(triples) == 0:
+        _check(lib.cc3_ctx_set_triples(ctx, 0, None), "cc3_ctx_set_triples")
+        return
+    arr = np.ascontiguousarray(np.asarray(triples, dtype=np.int32).reshape(-1, 3))
+    _check(lib.cc3_ctx_set_triples(ctx, int(arr.shape[0]), arr.ctypes.data_as(ctypes.c_void_p)),
+           "cc3_ctx_set_triples")
+
+
+def cc3_omega_triples(ctx, prec, Omega1, Omega2, E_T, stream=None):
+    _check(lib.cc3_omega_triples(ctx, int(prec), _ptr(Omega1), _ptr(Omega2), _ptr(E_T),
+                                 _stream(stream)), "cc3_omega_triples")
+
+
+def cc3_jacobian_triples(ctx, prec, nvec, omega, R1, R2, rho1, rho2, stream=None):
+    w = np.ascontiguousarray(np.asarray(omega, dtype=np.float64).reshape(-1))
+    _check(lib.cc3_jacobian_triples(ctx, int(prec), int(nvec), w.ctypes.data_as(ctypes.c_void_p),
+                                    _ptr(R1), _ptr(R2), _ptr(rho1), _ptr(rho2),
+                                    _stream(stream)), "cc3_jacobian_triples")
+
+
+def cc3_ctx_counters(ctx):
+    c = Counters()
+    _check(lib.cc3_ctx_counters(ctx, ctypes.byref(c)), "cc3_ctx_counters")
+    return dict(nominal_flop=c.nominal_flop, executed_flop=c.executed_flop,
+                launches=c.launches, slices=c.slices)
+
+
+def cc3_ctx_set_slices(ctx, slices):
+    _check(lib.cc3_ctx_set_slices(ctx, int(slices)), "cc3_ctx_set_slices")
+
+
+# ---- convenience wrapper -----------------------------------------------------
+class Context:
+    """Owns one cc3_ctx.  ``inputs`` has the fields of cc3_inputs.CC3Inputs
+    (no, nv, eps_o, eps_v, t2, g_vvvo, g_ooov, g_ovov, F_ov, chol_L).  With
+    ``device=True`` the inputs are uploaded through torch CUDA tensors and the
+    context works on device pointers."""
+
+    def __init__(self, inputs, device: bool = False, stream=None, flags: int = 0):
+        self.no, self.nv = int(inputs.no), int(inputs.nv)
+        self.device = device
+        self.stream = stream
+        L = getattr(inputs, "chol_L", None)
+        names = ["eps_o", "eps_v", "t2", "g_vvvo", "g_ooov", "g_ovov", "F_ov"]
+        arrs = {n: np.ascontiguousarray(getattr(inputs, n), dtype=np.float64) for n in names}
+        if L is not None:
+            arrs["chol_L"] = np.ascontiguousarray(L, dtype=np.float64)
+        if device:
+            import torch
+            self._keep = {n: torch.from_numpy(a).cuda() for n, a in arrs.items()}
+            src = self._keep
+            flags |= CC3_DEVICE_PTRS
+        else:
+            src = arrs
+        naux = 0 if L is None else int(L.shape[0])
+        self.ctx = cc3_ctx_create(self.no, self.nv, src["eps_o"], src["eps_v"], src["t2"],
+                                  src["g_vvvo"], src["g_ooov"], src["g_ovov"], src["F_ov"],
+                                  src.get("chol_L"), naux, flags, stream)
+        if device:
+            import torch
+            torch.cuda.synchronize()
+            self._keep = None
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            cc3_ctx_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_triples(self, triples=None):
+        cc3_ctx_set_triples(self.ctx, triples)
+
+    def set_slices(self, s):
+        cc3_ctx_set_slices(self.ctx, s)
+
+    def counters(self):
+        return cc3_ctx_counters(self.ctx)
+
+    def _new(self, shape):
+        if self.device:
+            import torch
+            return torch.empty(shape, dtype=torch.float64, device="cuda")
+        return np.empty(shape, dtype=np.float64)
+
+    def omega(self, prec=CC3_FP64, out=None):
+        """Returns (Omega1, Omega2, E_T) as numpy (host mode) or torch (device)."""
+        no, nv = self.no, self.nv
+        if out is None:
+            out = (self._new((no, nv)), self._new((no, no, nv, nv)), self._new((1,)))
+        o1, o2, e = out
+        cc3_omega_triples(self.ctx, prec, o1, o2, e, self.stream)
+        return o1, o2, e
+
+    def jacobian(self, R1, R2, omega, prec=CC3_FP64):
+        no, nv = self.no, self.nv
+        nvec = int(R1.shape[0])
+        r1 = self._new((nvec, no, nv))
+        r2 = self._new((nvec, no, no, nv, nv))
+        cc3_jacobian_triples(self.ctx, prec, nvec, omega, R1, R2, r1, r2, self.stream)
+        return r1, r2

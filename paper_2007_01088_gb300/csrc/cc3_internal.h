@@ -1,0 +1,145 @@
+// Internal declarations of libcc3 (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <vector>
+
+#include "../../include/cc3.h"
+
+namespace cc3 {
+
+// ---------------------------------------------------------------------------
+// Strided operand of a contraction: element (m, k) of an M x K matrix sits at
+//   base[buf] + off + batch*sb + (m / m_in)*sm1 + (m % m_in)*sm0
+//                              + (k / k_in)*sk1 + (k % k_in)*sk0
+// (two-level row and column indices cover the permuted views of the nv^3
+// triples amplitudes and the integral blocks without reordering them).
+// ---------------------------------------------------------------------------
+struct Opnd {
+  int buf;
+  int m_in, k_in;
+  int neg;  // 1: operand enters with a minus sign
+  long long off, sb, sm1, sm0, sk1, sk0;
+};
+
+// One term of a multi-term contraction C[m][n] += sum_k A[m][k] * B[n][k].
+// Columns n >= Job::Nm take their B values from Bt (the "tail" columns, e.g.
+// the singles contraction riding along with the vvov contraction).
+struct Term {
+  Opnd A, B, Bt;
+  int K;
+};
+
+struct OutD {
+  int buf;
+  int m_in, n_in;
+  long long off, sb, sm1, sm0, sn1, sn0;
+};
+
+enum EpiMode { EPI_STORE = 0, EPI_ATOMIC = 1, EPI_TAU = 2 };
+
+struct Job {
+  int M, N, Nm, batch;
+  int term0, nterm;
+  int tiles_m, tiles_n, ksplit;
+  int mode;
+  long long tile_base;  // first CTA of this job within its launch
+  OutD C, Ct;           // main and tail outputs
+  // EPI_TAU: C = (C + acc) / (w - eps), eps = ev[m] + ev[n / nv] + ev[n % nv] - eo
+  double w, eo;
+};
+
+enum { MAX_BUFS = 32 };
+struct PtrTable {
+  double *p[MAX_BUFS];
+};
+
+// Buffer ids of the pointer table.
+enum BufId {
+  B_T2 = 0, B_VVVO, B_OOVO, B_OOOV, B_OVOV, B_FOV, B_EPSV, B_EPSO,
+  B_WS_W, B_WS_TT, B_OMT, B_OM1,
+  B_R2, B_HVVVO, B_HOOVO, B_HF, B_ZV, B_ZO, B_VVOO, B_OOOO,
+  B_RHOT, B_RHO1, B_TT_TAU, B_SCRATCH,
+  B_COUNT
+};
+
+struct Plan {  // a host-built list of jobs for one launch
+  std::vector<Job> jobs;
+  std::vector<Term> terms;
+  long long tiles = 0;
+};
+
+struct DevPlan {  // the same, resident on the device
+  Job *jobs = nullptr;
+  Term *terms = nullptr;
+  int njobs = 0;
+  long long tiles = 0;
+  int tile_kind = 0;  // 0: 64x64 tiles, 1: 128x4 thin tiles
+};
+
+}  // namespace cc3
+
+struct cc3_ctx {
+  int no = 0, nv = 0, naux = 0;
+  unsigned flags = 0;
+  int device = 0;
+  cudaStream_t stream0 = nullptr;
+  // device copies (FP64)
+  double *eps_o = nullptr, *eps_v = nullptr, *t2 = nullptr, *vvvo = nullptr,
+         *oovo = nullptr, *ooov = nullptr, *ovov = nullptr, *F_ov = nullptr,
+         *chol = nullptr, *vvoo = nullptr, *oooo = nullptr;
+  // triple list (device and host), weights
+  std::vector<int> tri_host;  // 3 per triple
+  int ntri = 0;
+  // workspace
+  int batch = 0;  // triples per batch
+  double *ws_w = nullptr, *ws_tt = nullptr, *ws_tt2 = nullptr;
+  double *omt = nullptr, *om1 = nullptr;
+  // Jacobian cache (Algorithm 2 intermediates)
+  double *Zv = nullptr, *Zo = nullptr;
+  bool prep_valid = false;
+  // Jacobian per-vector scratch
+  double *R2 = nullptr, *hvvvo = nullptr, *hoovo = nullptr, *hF = nullptr,
+         *rhot = nullptr, *rho1 = nullptr, *Mj = nullptr;
+  // driver state private to api.cu / split path state private to split.cu
+  void *ext = nullptr;
+  void *split = nullptr;
+  int slices = 0;
+  // counters
+  cc3_counters counters{};
+  // device status word (bounded waits)
+  int *status = nullptr;
+  std::mutex mu;
+};
+
+namespace cc3 {
+// engine (fp64_engine.cu)
+int upload_plan(const Plan &p, DevPlan *d, cudaStream_t s);
+void free_plan(DevPlan *d);
+int launch_plan(const DevPlan &d, const PtrTable &ptrs, cudaStream_t s,
+                long long *launches);
+
+// misc kernels (kernels.cu)
+int launch_contravariant(const double *tau_cab, double *tt_abc, int nv,
+                         int nslot, cudaStream_t s);
+int launch_back_transform(const double *omt, double *om2, int no, int nv,
+                          cudaStream_t s);
+int launch_energy(const double *t2, const double *omt, double *E, int no,
+                  int nv, cudaStream_t s);
+int launch_transpose_ooov_to_oovo(const double *ooov, double *oovo, int no,
+                                  int nv, cudaStream_t s);
+int launch_zero(double *p, size_t n, cudaStream_t s);
+
+// plans (plans.cu)
+struct TermSet { int bt, bv, bo; };  // (t-like, vvvo-like, oovo-like) buffers
+void plan_w_build(Plan &P, int no, int nv, const int ijk[3], int slot,
+                  int buf_w, const TermSet *sets, int nsets, double w,
+                  double eo, int phase);
+void plan_omega_contractions(Plan &P, int no, int nv, const int ijk[3],
+                             int slot, int buf_tt, int buf_ovov, int buf_fov,
+                             int buf_ooov, bool vvov_from_vvvo, int buf_vvov,
+                             int buf_omt, int buf_om1, int ksplit, int which);
+double nominal_flop_omega(int no, int nv, int ntri_weighted);
+}  // namespace cc3
