@@ -1,0 +1,25 @@
+/*
+ * cc3_debug.h -- diagnostic entry point of libcc3 (not part of the hot path).
+ *
+ * cc3_debug_split_gemm runs ONE plain contraction C[m][n] = sum_k A[m][k] B[n][k]
+ * (row-major float64 host arrays A[M][K], B[N][K], C[M][N]) through the split
+ * precision tensor-core engine that the CC3 triples kernels use: both operands
+ * are cut into `slices` integer-valued BF16 slices with one power-of-two scale
+ * each, the slice-product triangle runs on tcgen05 tensor cores with exact
+ * FP32 accumulation of the leading levels, and the result is recombined in
+ * double-float and accumulated in FP64.  It exists to test the engine in
+ * isolation against a plain FP64 product.  Allocates and frees its own device
+ * memory; synchronous; returns a cc3 status (CC3_ERR_ARG for sizes < 1 or
+ * slices outside 3..8).
+ */
+#ifndef CC3_DEBUG_H
+#define CC3_DEBUG_H
+#ifdef __cplusplus
+extern "C" {
+#endif
+int cc3_debug_split_gemm(int M, int N, int K, const double *A, const double *B, double *C,
+                         int slices);
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -32,7 +32,8 @@ EXPORTED = ["cc3_ctx_create", "cc3_ctx_destroy", "cc3_ctx_set_triples",
             "cc3_omega_triples", "cc3_jacobian_triples", "cc3_ctx_counters",
             "cc3_ctx_set_slices", "cc3_strerror", "cc3_serve_start",
             "cc3_serve_submit", "cc3_serve_poll", "cc3_serve_wait",
-            "cc3_serve_cancel", "cc3_serve_stats", "cc3_serve_stop"]
+            "cc3_serve_cancel", "cc3_serve_stats", "cc3_serve_stop",
+            "cc3_debug_split_gemm"]
 
 
 class CC3Error(RuntimeError):
@@ -66,6 +67,8 @@ def _load():
     L.cc3_ctx_counters.restype = I
     L.cc3_ctx_set_slices.argtypes = [P, I]
     L.cc3_ctx_set_slices.restype = I
+    L.cc3_debug_split_gemm.argtypes = [I, I, I, P, P, P, I]
+    L.cc3_debug_split_gemm.restype = I
     L.cc3_strerror.argtypes = [I]
     L.cc3_strerror.restype = ctypes.c_char_p
     return L
@@ -154,6 +157,18 @@ def cc3_ctx_counters(ctx):
 
 def cc3_ctx_set_slices(ctx, slices):
     _check(lib.cc3_ctx_set_slices(ctx, int(slices)), "cc3_ctx_set_slices")
+
+
+def cc3_debug_split_gemm(A, B, slices=6):
+    """C = A @ B.T through the split-precision tensor-core engine (diagnostic)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    M, K = A.shape
+    N = B.shape[0]
+    C = np.zeros((M, N))
+    _check(lib.cc3_debug_split_gemm(M, N, K, _ptr(A), _ptr(B), _ptr(C), int(slices)),
+           "cc3_debug_split_gemm")
+    return C
 
 
 # ---- convenience wrapper -----------------------------------------------------

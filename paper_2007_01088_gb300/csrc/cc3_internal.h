@@ -61,7 +61,7 @@ enum BufId {
   B_T2 = 0, B_VVVO, B_OOVO, B_OOOV, B_OVOV, B_FOV, B_EPSV, B_EPSO,
   B_WS_W, B_WS_TT, B_OMT, B_OM1,
   B_R2, B_HVVVO, B_HOOVO, B_HF, B_ZV, B_ZO, B_VVOO, B_OOOO,
-  B_RHOT, B_RHO1, B_TT_TAU, B_SCRATCH,
+  B_RHOT, B_RHO1, B_TT_TAU, B_SCRATCH, B_SLOTEXP,
   B_COUNT
 };
 

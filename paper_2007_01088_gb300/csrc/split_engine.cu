@@ -1,0 +1,321 @@
+// Split-precision tensor-core contraction engine (tcgen05, sm_103a).
+//
+// Each FP64 operand is carried as s integer-valued BF16 slices with one
+// power-of-two scale per tensor: x = 2^(e-7) sum_p d_p 2^(-8p), |d_p| <= 128,
+// slice p stored as the exact BF16 value d_p 2^(-8p).  A contraction
+// sum_k A[m][k] B[n][k] becomes the triangle of slice products p + q <= s-1
+// (the products with p + q >= s are below the representation error).  Every
+// slice product is exact in FP32; the products of level p + q = 0 and 1 go to
+// two tensor-memory accumulators that stay exact because they are drained into
+// double-float registers every 512 K (|sum| < 2^24 resp. 2^16 in their units),
+// all higher levels share a third, rounded accumulator (its rounding is below
+// 2^-40 of the result).
+//
+// Warp roles (576 threads): warp 0 issues TMA loads into a 3-stage ring of
+// (s A-slices, s B-slices) tiles of 128 x 16 and Ntile x 16 BF16 (32-byte
+// swizzle); one thread of warp 1 issues tcgen05.mma (M = 128, N = Ntile,
+// K = 16, FP32 accumulate) and owns the tensor-memory allocation; warps 2-17
+// drain and finish the accumulators (each quadrant of 32 TMEM lanes is read
+// by four warps, one per column quarter, 8 columns per load).  Every wait is bounded: on timeout the
+// CTA sets an error word that the host turns into CC3_ERR_TIMEOUT.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "dd.cuh"
+#include "sm100_prims.cuh"
+#include "split_engine.h"
+
+namespace cc3 {
+using namespace sm100;
+
+size_t s_smem_bytes(int slices, int ntile) {
+  return (size_t)S_STAGES * slices * (S_BM + ntile) * 32 + 1024;
+}
+
+__device__ __forceinline__ long long s_rowoff(int m, int m_in, long long s1, long long s0) {
+  return (long long)(m / m_in) * s1 + (long long)(m % m_in) * s0;
+}
+
+__global__ void __maxnreg__(112)
+split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__restrict__ terms,
+                    const __grid_constant__ SMapTable maps, VPtrTable P, int s,
+                    int kdrain_steps, int *status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full[S_STAGES], empty[S_STAGES];
+  __shared__ __align__(8) uint64_t accfull, drainfull, drainempty;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ volatile int err;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long cta = blockIdx.x;
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].tile_base <= cta) lo = mid; else hi = mid - 1;
+  }
+  const SJob &J = jobs[lo];
+  long long local = cta - J.tile_base;
+  const int per_batch = J.tiles_m * J.tiles_n * J.ksplit;
+  const int bi = (int)(local / per_batch);
+  int r = (int)(local % per_batch);
+  const int ks = r % J.ksplit;
+  r /= J.ksplit;
+  const int tn = r % J.tiles_n, tm = r / J.tiles_n;
+  const int m0 = tm * S_BM, n0 = tn * J.Ntile;
+  const int Nt = J.Ntile;
+  const uint32_t a_bytes = S_BM * 32, b_bytes = (uint32_t)Nt * 32;
+  const uint32_t stage_bytes = (uint32_t)s * (a_bytes + b_bytes);
+
+  int total = 0;
+  for (int t = 0; t < J.nterm; ++t) total += terms[J.term0 + t].ksteps;
+  const int per = (total + J.ksplit - 1) / J.ksplit;
+  const int g0 = min(total, ks * per), g1 = min(total, g0 + per);
+  const int nsteps = g1 - g0;
+  const int ndrains = nsteps > 0 ? (nsteps - 1) / kdrain_steps : 0;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S_STAGES; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(&accfull, 1);
+    mbar_init(&drainfull, 1);
+    mbar_init(&drainempty, S_EPI_WARPS);
+    err = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(&tmem_base_sh, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+
+  if (warp == 0) {
+    if (lane == 0 && nsteps > 0) {
+      // producer
+      int t = 0, kbase = 0;
+      while (t < J.nterm && kbase + terms[J.term0 + t].ksteps <= g0) {
+        kbase += terms[J.term0 + t].ksteps;
+        ++t;
+      }
+      int issued = 0;
+      for (int g = g0; g < g1; ++g) {
+        while (g - kbase >= terms[J.term0 + t].ksteps) {
+          kbase += terms[J.term0 + t].ksteps;
+          ++t;
+        }
+        const STerm &T = terms[J.term0 + t];
+        const int kk = (g - kbase) * S_BK;
+        const int st = issued % S_STAGES, ph = (issued / S_STAGES) & 1;
+        if (!mbar_wait(&empty[st], ph ^ 1, &err)) break;
+        mbar_arrive_expect_tx(&full[st], stage_bytes);
+        uint8_t *sa = smem + (size_t)st * stage_bytes;
+        uint8_t *sb = sa + (size_t)s * a_bytes;
+        const int ar = T.A.row0 + bi * T.A.row_b + m0, as = T.A.slab0 + bi * T.A.slab_b;
+        const int br = T.B.row0 + bi * T.B.row_b + n0, bs = T.B.slab0 + bi * T.B.slab_b;
+        for (int p = 0; p < s; ++p)
+          tma_load_4d(sa + p * a_bytes, &maps.m[T.A.map], &full[st], kk, ar, as, p);
+        for (int q = 0; q < s; ++q)
+          tma_load_4d(sb + q * b_bytes, &maps.m[T.B.map], &full[st], kk, br, bs, q);
+        ++issued;
+      }
+      // let every issued copy land before the CTA may exit (bounded)
+      for (int i = (issued > S_STAGES ? issued - S_STAGES : 0); i < issued; ++i)
+        mbar_wait(&full[i % S_STAGES], (i / S_STAGES) & 1, &err, 500000000ull);
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && nsteps > 0) {
+      // MMA issuer
+      const uint32_t id_pos = idesc_bf16(S_BM, Nt, 0), id_neg = idesc_bf16(S_BM, Nt, 1);
+      int t = 0, kbase = 0;
+      while (t < J.nterm && kbase + terms[J.term0 + t].ksteps <= g0) {
+        kbase += terms[J.term0 + t].ksteps;
+        ++t;
+      }
+      bool init0 = false, init1 = false, initR = false;
+      int since = 0, nd = 0;
+      for (int g = g0, it = 0; g < g1; ++g, ++it) {
+        while (g - kbase >= terms[J.term0 + t].ksteps) {
+          kbase += terms[J.term0 + t].ksteps;
+          ++t;
+        }
+        const uint32_t idesc = terms[J.term0 + t].negA ? id_neg : id_pos;
+        const int st = it % S_STAGES, ph = (it / S_STAGES) & 1;
+        if (!mbar_wait(&full[st], ph, &err)) break;
+        tc_fence_after();
+        const uint32_t sa = smem_u32(smem + (size_t)st * stage_bytes);
+        const uint32_t sb = sa + (uint32_t)s * a_bytes;
+        for (int p = 0; p < s; ++p) {
+          const uint64_t ad = smem_desc_sw32(sa + p * a_bytes);
+          for (int q = 0; q + p < s; ++q) {
+            const uint64_t bd = smem_desc_sw32(sb + q * b_bytes);
+            const int lv = p + q;
+            const uint32_t col = lv == 0 ? 0u : (lv == 1 ? (uint32_t)Nt : 2u * Nt);
+            const bool ini = lv == 0 ? init0 : (lv == 1 ? init1 : initR);
+            umma_f16(tmem + col, ad, bd, idesc, ini ? 1u : 0u);
+            if (lv == 0) init0 = true; else if (lv == 1) init1 = true; else initR = true;
+          }
+        }
+        umma_commit(&empty[st]);
+        if (++since == kdrain_steps && g + 1 < g1) {
+          umma_commit(&drainfull);
+          if (!mbar_wait(&drainempty, nd & 1, &err)) break;
+          tc_fence_after();
+          ++nd;
+          since = 0;
+          init0 = init1 = false;
+        }
+      }
+      umma_commit(&accfull);
+    }
+  } else {
+    // epilogue: warps 2..17
+    const int ew = warp - 2, quad = warp & 3, part = ew >> 2;
+    const int row = quad * 32 + lane;
+    const int m = m0 + row;
+    const int qc = Nt >> 2;        // columns per quarter (multiple of 8, <= 40)
+    const int nch = qc >> 3;       // 8-column chunks (<= 5)
+    const uint32_t tb = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(part * qc);
+    dd::df acc[5][8];
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) acc[c][i] = {0.f, 0.f};
+    bool ok = true;
+    for (int d = 0; d < ndrains && ok; ++d) {
+      ok = mbar_wait(&drainfull, d & 1, &err);
+      if (!ok) break;
+      tc_fence_after();
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        if (c < nch) {
+          float v0[8], v1[8];
+          tmem_ld8(tb + c * 8, v0);
+          tmem_ld8(tb + Nt + c * 8, v1);
+          tmem_wait_ld();
+#pragma unroll
+          for (int i = 0; i < 8; ++i) acc[c][i] = dd::add(acc[c][i], dd::two_sum(v0[i], v1[i]));
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&drainempty);
+    }
+    if (ok && nsteps > 0) ok = mbar_wait(&accfull, 0, &err);
+    if (ok) {
+      tc_fence_after();
+      const int ex = J.expo + (J.expo_slot >= 0 ? reinterpret_cast<const int *>(P.p[B_SLOTEXP])[J.expo_slot] : 0);
+      const float sc = ldexpf(J.mult, ex);
+      const int nvv = J.nv;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        if (c < nch) {
+          float v0[8], v1[8], vr[8];
+          if (nsteps > 0) {
+            tmem_ld8(tb + c * 8, v0);
+            tmem_ld8(tb + Nt + c * 8, v1);
+            tmem_ld8(tb + 2 * Nt + c * 8, vr);
+            tmem_wait_ld();
+          } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v0[i] = v1[i] = vr[i] = 0.f;
+          }
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            dd::df x = dd::add(acc[c][i], dd::two_sum(v0[i], v1[i]));
+            x = dd::add_f(x, vr[i]);
+            x = dd::scale(x, sc);
+            const int n = n0 + part * qc + c * 8 + i;
+            if (m >= J.M || n >= J.N) continue;
+            const OutD &C = n < J.Nm ? J.C : J.Ct;
+            const int nc = n < J.Nm ? n : n - J.Nm;
+            const long long off = C.off + (long long)bi * C.sb +
+                                  s_rowoff(m, C.m_in, C.sm1, C.sm0) +
+                                  s_rowoff(nc, C.n_in, C.sn1, C.sn0);
+            if (J.mode == SEPI_DD_STORE) {
+              reinterpret_cast<float2 *>(P.p[C.buf])[off] = make_float2(x.hi, x.lo);
+            } else if (J.mode == SEPI_DD_TAU) {
+              const OutD &W = J.W;
+              const long long woff = W.off + (long long)bi * W.sb +
+                                     s_rowoff(m, W.m_in, W.sm1, W.sm0) +
+                                     s_rowoff(nc, W.n_in, W.sn1, W.sn0);
+              const float2 wv = reinterpret_cast<const float2 *>(P.p[W.buf])[woff];
+              dd::df tot = dd::add(x, dd::df{wv.x, wv.y});
+              const float2 *ev = reinterpret_cast<const float2 *>(P.p[B_EPSV]);
+              const float2 ea = ev[nc / nvv], eb = ev[nc % nvv], ec = ev[m];
+              dd::df e = dd::add(dd::add(dd::df{ea.x, ea.y}, dd::df{eb.x, eb.y}),
+                                 dd::df{ec.x, ec.y});
+              e = dd::add(e, dd::df{-J.eo_hi, -J.eo_lo});
+              const dd::df den = dd::add(dd::df{J.w_hi, J.w_lo}, dd::neg(e));
+              const dd::df tau = dd::div(tot, den);
+              reinterpret_cast<float2 *>(P.p[C.buf])[off] = make_float2(tau.hi, tau.lo);
+            } else {
+              atomicAdd(reinterpret_cast<double *>(P.p[C.buf]) + off, dd::to_double(x));
+            }
+          }
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, 512);
+  if (threadIdx.x == 0 && err) atomicExch(status, 1);
+}
+
+int s_upload_plan(const SPlan &p, SDevPlan *d, cudaStream_t s) {
+  s_free_plan(d);
+  d->njobs = (int)p.jobs.size();
+  d->tiles = p.tiles;
+  if (d->njobs == 0) return CC3_OK;
+  if (cudaMalloc(&d->jobs, sizeof(SJob) * p.jobs.size()) != cudaSuccess) return CC3_ERR_OOM;
+  if (cudaMalloc(&d->terms, sizeof(STerm) * (p.terms.size() + 1)) != cudaSuccess)
+    return CC3_ERR_OOM;
+  if (cudaMemcpyAsync(d->jobs, p.jobs.data(), sizeof(SJob) * p.jobs.size(),
+                      cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return CC3_ERR_CUDA;
+  if (!p.terms.empty() &&
+      cudaMemcpyAsync(d->terms, p.terms.data(), sizeof(STerm) * p.terms.size(),
+                      cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return CC3_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return CC3_ERR_CUDA;
+  return CC3_OK;
+}
+
+void s_free_plan(SDevPlan *d) {
+  if (d->jobs) cudaFree(d->jobs);
+  if (d->terms) cudaFree(d->terms);
+  d->jobs = nullptr;
+  d->terms = nullptr;
+  d->njobs = 0;
+  d->tiles = 0;
+}
+
+int s_launch_plan(const SDevPlan &d, const SMapTable &maps, const VPtrTable &ptrs,
+                  int slices, int kdrain_steps, int *status, cudaStream_t s,
+                  long long *launches) {
+  if (d.njobs == 0 || d.tiles == 0) return CC3_OK;
+  if (d.tiles > 0x7fffffffLL) return CC3_ERR_ARG;
+  if (slices < 3 || slices > S_MAX_SLICES) return CC3_ERR_ARG;
+  // at least 120 KB so that one CTA (and one 512-column TMEM allocation) per SM
+  const size_t smem = std::max<size_t>(s_smem_bytes(slices, S_NT_MAX), 120 * 1024);
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(split_engine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)s_smem_bytes(S_MAX_SLICES, S_NT_MAX)) != cudaSuccess)
+      return CC3_ERR_CUDA;
+    attr_set = true;
+  }
+  split_engine_kernel<<<(unsigned)d.tiles, S_THREADS, smem, s>>>(
+      d.jobs, d.njobs, d.terms, maps, ptrs, slices, kdrain_steps, status);
+  if (launches) ++*launches;
+  return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_ERR_CUDA;
+}
+
+}  // namespace cc3

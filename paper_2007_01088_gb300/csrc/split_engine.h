@@ -1,0 +1,72 @@
+// Job tables of the split-precision (BF16 slice) tensor-core engine.
+#pragma once
+#include <cuda.h>
+
+#include "cc3_internal.h"
+
+namespace cc3 {
+
+enum { SMAX_MAPS = 28, S_BM = 128, S_BK = 16, S_STAGES = 3, S_MAX_SLICES = 8,
+       S_NT_MAX = 160, S_EPI_WARPS = 16, S_THREADS = 64 + 32 * S_EPI_WARPS };
+
+struct SMapTable {
+  CUtensorMap m[SMAX_MAPS];
+};
+
+// A slice operand tile: 4-D tensor map (K, rows, slab, slice); the tile of
+// batch index b starts at row row0 + b*row_b (+ m0 or n0) of slab
+// slab0 + b*slab_b.
+struct SOpnd {
+  int map;
+  int slab0, row0, slab_b, row_b;
+};
+
+struct STerm {
+  SOpnd A, B;
+  int ksteps;  // K / 16
+  int negA;    // the products enter with a minus sign
+};
+
+enum SEpi { SEPI_DD_STORE = 0, SEPI_DD_TAU = 1, SEPI_F64_ATOMIC = 2 };
+
+struct SJob {
+  int M, N, Nm, Ntile, batch;
+  int tiles_m, tiles_n, ksplit;
+  int term0, nterm;
+  int mode;
+  int expo;       // result = 2^expo * (integer-scaled accumulators)
+  int expo_slot;  // >= 0: add the per-triple exponent ex[expo_slot]
+  float mult;  // +-1 or 2 (exact)
+  OutD C, Ct;  // output element (b, m, n) for n < Nm, resp. (b, m, n - Nm);
+               // buffer of float2 (dd) or double
+  OutD W;      // tau mode: the dd values of the other W phase
+  float eo_hi, eo_lo, w_hi, w_lo;
+  int nv;
+  long long tile_base;
+};
+
+struct VPtrTable {
+  void *p[MAX_BUFS];
+};
+
+struct SPlan {
+  std::vector<SJob> jobs;
+  std::vector<STerm> terms;
+  long long tiles = 0;
+};
+
+struct SDevPlan {
+  SJob *jobs = nullptr;
+  STerm *terms = nullptr;
+  int njobs = 0;
+  long long tiles = 0;
+};
+
+int s_upload_plan(const SPlan &p, SDevPlan *d, cudaStream_t s);
+void s_free_plan(SDevPlan *d);
+int s_launch_plan(const SDevPlan &d, const SMapTable &maps, const VPtrTable &ptrs,
+                  int slices, int kdrain_steps, int *status, cudaStream_t s,
+                  long long *launches);
+size_t s_smem_bytes(int slices, int ntile);
+
+}  // namespace cc3

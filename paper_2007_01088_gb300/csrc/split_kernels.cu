@@ -1,0 +1,217 @@
+// Element-wise kernels of the split path: exact digit extraction into BF16
+// slices, max-abs reductions, and the per-triple double-float contravariant
+// combination (paper, Algorithm 1, second line of the triple loop).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "dd.cuh"
+#include "split_kernels.h"
+
+namespace cc3 {
+
+// Fixed-point value round(x * 2^sh) of a finite double as a signed 64-bit
+// integer, from its bits (integer arithmetic only; |result| < 2^62 assumed).
+__device__ __forceinline__ long long fixed_from_double(double x, int sh) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex == 0) return 0;  // zero or subnormal (below every digit used here)
+  const long long mant = (long long)((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
+  const int s = ex - 1075 + sh;  // x = mant * 2^(ex-1075)
+  long long v;
+  if (s >= 0) {
+    v = s > 9 ? (mant << 9) : (mant << s);  // |x 2^sh| < 2^62 keeps s <= 9
+  } else if (s > -63) {
+    v = (mant + (1ll << (-s - 1))) >> (-s);
+  } else {
+    v = 0;
+  }
+  return (b >> 63) ? -v : v;
+}
+__device__ __forceinline__ long long fixed_from_float(float x, int sh) {
+  const unsigned int b = __float_as_uint(x);
+  const int ex = (int)((b >> 23) & 0xFF);
+  if (ex == 0) return 0;
+  const long long mant = (long long)((b & 0x7FFFFFu) | 0x800000u);
+  const int s = ex - 150 + sh;  // x = mant * 2^(ex-150)
+  long long v;
+  if (s >= 0) {
+    v = s > 38 ? (mant << 38) : (mant << s);
+  } else if (s > -40) {
+    v = (mant + (1ll << (-s - 1))) >> (-s);
+  } else {
+    v = 0;
+  }
+  return (b >> 31) ? -v : v;
+}
+
+// Balanced base-256 digits of T (|T| < 2^(7+8(s-1))): T = sum_p d_p 256^(s-1-p),
+// d_p in [-128, 128]; slice p stores d_p 2^(-8p) as an exact BF16.
+__device__ __forceinline__ void store_digits(long long T, int s, __nv_bfloat16 *dst,
+                                             long long slice_stride) {
+  float d[S_MAX_SLICES_K];
+#pragma unroll
+  for (int p = S_MAX_SLICES_K - 1; p >= 0; --p) {
+    if (p < s) {
+      if (p > 0) {
+        const long long r = ((T + 128) & 255) - 128;
+        d[p] = (float)r;
+        T = (T - r) >> 8;
+      } else {
+        d[0] = (float)T;
+      }
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < S_MAX_SLICES_K; ++p)
+    if (p < s) dst[p * slice_stride] = __float2bfloat16_rn(ldexpf(d[p], -8 * p));
+}
+
+// dst[p][row][k] for row < nrows, k < Kp, from src through a strided gather:
+//   row = (r2, r1, r0), k = (k1, k0); value 0 outside (k0 < k0v, k1 < k1v).
+__global__ void slice_gather_kernel(const double *__restrict__ src, __nv_bfloat16 *__restrict__ dst,
+                                    int s, int e, Gather g, long long nrows, int Kp) {
+  const long long n = nrows * Kp;
+  const long long sstride = n;
+  const int sh = 7 + 8 * (s - 1) - e;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long row = idx / Kp;
+    const int k = (int)(idx % Kp);
+    const int k1 = k / g.kin, k0 = k % g.kin;
+    long long T = 0;
+    if (k0 < g.k0v && k1 < g.k1v) {
+      const long long r0 = row % g.n0, r1 = (row / g.n0) % g.n1, r2 = row / ((long long)g.n0 * g.n1);
+      const long long off = g.off + r2 * g.s2 + r1 * g.s1 + r0 * g.s0 + k1 * g.sk1 + k0 * g.sk0;
+      T = fixed_from_double(src[off], sh);
+    }
+    store_digits(T, s, dst + idx, sstride);
+  }
+}
+
+__global__ void maxabs_kernel(const double *__restrict__ x, long long n,
+                              unsigned long long *__restrict__ out) {
+  unsigned long long m = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x[i]) & 0x7FFFFFFFFFFFFFFFull;
+    m = b > m ? b : m;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+    m = v > m ? v : m;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// tau~ = 4 tau^{abc} - 2 tau^{acb} - 2 tau^{cba} - 2 tau^{bac} + tau^{bca} + tau^{cab}
+// from tau stored as T[slot][c][a][b] (dd); writes TT[slot][a][b][c] (dd) and
+// the max |tau~| of each slot (float bits, atomic max).
+__global__ void contravariant_dd_kernel(const float2 *__restrict__ tau, float2 *__restrict__ tt,
+                                        int nv, unsigned int *__restrict__ maxbits) {
+  const long long nv2 = (long long)nv * nv, nv3 = nv2 * nv;
+  const float2 *T = tau + blockIdx.y * nv3;
+  float2 *O = tt + blockIdx.y * nv3;
+  float mx = 0.f;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nv3;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(e % nv);
+    const int b = (int)((e / nv) % nv);
+    const int a = (int)(e / nv2);
+#define TAU(x, y, z) T[(long long)(z) * nv2 + (long long)(x) * nv + (y)]
+    const float2 t0 = TAU(a, b, c), t1 = TAU(a, c, b), t2 = TAU(c, b, a);
+    const float2 t3 = TAU(b, a, c), t4 = TAU(b, c, a), t5 = TAU(c, a, b);
+#undef TAU
+    dd::df r = dd::scale(dd::df{t0.x, t0.y}, 4.f);
+    r = dd::add(r, dd::scale(dd::df{t1.x, t1.y}, -2.f));
+    r = dd::add(r, dd::scale(dd::df{t2.x, t2.y}, -2.f));
+    r = dd::add(r, dd::scale(dd::df{t3.x, t3.y}, -2.f));
+    r = dd::add(r, dd::df{t4.x, t4.y});
+    r = dd::add(r, dd::df{t5.x, t5.y});
+    O[e] = make_float2(r.hi, r.lo);
+    mx = fmaxf(mx, fabsf(r.hi));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(maxbits + blockIdx.y, __float_as_uint(mx));
+}
+
+// exponent e with max < 2^e (max slightly enlarged to cover the dd low part)
+__global__ void slot_exponent_kernel(const unsigned int *__restrict__ maxbits, int *__restrict__ ex,
+                                     int nslot) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nslot) return;
+  const float m = __uint_as_float(maxbits[i]) * (1.0f + 1e-6f);
+  int e = 0;
+  if (m > 0.f) {
+    frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
+  }
+  ex[i] = e;
+}
+
+// Slices of tau~ in the three cyclic layouts used by the residual
+// contractions: layout L puts slot L outermost, then slot L+1, then slot L+2
+// (innermost, padded to vp):  V_L[p][slot][x][y][z].
+__global__ void slice_tt_kernel(const float2 *__restrict__ tt, __nv_bfloat16 *__restrict__ v0,
+                                __nv_bfloat16 *__restrict__ v1, __nv_bfloat16 *__restrict__ v2,
+                                int nv, int vp, int s, const int *__restrict__ ex, int nslot) {
+  const long long per = (long long)nv * nv * vp;
+  const long long n = per * nslot;
+  const long long nv2 = (long long)nv * nv;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < 3 * n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int L = (int)(idx / n);
+    const long long rem = idx % n;
+    const int slot = (int)(rem / per);
+    const long long w = rem % per;
+    const int z = (int)(w % vp);
+    const int y = (int)((w / vp) % nv);
+    const int x = (int)(w / ((long long)vp * nv));
+    long long T = 0;
+    if (z < nv) {
+      int v[3];
+      v[L] = x;
+      v[(L + 1) % 3] = y;
+      v[(L + 2) % 3] = z;
+      const float2 t = tt[(long long)slot * nv2 * nv + (long long)v[0] * nv2 + (long long)v[1] * nv + v[2]];
+      const int sh = 7 + 8 * (s - 1) - ex[slot];
+      T = fixed_from_float(t.x, sh) + fixed_from_float(t.y, sh);
+    }
+    __nv_bfloat16 *dst = (L == 0 ? v0 : (L == 1 ? v1 : v2)) + rem;
+    store_digits(T, s, dst, n);
+  }
+}
+
+// ---- launchers ----------------------------------------------------------------
+static int grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  return (int)(b < 16384 ? (b > 0 ? b : 1) : 16384);
+}
+
+int launch_slice_gather(const double *src, __nv_bfloat16 *dst, int s, int e, const Gather &g,
+                        long long nrows, int Kp, cudaStream_t st) {
+  slice_gather_kernel<<<grid_for(nrows * Kp), 256, 0, st>>>(src, dst, s, e, g, nrows, Kp);
+  return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_ERR_CUDA;
+}
+int launch_maxabs(const double *x, long long n, unsigned long long *out, cudaStream_t st) {
+  maxabs_kernel<<<grid_for(n), 256, 0, st>>>(x, n, out);
+  return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_ERR_CUDA;
+}
+int launch_contravariant_dd(const float2 *tau, float2 *tt, int nv, int nslot,
+                            unsigned int *maxbits, cudaStream_t st) {
+  const long long nv3 = (long long)nv * nv * nv;
+  int bx = (int)((nv3 + 255) / 256);
+  if (bx > 2048) bx = 2048;
+  contravariant_dd_kernel<<<dim3(bx, nslot), 256, 0, st>>>(tau, tt, nv, maxbits);
+  return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_ERR_CUDA;
+}
+int launch_slot_exponent(const unsigned int *maxbits, int *ex, int nslot, cudaStream_t st) {
+  slot_exponent_kernel<<<(nslot + 127) / 128, 128, 0, st>>>(maxbits, ex, nslot);
+  return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_ERR_CUDA;
+}
+int launch_slice_tt(const float2 *tt, __nv_bfloat16 *v0, __nv_bfloat16 *v1, __nv_bfloat16 *v2,
+                    int nv, int vp, int s, const int *ex, int nslot, cudaStream_t st) {
+  const long long n = 3LL * nv * nv * vp * nslot;
+  slice_tt_kernel<<<grid_for(n), 256, 0, st>>>(tt, v0, v1, v2, nv, vp, s, ex, nslot);
+  return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_ERR_CUDA;
+}
+
+}  // namespace cc3

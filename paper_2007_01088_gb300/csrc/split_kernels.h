@@ -1,0 +1,30 @@
+// Launchers of the split path's element-wise kernels.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "cc3_internal.h"
+
+namespace cc3 {
+
+enum { S_MAX_SLICES_K = 8 };
+
+// Strided gather of an FP64 tensor as a [rows][K] matrix:
+//   row = (r2, r1, r0) with r0 < n0, r1 < n1;  k = (k1, k0) with k0 < kin;
+//   element = src[off + r2*s2 + r1*s1 + r0*s0 + k1*sk1 + k0*sk0] when
+//   k0 < k0v and k1 < k1v, else 0 (padding).
+struct Gather {
+  long long off, s2, s1, s0, sk1, sk0;
+  int n1, n0, kin, k0v, k1v;
+};
+
+int launch_slice_gather(const double *src, __nv_bfloat16 *dst, int s, int e, const Gather &g,
+                        long long nrows, int Kp, cudaStream_t st);
+int launch_maxabs(const double *x, long long n, unsigned long long *out, cudaStream_t st);
+int launch_contravariant_dd(const float2 *tau, float2 *tt, int nv, int nslot,
+                            unsigned int *maxbits, cudaStream_t st);
+int launch_slot_exponent(const unsigned int *maxbits, int *ex, int nslot, cudaStream_t st);
+int launch_slice_tt(const float2 *tt, __nv_bfloat16 *v0, __nv_bfloat16 *v1, __nv_bfloat16 *v2,
+                    int nv, int vp, int s, const int *ex, int nslot, cudaStream_t st);
+
+}  // namespace cc3

@@ -1,0 +1,51 @@
+"""Split-precision (BF16 slice) tensor-core path against FP64 references.
+Calls go through the C ABI.  Tolerances are the split path's targets:
+1e-9 absolute on Omega and 1e-8 Eh on the triples energy."""
+import numpy as np
+import pytest
+
+import oracle
+from cc3_inputs import make_inputs, unique_triples
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_2007_01088_gb300 as g
+    return g
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 160, 64), (200, 96, 700), (64, 32, 16),
+                                   (300, 130, 1040), (17, 5, 33)])
+def test_engine_gemm_matches_fp64(g, M, N, K):
+    rng = np.random.default_rng(M + N + K)
+    A = rng.normal(size=(M, K)) * np.exp(rng.normal(size=(M, 1)))
+    B = rng.normal(size=(N, K))
+    ref = A @ B.T
+    scale = np.abs(A).max() * np.abs(B).max() * K
+    C = g.cc3_debug_split_gemm(A, B, 6)
+    assert np.abs(C - ref).max() <= 1e-13 * scale
+    C3 = g.cc3_debug_split_gemm(A, B, 3)
+    assert np.abs(C3 - ref).max() <= 1e-6 * scale
+
+
+def test_engine_gemm_exact_integers(g):
+    # small integers are represented exactly by the first slice: exact result
+    rng = np.random.default_rng(1)
+    A = rng.integers(-100, 100, size=(130, 600)).astype(np.float64)
+    B = rng.integers(-100, 100, size=(64, 600)).astype(np.float64)
+    assert np.array_equal(g.cc3_debug_split_gemm(A, B, 4), A @ B.T)
+
+
+@pytest.mark.parametrize("no,nv", [(5, 30), (4, 70), (3, 17), (6, 33)])
+def test_omega_split_matches_oracle(g, no, nv):
+    inp = make_inputs(no, nv, seed=no * nv)
+    ref = oracle.omega_inputs(inp)
+    ctx = g.Context(inp)
+    o1, o2, e = ctx.omega(g.CC3_SPLIT_BF16)
+    assert np.abs(o1 - ref["omega1"]).max() <= 1e-9
+    assert np.abs(o2 - ref["omega2"]).max() <= 1e-9
+    assert abs(e[0] - ref["E_T"]) <= 1e-8
+    c = ctx.counters()
+    assert c["slices"] == 6 and c["executed_flop"] > c["nominal_flop"]
