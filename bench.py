@@ -104,12 +104,15 @@ def oracle_sample(inp, seconds_target=15.0, nthreads=0):
     tr = unique_triples(inp.no)
     rng = np.random.default_rng(11)
     order = rng.permutation(len(tr))
-    # calibrate on one triple, then size the sample to ~seconds_target
+    # calibrate on one triple per thread, then size the sample to ~seconds_target
+    import os as _os
+    threads = len(_os.sched_getaffinity(0)) if nthreads <= 0 else nthreads
+    ncal = min(len(tr), threads)
     t0 = time.perf_counter()
-    r = oracle.omega_inputs(inp, triples=[tr[order[0]][:3]], nthreads=nthreads)
+    r = oracle.omega_inputs(inp, triples=[tr[x][:3] for x in order[:ncal]], nthreads=nthreads)
     dt1 = time.perf_counter() - t0
     threads = r["threads"]
-    n = int(max(1, min(len(tr), seconds_target / max(dt1, 1e-3) * min(threads, 8))))
+    n = int(max(ncal, min(len(tr), ncal * seconds_target / max(dt1, 1e-3))))
     sel = [tr[x][:3] for x in order[:n]]
     w = sum(tr[x][3] for x in order[:n])
     t0 = time.perf_counter()
@@ -179,7 +182,7 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         ctx = g.Context(inp, device=True, stream=stream)
-        g.lib.cc3_ctx_set_tracing(ctx.ctx, 1) if hasattr(g.lib, "cc3_ctx_set_tracing") else None
+        ctx.set_tracing(True)
         out = (torch.empty((NO, NV), dtype=torch.float64, device=dev),
                torch.empty((NO, NO, NV, NV), dtype=torch.float64, device=dev),
                torch.empty((1,), dtype=torch.float64, device=dev))
@@ -195,9 +198,14 @@ def main():
         torch.cuda.synchronize()
         e0.record(stream)
         launches = 0
+        traces = {}
         for _ in range(args.steps):
             ctx.omega(prec, out=out)
             launches += ctx.counters()["launches"]
+            for k, v in ctx.trace().items():
+                a = traces.setdefault(k, dict(launches=0, ms=0.0, flop=0.0, slice_flop=0.0))
+                for f in a:
+                    a[f] += v[f]
         e1.record(stream)
         torch.cuda.synchronize()
         clk = clocks.stop()
@@ -235,13 +243,22 @@ def main():
         peak = pk["bf16_tflops"]
         roof = {"bound": "tensor", "achieved": None, "peak": peak, "unit": "TFLOP/s",
                 "frac": None, "traffic": None, "peak_source": f"{src} bf16 burst"}
-    kt = getattr(ctx, "kernel_times", None)
-    if callable(kt):
-        info = kt()
-        if info:
-            roof.update(info)
-    if roof.get("achieved") is not None:
-        roof["frac"] = roof["achieved"] / roof["peak"]
+    # dominant kernel class by device time (CUDA events on the launching stream)
+    dom = max(traces.items(), key=lambda kv: kv[1]["ms"])
+    name, d = dom
+    total_ms = sum(v["ms"] for v in traces.values())
+    if prec == g.CC3_FP64:
+        roof["achieved"] = d["flop"] / (d["ms"] * 1e-3) / 1e12
+    else:
+        roof["achieved"] = d["slice_flop"] / (d["ms"] * 1e-3) / 1e12
+        roof["fp64_equivalent_tflops"] = d["flop"] / (d["ms"] * 1e-3) / 1e12
+    roof["kernel"] = name
+    roof["kernel_share"] = d["ms"] / total_ms if total_ms > 0 else None
+    roof["kernel_avg_launch_ms"] = d["ms"] / max(1, d["launches"])
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["classes"] = {k: {"ms_per_step": v["ms"] / args.steps,
+                           "launches_per_step": v["launches"] / args.steps}
+                       for k, v in traces.items() if v["launches"]}
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -131,11 +131,39 @@ typedef struct {
 } cc3_counters;
 int cc3_ctx_counters(const cc3_ctx *ctx, cc3_counters *out);
 
+/* Kernel tracing.  With tracing on, every library kernel launch is bracketed
+ * by CUDA events recorded on the launching stream, grouped by kernel class;
+ * cc3_ctx_trace returns, for the last call, each class's launches, summed
+ * device time (ms) and algorithmic FLOP (FP64-equivalent useful FLOP of the
+ * contractions; for the split engine also the BF16 slice-product FLOP).
+ * Tracing synchronises the stream at the end of each call. */
+typedef struct {
+  char name[32];
+  long long launches;
+  double ms;
+  double flop;        /* FP64-equivalent useful FLOP                     */
+  double slice_flop;  /* BF16 slice-product FLOP (split engine), else 0 */
+} cc3_trace_entry;
+typedef struct {
+  int n;
+  cc3_trace_entry e[8];
+} cc3_trace;
+int cc3_ctx_set_tracing(cc3_ctx *ctx, int on);
+int cc3_ctx_trace(const cc3_ctx *ctx, cc3_trace *out);
+
 /* Set the number of BF16 slices per FP64 operand of the split path
- * (3 <= s <= 8; default chosen from the tolerances, see DESIGN).  */
+ * (3 <= s <= 7; default 6: 48 bits per operand, which keeps the residual
+ * within 1e-9 absolute and the energy within 1e-8 Eh at the no = 16,
+ * nv = 160 scale).  */
 int cc3_ctx_set_slices(cc3_ctx *ctx, int slices);
 
 const char *cc3_strerror(int status);
+
+/* Detail of the most recent failure on the calling thread (the library call
+ * site and, for CUDA errors, the CUDA error string); "" if none.  The string
+ * is owned by the library and valid until the next failing call on the same
+ * thread. */
+const char *cc3_last_error(void);
 
 /* ---------------------------------------------------------------------
  * Serving: a request loop with continuous batching.  Requests (residual or

@@ -10,7 +10,7 @@
  * double-float and accumulated in FP64.  It exists to test the engine in
  * isolation against a plain FP64 product.  Allocates and frees its own device
  * memory; synchronous; returns a cc3 status (CC3_ERR_ARG for sizes < 1 or
- * slices outside 3..8).
+ * slices outside 3..7).
  */
 #ifndef CC3_DEBUG_H
 #define CC3_DEBUG_H

@@ -33,13 +33,25 @@ EXPORTED = ["cc3_ctx_create", "cc3_ctx_destroy", "cc3_ctx_set_triples",
             "cc3_ctx_set_slices", "cc3_strerror", "cc3_serve_start",
             "cc3_serve_submit", "cc3_serve_poll", "cc3_serve_wait",
             "cc3_serve_cancel", "cc3_serve_stats", "cc3_serve_stop",
-            "cc3_debug_split_gemm"]
+            "cc3_debug_split_gemm", "cc3_last_error", "cc3_ctx_set_tracing",
+            "cc3_ctx_trace"]
 
 
 class CC3Error(RuntimeError):
     def __init__(self, status: int, where: str):
-        super().__init__(f"{where}: {cc3_strerror(status)} ({status})")
+        detail = lib.cc3_last_error().decode()
+        super().__init__(f"{where}: {cc3_strerror(status)} ({status}) [{detail}]")
         self.status = status
+
+
+class TraceEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_longlong),
+                ("ms", ctypes.c_double), ("flop", ctypes.c_double),
+                ("slice_flop", ctypes.c_double)]
+
+
+class Trace(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("e", TraceEntry * 8)]
 
 
 class Counters(ctypes.Structure):
@@ -69,12 +81,22 @@ def _load():
     L.cc3_ctx_set_slices.restype = I
     L.cc3_debug_split_gemm.argtypes = [I, I, I, P, P, P, I]
     L.cc3_debug_split_gemm.restype = I
+    L.cc3_ctx_set_tracing.argtypes = [P, I]
+    L.cc3_ctx_set_tracing.restype = I
+    L.cc3_ctx_trace.argtypes = [P, ctypes.POINTER(Trace)]
+    L.cc3_ctx_trace.restype = I
+    L.cc3_last_error.argtypes = []
+    L.cc3_last_error.restype = ctypes.c_char_p
     L.cc3_strerror.argtypes = [I]
     L.cc3_strerror.restype = ctypes.c_char_p
     return L
 
 
 lib = _load()
+
+
+def cc3_last_error() -> str:
+    return lib.cc3_last_error().decode()
 
 
 def cc3_strerror(status: int) -> str:
@@ -155,6 +177,19 @@ def cc3_ctx_counters(ctx):
                 launches=c.launches, slices=c.slices)
 
 
+def cc3_ctx_set_tracing(ctx, on=True):
+    _check(lib.cc3_ctx_set_tracing(ctx, int(bool(on))), "cc3_ctx_set_tracing")
+
+
+def cc3_ctx_trace(ctx):
+    """Per kernel class of the last call: launches, ms, flop, slice_flop."""
+    t = Trace()
+    _check(lib.cc3_ctx_trace(ctx, ctypes.byref(t)), "cc3_ctx_trace")
+    return {t.e[i].name.decode(): dict(launches=t.e[i].launches, ms=t.e[i].ms,
+                                       flop=t.e[i].flop, slice_flop=t.e[i].slice_flop)
+            for i in range(t.n)}
+
+
 def cc3_ctx_set_slices(ctx, slices):
     _check(lib.cc3_ctx_set_slices(ctx, int(slices)), "cc3_ctx_set_slices")
 
@@ -222,6 +257,12 @@ class Context:
 
     def counters(self):
         return cc3_ctx_counters(self.ctx)
+
+    def set_tracing(self, on=True):
+        cc3_ctx_set_tracing(self.ctx, on)
+
+    def trace(self):
+        return cc3_ctx_trace(self.ctx)
 
     def _new(self, shape):
         if self.device:

@@ -14,10 +14,10 @@
 
 using namespace cc3;
 
-#define CU(x)                                  \
-  do {                                         \
-    cudaError_t e_ = (x);                      \
-    if (e_ != cudaSuccess) return CC3_ERR_CUDA; \
+#define CU(x)                                                          \
+  do {                                                                 \
+    cudaError_t e_ = (x);                                              \
+    if (e_ != cudaSuccess) return CC3_FAIL(CC3_ERR_CUDA, cudaGetErrorString(e_)); \
   } while (0)
 #define TRY(x)              \
   do {                      \
@@ -132,6 +132,10 @@ int build_omega_plans(cc3_ctx *c, cudaStream_t s) {
     TRY(upload_plan(pc, &OP.c.back(), s));
     TRY(upload_plan(pom, &OP.om.back(), s));
     TRY(upload_plan(pth, &OP.thin.back(), s));
+    OP.ab.back().flop = plan_flops(pab);
+    OP.c.back().flop = plan_flops(pc);
+    OP.om.back().flop = plan_flops(pom);
+    OP.thin.back().flop = plan_flops(pth);
     OP.ab.back().tile_kind = 0; OP.c.back().tile_kind = 0;
     OP.om.back().tile_kind = 0; OP.thin.back().tile_kind = 1;
     OP.nslot.push_back(t1 - t0);
@@ -175,7 +179,88 @@ int alloc_workspace(cc3_ctx *c) {
 
 }  // namespace
 
+namespace cc3 {
+static thread_local char g_last_error[512] = "";
+int record_error(int status, const char *file, int line, const char *what) {
+  const char *base = std::strrchr(file, '/');
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s:%d: %s (%s)", base ? base + 1 : file,
+                line, what ? what : "", cc3_strerror(status));
+  return status;
+}
+}  // namespace cc3
+
+namespace cc3 {
+static const char *kTraceNames[TR_NCLASS] = {"fp64_engine", "fp64_elementwise", "split_w_build",
+                                             "split_omega", "split_elementwise", "output"};
+void trace_begin(cc3_ctx *c, int cls, cudaStream_t s) {
+  Tracer &T = c->trace;
+  if (!T.on) return;
+  auto &v = T.ev[cls];
+  if ((int)v.size() < 2 * (T.used[cls] + 1)) {
+    for (int k = 0; k < 2; ++k) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      v.push_back(e);
+    }
+  }
+  cudaEventRecord(v[2 * T.used[cls]], s);
+}
+void trace_end(cc3_ctx *c, int cls, cudaStream_t s, double flop, double slice_flop) {
+  Tracer &T = c->trace;
+  if (!T.on) return;
+  auto &v = T.ev[cls];
+  if ((int)v.size() < 2 * (T.used[cls] + 1)) return;
+  cudaEventRecord(v[2 * T.used[cls] + 1], s);
+  T.used[cls]++;
+  T.launches[cls]++;
+  T.flop[cls] += flop;
+  T.slice_flop[cls] += slice_flop;
+}
+void trace_reset(cc3_ctx *c) {
+  Tracer &T = c->trace;
+  for (int k = 0; k < TR_NCLASS; ++k) {
+    T.used[k] = 0;
+    T.launches[k] = 0;
+    T.flop[k] = T.slice_flop[k] = T.ms[k] = 0.0;
+  }
+}
+int trace_collect(cc3_ctx *c, cudaStream_t s) {
+  Tracer &T = c->trace;
+  if (!T.on) return CC3_OK;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return CC3_FAIL(CC3_ERR_CUDA, "trace sync");
+  for (int k = 0; k < TR_NCLASS; ++k)
+    for (int i = 0; i < T.used[k]; ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, T.ev[k][2 * i], T.ev[k][2 * i + 1]) == cudaSuccess)
+        T.ms[k] += ms;
+    }
+  return CC3_OK;
+}
+}  // namespace cc3
+
 extern "C" {
+
+const char *cc3_last_error(void) { return cc3::g_last_error; }
+
+int cc3_ctx_set_tracing(cc3_ctx *c, int on) {
+  if (!c) return CC3_ERR_ARG;
+  c->trace.on = on != 0;
+  return CC3_OK;
+}
+
+int cc3_ctx_trace(const cc3_ctx *c, cc3_trace *out) {
+  if (!c || !out) return CC3_ERR_ARG;
+  std::memset(out, 0, sizeof(*out));
+  for (int k = 0; k < TR_NCLASS; ++k) {
+    cc3_trace_entry &e = out->e[out->n++];
+    std::snprintf(e.name, sizeof(e.name), "%s", kTraceNames[k]);
+    e.launches = c->trace.launches[k];
+    e.ms = c->trace.ms[k];
+    e.flop = c->trace.flop[k];
+    e.slice_flop = c->trace.slice_flop[k];
+  }
+  return CC3_OK;
+}
 
 const char *cc3_strerror(int status) {
   switch (status) {
@@ -203,6 +288,8 @@ void cc3_ctx_destroy(cc3_ctx *c) {
     delete X;
   }
   split_destroy(c);
+  for (int k = 0; k < TR_NCLASS; ++k)
+    for (cudaEvent_t e : c->trace.ev[k]) cudaEventDestroy(e);
   double *bufs[] = {c->eps_o, c->eps_v, c->t2, c->vvvo, c->oovo, c->ooov,
                     c->ovov, c->F_ov, c->chol, c->vvoo, c->oooo, c->ws_w,
                     c->ws_tt, c->ws_tt2, c->omt, c->om1, c->Zv, c->Zo, c->R2,
@@ -319,7 +406,7 @@ int cc3_ctx_counters(const cc3_ctx *c, cc3_counters *out) {
 }
 
 int cc3_ctx_set_slices(cc3_ctx *c, int slices) {
-  if (!c || slices < 3 || slices > 8) return CC3_ERR_ARG;
+  if (!c || slices < 3 || slices > 7) return CC3_ERR_ARG;
   c->slices = slices;
   split_invalidate(c);
   return CC3_OK;
@@ -367,12 +454,20 @@ static int omega_fp64(cc3_ctx *c, cudaStream_t s) {
   fill_ptrs(c, &pt);
   const size_t nv3 = (size_t)c->nv * c->nv * c->nv;
   for (size_t b = 0; b < X->omega.ab.size(); ++b) {
-    TRY(launch_plan(X->omega.ab[b], pt, s, &c->counters.launches));
-    TRY(launch_plan(X->omega.c[b], pt, s, &c->counters.launches));
+    for (const DevPlan *d : {&X->omega.ab[b], &X->omega.c[b]}) {
+      trace_begin(c, TR_FP64_ENGINE, s);
+      TRY(launch_plan(*d, pt, s, &c->counters.launches));
+      trace_end(c, TR_FP64_ENGINE, s, d->flop, 0.0);
+    }
+    trace_begin(c, TR_FP64_ELEM, s);
     TRY(launch_contravariant(c->ws_w, c->ws_tt, c->nv, X->omega.nslot[b], s));
+    trace_end(c, TR_FP64_ELEM, s, 0.0, 0.0);
     c->counters.launches++;
-    TRY(launch_plan(X->omega.om[b], pt, s, &c->counters.launches));
-    TRY(launch_plan(X->omega.thin[b], pt, s, &c->counters.launches));
+    for (const DevPlan *d : {&X->omega.om[b], &X->omega.thin[b]}) {
+      trace_begin(c, TR_FP64_ENGINE, s);
+      TRY(launch_plan(*d, pt, s, &c->counters.launches));
+      trace_end(c, TR_FP64_ENGINE, s, d->flop, 0.0);
+    }
   }
   (void)nv3;
   c->counters.executed_flop = X->omega.executed;
@@ -391,6 +486,7 @@ int cc3_omega_triples(cc3_ctx *c, cc3_prec prec, double *Omega1,
   const int no = c->no, nv = c->nv;
   const size_t nt2 = (size_t)no * no * nv * nv;
   c->counters = cc3_counters{};
+  trace_reset(c);
   c->counters.nominal_flop = 4.0 * (double)nv * nv * nv * nv * (double)weighted(c);
   TRY(launch_zero(c->omt, nt2, s));
   TRY(launch_zero(c->om1, (size_t)no * nv, s));
@@ -400,7 +496,11 @@ int cc3_omega_triples(cc3_ctx *c, cc3_prec prec, double *Omega1,
   } else {
     TRY(split_omega(c, s));
   }
-  return finish_outputs(c, Omega1, Omega2, E_T, s);
+  trace_begin(c, TR_OUTPUT, s);
+  const int rc = finish_outputs(c, Omega1, Omega2, E_T, s);
+  trace_end(c, TR_OUTPUT, s, 0.0, 0.0);
+  if (rc != CC3_OK) return rc;
+  return trace_collect(c, s);
 }
 
 }  // extern "C"

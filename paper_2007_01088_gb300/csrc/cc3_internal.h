@@ -77,6 +77,20 @@ struct DevPlan {  // the same, resident on the device
   int njobs = 0;
   long long tiles = 0;
   int tile_kind = 0;  // 0: 64x64 tiles, 1: 128x4 thin tiles
+  double flop = 0.0;  // useful FLOP of the launch
+};
+
+// Kernel classes of the tracer.
+enum TraceClass {
+  TR_FP64_ENGINE = 0, TR_FP64_ELEM, TR_SPLIT_W, TR_SPLIT_OMEGA, TR_SPLIT_ELEM, TR_OUTPUT,
+  TR_NCLASS
+};
+struct Tracer {
+  bool on = false;
+  std::vector<cudaEvent_t> ev[TR_NCLASS];  // start/stop pairs
+  int used[TR_NCLASS] = {0};
+  long long launches[TR_NCLASS] = {0};
+  double flop[TR_NCLASS] = {0}, slice_flop[TR_NCLASS] = {0}, ms[TR_NCLASS] = {0};
 };
 
 }  // namespace cc3
@@ -107,14 +121,24 @@ struct cc3_ctx {
   void *ext = nullptr;
   void *split = nullptr;
   int slices = 0;
-  // counters
+  // counters and tracing
   cc3_counters counters{};
+  cc3::Tracer trace;
   // device status word (bounded waits)
   int *status = nullptr;
   std::mutex mu;
 };
 
 namespace cc3 {
+// tracing helpers (api.cu): bracket one launch of class `cls`
+void trace_begin(cc3_ctx *c, int cls, cudaStream_t s);
+void trace_end(cc3_ctx *c, int cls, cudaStream_t s, double flop, double slice_flop);
+void trace_reset(cc3_ctx *c);
+int trace_collect(cc3_ctx *c, cudaStream_t s);
+// failure detail for cc3_last_error (api.cu); returns `status`
+int record_error(int status, const char *file, int line, const char *what);
+#define CC3_FAIL(status, what) ::cc3::record_error((status), __FILE__, __LINE__, (what))
+
 // engine (fp64_engine.cu)
 int upload_plan(const Plan &p, DevPlan *d, cudaStream_t s);
 void free_plan(DevPlan *d);

@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -29,9 +30,10 @@
 
 namespace cc3 {
 
-#define CU(x)                                  \
-  do {                                         \
-    if ((x) != cudaSuccess) return CC3_ERR_CUDA; \
+#define CU(x)                                                              \
+  do {                                                                     \
+    cudaError_t e_ = (x);                                                  \
+    if (e_ != cudaSuccess) return CC3_FAIL(CC3_ERR_CUDA, cudaGetErrorString(e_)); \
   } while (0)
 #define TRY(x)                  \
   do {                          \
@@ -58,8 +60,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 int make_map(CUtensorMap *m, const void *base, long long K, long long rows, long long slabs,
              int slices, int box_rows) {
   auto fn = encode_fn();
-  if (!fn) return CC3_ERR_CUDA;
-  if (K % 8 != 0 || box_rows < 8 || box_rows > 256) return CC3_ERR_ARG;
+  if (!fn) return CC3_FAIL(CC3_ERR_CUDA, "cuTensorMapEncodeTiled entry point not found");
+  if (K % 8 != 0 || box_rows < 8 || box_rows > 256) return CC3_FAIL(CC3_ERR_ARG, "tensor map shape");
   cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)slabs, (cuuint64_t)slices};
   cuuint64_t strides[3] = {(cuuint64_t)K * 2, (cuuint64_t)(K * rows * 2),
                            (cuuint64_t)(K * rows * slabs * 2)};
@@ -68,7 +70,13 @@ int make_map(CUtensorMap *m, const void *base, long long K, long long rows, long
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base), dims, strides,
                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? CC3_OK : CC3_ERR_CUDA;
+  if (r != CUDA_SUCCESS) {
+    static thread_local char msg[160];
+    std::snprintf(msg, sizeof(msg), "cuTensorMapEncodeTiled error %d (K %lld rows %lld slabs %lld box %d)",
+                  (int)r, K, rows, slabs, box_rows);
+    return CC3_FAIL(CC3_ERR_CUDA, msg);
+  }
+  return CC3_OK;
 }
 
 inline int rup(int x, int m) { return (x + m - 1) / m * m; }
@@ -80,10 +88,10 @@ int exponent_of(double mx) {
   return e;
 }
 
-// N tile: at most S_NT_MAX (160) columns, a multiple of 32, balanced over tiles
+// N tile: at most S_NT_MAX (96) columns, a multiple of 16, balanced over tiles
 int ntile_for(int N) {
   const int nt = (N + S_NT_MAX - 1) / S_NT_MAX;
-  return std::min<int>(S_NT_MAX, rup((N + nt - 1) / nt, 32));
+  return std::min<int>(S_NT_MAX, rup((N + nt - 1) / nt, 16));
 }
 
 enum MapId {
@@ -95,7 +103,7 @@ static_assert(MAP_COUNT <= SMAX_MAPS, "map table");
 
 struct SplitState {
   int s = 0, vp = 0, op = 0, Et = 0, Eg = 0;
-  int Nab = 0, Nc = 0, N3 = 0, N1 = 32;
+  int Nab = 0, Nc = 0, N3 = 0, N1 = 16;
   __nv_bfloat16 *T2S = nullptr, *T2C = nullptr, *T2R = nullptr, *XS = nullptr, *YS = nullptr,
                 *OS = nullptr, *Zg = nullptr, *Zh = nullptr, *OO = nullptr, *OV = nullptr;
   float2 *evdd = nullptr;
@@ -246,8 +254,8 @@ int stage(cc3_ctx *c, SplitState *S, cudaStream_t st) {
 
   // tensor maps
   S->Nab = ntile_for(nv);
-  S->Nc = std::min<int>(S_NT_MAX, rup(std::min<int>(nv * nv, S_NT_MAX), 32));
-  S->N3 = rup(no + 1, 32);
+  S->Nc = std::min<int>(S_NT_MAX, rup(std::min<int>(nv * nv, S_NT_MAX), 16));
+  S->N3 = rup(no + 1, 16);
   if (S->N3 > S_NT_MAX) return CC3_ERR_UNSUPPORTED;
   CUtensorMap *M = S->maps.m;
   std::memset(&S->maps, 0, sizeof(S->maps));
@@ -344,6 +352,9 @@ void add_sterm(SPlan &P, int job, SOpnd A, SOpnd B, int K, int negA, double &exe
   j.nterm++;
   executed += 2.0 * j.tiles_m * S_BM * (double)j.tiles_n * j.Ntile * K * j.batch *
               (slices * (slices + 1) / 2);
+  const double useful = 2.0 * j.M * (double)j.N * K * j.batch;
+  P.flop += useful;
+  P.slice_flop += useful * (slices * (slices + 1) / 2);
 }
 
 void plan_w_split(SPlan &pab, SPlan &pc, SplitState *S, int no, int nv, const int ijk[3],
@@ -513,17 +524,25 @@ int split_omega(cc3_ctx *c, cudaStream_t st) {
   VPtrTable P;
   fill_vptrs(c, S, &P);
   const int nv = c->nv;
-  const int kdrain = 512 / S_BK;
+  const int kdrain = S_DRAIN_STEPS;
   for (size_t b = 0; b < S->ab.size(); ++b) {
     const int ns = S->nslot[b];
-    TRY(s_launch_plan(S->ab[b], S->maps, P, s, kdrain, S->status, st, &c->counters.launches));
-    TRY(s_launch_plan(S->cc[b], S->maps, P, s, kdrain, S->status, st, &c->counters.launches));
+    for (const SDevPlan *d : {&S->ab[b], &S->cc[b]}) {
+      trace_begin(c, TR_SPLIT_W, st);
+      TRY(s_launch_plan(*d, S->maps, P, s, kdrain, S->status, st, &c->counters.launches));
+      trace_end(c, TR_SPLIT_W, st, d->flop, d->slice_flop);
+    }
+    trace_begin(c, TR_SPLIT_ELEM, st);
     CU(cudaMemsetAsync(S->maxbits, 0, sizeof(unsigned int) * ns, st));
     TRY(launch_contravariant_dd(S->Wdd, S->TTdd, nv, ns, S->maxbits, st));
     TRY(launch_slot_exponent(S->maxbits, S->slot_ex, ns, st));
-    TRY(launch_slice_tt(S->TTdd, S->V[0], S->V[1], S->V[2], nv, S->vp, s, S->slot_ex, ns, st));
+    TRY(launch_slice_tt(S->TTdd, S->V[0], S->V[1], S->V[2], nv, S->vp, s, S->slot_ex, ns,
+                        S->batch, st));
+    trace_end(c, TR_SPLIT_ELEM, st, 0.0, 0.0);
     c->counters.launches += 3;
+    trace_begin(c, TR_SPLIT_OMEGA, st);
     TRY(s_launch_plan(S->om[b], S->maps, P, s, kdrain, S->status, st, &c->counters.launches));
+    trace_end(c, TR_SPLIT_OMEGA, st, S->om[b].flop, S->om[b].slice_flop);
   }
   int hs = 0;
   CU(cudaMemcpyAsync(&hs, S->status, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -581,7 +600,7 @@ int debug_split_gemm(int M, int N, int K, const double *A, const double *B, doub
   } while (0)
 #define CKC(x)                                   \
   do {                                           \
-    if ((x) != cudaSuccess) { rc = CC3_ERR_CUDA; goto done; } \
+    if ((x) != cudaSuccess) { rc = CC3_FAIL(CC3_ERR_CUDA, "debug gemm cuda call"); goto done; } \
   } while (0)
   CK(alloc(&dA, (size_t)M * K));
   CK(alloc(&dB, (size_t)N * K));
@@ -617,7 +636,7 @@ int debug_split_gemm(int M, int N, int K, const double *A, const double *B, doub
     add_sterm(P, jb, opd(0, 0), opd(1, 0), Kp, 0, ex, s);
     CK(s_upload_plan(P, &D, st));
     ptr.p[0] = dC;
-    CK(s_launch_plan(D, maps, ptr, s, 512 / S_BK, status, st, nullptr));
+    CK(s_launch_plan(D, maps, ptr, s, S_DRAIN_STEPS, status, st, nullptr));
     int hs = 0;
     CKC(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
     CKC(cudaMemcpyAsync(C, dC, sizeof(double) * M * N, cudaMemcpyDeviceToHost, st));

@@ -5,19 +5,24 @@
 // slice p stored as the exact BF16 value d_p 2^(-8p).  A contraction
 // sum_k A[m][k] B[n][k] becomes the triangle of slice products p + q <= s-1
 // (the products with p + q >= s are below the representation error).  Every
-// slice product is exact in FP32; the products of level p + q = 0 and 1 go to
-// two tensor-memory accumulators that stay exact because they are drained into
-// double-float registers every 512 K (|sum| < 2^24 resp. 2^16 in their units),
-// all higher levels share a third, rounded accumulator (its rounding is below
-// 2^-40 of the result).
+// slice product is exact in FP32, but the tensor core's FP32 accumulation
+// does not round to nearest when addends of very different size meet, so
+// each level L = p + q <= 3 gets its own tensor-memory accumulator, whose
+// values stay exactly representable (multiples of 2^-8L below 2^(24-8L))
+// because it is drained into double-float registers every 256 K (at most
+// 4 products of |d d'| <= 2^14 per K); the levels >= 4 share a fifth,
+// rounded accumulator (its error stays below 2^-50 of the result).
 //
 // Warp roles (576 threads): warp 0 issues TMA loads into a 3-stage ring of
 // (s A-slices, s B-slices) tiles of 128 x 16 and Ntile x 16 BF16 (32-byte
-// swizzle); one thread of warp 1 issues tcgen05.mma (M = 128, N = Ntile,
-// K = 16, FP32 accumulate) and owns the tensor-memory allocation; warps 2-17
-// drain and finish the accumulators (each quadrant of 32 TMEM lanes is read
-// by four warps, one per column quarter, 8 columns per load).  Every wait is bounded: on timeout the
-// CTA sets an error word that the host turns into CC3_ERR_TIMEOUT.
+// swizzle); one thread of warp 1 issues tcgen05.mma (M = 128, N = Ntile <= 96,
+// K = 16, FP32 accumulate) and owns the tensor-memory allocation (5 x Ntile
+// columns); warps 2-17 drain and finish the accumulators (each quadrant of 32
+// TMEM lanes is read by four warps, one per column quarter, 4 columns per
+// load).  At a drain point the issuer queues the next step's level >= 4
+// products before it waits for the drain, so the drain overlaps tensor work.
+// Every wait is bounded: on timeout the CTA sets an error word that the host
+// turns into CC3_ERR_TIMEOUT.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -38,7 +43,7 @@ __device__ __forceinline__ long long s_rowoff(int m, int m_in, long long s1, lon
   return (long long)(m / m_in) * s1 + (long long)(m % m_in) * s0;
 }
 
-__global__ void __maxnreg__(112)
+__global__ void __maxnreg__(96)
 split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__restrict__ terms,
                     const __grid_constant__ SMapTable maps, VPtrTable P, int s,
                     int kdrain_steps, int *status) {
@@ -136,8 +141,9 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
         kbase += terms[J.term0 + t].ksteps;
         ++t;
       }
-      bool init0 = false, init1 = false, initR = false;
+      bool init[S_NACC] = {false, false, false, false, false};
       int since = 0, nd = 0;
+      bool pending = false;
       for (int g = g0, it = 0; g < g1; ++g, ++it) {
         while (g - kbase >= terms[J.term0 + t].ksteps) {
           kbase += terms[J.term0 + t].ksteps;
@@ -149,25 +155,33 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
         tc_fence_after();
         const uint32_t sa = smem_u32(smem + (size_t)st * stage_bytes);
         const uint32_t sb = sa + (uint32_t)s * a_bytes;
-        for (int p = 0; p < s; ++p) {
-          const uint64_t ad = smem_desc_sw32(sa + p * a_bytes);
-          for (int q = 0; q + p < s; ++q) {
-            const uint64_t bd = smem_desc_sw32(sb + q * b_bytes);
-            const int lv = p + q;
-            const uint32_t col = lv == 0 ? 0u : (lv == 1 ? (uint32_t)Nt : 2u * Nt);
-            const bool ini = lv == 0 ? init0 : (lv == 1 ? init1 : initR);
-            umma_f16(tmem + col, ad, bd, idesc, ini ? 1u : 0u);
-            if (lv == 0) init0 = true; else if (lv == 1) init1 = true; else initR = true;
+        // levels >= 4 first (they never wait for a drain), then levels 0..3
+        for (int pass = 0; pass < 2; ++pass) {
+          if (pass == 1 && pending) {
+            if (!mbar_wait(&drainempty, nd & 1, &err)) break;
+            tc_fence_after();
+            ++nd;
+            pending = false;
+            init[0] = init[1] = init[2] = init[3] = false;
+          }
+          for (int p = 0; p < s; ++p) {
+            const uint64_t ad = smem_desc_sw32(sa + p * a_bytes);
+            for (int q = 0; q + p < s; ++q) {
+              const int lv = p + q;
+              if ((pass == 0) != (lv >= 4)) continue;
+              const int acc = lv < 4 ? lv : 4;
+              const uint64_t bd = smem_desc_sw32(sb + q * b_bytes);
+              umma_f16(tmem + (uint32_t)(acc * Nt), ad, bd, idesc, init[acc] ? 1u : 0u);
+              init[acc] = true;
+            }
           }
         }
+        if (err) break;
         umma_commit(&empty[st]);
         if (++since == kdrain_steps && g + 1 < g1) {
           umma_commit(&drainfull);
-          if (!mbar_wait(&drainempty, nd & 1, &err)) break;
-          tc_fence_after();
-          ++nd;
+          pending = true;
           since = 0;
-          init0 = init1 = false;
         }
       }
       umma_commit(&accfull);
@@ -177,28 +191,33 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
     const int ew = warp - 2, quad = warp & 3, part = ew >> 2;
     const int row = quad * 32 + lane;
     const int m = m0 + row;
-    const int qc = Nt >> 2;        // columns per quarter (multiple of 8, <= 40)
-    const int nch = qc >> 3;       // 8-column chunks (<= 5)
+    const int qc = Nt >> 2;        // columns per quarter (multiple of 4, <= 24)
+    const int nch = qc >> 2;       // 4-column chunks (<= 6)
     const uint32_t tb = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(part * qc);
-    dd::df acc[5][8];
+    dd::df acc[6][4];
 #pragma unroll
-    for (int c = 0; c < 5; ++c)
+    for (int c = 0; c < 6; ++c)
 #pragma unroll
-      for (int i = 0; i < 8; ++i) acc[c][i] = {0.f, 0.f};
+      for (int i = 0; i < 4; ++i) acc[c][i] = {0.f, 0.f};
     bool ok = true;
     for (int d = 0; d < ndrains && ok; ++d) {
       ok = mbar_wait(&drainfull, d & 1, &err);
       if (!ok) break;
       tc_fence_after();
 #pragma unroll
-      for (int c = 0; c < 5; ++c) {
+      for (int c = 0; c < 6; ++c) {
         if (c < nch) {
-          float v0[8], v1[8];
-          tmem_ld8(tb + c * 8, v0);
-          tmem_ld8(tb + Nt + c * 8, v1);
+          float v[4][4];
+#pragma unroll
+          for (int L = 0; L < 4; ++L) tmem_ld4(tb + L * Nt + c * 4, v[L]);
           tmem_wait_ld();
 #pragma unroll
-          for (int i = 0; i < 8; ++i) acc[c][i] = dd::add(acc[c][i], dd::two_sum(v0[i], v1[i]));
+          for (int i = 0; i < 4; ++i) {
+            dd::df x = dd::two_sum(v[0][i], v[1][i]);
+            x = dd::add_f(x, v[2][i]);
+            x = dd::add_f(x, v[3][i]);
+            acc[c][i] = dd::add(acc[c][i], x);
+          }
         }
       }
       tc_fence_before();
@@ -212,24 +231,28 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
       const float sc = ldexpf(J.mult, ex);
       const int nvv = J.nv;
 #pragma unroll
-      for (int c = 0; c < 5; ++c) {
+      for (int c = 0; c < 6; ++c) {
         if (c < nch) {
-          float v0[8], v1[8], vr[8];
+          float v[5][4];
           if (nsteps > 0) {
-            tmem_ld8(tb + c * 8, v0);
-            tmem_ld8(tb + Nt + c * 8, v1);
-            tmem_ld8(tb + 2 * Nt + c * 8, vr);
+#pragma unroll
+            for (int L = 0; L < 5; ++L) tmem_ld4(tb + L * Nt + c * 4, v[L]);
             tmem_wait_ld();
           } else {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) v0[i] = v1[i] = vr[i] = 0.f;
+            for (int L = 0; L < 5; ++L)
+#pragma unroll
+              for (int i = 0; i < 4; ++i) v[L][i] = 0.f;
           }
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            dd::df x = dd::add(acc[c][i], dd::two_sum(v0[i], v1[i]));
-            x = dd::add_f(x, vr[i]);
+          for (int i = 0; i < 4; ++i) {
+            dd::df x = dd::two_sum(v[0][i], v[1][i]);
+            x = dd::add_f(x, v[2][i]);
+            x = dd::add_f(x, v[3][i]);
+            x = dd::add(acc[c][i], x);
+            x = dd::add_f(x, v[4][i]);
             x = dd::scale(x, sc);
-            const int n = n0 + part * qc + c * 8 + i;
+            const int n = n0 + part * qc + c * 4 + i;
             if (m >= J.M || n >= J.N) continue;
             const OutD &C = n < J.Nm ? J.C : J.Ct;
             const int nc = n < J.Nm ? n : n - J.Nm;
@@ -273,6 +296,8 @@ int s_upload_plan(const SPlan &p, SDevPlan *d, cudaStream_t s) {
   s_free_plan(d);
   d->njobs = (int)p.jobs.size();
   d->tiles = p.tiles;
+  d->flop = p.flop;
+  d->slice_flop = p.slice_flop;
   if (d->njobs == 0) return CC3_OK;
   if (cudaMalloc(&d->jobs, sizeof(SJob) * p.jobs.size()) != cudaSuccess) return CC3_ERR_OOM;
   if (cudaMalloc(&d->terms, sizeof(STerm) * (p.terms.size() + 1)) != cudaSuccess)
@@ -307,15 +332,22 @@ int s_launch_plan(const SDevPlan &d, const SMapTable &maps, const VPtrTable &ptr
   const size_t smem = std::max<size_t>(s_smem_bytes(slices, S_NT_MAX), 120 * 1024);
   static bool attr_set = false;
   if (!attr_set) {
-    if (cudaFuncSetAttribute(split_engine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)s_smem_bytes(S_MAX_SLICES, S_NT_MAX)) != cudaSuccess)
-      return CC3_ERR_CUDA;
+    cudaError_t e = cudaFuncSetAttribute(split_engine_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)s_smem_bytes(S_MAX_SLICES, S_NT_MAX));
+    if (e != cudaSuccess) return CC3_FAIL(CC3_ERR_CUDA, cudaGetErrorString(e));
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, split_engine_kernel, S_THREADS,
+                                                      s_smem_bytes(S_MAX_SLICES, S_NT_MAX));
+    if (e != cudaSuccess || nb < 1)
+      return CC3_FAIL(CC3_ERR_CUDA, "split engine kernel does not fit on an SM");
     attr_set = true;
   }
   split_engine_kernel<<<(unsigned)d.tiles, S_THREADS, smem, s>>>(
       d.jobs, d.njobs, d.terms, maps, ptrs, slices, kdrain_steps, status);
   if (launches) ++*launches;
-  return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_ERR_CUDA;
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? CC3_OK : CC3_FAIL(CC3_ERR_CUDA, cudaGetErrorString(e));
 }
 
 }  // namespace cc3

@@ -6,8 +6,8 @@
 
 namespace cc3 {
 
-enum { SMAX_MAPS = 28, S_BM = 128, S_BK = 16, S_STAGES = 3, S_MAX_SLICES = 8,
-       S_NT_MAX = 160, S_EPI_WARPS = 16, S_THREADS = 64 + 32 * S_EPI_WARPS };
+enum { SMAX_MAPS = 28, S_BM = 128, S_BK = 16, S_STAGES = 3, S_MAX_SLICES = 7,
+       S_NT_MAX = 96, S_NACC = 5, S_DRAIN_STEPS = 16, S_EPI_WARPS = 16, S_THREADS = 64 + 32 * S_EPI_WARPS };
 
 struct SMapTable {
   CUtensorMap m[SMAX_MAPS];
@@ -53,6 +53,7 @@ struct SPlan {
   std::vector<SJob> jobs;
   std::vector<STerm> terms;
   long long tiles = 0;
+  double flop = 0.0, slice_flop = 0.0;
 };
 
 struct SDevPlan {
@@ -60,6 +61,7 @@ struct SDevPlan {
   STerm *terms = nullptr;
   int njobs = 0;
   long long tiles = 0;
+  double flop = 0.0, slice_flop = 0.0;  // useful FP64-equivalent / slice-product FLOP
 };
 
 int s_upload_plan(const SPlan &p, SDevPlan *d, cudaStream_t s);

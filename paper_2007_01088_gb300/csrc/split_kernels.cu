@@ -152,9 +152,11 @@ __global__ void slot_exponent_kernel(const unsigned int *__restrict__ maxbits, i
 // (innermost, padded to vp):  V_L[p][slot][x][y][z].
 __global__ void slice_tt_kernel(const float2 *__restrict__ tt, __nv_bfloat16 *__restrict__ v0,
                                 __nv_bfloat16 *__restrict__ v1, __nv_bfloat16 *__restrict__ v2,
-                                int nv, int vp, int s, const int *__restrict__ ex, int nslot) {
+                                int nv, int vp, int s, const int *__restrict__ ex, int nslot,
+                                int nslot_alloc) {
   const long long per = (long long)nv * nv * vp;
   const long long n = per * nslot;
+  const long long sstride = per * nslot_alloc;  // slices are nslot_alloc slots apart
   const long long nv2 = (long long)nv * nv;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < 3 * n;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -176,7 +178,7 @@ __global__ void slice_tt_kernel(const float2 *__restrict__ tt, __nv_bfloat16 *__
       T = fixed_from_float(t.x, sh) + fixed_from_float(t.y, sh);
     }
     __nv_bfloat16 *dst = (L == 0 ? v0 : (L == 1 ? v1 : v2)) + rem;
-    store_digits(T, s, dst, n);
+    store_digits(T, s, dst, sstride);
   }
 }
 
@@ -189,11 +191,11 @@ static int grid_for(long long n) {
 int launch_slice_gather(const double *src, __nv_bfloat16 *dst, int s, int e, const Gather &g,
                         long long nrows, int Kp, cudaStream_t st) {
   slice_gather_kernel<<<grid_for(nrows * Kp), 256, 0, st>>>(src, dst, s, e, g, nrows, Kp);
-  return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_ERR_CUDA;
+  return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_FAIL(CC3_ERR_CUDA, "split element-wise kernel launch");
 }
 int launch_maxabs(const double *x, long long n, unsigned long long *out, cudaStream_t st) {
   maxabs_kernel<<<grid_for(n), 256, 0, st>>>(x, n, out);
-  return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_ERR_CUDA;
+  return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_FAIL(CC3_ERR_CUDA, "split element-wise kernel launch");
 }
 int launch_contravariant_dd(const float2 *tau, float2 *tt, int nv, int nslot,
                             unsigned int *maxbits, cudaStream_t st) {
@@ -201,17 +203,18 @@ int launch_contravariant_dd(const float2 *tau, float2 *tt, int nv, int nslot,
   int bx = (int)((nv3 + 255) / 256);
   if (bx > 2048) bx = 2048;
   contravariant_dd_kernel<<<dim3(bx, nslot), 256, 0, st>>>(tau, tt, nv, maxbits);
-  return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_ERR_CUDA;
+  return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_FAIL(CC3_ERR_CUDA, "split element-wise kernel launch");
 }
 int launch_slot_exponent(const unsigned int *maxbits, int *ex, int nslot, cudaStream_t st) {
   slot_exponent_kernel<<<(nslot + 127) / 128, 128, 0, st>>>(maxbits, ex, nslot);
-  return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_ERR_CUDA;
+  return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_FAIL(CC3_ERR_CUDA, "split element-wise kernel launch");
 }
 int launch_slice_tt(const float2 *tt, __nv_bfloat16 *v0, __nv_bfloat16 *v1, __nv_bfloat16 *v2,
-                    int nv, int vp, int s, const int *ex, int nslot, cudaStream_t st) {
+                    int nv, int vp, int s, const int *ex, int nslot, int nslot_alloc,
+                    cudaStream_t st) {
   const long long n = 3LL * nv * nv * vp * nslot;
-  slice_tt_kernel<<<grid_for(n), 256, 0, st>>>(tt, v0, v1, v2, nv, vp, s, ex, nslot);
-  return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_ERR_CUDA;
+  slice_tt_kernel<<<grid_for(n), 256, 0, st>>>(tt, v0, v1, v2, nv, vp, s, ex, nslot, nslot_alloc);
+  return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_FAIL(CC3_ERR_CUDA, "split element-wise kernel launch");
 }
 
 }  // namespace cc3

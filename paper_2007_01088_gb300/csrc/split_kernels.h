@@ -25,6 +25,7 @@ int launch_contravariant_dd(const float2 *tau, float2 *tt, int nv, int nslot,
                             unsigned int *maxbits, cudaStream_t st);
 int launch_slot_exponent(const unsigned int *maxbits, int *ex, int nslot, cudaStream_t st);
 int launch_slice_tt(const float2 *tt, __nv_bfloat16 *v0, __nv_bfloat16 *v1, __nv_bfloat16 *v2,
-                    int nv, int vp, int s, const int *ex, int nslot, cudaStream_t st);
+                    int nv, int vp, int s, const int *ex, int nslot, int nslot_alloc,
+                    cudaStream_t st);
 
 }  // namespace cc3

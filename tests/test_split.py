@@ -28,6 +28,8 @@ def test_engine_gemm_matches_fp64(g, M, N, K):
     assert np.abs(C - ref).max() <= 1e-13 * scale
     C3 = g.cc3_debug_split_gemm(A, B, 3)
     assert np.abs(C3 - ref).max() <= 1e-6 * scale
+    C7 = g.cc3_debug_split_gemm(A, B, 7)
+    assert np.abs(C7 - ref).max() <= 1e-15 * scale
 
 
 def test_engine_gemm_exact_integers(g):
