@@ -79,6 +79,45 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, u
       : "memory");
 }
 
+// Contiguous bulk copy global -> shared (16-byte aligned, size % 16 == 0),
+// completion counted on `bar` (transaction bytes).
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
+                                          uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// 5-D tiled TMA load
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int c0, int c1, int c2, int c3, int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2),
+      "r"(c3), "r"(c4)
+      : "memory");
+}
+
+// Bounded wait with back-off (nanosleep between polls) for threads that may
+// wait for a whole main loop.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t *bar, uint32_t parity, volatile int *err,
+                                                uint64_t limit_ns = 2000000000ull) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*err) return false;
+    __nanosleep(256);
+    if (globaltimer_ns() - t0 > limit_ns) {
+      *err = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
@@ -110,8 +149,7 @@ __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a_desc, uint6
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-      : "memory");
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
 }
 
 // arrive on `bar` when every previously issued tcgen05.mma of this thread completes
@@ -172,6 +210,19 @@ __device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t saddr) {
   d |= (uint64_t)1 << 46;                           // descriptor version (sm100)
   d |= (uint64_t)6 << 61;                           // SWIZZLE_32B
   return d;
+}
+
+// Shared-memory matrix descriptor, K-major operand without swizzling: core
+// matrices of 8 rows x 16 bytes (128 contiguous bytes), the two K halves of a
+// 16-element K step 128 bytes apart (leading byte offset), 8-row groups 256
+// bytes apart (stride byte offset).
+__device__ __forceinline__ uint64_t smem_desc_noswz(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);          // start address
+  d |= (uint64_t)((128 >> 4) & 0x3FFF) << 16;       // leading byte offset (K direction)
+  d |= (uint64_t)((256 >> 4) & 0x3FFF) << 32;       // stride byte offset (M/N direction)
+  d |= (uint64_t)1 << 46;                           // descriptor version (sm100)
+  return d;                                         // layout type 0: no swizzle
 }
 
 // Instruction descriptor: BF16 x BF16 -> FP32, K-major A and B, M x N.

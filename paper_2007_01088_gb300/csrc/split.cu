@@ -1,9 +1,10 @@
 // Split-precision path of the CC3 triples residual (paper, Algorithm 1) on the
-// tensor cores: staging of BF16 slice arrays, tensor maps, job plans and the
+// tensor cores: staging of BF16 slice arrays, job plans and the
 // per-batch launch sequence.
 //
-// Layouts (bf16, every array [slice][slab][row][K], K innermost, zero padded to
-// a multiple of 16; vp = nv rounded up, op = no rounded up):
+// Layouts (bf16, every array K-blocked as [slice][slab][K/16][row][16] so that
+// each 16 x R tile read by the tensor cores is one contiguous block; K zero
+// padded to a multiple of 16; vp = nv rounded up, op = no rounded up):
 //   T2S[(p,q)][x][d]  = t^{xd}_{pq}          T2C[(p,y)][x][l] = t^{xy}_{pl}
 //   T2R[(p,x)][y][l]  = t^{xy}_{pl}          OS[(q,r)][z][l]  = (lq|zr)
 //   XS[(r,z)][y][d]   = (yd|zr)              YS[(r,y)][z][d]  = (yd|zr)
@@ -11,11 +12,13 @@
 //   OO[(q,r)][l'][z]  = (ql'|rz) for l' < no, -F_rz for l' = no
 //   OV[(q,r)][0][(u,w)] = (qu|rw)
 // and per triple in flight (slot) the contravariant amplitudes in three cyclic
-// layouts V_L[slot][x][y][z] (slot L outermost, L+2 innermost).
+// layouts V_L (slot L outermost = x, L+1 = y, L+2 = z innermost) with K blocks
+// ordered (z block, y): read as rows x, K = (zb, y, zz) by the vvov and
+// singles contractions, and as rows (y, x), K = z by the ooov and F ones.
+// Zg, Zh and OV use the same (zb, u, zz) K order.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
-#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -43,40 +46,19 @@ namespace cc3 {
 
 namespace {
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    cudaDriverEntryPointQueryResult q;
-    void *p = nullptr;
-    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
+// Slice-array descriptor: [slice][slab][K/16][rows8 x 16 core-matrix block]
+SArr make_arr(const void *base, long long K, long long rps, long long slabs) {
+  SArr a;
+  a.base = reinterpret_cast<unsigned long long>(base);
+  a.kblocks = (int)(K / 16);
+  a.rows = (int)((rps + 7) / 8 * 8);
+  a.slabs = (int)slabs;
+  a.slab_stride = (long long)a.kblocks * a.rows * 16;
+  a.slice_stride = slabs * a.slab_stride;
+  return a;
 }
-
-// 4-D map over a [slices][slabs][rows][K] bf16 array, box (16, box_rows, 1, 1)
-int make_map(CUtensorMap *m, const void *base, long long K, long long rows, long long slabs,
-             int slices, int box_rows) {
-  auto fn = encode_fn();
-  if (!fn) return CC3_FAIL(CC3_ERR_CUDA, "cuTensorMapEncodeTiled entry point not found");
-  if (K % 8 != 0 || box_rows < 8 || box_rows > 256) return CC3_FAIL(CC3_ERR_ARG, "tensor map shape");
-  cuuint64_t dims[4] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)slabs, (cuuint64_t)slices};
-  cuuint64_t strides[3] = {(cuuint64_t)K * 2, (cuuint64_t)(K * rows * 2),
-                           (cuuint64_t)(K * rows * slabs * 2)};
-  cuuint32_t box[4] = {16, (cuuint32_t)box_rows, 1, 1};
-  cuuint32_t es[4] = {1, 1, 1, 1};
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(base), dims, strides,
-                  box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) {
-    static thread_local char msg[160];
-    std::snprintf(msg, sizeof(msg), "cuTensorMapEncodeTiled error %d (K %lld rows %lld slabs %lld box %d)",
-                  (int)r, K, rows, slabs, box_rows);
-    return CC3_FAIL(CC3_ERR_CUDA, msg);
-  }
-  return CC3_OK;
+size_t arr_elems(long long K, long long rps, long long slabs, int slices) {
+  return (size_t)slices * slabs * (K / 16) * ((rps + 7) / 8 * 8) * 16;
 }
 
 inline int rup(int x, int m) { return (x + m - 1) / m * m; }
@@ -96,24 +78,24 @@ int ntile_for(int N) {
 
 enum MapId {
   MA_T2S = 0, MA_T2C, MA_T2R, MA_XS, MA_YS, MA_OS, MA_V0, MA_V1, MA_V2, MA_V0K, MA_V1K, MA_V2K,
-  MB_T2S, MB_T2C, MB_T2R, MB_XS, MB_YS, MB_OS, MB_XSF, MB_YSF, MB_T2RF, MB_T2CF, MB_ZG, MB_ZH,
-  MB_OO, MB_OV, MAP_COUNT
+  MB_T2S, MB_T2C, MB_T2R, MB_XS, MB_YS, MB_OS, MB_ZG, MB_ZH, MB_OO, MB_OV, MAP_COUNT
 };
 static_assert(MAP_COUNT <= SMAX_MAPS, "map table");
 
 struct SplitState {
   int s = 0, vp = 0, op = 0, Et = 0, Eg = 0;
-  int Nab = 0, Nc = 0, N3 = 0, N1 = 16;
+  int Nab = 0, N3 = 0, N1 = 16;
   __nv_bfloat16 *T2S = nullptr, *T2C = nullptr, *T2R = nullptr, *XS = nullptr, *YS = nullptr,
                 *OS = nullptr, *Zg = nullptr, *Zh = nullptr, *OO = nullptr, *OV = nullptr;
   float2 *evdd = nullptr;
   int batch = 0;
   float2 *Wdd = nullptr, *TTdd = nullptr;
   __nv_bfloat16 *V[3] = {nullptr, nullptr, nullptr};
+  __nv_bfloat16 **vptr = nullptr;  // device copy of {V[0..2]}
   unsigned int *maxbits = nullptr;
   int *slot_ex = nullptr;
   int *status = nullptr;
-  SMapTable maps;
+  SArrTable arrs;
   std::vector<SDevPlan> ab, cc, om;
   std::vector<int> nslot;
   double executed = 0.0;
@@ -134,8 +116,8 @@ int alloc(T **p, size_t n) {
 
 void free_state_buffers(SplitState *S) {
   void *bufs[] = {S->T2S, S->T2C, S->T2R, S->XS, S->YS, S->OS, S->Zg, S->Zh, S->OO, S->OV,
-                  S->evdd, S->Wdd, S->TTdd, S->V[0], S->V[1], S->V[2], S->maxbits, S->slot_ex,
-                  S->status};
+                  S->evdd, S->Wdd, S->TTdd, S->V[0], S->V[1], S->V[2], S->vptr, S->maxbits,
+                  S->slot_ex, S->status};
   for (void *p : bufs)
     if (p) cudaFree(p);
   for (auto *v : {&S->ab, &S->cc, &S->om})
@@ -181,34 +163,36 @@ int stage(cc3_ctx *c, SplitState *S, cudaStream_t st) {
   S->Eg = exponent_of(std::max(std::max(hv[1], hv[2]), std::max(hv[3], hv[4])));
 
   auto slab = [&](__nv_bfloat16 **dst, const double *src, long long rows, int Kp, int E,
-                  const Gather &g) -> int {
-    TRY(alloc(dst, (size_t)s * rows * Kp));
-    return launch_slice_gather(src, *dst, s, E, g, rows, Kp, st);
+                  const Gather &g, int rps) -> int {
+    const size_t n = arr_elems(Kp, rps, rows / rps, s);
+    TRY(alloc(dst, n));
+    CU(cudaMemsetAsync(*dst, 0, n * sizeof(__nv_bfloat16), st));
+    return launch_slice_gather(src, *dst, s, E, g, rows, Kp, rps, st);
   };
   Gather g;
   // T2S[(p,q)][x][d] = t2[p][q][x][d]
   g = {0, (long long)no * nv2, nv2, nv, 0, 1, no, nv, vp, nv, 1};
-  TRY(slab(&S->T2S, c->t2, (long long)no * no * nv, vp, S->Et, g));
+  TRY(slab(&S->T2S, c->t2, (long long)no * no * nv, vp, S->Et, g, nv));
   // T2C[(p,y)][x][l] = t2[p][l][x][y]
   g = {0, (long long)no * nv2, 1, nv, 0, nv2, nv, nv, op, no, 1};
-  TRY(slab(&S->T2C, c->t2, (long long)no * nv * nv, op, S->Et, g));
+  TRY(slab(&S->T2C, c->t2, (long long)no * nv * nv, op, S->Et, g, nv));
   // T2R[(p,x)][y][l] = t2[p][l][x][y]
   g = {0, (long long)no * nv2, nv, 1, 0, nv2, nv, nv, op, no, 1};
-  TRY(slab(&S->T2R, c->t2, (long long)no * nv * nv, op, S->Et, g));
+  TRY(slab(&S->T2R, c->t2, (long long)no * nv * nv, op, S->Et, g, nv));
   // XS[(r,z)][y][d] = vvvo[y][d][z][r]
   g = {0, 1, no, nv2 * no, 0, (long long)nv * no, nv, nv, vp, nv, 1};
-  TRY(slab(&S->XS, c->vvvo, (long long)no * nv * nv, vp, S->Eg, g));
+  TRY(slab(&S->XS, c->vvvo, (long long)no * nv * nv, vp, S->Eg, g, nv));
   // YS[(r,y)][z][d] = vvvo[y][d][z][r]
   g = {0, 1, nv2 * no, no, 0, (long long)nv * no, nv, nv, vp, nv, 1};
-  TRY(slab(&S->YS, c->vvvo, (long long)no * nv * nv, vp, S->Eg, g));
+  TRY(slab(&S->YS, c->vvvo, (long long)no * nv * nv, vp, S->Eg, g, nv));
   // OS[(q,r)][z][l] = oovo[l][q][z][r]
   g = {0, (long long)nv * no, 1, no, 0, (long long)no * nv * no, no, nv, op, no, 1};
-  TRY(slab(&S->OS, c->oovo, (long long)no * no * nv, op, S->Eg, g));
+  TRY(slab(&S->OS, c->oovo, (long long)no * no * nv, op, S->Eg, g, nv));
   // Zg[r][d][(u,w)] = vvvo[u][d][w][r];  Zh[r][d][(u,w)] = vvvo[w][d][u][r]
-  g = {0, 0, 1, (long long)nv * no, nv2 * no, no, no, nv, vp, nv, nv};
-  TRY(slab(&S->Zg, c->vvvo, (long long)no * nv, nv * vp, S->Eg, g));
-  g = {0, 0, 1, (long long)nv * no, no, nv2 * no, no, nv, vp, nv, nv};
-  TRY(slab(&S->Zh, c->vvvo, (long long)no * nv, nv * vp, S->Eg, g));
+  g = {0, 0, 1, (long long)nv * no, nv2 * no, no, no, nv, nv, nv, nv, 1};
+  TRY(slab(&S->Zg, c->vvvo, (long long)no * nv, nv * vp, S->Eg, g, nv));
+  g = {0, 0, 1, (long long)nv * no, no, nv2 * no, no, nv, nv, nv, nv, 1};
+  TRY(slab(&S->Zh, c->vvvo, (long long)no * nv, nv * vp, S->Eg, g, nv));
   // OO[(q,r)][l'][z]
   {
     double *oo = nullptr;
@@ -219,13 +203,13 @@ int stage(cc3_ctx *c, SplitState *S, cudaStream_t st) {
     CU(cudaGetLastError());
     // rows ((q,r), l') flattened and contiguous: r0 = row, stride nv
     g = {0, 0, 0, nv, 0, 1, 1, 1 << 30, vp, nv, 1};
-    TRY(slab(&S->OO, oo, (long long)no * no * (no + 1), vp, S->Eg, g));
+    TRY(slab(&S->OO, oo, (long long)no * no * (no + 1), vp, S->Eg, g, no + 1));
     CU(cudaStreamSynchronize(st));
     cudaFree(oo);
   }
   // OV[(q,r)][0][(u,w)] = ovov[q][u][r][w]
-  g = {0, 0, (long long)nv * no * nv, nv, (long long)no * nv, 1, no, no, vp, nv, nv};
-  TRY(slab(&S->OV, c->ovov, (long long)no * no, nv * vp, S->Eg, g));
+  g = {0, 0, (long long)nv * no * nv, nv, (long long)no * nv, 1, no, no, nv, nv, nv, 1};
+  TRY(slab(&S->OV, c->ovov, (long long)no * no, nv * vp, S->Eg, g, 1));
   // dd orbital energies
   {
     std::vector<double> ev(nv);
@@ -246,46 +230,43 @@ int stage(cc3_ctx *c, SplitState *S, cudaStream_t st) {
   const size_t nb = (size_t)S->batch;
   TRY(alloc(&S->Wdd, nb * nv2 * nv));
   TRY(alloc(&S->TTdd, nb * nv2 * nv));
-  for (int L = 0; L < 3; ++L) TRY(alloc(&S->V[L], (size_t)s * nb * nv2 * vp));
+  for (int L = 0; L < 3; ++L) {
+    const size_t n4 = arr_elems((long long)nv * vp, nv, (long long)nb, s);
+    TRY(alloc(&S->V[L], n4));
+    CU(cudaMemsetAsync(S->V[L], 0, n4 * sizeof(__nv_bfloat16), st));
+  }
+  {
+    __nv_bfloat16 *h[3] = {S->V[0], S->V[1], S->V[2]};
+    TRY(alloc(&S->vptr, 3));
+    CU(cudaMemcpyAsync(S->vptr, h, sizeof(h), cudaMemcpyHostToDevice, st));
+  }
   TRY(alloc(&S->maxbits, nb));
   TRY(alloc(&S->slot_ex, nb));
   TRY(alloc(&S->status, 4));
   CU(cudaMemsetAsync(S->status, 0, 4 * sizeof(int), st));
 
-  // tensor maps
+  // slice-array table (the same descriptor serves an array as A or B operand)
   S->Nab = ntile_for(nv);
-  S->Nc = std::min<int>(S_NT_MAX, rup(std::min<int>(nv * nv, S_NT_MAX), 16));
   S->N3 = rup(no + 1, 16);
   if (S->N3 > S_NT_MAX) return CC3_ERR_UNSUPPORTED;
-  CUtensorMap *M = S->maps.m;
-  std::memset(&S->maps, 0, sizeof(S->maps));
+  SArr *M = S->arrs.a;
+  std::memset(&S->arrs, 0, sizeof(S->arrs));
   const long long n_o = no, n_v = nv;
-  TRY(make_map(&M[MA_T2S], S->T2S, vp, n_v, n_o * n_o, s, 128));
-  TRY(make_map(&M[MA_T2C], S->T2C, op, n_v, n_o * n_v, s, 128));
-  TRY(make_map(&M[MA_T2R], S->T2R, op, n_v, n_o * n_v, s, 128));
-  TRY(make_map(&M[MA_XS], S->XS, vp, n_v, n_o * n_v, s, 128));
-  TRY(make_map(&M[MA_YS], S->YS, vp, n_v, n_o * n_v, s, 128));
-  TRY(make_map(&M[MA_OS], S->OS, op, n_v, n_o * n_o, s, 128));
+  M[MA_T2S] = M[MB_T2S] = make_arr(S->T2S, vp, n_v, n_o * n_o);
+  M[MA_T2C] = M[MB_T2C] = make_arr(S->T2C, op, n_v, n_o * n_v);
+  M[MA_T2R] = M[MB_T2R] = make_arr(S->T2R, op, n_v, n_o * n_v);
+  M[MA_XS] = M[MB_XS] = make_arr(S->XS, vp, n_v, n_o * n_v);
+  M[MA_YS] = M[MB_YS] = make_arr(S->YS, vp, n_v, n_o * n_v);
+  M[MA_OS] = M[MB_OS] = make_arr(S->OS, op, n_v, n_o * n_o);
+  const long long nv8 = (n_v + 7) / 8 * 8;
   for (int L = 0; L < 3; ++L) {
-    // residual (vvov / singles) view: rows x, K = (y, z)
-    TRY(make_map(&M[MA_V0 + L], S->V[L], n_v * vp, n_v, (long long)nb, s, 128));
-    // ooov view: rows (x, y), K = z
-    TRY(make_map(&M[MA_V0K + L], S->V[L], vp, n_v * n_v, (long long)nb, s, 128));
+    M[MA_V0 + L] = make_arr(S->V[L], n_v * vp, n_v, (long long)nb);        // rows x, K = (zb, y, zz)
+    M[MA_V0K + L] = make_arr(S->V[L], vp, n_v * nv8, (long long)nb);       // rows (y, x), K = z
   }
-  TRY(make_map(&M[MB_T2S], S->T2S, vp, n_v, n_o * n_o, s, S->Nab));
-  TRY(make_map(&M[MB_T2C], S->T2C, op, n_v, n_o * n_v, s, S->Nab));
-  TRY(make_map(&M[MB_T2R], S->T2R, op, n_v, n_o * n_v, s, S->Nab));
-  TRY(make_map(&M[MB_XS], S->XS, vp, n_v, n_o * n_v, s, S->Nab));
-  TRY(make_map(&M[MB_YS], S->YS, vp, n_v, n_o * n_v, s, S->Nab));
-  TRY(make_map(&M[MB_OS], S->OS, op, n_v, n_o * n_o, s, S->Nab));
-  TRY(make_map(&M[MB_XSF], S->XS, vp, n_v * n_v, n_o, s, S->Nc));
-  TRY(make_map(&M[MB_YSF], S->YS, vp, n_v * n_v, n_o, s, S->Nc));
-  TRY(make_map(&M[MB_T2RF], S->T2R, op, n_v * n_v, n_o, s, S->Nc));
-  TRY(make_map(&M[MB_T2CF], S->T2C, op, n_v * n_v, n_o, s, S->Nc));
-  TRY(make_map(&M[MB_ZG], S->Zg, n_v * vp, n_v, n_o, s, S->Nab));
-  TRY(make_map(&M[MB_ZH], S->Zh, n_v * vp, n_v, n_o, s, S->Nab));
-  TRY(make_map(&M[MB_OO], S->OO, vp, n_o + 1, n_o * n_o, s, S->N3));
-  TRY(make_map(&M[MB_OV], S->OV, n_v * vp, 1, n_o * n_o, s, S->N1));
+  M[MB_ZG] = make_arr(S->Zg, n_v * vp, n_v, n_o);
+  M[MB_ZH] = make_arr(S->Zh, n_v * vp, n_v, n_o);
+  M[MB_OO] = make_arr(S->OO, vp, n_o + 1, n_o * n_o);
+  M[MB_OV] = make_arr(S->OV, n_v * vp, 1, n_o * n_o);
   CU(cudaStreamSynchronize(st));
   S->staged = true;
   return CC3_OK;
@@ -376,11 +357,9 @@ void plan_w_split(SPlan &pab, SPlan &pc, SplitState *S, int no, int nv, const in
   add_sterm(pab, jb, opd(MA_OS, j * no + i), opd(MB_T2R, k * nv, 1), op, 1, ex, s);
   add_sterm(pab, jb, opd(MA_T2R, k * nv, 1), opd(MB_OS, i * no + j), op, 1, ex, s);
   add_sterm(pab, jb, opd(MA_T2C, i * nv, 1), opd(MB_OS, k * no + j), op, 1, ex, s);
-  // phase C: tile (c, (a,b)), epilogue tau = W / (w - eps)
-  int jc = new_sjob(pc, nv, (int)nv2, S->Nc, 1, 1, SEPI_DD_TAU, E, ex, s);
-  OutD C = outd(B_WS_W, slot * nv3, nv2, 1);
-  C.n_in = nv;
-  C.sn1 = nv;
+  // phase C: tile (c, b) at fixed a (batch index), epilogue tau = W / (w - eps)
+  int jc = new_sjob(pc, nv, nv, S->Nab, nv, 1, SEPI_DD_TAU, E, ex, s);
+  OutD C = outd(B_WS_W, slot * nv3, nv2, 1, nv);  // W[c][a][b]: m = c, n = b, batch a
   pc.jobs[jc].C = C;
   pc.jobs[jc].Ct = C;
   pc.jobs[jc].W = C;
@@ -389,10 +368,14 @@ void plan_w_split(SPlan &pab, SPlan &pc, SplitState *S, int no, int nv, const in
   pc.jobs[jc].eo_lo = eo_dd[1];
   pc.jobs[jc].w_hi = 0.f;
   pc.jobs[jc].w_lo = 0.f;
-  add_sterm(pc, jc, opd(MA_T2S, k * no + i), opd(MB_YSF, j), vp, 0, ex, s);
-  add_sterm(pc, jc, opd(MA_T2S, k * no + j), opd(MB_XSF, i), vp, 0, ex, s);
-  add_sterm(pc, jc, opd(MA_OS, j * no + k), opd(MB_T2RF, i), op, 1, ex, s);
-  add_sterm(pc, jc, opd(MA_OS, i * no + k), opd(MB_T2CF, j), op, 1, ex, s);
+  // (k,i,j): sum_d t_ki[c][d] (ad|bj) -> YS slab (j, a) rows b
+  add_sterm(pc, jc, opd(MA_T2S, k * no + i), opd(MB_YS, j * nv, 1), vp, 0, ex, s);
+  // (k,j,i): sum_d t_kj[c][d] (bd|ai) -> XS slab (i, a) rows b
+  add_sterm(pc, jc, opd(MA_T2S, k * no + j), opd(MB_XS, i * nv, 1), vp, 0, ex, s);
+  // (i,j,k) occupied: - sum_l (lj|ck) t^{ab}_{il} -> T2R slab (i, a) rows b
+  add_sterm(pc, jc, opd(MA_OS, j * no + k), opd(MB_T2R, i * nv, 1), op, 1, ex, s);
+  // (j,i,k) occupied: - sum_l (li|ck) t^{ba}_{jl} -> T2C slab (j, a) rows b
+  add_sterm(pc, jc, opd(MA_OS, i * no + k), opd(MB_T2C, j * nv, 1), op, 1, ex, s);
 }
 
 // residual contractions of one triple (every distinct permutation)
@@ -435,18 +418,24 @@ void plan_omega_split(SPlan &P, SplitState *S, int no, int nv, const int ijk[3],
                 0, ex, s);
     }
     {  // Omega~^{xy}_{pl} -= sum_z V (ql|rz);  Omega~^{xy}_{pq} += sum_z V F_rz
-      const int Lz = (m[2] + 1) % 3;  // layout whose innermost slot is z
-      const bool xfirst = (m[0] == Lz);
-      int jb = new_sjob(P, (int)nv2, no + 1, S->N3, 1, 1, SEPI_F64_ATOMIC, E, ex, s);
+      // layout Lz has z innermost; its rows (y_L, x_L) are the perm's (y, x) when
+      // the perm's x slot is Lz, else (x, y); row m = y_L * nv8 + x_L
+      const int Lz = (m[2] + 1) % 3;
+      const bool xouter = (m[0] == Lz);
+      const int nv8 = (nv + 7) / 8 * 8;
+      int jb = new_sjob(P, nv * nv8, no + 1, S->N3, 1, 1, SEPI_F64_ATOMIC, E, ex, s);
       P.jobs[jb].expo_slot = slot;
       P.jobs[jb].Nm = no;
-      OutD c = outd(B_OMT, (long long)p * no * nv2, xfirst ? 1 : nv, nv2);
-      c.m_in = nv;
-      c.sm1 = xfirst ? nv : 1;
+      P.jobs[jb].m_pad = nv8;
+      P.jobs[jb].m_valid = nv;
+      // m / nv8 = y_L, m % nv8 = x_L;  Omega~[p][l][x][y] at x*nv + y
+      OutD c = outd(B_OMT, (long long)p * no * nv2, xouter ? nv : 1, nv2);
+      c.m_in = nv8;
+      c.sm1 = xouter ? 1 : nv;
       P.jobs[jb].C = c;
-      OutD ct = outd(B_OMT, ((long long)p * no + q) * nv2, xfirst ? 1 : nv, 0);
-      ct.m_in = nv;
-      ct.sm1 = xfirst ? nv : 1;
+      OutD ct = outd(B_OMT, ((long long)p * no + q) * nv2, xouter ? nv : 1, 0);
+      ct.m_in = nv8;
+      ct.sm1 = xouter ? 1 : nv;
       P.jobs[jb].Ct = ct;
       add_sterm(P, jb, opd(MA_V0K + Lz, slot), opd(MB_OO, q * no + r), vp, 1, ex, s);
     }
@@ -529,19 +518,18 @@ int split_omega(cc3_ctx *c, cudaStream_t st) {
     const int ns = S->nslot[b];
     for (const SDevPlan *d : {&S->ab[b], &S->cc[b]}) {
       trace_begin(c, TR_SPLIT_W, st);
-      TRY(s_launch_plan(*d, S->maps, P, s, kdrain, S->status, st, &c->counters.launches));
+      TRY(s_launch_plan(*d, S->arrs, P, s, kdrain, S->status, st, &c->counters.launches));
       trace_end(c, TR_SPLIT_W, st, d->flop, d->slice_flop);
     }
     trace_begin(c, TR_SPLIT_ELEM, st);
     CU(cudaMemsetAsync(S->maxbits, 0, sizeof(unsigned int) * ns, st));
     TRY(launch_contravariant_dd(S->Wdd, S->TTdd, nv, ns, S->maxbits, st));
     TRY(launch_slot_exponent(S->maxbits, S->slot_ex, ns, st));
-    TRY(launch_slice_tt(S->TTdd, S->V[0], S->V[1], S->V[2], nv, S->vp, s, S->slot_ex, ns,
-                        S->batch, st));
+    TRY(launch_slice_tt(S->TTdd, S->vptr, nv, S->vp, s, S->slot_ex, ns, S->batch, st));
     trace_end(c, TR_SPLIT_ELEM, st, 0.0, 0.0);
     c->counters.launches += 3;
     trace_begin(c, TR_SPLIT_OMEGA, st);
-    TRY(s_launch_plan(S->om[b], S->maps, P, s, kdrain, S->status, st, &c->counters.launches));
+    TRY(s_launch_plan(S->om[b], S->arrs, P, s, kdrain, S->status, st, &c->counters.launches));
     trace_end(c, TR_SPLIT_OMEGA, st, S->om[b].flop, S->om[b].slice_flop);
   }
   int hs = 0;
@@ -549,7 +537,8 @@ int split_omega(cc3_ctx *c, cudaStream_t st) {
   CU(cudaStreamSynchronize(st));
   if (hs != 0) {
     cudaMemsetAsync(S->status, 0, sizeof(int), st);
-    return CC3_ERR_TIMEOUT;
+    return hs == 2 ? CC3_FAIL(CC3_ERR_ARG, "a contraction plan addressed outside a slice array")
+                   : CC3_FAIL(CC3_ERR_TIMEOUT, "split engine wait gave up");
   }
   c->counters.executed_flop = S->executed;
   c->counters.slices = s;
@@ -586,13 +575,13 @@ int debug_split_gemm(int M, int N, int K, const double *A, const double *B, doub
   int rc = CC3_OK;
   SPlan P;
   SDevPlan D;
-  SMapTable maps;
+  SArrTable arrs;
   VPtrTable ptr;
   double ex = 0.0;
   unsigned long long h[2];
   double ma, mb;
   Gather gA, gB;
-  std::memset(&maps, 0, sizeof(maps));
+  std::memset(&arrs, 0, sizeof(arrs));
   std::memset(&ptr, 0, sizeof(ptr));
 #define CK(x)                    \
   do {                           \
@@ -605,8 +594,10 @@ int debug_split_gemm(int M, int N, int K, const double *A, const double *B, doub
   CK(alloc(&dA, (size_t)M * K));
   CK(alloc(&dB, (size_t)N * K));
   CK(alloc(&dC, (size_t)M * N));
-  CK(alloc(&sA, (size_t)s * M * Kp));
-  CK(alloc(&sB, (size_t)s * N * Kp));
+  CK(alloc(&sA, arr_elems(Kp, M, 1, s)));
+  CK(alloc(&sB, arr_elems(Kp, N, 1, s)));
+  CKC(cudaMemsetAsync(sA, 0, arr_elems(Kp, M, 1, s) * 2, st));
+  CKC(cudaMemsetAsync(sB, 0, arr_elems(Kp, N, 1, s) * 2, st));
   CK(alloc(&mx, 2));
   CK(alloc(&status, 1));
   CKC(cudaMemcpyAsync(dA, A, sizeof(double) * M * K, cudaMemcpyHostToDevice, st));
@@ -626,17 +617,17 @@ int debug_split_gemm(int M, int N, int K, const double *A, const double *B, doub
     gA.n1 = 1;
     gA.n0 = 1 << 30;
     gB = gA;
-    CK(launch_slice_gather(dA, sA, s, eA, gA, M, Kp, st));
-    CK(launch_slice_gather(dB, sB, s, eB, gB, N, Kp, st));
-    CK(make_map(&maps.m[0], sA, Kp, M, 1, s, 128));
-    CK(make_map(&maps.m[1], sB, Kp, N, 1, s, Nt));
+    CK(launch_slice_gather(dA, sA, s, eA, gA, M, Kp, M, st));
+    CK(launch_slice_gather(dB, sB, s, eB, gB, N, Kp, N, st));
+    arrs.a[0] = make_arr(sA, Kp, M, 1);
+    arrs.a[1] = make_arr(sB, Kp, N, 1);
     int jb = new_sjob(P, M, N, Nt, 1, 1, SEPI_F64_ATOMIC, eA + eB - 14, ex, s);
     P.jobs[jb].C = outd(0, 0, N, 1);
     P.jobs[jb].Ct = P.jobs[jb].C;
     add_sterm(P, jb, opd(0, 0), opd(1, 0), Kp, 0, ex, s);
     CK(s_upload_plan(P, &D, st));
     ptr.p[0] = dC;
-    CK(s_launch_plan(D, maps, ptr, s, S_DRAIN_STEPS, status, st, nullptr));
+    CK(s_launch_plan(D, arrs, ptr, s, S_DRAIN_STEPS, status, st, nullptr));
     int hs = 0;
     CKC(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
     CKC(cudaMemcpyAsync(C, dC, sizeof(double) * M * N, cudaMemcpyDeviceToHost, st));

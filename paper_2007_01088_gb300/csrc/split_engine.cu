@@ -13,9 +13,9 @@
 // 4 products of |d d'| <= 2^14 per K); the levels >= 4 share a fifth,
 // rounded accumulator (its error stays below 2^-50 of the result).
 //
-// Warp roles (576 threads): warp 0 issues TMA loads into a 3-stage ring of
-// (s A-slices, s B-slices) tiles of 128 x 16 and Ntile x 16 BF16 (32-byte
-// swizzle); one thread of warp 1 issues tcgen05.mma (M = 128, N = Ntile <= 96,
+// Warp roles (576 threads): warp 0 issues one bulk copy per slice tile into a
+// 3-stage ring of (s A-slices, s B-slices) tiles of 128 x 16 and Ntile x 16
+// BF16 (pre-tiled in global memory in the canonical no-swizzle order); one thread of warp 1 issues tcgen05.mma (M = 128, N = Ntile <= 96,
 // K = 16, FP32 accumulate) and owns the tensor-memory allocation (5 x Ntile
 // columns); warps 2-17 drain and finish the accumulators (each quadrant of 32
 // TMEM lanes is read by four warps, one per column quarter, 4 columns per
@@ -28,6 +28,8 @@
 
 #include <algorithm>
 
+#include <cuda_bf16.h>
+
 #include "dd.cuh"
 #include "sm100_prims.cuh"
 #include "split_engine.h"
@@ -36,17 +38,45 @@ namespace cc3 {
 using namespace sm100;
 
 size_t s_smem_bytes(int slices, int ntile) {
-  return (size_t)S_STAGES * slices * (S_BM + ntile) * 32 + 1024;
+  return (size_t)s_stages(slices) * slices * (S_BM + ntile) * 32 + 1024;
 }
 
 __device__ __forceinline__ long long s_rowoff(int m, int m_in, long long s1, long long s0) {
   return (long long)(m / m_in) * s1 + (long long)(m % m_in) * s0;
 }
 
+// Issues the slice products of one K step whose level is >= 4 (HIGH) or
+// <= 3 (!HIGH), fully unrolled; bit L of `fresh` marks accumulator L as not
+// yet written since its last reset (its first product overwrites it).
+template <int S, bool HIGH>
+__device__ __forceinline__ void issue_products(uint32_t tmem, uint64_t dA, uint64_t dB,
+                                               uint32_t a16, uint32_t b16, uint32_t Nt,
+                                               uint32_t idesc, uint32_t &fresh) {
+#pragma unroll
+  for (int p = 0; p < S; ++p) {
+#pragma unroll
+    for (int q = 0; q < S - p; ++q) {
+      const int lv = p + q;
+      if (HIGH != (lv >= 4)) continue;
+      const int acc = lv < 4 ? lv : 4;
+      umma_f16(tmem + (uint32_t)acc * Nt, dA + (uint64_t)(p * a16), dB + (uint64_t)(q * b16),
+               idesc, ((fresh >> acc) & 1u) ^ 1u);
+      fresh &= ~(1u << acc);
+    }
+  }
+}
+
+template <int S>
 __global__ void __maxnreg__(96)
 split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__restrict__ terms,
-                    const __grid_constant__ SMapTable maps, VPtrTable P, int s,
+                    const __grid_constant__ SArrTable arrs, VPtrTable P,
                     int kdrain_steps, int *status) {
+  constexpr int s = S;
+  constexpr int S_STAGES = s_stages(S);
+  // accumulators that receive products: level L <= 3 exists iff L <= S-1,
+  // the shared one (levels >= 4) iff S >= 5
+  constexpr int NLOW = S < 4 ? S : 4;
+  constexpr bool HAS_HIGH = S >= 5;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -114,18 +144,33 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
           ++t;
         }
         const STerm &T = terms[J.term0 + t];
-        const int kk = (g - kbase) * S_BK;
+        const int kb = g - kbase;
         const int st = issued % S_STAGES, ph = (issued / S_STAGES) & 1;
         if (!mbar_wait(&empty[st], ph ^ 1, &err)) break;
-        mbar_arrive_expect_tx(&full[st], stage_bytes);
-        uint8_t *sa = smem + (size_t)st * stage_bytes;
-        uint8_t *sb = sa + (size_t)s * a_bytes;
+        const SArr &XA = arrs.a[T.A.map], &XB = arrs.a[T.B.map];
         const int ar = T.A.row0 + bi * T.A.row_b + m0, as = T.A.slab0 + bi * T.A.slab_b;
         const int br = T.B.row0 + bi * T.B.row_b + n0, bs = T.B.slab0 + bi * T.B.slab_b;
+        if (as < 0 || as >= XA.slabs || bs < 0 || bs >= XB.slabs || kb >= XA.kblocks ||
+            kb >= XB.kblocks || ar < 0 || br < 0 || ar >= XA.rows || br >= XB.rows) {
+          err = 2;  // a plan addressed outside its slice array: stop, report
+          break;
+        }
+        const int ra = min(S_BM, XA.rows - ar), rb = min(Nt, XB.rows - br);
+        const uint32_t abytes = ra > 0 ? (uint32_t)ra * 32u : 0u;
+        const uint32_t bbytes = rb > 0 ? (uint32_t)rb * 32u : 0u;
+        mbar_arrive_expect_tx(&full[st], (uint32_t)s * (abytes + bbytes));
+        uint8_t *sa = smem + (size_t)st * stage_bytes;
+        uint8_t *sb = sa + (size_t)s * a_bytes;
+        const __nv_bfloat16 *ga = reinterpret_cast<const __nv_bfloat16 *>(XA.base) +
+                                  (long long)as * XA.slab_stride +
+                                  ((long long)kb * XA.rows + ar) * 16;
+        const __nv_bfloat16 *gb = reinterpret_cast<const __nv_bfloat16 *>(XB.base) +
+                                  (long long)bs * XB.slab_stride +
+                                  ((long long)kb * XB.rows + br) * 16;
         for (int p = 0; p < s; ++p)
-          tma_load_4d(sa + p * a_bytes, &maps.m[T.A.map], &full[st], kk, ar, as, p);
+          if (abytes) bulk_load(sa + p * a_bytes, ga + p * XA.slice_stride, abytes, &full[st]);
         for (int q = 0; q < s; ++q)
-          tma_load_4d(sb + q * b_bytes, &maps.m[T.B.map], &full[st], kk, br, bs, q);
+          if (bbytes) bulk_load(sb + q * b_bytes, gb + q * XB.slice_stride, bbytes, &full[st]);
         ++issued;
       }
       // let every issued copy land before the CTA may exit (bounded)
@@ -141,7 +186,7 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
         kbase += terms[J.term0 + t].ksteps;
         ++t;
       }
-      bool init[S_NACC] = {false, false, false, false, false};
+      uint32_t fresh = (1u << S_NACC) - 1;
       int since = 0, nd = 0;
       bool pending = false;
       for (int g = g0, it = 0; g < g1; ++g, ++it) {
@@ -154,29 +199,17 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
         if (!mbar_wait(&full[st], ph, &err)) break;
         tc_fence_after();
         const uint32_t sa = smem_u32(smem + (size_t)st * stage_bytes);
-        const uint32_t sb = sa + (uint32_t)s * a_bytes;
+        const uint64_t dA = smem_desc_noswz(sa), dB = smem_desc_noswz(sa + (uint32_t)s * a_bytes);
         // levels >= 4 first (they never wait for a drain), then levels 0..3
-        for (int pass = 0; pass < 2; ++pass) {
-          if (pass == 1 && pending) {
-            if (!mbar_wait(&drainempty, nd & 1, &err)) break;
-            tc_fence_after();
-            ++nd;
-            pending = false;
-            init[0] = init[1] = init[2] = init[3] = false;
-          }
-          for (int p = 0; p < s; ++p) {
-            const uint64_t ad = smem_desc_sw32(sa + p * a_bytes);
-            for (int q = 0; q + p < s; ++q) {
-              const int lv = p + q;
-              if ((pass == 0) != (lv >= 4)) continue;
-              const int acc = lv < 4 ? lv : 4;
-              const uint64_t bd = smem_desc_sw32(sb + q * b_bytes);
-              umma_f16(tmem + (uint32_t)(acc * Nt), ad, bd, idesc, init[acc] ? 1u : 0u);
-              init[acc] = true;
-            }
-          }
+        issue_products<S, true>(tmem, dA, dB, a_bytes >> 4, b_bytes >> 4, (uint32_t)Nt, idesc, fresh);
+        if (pending) {
+          if (!mbar_wait(&drainempty, nd & 1, &err)) break;
+          tc_fence_after();
+          ++nd;
+          pending = false;
+          fresh |= 0xFu;
         }
-        if (err) break;
+        issue_products<S, false>(tmem, dA, dB, a_bytes >> 4, b_bytes >> 4, (uint32_t)Nt, idesc, fresh);
         umma_commit(&empty[st]);
         if (++since == kdrain_steps && g + 1 < g1) {
           umma_commit(&drainfull);
@@ -201,7 +234,7 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
       for (int i = 0; i < 4; ++i) acc[c][i] = {0.f, 0.f};
     bool ok = true;
     for (int d = 0; d < ndrains && ok; ++d) {
-      ok = mbar_wait(&drainfull, d & 1, &err);
+      ok = mbar_wait_sleep(&drainfull, d & 1, &err);
       if (!ok) break;
       tc_fence_after();
 #pragma unroll
@@ -209,7 +242,14 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
         if (c < nch) {
           float v[4][4];
 #pragma unroll
-          for (int L = 0; L < 4; ++L) tmem_ld4(tb + L * Nt + c * 4, v[L]);
+          for (int L = 0; L < 4; ++L) {
+            if (L < NLOW) {
+              tmem_ld4(tb + L * Nt + c * 4, v[L]);
+            } else {
+#pragma unroll
+              for (int i = 0; i < 4; ++i) v[L][i] = 0.f;
+            }
+          }
           tmem_wait_ld();
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
@@ -224,19 +264,25 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
       __syncwarp();
       if (lane == 0) mbar_arrive(&drainempty);
     }
-    if (ok && nsteps > 0) ok = mbar_wait(&accfull, 0, &err);
+    if (ok && nsteps > 0) ok = mbar_wait_sleep(&accfull, 0, &err);
     if (ok) {
       tc_fence_after();
       const int ex = J.expo + (J.expo_slot >= 0 ? reinterpret_cast<const int *>(P.p[B_SLOTEXP])[J.expo_slot] : 0);
       const float sc = ldexpf(J.mult, ex);
-      const int nvv = J.nv;
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
         if (c < nch) {
           float v[5][4];
           if (nsteps > 0) {
 #pragma unroll
-            for (int L = 0; L < 5; ++L) tmem_ld4(tb + L * Nt + c * 4, v[L]);
+            for (int L = 0; L < 5; ++L) {
+              if (L < NLOW || (L == 4 && HAS_HIGH)) {
+                tmem_ld4(tb + L * Nt + c * 4, v[L]);
+              } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) v[L][i] = 0.f;
+              }
+            }
             tmem_wait_ld();
           } else {
 #pragma unroll
@@ -253,7 +299,7 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
             x = dd::add_f(x, v[4][i]);
             x = dd::scale(x, sc);
             const int n = n0 + part * qc + c * 4 + i;
-            if (m >= J.M || n >= J.N) continue;
+            if (m >= J.M || n >= J.N || (J.m_pad > 0 && (m % J.m_pad) >= J.m_valid)) continue;
             const OutD &C = n < J.Nm ? J.C : J.Ct;
             const int nc = n < J.Nm ? n : n - J.Nm;
             const long long off = C.off + (long long)bi * C.sb +
@@ -269,7 +315,8 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
               const float2 wv = reinterpret_cast<const float2 *>(P.p[W.buf])[woff];
               dd::df tot = dd::add(x, dd::df{wv.x, wv.y});
               const float2 *ev = reinterpret_cast<const float2 *>(P.p[B_EPSV]);
-              const float2 ea = ev[nc / nvv], eb = ev[nc % nvv], ec = ev[m];
+              // tile (c = m, b = n) at fixed a = batch index
+              const float2 ea = ev[bi], eb = ev[nc], ec = ev[m];
               dd::df e = dd::add(dd::add(dd::df{ea.x, ea.y}, dd::df{eb.x, eb.y}),
                                  dd::df{ec.x, ec.y});
               e = dd::add(e, dd::df{-J.eo_hi, -J.eo_lo});
@@ -289,7 +336,7 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
   __syncthreads();
   tc_fence_after();
   if (warp == 1) tmem_dealloc(tmem, 512);
-  if (threadIdx.x == 0 && err) atomicExch(status, 1);
+  if (threadIdx.x == 0 && err) atomicExch(status, err);
 }
 
 int s_upload_plan(const SPlan &p, SDevPlan *d, cudaStream_t s) {
@@ -322,7 +369,7 @@ void s_free_plan(SDevPlan *d) {
   d->tiles = 0;
 }
 
-int s_launch_plan(const SDevPlan &d, const SMapTable &maps, const VPtrTable &ptrs,
+int s_launch_plan(const SDevPlan &d, const SArrTable &arrs, const VPtrTable &ptrs,
                   int slices, int kdrain_steps, int *status, cudaStream_t s,
                   long long *launches) {
   if (d.njobs == 0 || d.tiles == 0) return CC3_OK;
@@ -332,19 +379,36 @@ int s_launch_plan(const SDevPlan &d, const SMapTable &maps, const VPtrTable &ptr
   const size_t smem = std::max<size_t>(s_smem_bytes(slices, S_NT_MAX), 120 * 1024);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(split_engine_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)s_smem_bytes(S_MAX_SLICES, S_NT_MAX));
-    if (e != cudaSuccess) return CC3_FAIL(CC3_ERR_CUDA, cudaGetErrorString(e));
-    int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, split_engine_kernel, S_THREADS,
-                                                      s_smem_bytes(S_MAX_SLICES, S_NT_MAX));
-    if (e != cudaSuccess || nb < 1)
-      return CC3_FAIL(CC3_ERR_CUDA, "split engine kernel does not fit on an SM");
+    const void *fns[] = {(const void *)split_engine_kernel<3>, (const void *)split_engine_kernel<4>,
+                         (const void *)split_engine_kernel<5>, (const void *)split_engine_kernel<6>,
+                         (const void *)split_engine_kernel<7>};
+    for (int S = 3; S <= 7; ++S) {
+      const void *f = fns[S - 3];
+      const int mx = (int)std::max<size_t>(s_smem_bytes(S, S_NT_MAX), 120 * 1024);
+      cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+      if (e != cudaSuccess) return CC3_FAIL(CC3_ERR_CUDA, cudaGetErrorString(e));
+      int nb = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, S_THREADS, (size_t)mx);
+      if (e != cudaSuccess || nb < 1)
+        return CC3_FAIL(CC3_ERR_CUDA, "split engine kernel does not fit on an SM");
+    }
     attr_set = true;
   }
-  split_engine_kernel<<<(unsigned)d.tiles, S_THREADS, smem, s>>>(
-      d.jobs, d.njobs, d.terms, maps, ptrs, slices, kdrain_steps, status);
+  switch (slices) {
+#define CC3_SPLIT_LAUNCH(S_)                                                              \
+  case S_:                                                                                \
+    split_engine_kernel<S_><<<(unsigned)d.tiles, S_THREADS, smem, s>>>(                   \
+        d.jobs, d.njobs, d.terms, arrs, ptrs, kdrain_steps, status);                      \
+    break;
+    CC3_SPLIT_LAUNCH(3)
+    CC3_SPLIT_LAUNCH(4)
+    CC3_SPLIT_LAUNCH(5)
+    CC3_SPLIT_LAUNCH(6)
+    CC3_SPLIT_LAUNCH(7)
+#undef CC3_SPLIT_LAUNCH
+    default:
+      return CC3_FAIL(CC3_ERR_ARG, "slices");
+  }
   if (launches) ++*launches;
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? CC3_OK : CC3_FAIL(CC3_ERR_CUDA, cudaGetErrorString(e));

@@ -6,16 +6,35 @@
 
 namespace cc3 {
 
-enum { SMAX_MAPS = 28, S_BM = 128, S_BK = 16, S_STAGES = 3, S_MAX_SLICES = 7,
+enum { SMAX_MAPS = 28, S_BM = 128, S_BK = 16, S_STAGES_MAX = 6, S_MAX_SLICES = 7,
        S_NT_MAX = 96, S_NACC = 5, S_DRAIN_STEPS = 16, S_EPI_WARPS = 16, S_THREADS = 64 + 32 * S_EPI_WARPS };
 
-struct SMapTable {
-  CUtensorMap m[SMAX_MAPS];
+// A BF16 slice array in the tensor cores' canonical no-swizzle K-major order:
+// [slice][slab][K/16][row groups of 8][2 K halves][8 rows][8 elements].  Each
+// 16 x R tile (R rows from a multiple of 8) is then one contiguous block of
+// 32 R bytes, moved by a single bulk copy.
+// Pipeline depth for S slices: as many (A, B) stages of 128 + 96 rows as fit
+// in ~216 KB of shared memory, at most S_STAGES_MAX.
+__host__ __device__ constexpr int s_stages(int S) {
+  return (216 * 1024) / (S * (128 + 96) * 32) < S_STAGES_MAX
+             ? (216 * 1024) / (S * (128 + 96) * 32)
+             : S_STAGES_MAX;
+}
+
+struct SArr {
+  unsigned long long base;  // device address
+  long long slab_stride;    // elements
+  long long slice_stride;   // elements
+  int rows;                 // rows per slab, padded to a multiple of 8
+  int kblocks;              // K / 16
+  int slabs;                // number of slabs (bounds check)
+};
+struct SArrTable {
+  SArr a[SMAX_MAPS];
 };
 
-// A slice operand tile: 4-D tensor map (K, rows, slab, slice); the tile of
-// batch index b starts at row row0 + b*row_b (+ m0 or n0) of slab
-// slab0 + b*slab_b.
+// A slice operand tile: array `map`; the tile of batch index b starts at row
+// row0 + b*row_b (+ m0 or n0) of slab slab0 + b*slab_b.
 struct SOpnd {
   int map;
   int slab0, row0, slab_b, row_b;
@@ -36,6 +55,7 @@ struct SJob {
   int mode;
   int expo;       // result = 2^expo * (integer-scaled accumulators)
   int expo_slot;  // >= 0: add the per-triple exponent ex[expo_slot]
+  int m_pad, m_valid;  // m_pad > 0: rows with m % m_pad >= m_valid are padding
   float mult;  // +-1 or 2 (exact)
   OutD C, Ct;  // output element (b, m, n) for n < Nm, resp. (b, m, n - Nm);
                // buffer of float2 (dd) or double
@@ -66,7 +86,7 @@ struct SDevPlan {
 
 int s_upload_plan(const SPlan &p, SDevPlan *d, cudaStream_t s);
 void s_free_plan(SDevPlan *d);
-int s_launch_plan(const SDevPlan &d, const SMapTable &maps, const VPtrTable &ptrs,
+int s_launch_plan(const SDevPlan &d, const SArrTable &arrs, const VPtrTable &ptrs,
                   int slices, int kdrain_steps, int *status, cudaStream_t s,
                   long long *launches);
 size_t s_smem_bytes(int slices, int ntile);

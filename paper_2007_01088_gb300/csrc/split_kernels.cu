@@ -66,25 +66,47 @@ __device__ __forceinline__ void store_digits(long long T, int s, __nv_bfloat16 *
     if (p < s) dst[p * slice_stride] = __float2bfloat16_rn(ldexpf(d[p], -8 * p));
 }
 
-// dst[p][row][k] for row < nrows, k < Kp, from src through a strided gather:
-//   row = (r2, r1, r0), k = (k1, k0); value 0 outside (k0 < k0v, k1 < k1v).
+// Offset of (row r, k in 0..15) inside one 16-column K block of R8 rows, in
+// the tensor cores' canonical no-swizzle K-major order: core matrices of
+// 8 rows x 8 elements (128 contiguous bytes), the two K halves 64 elements
+// apart, 8-row groups 128 elements apart.
+__device__ __forceinline__ long long cm_off(long long r, int k) {
+  return (r >> 3) * 128 + (k >> 3) * 64 + (r & 7) * 8 + (k & 7);
+}
+
+// Slices of an FP64 tensor read through a strided gather
+//   row = (r2, r1, r0), k = (k1, k0); value 0 outside (k0 < k0v, k1 < k1v),
+// stored K-blocked: [p][slab][K/16][rps8 rows, core-matrix order], row =
+// slab * rps + r, rps8 = rps rounded up to 8.  Every 16 x R tile the tensor
+// cores read is one contiguous block.
 __global__ void slice_gather_kernel(const double *__restrict__ src, __nv_bfloat16 *__restrict__ dst,
-                                    int s, int e, Gather g, long long nrows, int Kp) {
+                                    int s, int e, Gather g, long long nrows, int Kp, int rps) {
   const long long n = nrows * Kp;
-  const long long sstride = n;
   const int sh = 7 + 8 * (s - 1) - e;
+  const long long KB = Kp / 16;
+  const long long rps8 = (rps + 7) / 8 * 8;
+  const long long sstride = (nrows / rps) * KB * rps8 * 16;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
        idx += (long long)gridDim.x * blockDim.x) {
     const long long row = idx / Kp;
     const int k = (int)(idx % Kp);
-    const int k1 = k / g.kin, k0 = k % g.kin;
+    int k1, k0;
+    if (g.zblk) {
+      k1 = (k / 16) % g.kin;
+      k0 = 16 * (k / (16 * g.kin)) + (k % 16);
+    } else {
+      k1 = k / g.kin;
+      k0 = k % g.kin;
+    }
     long long T = 0;
     if (k0 < g.k0v && k1 < g.k1v) {
       const long long r0 = row % g.n0, r1 = (row / g.n0) % g.n1, r2 = row / ((long long)g.n0 * g.n1);
       const long long off = g.off + r2 * g.s2 + r1 * g.s1 + r0 * g.s0 + k1 * g.sk1 + k0 * g.sk0;
       T = fixed_from_double(src[off], sh);
     }
-    store_digits(T, s, dst + idx, sstride);
+    const long long slab = row / rps, r = row % rps;
+    const long long o = (slab * KB + k / 16) * rps8 * 16 + cm_off(r, k % 16);
+    store_digits(T, s, dst + o, sstride);
   }
 }
 
@@ -148,37 +170,93 @@ __global__ void slot_exponent_kernel(const unsigned int *__restrict__ maxbits, i
 }
 
 // Slices of tau~ in the three cyclic layouts used by the residual
-// contractions: layout L puts slot L outermost, then slot L+1, then slot L+2
-// (innermost, padded to vp):  V_L[p][slot][x][y][z].
-__global__ void slice_tt_kernel(const float2 *__restrict__ tt, __nv_bfloat16 *__restrict__ v0,
-                                __nv_bfloat16 *__restrict__ v1, __nv_bfloat16 *__restrict__ v2,
-                                int nv, int vp, int s, const int *__restrict__ ex, int nslot,
-                                int nslot_alloc) {
-  const long long per = (long long)nv * nv * vp;
-  const long long n = per * nslot;
-  const long long sstride = per * nslot_alloc;  // slices are nslot_alloc slots apart
+// contractions.  Layout L puts slot L outermost (rows x), then slot L+1 (y),
+// then slot L+2 (z, padded to vp):
+//   V_L[p][slot][kb = zb*nv + y][x (nv8 rows)][16 (zz)],  z = 16 zb + zz,
+// core-matrix order inside every 16-column block.  Read as rows x with
+// K = (zb, y, zz) it serves the vvov and singles contractions; read as rows
+// (y, x) with K = z (the nv blocks of one zb are consecutive) it serves the
+// ooov and F contractions.  One CTA stages a 16^3 cube of tau~ in shared
+// memory (coalesced along the innermost index of tt for every rotation) and
+// writes each slice as whole 16-byte core rows.
+__global__ void __launch_bounds__(256)
+slice_tt_kernel(const float2 *__restrict__ tt, __nv_bfloat16 *const *__restrict__ v, int nv,
+                int vp, int s, const int *__restrict__ ex, int nslot_alloc) {
+  __shared__ float2 cube[16][16][17];  // [x][y][z] (+1 pad)
+  const int nx = (nv + 15) / 16, nzb = vp / 16;
+  int b = blockIdx.x;
+  const int zb = b % nzb; b /= nzb;
+  const int yb = b % nx; b /= nx;
+  const int xb = b % nx; b /= nx;
+  const int L = b;  // 0..2
+  const int slot = blockIdx.y;
   const long long nv2 = (long long)nv * nv;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < 3 * n;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int L = (int)(idx / n);
-    const long long rem = idx % n;
-    const int slot = (int)(rem / per);
-    const long long w = rem % per;
-    const int z = (int)(w % vp);
-    const int y = (int)((w / vp) % nv);
-    const int x = (int)(w / ((long long)vp * nv));
-    long long T = 0;
-    if (z < nv) {
-      int v[3];
-      v[L] = x;
-      v[(L + 1) % 3] = y;
-      v[(L + 2) % 3] = z;
-      const float2 t = tt[(long long)slot * nv2 * nv + (long long)v[0] * nv2 + (long long)v[1] * nv + v[2]];
-      const int sh = 7 + 8 * (s - 1) - ex[slot];
-      T = fixed_from_float(t.x, sh) + fixed_from_float(t.y, sh);
+  const float2 *T = tt + (long long)slot * nv2 * nv;
+  // load: element (x, y, z) of layout L sits at slots (L, L+1, L+2) of (a,b,c);
+  // the thread index runs fastest along the cube axis that is c
+  for (int e = threadIdx.x; e < 4096; e += 256) {
+    const int i0 = e & 15, i1 = (e >> 4) & 15, i2 = e >> 8;
+    int x, y, z;  // cube axes chosen so that c varies fastest
+    if (L == 0) { z = i0; y = i1; x = i2; }       // (a,b,c) = (x,y,z)
+    else if (L == 1) { y = i0; x = i1; z = i2; }  // (a,b,c) = (z,x,y)
+    else { x = i0; z = i1; y = i2; }              // (a,b,c) = (y,z,x)
+    const int gx = xb * 16 + x, gy = yb * 16 + y, gz = zb * 16 + z;
+    float2 val = make_float2(0.f, 0.f);
+    if (gx < nv && gy < nv && gz < nv) {
+      int vv[3];
+      vv[L] = gx;
+      vv[(L + 1) % 3] = gy;
+      vv[(L + 2) % 3] = gz;
+      val = T[(long long)vv[0] * nv2 + (long long)vv[1] * nv + vv[2]];
     }
-    __nv_bfloat16 *dst = (L == 0 ? v0 : (L == 1 ? v1 : v2)) + rem;
-    store_digits(T, s, dst, sstride);
+    cube[x][y][z] = val;
+  }
+  __syncthreads();
+  const int x = threadIdx.x & 15, y = threadIdx.x >> 4;
+  const int gx = xb * 16 + x, gy = yb * 16 + y;
+  if (gx >= nv || gy >= nv) return;
+  const long long nv8 = (nv + 7) / 8 * 8;
+  const long long KB = (long long)nzb * nv;
+  const long long sstride = (long long)nslot_alloc * KB * nv8 * 16;
+  const long long blk = ((long long)slot * KB + (long long)zb * nv + gy) * nv8 * 16;
+  const int sh = 7 + 8 * (s - 1) - ex[slot];
+  __nv_bfloat16 *dst = v[L];
+#pragma unroll 1
+  for (int h = 0; h < 2; ++h) {
+    long long Tv[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const float2 t = cube[x][y][h * 8 + e];
+      Tv[e] = fixed_from_float(t.x, sh) + fixed_from_float(t.y, sh);
+    }
+    // balanced base-256 digits of the 8 values, slice by slice
+    float d[S_MAX_SLICES_K][8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      long long Tt = Tv[e];
+#pragma unroll
+      for (int p = S_MAX_SLICES_K - 1; p >= 0; --p) {
+        if (p < s) {
+          if (p > 0) {
+            const long long r = ((Tt + 128) & 255) - 128;
+            d[p][e] = (float)r;
+            Tt = (Tt - r) >> 8;
+          } else {
+            d[0][e] = (float)Tt;
+          }
+        }
+      }
+    }
+    const long long o = blk + cm_off(gx, h * 8);
+#pragma unroll
+    for (int p = 0; p < S_MAX_SLICES_K; ++p) {
+      if (p < s) {
+        __align__(16) __nv_bfloat16 out[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) out[e] = __float2bfloat16_rn(ldexpf(d[p][e], -8 * p));
+        *reinterpret_cast<uint4 *>(dst + p * sstride + o) = *reinterpret_cast<const uint4 *>(out);
+      }
+    }
   }
 }
 
@@ -189,8 +267,10 @@ static int grid_for(long long n) {
 }
 
 int launch_slice_gather(const double *src, __nv_bfloat16 *dst, int s, int e, const Gather &g,
-                        long long nrows, int Kp, cudaStream_t st) {
-  slice_gather_kernel<<<grid_for(nrows * Kp), 256, 0, st>>>(src, dst, s, e, g, nrows, Kp);
+                        long long nrows, int Kp, int rps, cudaStream_t st) {
+  if (Kp % 16 != 0 || rps < 1 || nrows % rps != 0)
+    return CC3_FAIL(CC3_ERR_ARG, "slice layout");
+  slice_gather_kernel<<<grid_for(nrows * Kp), 256, 0, st>>>(src, dst, s, e, g, nrows, Kp, rps);
   return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_FAIL(CC3_ERR_CUDA, "split element-wise kernel launch");
 }
 int launch_maxabs(const double *x, long long n, unsigned long long *out, cudaStream_t st) {
@@ -209,12 +289,12 @@ int launch_slot_exponent(const unsigned int *maxbits, int *ex, int nslot, cudaSt
   slot_exponent_kernel<<<(nslot + 127) / 128, 128, 0, st>>>(maxbits, ex, nslot);
   return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_FAIL(CC3_ERR_CUDA, "split element-wise kernel launch");
 }
-int launch_slice_tt(const float2 *tt, __nv_bfloat16 *v0, __nv_bfloat16 *v1, __nv_bfloat16 *v2,
-                    int nv, int vp, int s, const int *ex, int nslot, int nslot_alloc,
-                    cudaStream_t st) {
-  const long long n = 3LL * nv * nv * vp * nslot;
-  slice_tt_kernel<<<grid_for(n), 256, 0, st>>>(tt, v0, v1, v2, nv, vp, s, ex, nslot, nslot_alloc);
-  return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_FAIL(CC3_ERR_CUDA, "split element-wise kernel launch");
+int launch_slice_tt(const float2 *tt, __nv_bfloat16 *const *v, int nv, int vp, int s,
+                    const int *ex, int nslot, int nslot_alloc, cudaStream_t st) {
+  const int nx = (nv + 15) / 16;
+  dim3 grid(3 * nx * nx * (vp / 16), nslot);
+  slice_tt_kernel<<<grid, 256, 0, st>>>(tt, v, nv, vp, s, ex, nslot_alloc);
+  return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_FAIL(CC3_ERR_CUDA, "slice_tt launch");
 }
 
 }  // namespace cc3

@@ -13,19 +13,25 @@ enum { S_MAX_SLICES_K = 8 };
 //   row = (r2, r1, r0) with r0 < n0, r1 < n1;  k = (k1, k0) with k0 < kin;
 //   element = src[off + r2*s2 + r1*s1 + r0*s0 + k1*sk1 + k0*sk0] when
 //   k0 < k0v and k1 < k1v, else 0 (padding).
+// With zblk = 1 the K index is instead (zb, u, zz) = (k / (16 kin), (k / 16) % kin,
+// k % 16) and the element is src[... + u*sk1 + (16 zb + zz)*sk0], valid when
+// 16 zb + zz < k0v and u < k1v: K runs over 16-wide blocks of the inner index
+// with the outer index in between (the K order of the residual contractions).
 struct Gather {
   long long off, s2, s1, s0, sk1, sk0;
   int n1, n0, kin, k0v, k1v;
+  int zblk;
 };
 
+// dst layout: [slice][slab][K / 16][rps rows][16] (rows = slabs * rps)
 int launch_slice_gather(const double *src, __nv_bfloat16 *dst, int s, int e, const Gather &g,
-                        long long nrows, int Kp, cudaStream_t st);
+                        long long nrows, int Kp, int rps, cudaStream_t st);
 int launch_maxabs(const double *x, long long n, unsigned long long *out, cudaStream_t st);
 int launch_contravariant_dd(const float2 *tau, float2 *tt, int nv, int nslot,
                             unsigned int *maxbits, cudaStream_t st);
 int launch_slot_exponent(const unsigned int *maxbits, int *ex, int nslot, cudaStream_t st);
-int launch_slice_tt(const float2 *tt, __nv_bfloat16 *v0, __nv_bfloat16 *v1, __nv_bfloat16 *v2,
-                    int nv, int vp, int s, const int *ex, int nslot, int nslot_alloc,
-                    cudaStream_t st);
+// v: device array of 3 pointers (one per cyclic layout)
+int launch_slice_tt(const float2 *tt, __nv_bfloat16 *const *v, int nv, int vp, int s,
+                    const int *ex, int nslot, int nslot_alloc, cudaStream_t st);
 
 }  // namespace cc3
