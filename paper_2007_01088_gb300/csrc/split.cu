@@ -303,6 +303,7 @@ int new_sjob(SPlan &P, int M, int N, int Ntile, int batch, int ksplit, int mode,
   j.M = M;
   j.N = N;
   j.Nm = N;
+  j.n_valid = N;
   j.Ntile = Ntile;
   j.batch = batch;
   j.ksplit = std::max(1, ksplit);
@@ -322,10 +323,12 @@ int new_sjob(SPlan &P, int M, int N, int Ntile, int batch, int ksplit, int mode,
   return (int)P.jobs.size() - 1;
 }
 void add_sterm(SPlan &P, int job, SOpnd A, SOpnd B, int K, int negA, double &executed,
-               int slices) {
+               int slices, const SOpnd *Bt = nullptr, int nbm = 0) {
   STerm t;
   t.A = A;
   t.B = B;
+  t.Bt = Bt ? *Bt : B;
+  t.nbm = Bt ? nbm : 0;
   t.ksteps = K / S_BK;
   t.negA = negA;
   P.terms.push_back(t);
@@ -333,7 +336,7 @@ void add_sterm(SPlan &P, int job, SOpnd A, SOpnd B, int K, int negA, double &exe
   j.nterm++;
   executed += 2.0 * j.tiles_m * S_BM * (double)j.tiles_n * j.Ntile * K * j.batch *
               (slices * (slices + 1) / 2);
-  const double useful = 2.0 * j.M * (double)j.N * K * j.batch;
+  const double useful = 2.0 * j.M * (double)(j.n_valid + (j.N - j.Nm)) * K * j.batch;
   P.flop += useful;
   P.slice_flop += useful * (slices * (slices + 1) / 2);
 }
@@ -402,20 +405,18 @@ void plan_omega_split(SPlan &P, SplitState *S, int no, int nv, const int ijk[3],
     // layout with x slot outermost: K order (slot m0+1, slot m0+2)
     const int L = m[0];
     const bool yz = (m[1] == (L + 1) % 3);
-    {  // Omega~^{ad}_{pq} += sum_{yz} V[x][y][z] (dy|rz)
-      int jb = new_sjob(P, nv, nv, S->Nab, 1, ksplit4, SEPI_F64_ATOMIC, E, ex, s);
+    {  // Omega~^{ad}_{pq} += sum_{yz} V[x][y][z] (dy|rz)   columns d < nv
+       // Omega1^x_p       += sum_{yz} V[x][y][z] (qy|rz)   tail column nv8
+      const int nv8 = (nv + 7) / 8 * 8;
+      int jb = new_sjob(P, nv, nv8 + 1, ntile_for(nv8 + 1), 1, ksplit4, SEPI_F64_ATOMIC, E, ex, s);
       P.jobs[jb].expo_slot = slot;
+      P.jobs[jb].Nm = nv8;
+      P.jobs[jb].n_valid = nv;
       P.jobs[jb].C = outd(B_OMT, ((long long)p * no + q) * nv2, nv, 1);
-      P.jobs[jb].Ct = P.jobs[jb].C;
-      add_sterm(P, jb, opd(MA_V0 + L, slot), opd(yz ? MB_ZG : MB_ZH, r), nv * vp, 0, ex, s);
-    }
-    {  // Omega1^x_p += sum_{yz} V[x][y][z] (qy|rz)
-      int jb = new_sjob(P, nv, 1, S->N1, 1, 1, SEPI_F64_ATOMIC, E, ex, s);
-      P.jobs[jb].expo_slot = slot;
-      P.jobs[jb].C = outd(B_OM1, (long long)p * nv, 1, 0);
-      P.jobs[jb].Ct = P.jobs[jb].C;
-      add_sterm(P, jb, opd(MA_V0 + L, slot), opd(MB_OV, yz ? q * no + r : r * no + q), nv * vp,
-                0, ex, s);
+      P.jobs[jb].Ct = outd(B_OM1, (long long)p * nv, 1, 0);
+      const SOpnd tail = opd(MB_OV, yz ? q * no + r : r * no + q);
+      add_sterm(P, jb, opd(MA_V0 + L, slot), opd(yz ? MB_ZG : MB_ZH, r), nv * vp, 0, ex, s,
+                &tail, nv8);
     }
     {  // Omega~^{xy}_{pl} -= sum_z V (ql|rz);  Omega~^{xy}_{pq} += sum_z V F_rz
       // layout Lz has z innermost; its rows (y_L, x_L) are the perm's (y, x) when
@@ -457,7 +458,8 @@ int build_plans(cc3_ctx *c, SplitState *S, cudaStream_t st) {
   // K split of the vvov contraction: enough CTAs for two waves per batch
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-  const int tiles4 = ((nv + S_BM - 1) / S_BM) * ((nv + S->Nab - 1) / S->Nab) * 6 * S->batch;
+  const int nv8 = (nv + 7) / 8 * 8;
+  const int tiles4 = ((nv + S_BM - 1) / S_BM) * ((nv8 + 1 + ntile_for(nv8 + 1) - 1) / ntile_for(nv8 + 1)) * 6 * S->batch;
   const int kst = nv * S->vp / S_BK;
   int ks4 = std::max(1, std::min(kst / 64, (2 * sms + tiles4 - 1) / std::max(1, tiles4)));
   for (int t0 = 0; t0 < c->ntri; t0 += S->batch) {

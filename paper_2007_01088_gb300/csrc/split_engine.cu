@@ -147,30 +147,49 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
         const int kb = g - kbase;
         const int st = issued % S_STAGES, ph = (issued / S_STAGES) & 1;
         if (!mbar_wait(&empty[st], ph ^ 1, &err)) break;
-        const SArr &XA = arrs.a[T.A.map], &XB = arrs.a[T.B.map];
+        const SArr &XA = arrs.a[T.A.map], &XB = arrs.a[T.B.map], &XT = arrs.a[T.Bt.map];
         const int ar = T.A.row0 + bi * T.A.row_b + m0, as = T.A.slab0 + bi * T.A.slab_b;
-        const int br = T.B.row0 + bi * T.B.row_b + n0, bs = T.B.slab0 + bi * T.B.slab_b;
-        if (as < 0 || as >= XA.slabs || bs < 0 || bs >= XB.slabs || kb >= XA.kblocks ||
-            kb >= XB.kblocks || ar < 0 || br < 0 || ar >= XA.rows || br >= XB.rows) {
+        const int bs = T.B.slab0 + bi * T.B.slab_b, ts = T.Bt.slab0 + bi * T.Bt.slab_b;
+        // B tile rows [n0, n0 + Nt): main rows from B, rows >= nbm from the tail Bt
+        const int nbm = T.nbm > 0 ? T.nbm : (1 << 30);
+        const int br = T.B.row0 + bi * T.B.row_b + n0;
+        const int nmain = max(0, min(min(Nt, nbm - n0), XB.rows - br));
+        const int tfirst = max(n0, nbm);                  // first tail row of the tile
+        const int tr = T.Bt.row0 + tfirst - nbm;          // its row in Bt
+        const int ntail = T.nbm > 0 ? max(0, min(n0 + Nt - tfirst, XT.rows - tr)) : 0;
+        if (as < 0 || as >= XA.slabs || kb >= XA.kblocks || ar < 0 || ar >= XA.rows ||
+            (nmain > 0 && (bs < 0 || bs >= XB.slabs || kb >= XB.kblocks || br < 0)) ||
+            (ntail > 0 && (ts < 0 || ts >= XT.slabs || kb >= XT.kblocks || tr < 0 ||
+                           ((tfirst - n0) & 7) != 0))) {
           err = 2;  // a plan addressed outside its slice array: stop, report
           break;
         }
-        const int ra = min(S_BM, XA.rows - ar), rb = min(Nt, XB.rows - br);
-        const uint32_t abytes = ra > 0 ? (uint32_t)ra * 32u : 0u;
-        const uint32_t bbytes = rb > 0 ? (uint32_t)rb * 32u : 0u;
-        mbar_arrive_expect_tx(&full[st], (uint32_t)s * (abytes + bbytes));
+        const int ra = min(S_BM, XA.rows - ar);
+        const uint32_t abytes = (uint32_t)ra * 32u;
+        const uint32_t mbytes = (uint32_t)nmain * 32u, tbytes = (uint32_t)ntail * 32u;
+        mbar_arrive_expect_tx(&full[st], (uint32_t)s * (abytes + mbytes + tbytes));
         uint8_t *sa = smem + (size_t)st * stage_bytes;
         uint8_t *sb = sa + (size_t)s * a_bytes;
         const __nv_bfloat16 *ga = reinterpret_cast<const __nv_bfloat16 *>(XA.base) +
                                   (long long)as * XA.slab_stride +
                                   ((long long)kb * XA.rows + ar) * 16;
-        const __nv_bfloat16 *gb = reinterpret_cast<const __nv_bfloat16 *>(XB.base) +
-                                  (long long)bs * XB.slab_stride +
-                                  ((long long)kb * XB.rows + br) * 16;
         for (int p = 0; p < s; ++p)
-          if (abytes) bulk_load(sa + p * a_bytes, ga + p * XA.slice_stride, abytes, &full[st]);
-        for (int q = 0; q < s; ++q)
-          if (bbytes) bulk_load(sb + q * b_bytes, gb + q * XB.slice_stride, bbytes, &full[st]);
+          bulk_load(sa + p * a_bytes, ga + p * XA.slice_stride, abytes, &full[st]);
+        if (mbytes) {
+          const __nv_bfloat16 *gb = reinterpret_cast<const __nv_bfloat16 *>(XB.base) +
+                                    (long long)bs * XB.slab_stride +
+                                    ((long long)kb * XB.rows + br) * 16;
+          for (int q = 0; q < s; ++q)
+            bulk_load(sb + q * b_bytes, gb + q * XB.slice_stride, mbytes, &full[st]);
+        }
+        if (tbytes) {
+          const __nv_bfloat16 *gt = reinterpret_cast<const __nv_bfloat16 *>(XT.base) +
+                                    (long long)ts * XT.slab_stride +
+                                    ((long long)kb * XT.rows + tr) * 16;
+          for (int q = 0; q < s; ++q)
+            bulk_load(sb + q * b_bytes + (tfirst - n0) * 32, gt + q * XT.slice_stride, tbytes,
+                      &full[st]);
+        }
         ++issued;
       }
       // let every issued copy land before the CTA may exit (bounded)
@@ -299,7 +318,9 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
             x = dd::add_f(x, v[4][i]);
             x = dd::scale(x, sc);
             const int n = n0 + part * qc + c * 4 + i;
-            if (m >= J.M || n >= J.N || (J.m_pad > 0 && (m % J.m_pad) >= J.m_valid)) continue;
+            if (m >= J.M || n >= J.N || (J.m_pad > 0 && (m % J.m_pad) >= J.m_valid) ||
+                (n < J.Nm && n >= J.n_valid))
+              continue;
             const OutD &C = n < J.Nm ? J.C : J.Ct;
             const int nc = n < J.Nm ? n : n - J.Nm;
             const long long off = C.off + (long long)bi * C.sb +

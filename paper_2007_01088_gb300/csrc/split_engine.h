@@ -40,10 +40,13 @@ struct SOpnd {
   int slab0, row0, slab_b, row_b;
 };
 
+// B rows n < nbm come from B (row n), rows n >= nbm from Bt (row n - nbm);
+// nbm = 0: no tail (nbm is a multiple of 8).
 struct STerm {
-  SOpnd A, B;
+  SOpnd A, B, Bt;
   int ksteps;  // K / 16
   int negA;    // the products enter with a minus sign
+  int nbm;
 };
 
 enum SEpi { SEPI_DD_STORE = 0, SEPI_DD_TAU = 1, SEPI_F64_ATOMIC = 2 };
@@ -56,6 +59,7 @@ struct SJob {
   int expo;       // result = 2^expo * (integer-scaled accumulators)
   int expo_slot;  // >= 0: add the per-triple exponent ex[expo_slot]
   int m_pad, m_valid;  // m_pad > 0: rows with m % m_pad >= m_valid are padding
+  int n_valid;         // columns n in [n_valid, Nm) are padding
   float mult;  // +-1 or 2 (exact)
   OutD C, Ct;  // output element (b, m, n) for n < Nm, resp. (b, m, n - Nm);
                // buffer of float2 (dd) or double
