@@ -131,6 +131,28 @@ typedef struct {
 } cc3_counters;
 int cc3_ctx_counters(const cc3_ctx *ctx, cc3_counters *out);
 
+/* FP64 triples residual that allocates no device memory (the paper has no
+ * counterpart; this exists for callers that cannot call cudaMalloc, e.g. code
+ * embedded in a host application that owns the whole GPU memory pool, or code
+ * running while the application forbids new allocations).  Same result as
+ * cc3_omega_triples(ctx, CC3_FP64, ...) on the same inputs.  All pointers are
+ * DEVICE pointers owned by the caller, with the layouts of cc3_ctx_create and
+ * cc3_omega_triples; any output may be NULL.  Every piece of scratch (a
+ * transposed integral block, one triple's W and tau~, the residual
+ * accumulators, reduction partials and contraction tables) comes from one
+ * 16 MiB file-scope device array that every GPU loading the library keeps
+ * until process exit; it limits the size to no <= 12, nv <= 64 (larger sizes
+ * return CC3_ERR_ARG).  The first call on a device looks the array's address
+ * up for that device; make that first call before any stream capture.  Calls
+ * share the array: calls that overlap on the GPU race.  The call returns after
+ * enqueuing its kernels on cuda_stream (it synchronises cuda_stream once, while
+ * uploading its tables). */
+int cc3_omega_triples_noalloc(int no, int nv, const double *eps_o, const double *eps_v,
+                              const double *t2, const double *g_vvvo,
+                              const double *g_ooov, const double *g_ovov,
+                              const double *F_ov, double *Omega1, double *Omega2,
+                              double *E_T, void *cuda_stream);
+
 /* Kernel tracing.  With tracing on, every library kernel launch is bracketed
  * by CUDA events recorded on the launching stream, grouped by kernel class;
  * cc3_ctx_trace returns, for the last call, each class's launches, summed

@@ -34,7 +34,7 @@ EXPORTED = ["cc3_ctx_create", "cc3_ctx_destroy", "cc3_ctx_set_triples",
             "cc3_serve_submit", "cc3_serve_poll", "cc3_serve_wait",
             "cc3_serve_cancel", "cc3_serve_stats", "cc3_serve_stop",
             "cc3_debug_split_gemm", "cc3_last_error", "cc3_ctx_set_tracing",
-            "cc3_ctx_trace"]
+            "cc3_ctx_trace", "cc3_omega_triples_noalloc"]
 
 
 class CC3Error(RuntimeError):
@@ -85,6 +85,8 @@ def _load():
     L.cc3_ctx_set_tracing.restype = I
     L.cc3_ctx_trace.argtypes = [P, ctypes.POINTER(Trace)]
     L.cc3_ctx_trace.restype = I
+    L.cc3_omega_triples_noalloc.argtypes = [I, I] + [P] * 7 + [P, P, P, P]
+    L.cc3_omega_triples_noalloc.restype = I
     L.cc3_last_error.argtypes = []
     L.cc3_last_error.restype = ctypes.c_char_p
     L.cc3_strerror.argtypes = [I]
@@ -175,6 +177,15 @@ def cc3_ctx_counters(ctx):
     _check(lib.cc3_ctx_counters(ctx, ctypes.byref(c)), "cc3_ctx_counters")
     return dict(nominal_flop=c.nominal_flop, executed_flop=c.executed_flop,
                 launches=c.launches, slices=c.slices)
+
+
+def cc3_omega_triples_noalloc(no, nv, eps_o, eps_v, t2, g_vvvo, g_ooov, g_ovov, F_ov,
+                              Omega1, Omega2, E_T, stream=None):
+    """FP64 residual with no device allocation (all arguments CUDA tensors)."""
+    _check(lib.cc3_omega_triples_noalloc(int(no), int(nv), _ptr(eps_o), _ptr(eps_v), _ptr(t2),
+                                         _ptr(g_vvvo), _ptr(g_ooov), _ptr(g_ovov), _ptr(F_ov),
+                                         _ptr(Omega1), _ptr(Omega2), _ptr(E_T),
+                                         _stream(stream)), "cc3_omega_triples_noalloc")
 
 
 def cc3_ctx_set_tracing(ctx, on=True):
