@@ -288,6 +288,7 @@ void cc3_ctx_destroy(cc3_ctx *c) {
     delete X;
   }
   split_destroy(c);
+  jacobian_destroy(c);
   for (int k = 0; k < TR_NCLASS; ++k)
     for (cudaEvent_t e : c->trace.ev[k]) cudaEventDestroy(e);
   double *bufs[] = {c->eps_o, c->eps_v, c->t2, c->vvvo, c->oovo, c->ooov,

@@ -62,6 +62,7 @@ enum BufId {
   B_WS_W, B_WS_TT, B_OMT, B_OM1,
   B_R2, B_HVVVO, B_HOOVO, B_HF, B_ZV, B_ZO, B_VVOO, B_OOOO,
   B_RHOT, B_RHO1, B_TT_TAU, B_SCRATCH, B_SLOTEXP,
+  B_WS_WR, B_WS_TTR, B_MJ, B_CHOL, B_R1,
   B_COUNT
 };
 
@@ -114,9 +115,10 @@ struct cc3_ctx {
   // Jacobian cache (Algorithm 2 intermediates)
   double *Zv = nullptr, *Zo = nullptr;
   bool prep_valid = false;
-  // Jacobian per-vector scratch
+  // Jacobian scratch (per call)
   double *R2 = nullptr, *hvvvo = nullptr, *hoovo = nullptr, *hF = nullptr,
          *rhot = nullptr, *rho1 = nullptr, *Mj = nullptr;
+  void *jac = nullptr;  // Jacobian state private to jacobian.cu
   // driver state private to api.cu / split path state private to split.cu
   void *ext = nullptr;
   void *split = nullptr;
@@ -156,7 +158,14 @@ int launch_transpose_ooov_to_oovo(const double *ooov, double *oovo, int no,
                                   int nv, cudaStream_t s);
 int launch_zero(double *p, size_t n, cudaStream_t s);
 
-// plans (plans.cu)
+// plans (plans.cu): operand / output descriptors and job builders
+Opnd op(int buf, long long off, long long sm0, long long sk0, long long sb = 0, int neg = 0);
+Opnd with_m2(Opnd o, int m_in, long long sm1);
+Opnd with_k2(Opnd o, int k_in, long long sk1);
+OutD out(int buf, long long off, long long sm0, long long sn0, long long sb = 0);
+// kind 0: 64 x 64 tiles, kind 1: 256 x 4 tiles
+int new_job(Plan &P, int kind, int M, int N, int Nm, int batch, int ksplit, int mode);
+void add_term(Plan &P, int job, const Opnd &A, const Opnd &B, int K, const Opnd *Bt = nullptr);
 struct TermSet { int bt, bv, bo; };  // (t-like, vvvo-like, oovo-like) buffers
 void plan_w_build(Plan &P, int no, int nv, const int ijk[3], int slot,
                   int buf_w, const TermSet *sets, int nsets, double w,
@@ -166,4 +175,7 @@ void plan_omega_contractions(Plan &P, int no, int nv, const int ijk[3],
                              int buf_ooov, bool vvov_from_vvvo, int buf_vvov,
                              int buf_omt, int buf_om1, int ksplit, int which);
 double nominal_flop_omega(int no, int nv, int ntri_weighted);
+
+// Jacobian state (jacobian.cu)
+void jacobian_destroy(cc3_ctx *c);
 }  // namespace cc3

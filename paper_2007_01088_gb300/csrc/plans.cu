@@ -23,8 +23,7 @@ namespace cc3 {
 
 static const int BIG = 1 << 30;
 
-static Opnd op(int buf, long long off, long long sm0, long long sk0,
-               long long sb = 0, int neg = 0) {
+Opnd op(int buf, long long off, long long sm0, long long sk0, long long sb, int neg) {
   Opnd o;
   o.buf = buf;
   o.m_in = BIG;
@@ -38,18 +37,17 @@ static Opnd op(int buf, long long off, long long sm0, long long sk0,
   o.sk0 = sk0;
   return o;
 }
-static Opnd with_m2(Opnd o, int m_in, long long sm1) {
+Opnd with_m2(Opnd o, int m_in, long long sm1) {
   o.m_in = m_in;
   o.sm1 = sm1;
   return o;
 }
-static Opnd with_k2(Opnd o, int k_in, long long sk1) {
+Opnd with_k2(Opnd o, int k_in, long long sk1) {
   o.k_in = k_in;
   o.sk1 = sk1;
   return o;
 }
-static OutD out(int buf, long long off, long long sm0, long long sn0,
-                long long sb = 0) {
+OutD out(int buf, long long off, long long sm0, long long sn0, long long sb) {
   OutD c;
   c.buf = buf;
   c.m_in = BIG;
@@ -69,8 +67,7 @@ static void tile_dims(int kind, int *BM, int *BN) {
 }
 
 // Appends a job; returns its index.  Terms are appended with add_term.
-static int new_job(Plan &P, int kind, int M, int N, int Nm, int batch,
-                   int ksplit, int mode) {
+int new_job(Plan &P, int kind, int M, int N, int Nm, int batch, int ksplit, int mode) {
   int BM, BN;
   tile_dims(kind, &BM, &BN);
   Job j{};
@@ -91,8 +88,7 @@ static int new_job(Plan &P, int kind, int M, int N, int Nm, int batch,
   P.jobs.push_back(j);
   return (int)P.jobs.size() - 1;
 }
-static void add_term(Plan &P, int job, const Opnd &A, const Opnd &B, int K,
-                     const Opnd *Bt = nullptr) {
+void add_term(Plan &P, int job, const Opnd &A, const Opnd &B, int K, const Opnd *Bt) {
   Term t;
   t.A = A;
   t.B = B;
