@@ -6,8 +6,15 @@ the four contractions, back-transform and energy) on the seeded synthetic
 no = 16, nv = 160 problem, inputs resident in HBM.  The metric is nominal
 TFLOP/s with 4 nv^4 no^3 FLOP per evaluation (the paper's convention).
 
+The default is the split-precision (BF16 slice) tensor-core path; at one GPU
+the same problem is then evaluated once on the native FP64 path, and the line
+reports the split result's error against it (dE_T, max |dOmega|) and the
+speedup.  The kernel-level roofline comes from in-library CUDA-event tracing
+of every launch inside the timed region.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec split|fp64]
   python bench.py --impl reference ...    (the FP64 CPU oracle, bounded sample)
+  python bench.py --no 6 --nv 160 ...     (smaller problem, for profiling)
 
 Multi-GPU (torchrun): every rank evaluates its own independent problem of the
 same size (weak scaling, no collective on the data path); rank 0 prints the
@@ -32,6 +39,12 @@ sys.path.insert(0, ROOT)
 METRIC = "CC3 triples TFLOP/s (4 nv^4 no^3 per Omega) vs FP64 at dE<=1e-8 Eh; p99 lat"
 NO, NV = 16, 160
 WORKLOAD = "CC3 triples residual, no=16 nv=160, seeded synthetic (Cholesky-like integrals, MP2 t2)"
+
+
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
+# the dominant kernel from one ncu capture of the same workload; None where no
+# capture of the current kernel exists.
+TRAFFIC = {("split_engine_kernel", 16, 160): 6.39e9}
 
 
 def peaks():
@@ -131,7 +144,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     from cc3_inputs import make_inputs
-    inp = make_inputs(NO, NV, seed=0)
+    inp = make_inputs(args.no, args.nv, seed=0)
     vals = []
     per_step = max(5.0, 60.0 / max(1, args.steps + args.warmup))
     for s in range(args.warmup + args.steps):
@@ -144,7 +157,8 @@ def run_reference(args):
             "ms_per_step": 1e3 * statistics.median([x["seconds"] for x in vals]),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "no": NO, "nv": NV, "prec": "fp64-cpu-oracle"},
+            "config": {"workload": WORKLOAD.replace(f"no={NO} nv={NV}", f"no={args.no} nv={args.nv}"),
+                       "no": args.no, "nv": args.nv, "prec": "fp64-cpu-oracle"},
             "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": vals[-1]["cores"],
                              "kind": "oracle", "sample": vals[-1]["sample"]},
             "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
@@ -153,17 +167,37 @@ def run_reference(args):
     return 0
 
 
+# kernel of each tracer class (the split engine serves two classes)
+KERNEL_OF = {"fp64_engine": "fp64_engine_kernel", "fp64_elementwise": "elementwise",
+             "split_w_build": "split_engine_kernel", "split_omega": "split_engine_kernel",
+             "split_elementwise": "elementwise", "output": "elementwise"}
+
+
+def per_kernel(traces):
+    out = {}
+    for k, v in traces.items():
+        a = out.setdefault(KERNEL_OF.get(k, k), dict(launches=0, ms=0.0, flop=0.0, slice_flop=0.0))
+        for f in a:
+            a[f] += v[f]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native")
-    ap.add_argument("--prec", default="fp64", choices=["split", "fp64"])
+    ap.add_argument("--prec", default="split", choices=["split", "fp64"])
+    ap.add_argument("--no", type=int, default=NO, help="occupied orbitals (profiling cases)")
+    ap.add_argument("--nv", type=int, default=NV, help="virtual orbitals (profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = 3 if args.prec == "fp64" else 10
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be at least 3")
     if args.impl == "reference":
         return run_reference(args)
 
@@ -177,14 +211,17 @@ def main():
     torch.cuda.set_device(dev)
     import paper_2007_01088_gb300 as g
     from cc3_inputs import make_inputs
+    no, nv = args.no, args.nv
+    workload = WORKLOAD if (no, nv) == (NO, NV) else WORKLOAD.replace(
+        f"no={NO} nv={NV}", f"no={no} nv={nv}")
     prec = g.CC3_SPLIT_BF16 if args.prec == "split" else g.CC3_FP64
-    inp = make_inputs(NO, NV, seed=rank)
+    inp = make_inputs(no, nv, seed=rank)
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         ctx = g.Context(inp, device=True, stream=stream)
         ctx.set_tracing(True)
-        out = (torch.empty((NO, NV), dtype=torch.float64, device=dev),
-               torch.empty((NO, NO, NV, NV), dtype=torch.float64, device=dev),
+        out = (torch.empty((no, nv), dtype=torch.float64, device=dev),
+               torch.empty((no, no, nv, nv), dtype=torch.float64, device=dev),
                torch.empty((1,), dtype=torch.float64, device=dev))
         for _ in range(args.warmup):
             ctx.omega(prec, out=out)
@@ -209,6 +246,8 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         clk = clocks.stop()
+        if ws > 1:
+            torch.distributed.barrier()
     ms = e0.elapsed_time(e1) / args.steps
     cnt = ctx.counters()
     flop = cnt["nominal_flop"]
@@ -218,60 +257,89 @@ def main():
     ms_max = float(tmax.item())
     value = ws * flop / (ms_max * 1e-3) / 1e12
 
-    # end to end through the public API with host buffers: upload of the
-    # inputs, the evaluation and the download of Omega1, Omega2, E_T
-    h2d = sum(getattr(inp, n).nbytes for n in
-              ["eps_o", "eps_v", "t2", "g_vvvo", "g_ooov", "g_ovov", "F_ov"])
-    d2h = 8 * (NO * NV + NO * NO * NV * NV + 1)
+    # the same evaluation on the native FP64 path: error of the split result
+    # and its speedup (rank 0 at N = 1; one warm-up call builds the FP64 plans)
+    fp64 = None
+    if prec == g.CC3_SPLIT_BF16 and ws == 1 and not args.no_fp64_compare:
+        ref = (torch.empty_like(out[0]), torch.empty_like(out[1]), torch.empty_like(out[2]))
+        with torch.cuda.stream(stream):
+            ctx.omega(g.CC3_FP64, out=ref)
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            ctx.omega(g.CC3_FP64, out=ref)
+            f1.record(stream)
+        torch.cuda.synchronize()
+        fms = f0.elapsed_time(f1)
+        fval = flop / (fms * 1e-3) / 1e12
+        fp64 = {"value": fval, "unit": "TFLOP/s", "ms_per_step": fms,
+                "dE_T_Eh": abs(float(out[2][0] - ref[2][0])),
+                "E_T_Eh": float(ref[2][0]),
+                "max_abs_dOmega1": float((out[0] - ref[0]).abs().max()),
+                "max_abs_dOmega2": float((out[1] - ref[1]).abs().max()),
+                "split_speedup": value / fval}
+
+    # end to end through the public API with host buffers: context creation
+    # (upload of the inputs from pinned host memory), the evaluation and the
+    # download of Omega1, Omega2, E_T into pinned host memory
+    names = ["eps_o", "eps_v", "t2", "g_vvvo", "g_ooov", "g_ovov", "F_ov"]
+    from types import SimpleNamespace
+    pinned = SimpleNamespace(no=no, nv=nv, chol_L=None, **{
+        n: torch.from_numpy(np.ascontiguousarray(getattr(inp, n))).pin_memory() for n in names})
+    hout = tuple(torch.empty(s, dtype=torch.float64).pin_memory()
+                 for s in [(no, nv), (no, no, nv, nv), (1,)])
+    h2d = sum(getattr(pinned, n).numel() * 8 for n in names)
+    d2h = sum(t.numel() * 8 for t in hout)
     e2e_steps = max(1, min(args.steps, 3))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        hc = g.Context(inp, device=False)
-        hc.omega(prec)
+        hc = g.Context(pinned, device=False, stream=stream)
+        hc.omega(prec, out=hout)
         hc.close()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if ws > 1:
+        te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(te.item())
 
     pk, src = peaks()
-    ratio = 1.25 / 2250.0  # nominal FP64 / dense BF16 of GB300
-    if prec == g.CC3_FP64:
-        peak = pk["bf16_tflops"] * ratio
-        roof = {"bound": "tensor", "achieved": flop / (ms * 1e-3) / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "frac": None, "traffic": None,
-                "peak_source": f"{src} bf16 burst x nominal FP64/BF16 ratio (1.25/2250)"}
+    ratio = 1.25 / 2250.0  # nominal FP64 / dense BF16 tensor rate of GB300
+    kern = per_kernel(traces)
+    dom_name, d = max(kern.items(), key=lambda kv: kv[1]["ms"])
+    total_ms = sum(v["ms"] for v in kern.values())
+    if dom_name == "fp64_engine_kernel":
+        roof = {"bound": "tensor", "achieved": d["flop"] / (d["ms"] * 1e-3) / 1e12,
+                "peak": pk["bf16_tflops"] * ratio, "unit": "TFLOP/s",
+                "peak_source": f"FP64: {src} bf16 burst x nominal FP64/BF16 ratio (1.25/2250)"}
     else:
-        peak = pk["bf16_tflops"]
-        roof = {"bound": "tensor", "achieved": None, "peak": peak, "unit": "TFLOP/s",
-                "frac": None, "traffic": None, "peak_source": f"{src} bf16 burst"}
-    # dominant kernel class by device time (CUDA events on the launching stream)
-    dom = max(traces.items(), key=lambda kv: kv[1]["ms"])
-    name, d = dom
-    total_ms = sum(v["ms"] for v in traces.values())
-    if prec == g.CC3_FP64:
-        roof["achieved"] = d["flop"] / (d["ms"] * 1e-3) / 1e12
-    else:
-        roof["achieved"] = d["slice_flop"] / (d["ms"] * 1e-3) / 1e12
-        roof["fp64_equivalent_tflops"] = d["flop"] / (d["ms"] * 1e-3) / 1e12
-    roof["kernel"] = name
+        roof = {"bound": "tensor", "achieved": d["slice_flop"] / (d["ms"] * 1e-3) / 1e12,
+                "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                "peak_source": f"{src} bf16 burst",
+                "fp64_equivalent_tflops": d["flop"] / (d["ms"] * 1e-3) / 1e12}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = TRAFFIC.get((dom_name, no, nv))
+    roof["kernel"] = dom_name
     roof["kernel_share"] = d["ms"] / total_ms if total_ms > 0 else None
     roof["kernel_avg_launch_ms"] = d["ms"] / max(1, d["launches"])
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["classes"] = {k: {"ms_per_step": v["ms"] / args.steps,
+    roof["kernels"] = {k: {"ms_per_step": v["ms"] / args.steps,
                            "launches_per_step": v["launches"] / args.steps}
-                       for k, v in traces.items() if v["launches"]}
+                       for k, v in kern.items() if v["launches"]}
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == g.CC3_FP64 else "bf16",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "no": NO, "nv": NV,
+            "config": {"workload": workload, "no": no, "nv": nv,
                        "prec": args.prec, "parallelism": f"replicas{ws}",
-                       "l2": "inputs larger than L2 (g_vvvo 524 MB)"},
+                       "l2": f"inputs larger than L2 (g_vvvo {nv ** 3 * no * 8 / 1e6:.0f} MB)"},
             "roofline": roof,
             "e2e": {"value": ws * flop / e2e_s / 1e12, "unit": "TFLOP/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches), "clocks": clk,
             "executed_flop_per_step": cnt["executed_flop"]}
+    if fp64 is not None:
+        line["fp64"] = fp64
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = {k: v for k, v in oracle_sample(inp).items()
                                 if k in ("value", "unit", "cores", "kind", "sample")}

@@ -26,6 +26,8 @@ __all__ = ["CC3_FP64", "CC3_SPLIT_BF16", "CC3_SPLIT_INT8", "CC3_DEVICE_PTRS",
 
 CC3_FP64, CC3_SPLIT_BF16, CC3_SPLIT_INT8 = 0, 1, 2
 CC3_DEVICE_PTRS, CC3_DETERMINISTIC = 1, 2
+(CC3_OK, CC3_ERR_ARG, CC3_ERR_OOM, CC3_ERR_CUDA, CC3_ERR_TIMEOUT, CC3_ERR_DENOM, CC3_ERR_BUSY,
+ CC3_ERR_UNSUPPORTED, CC3_ERR_NOT_FOUND, CC3_ERR_CANCELLED) = range(0, -10, -1)
 
 # every symbol include/cc3.h declares
 EXPORTED = ["cc3_ctx_create", "cc3_ctx_destroy", "cc3_ctx_set_triples",
