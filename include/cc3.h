@@ -213,15 +213,33 @@ typedef struct {
   size_t hbm_in_use, hbm_peak;
 } cc3_stats;
 
+/* Starts a server on the current device with max_slots (1..64) worker
+ * threads, each with its own CUDA stream; at most max_slots requests run at
+ * once.  hbm_budget_bytes bounds the summed device footprint of the running
+ * requests (0: 90 % of the free device memory at start). */
 int cc3_serve_start(cc3_server **out, size_t hbm_budget_bytes, int max_slots);
-/* Copies the request's inputs (host pointers) at submit; returns a ticket. */
+/* Device bytes a request needs while it runs (inputs, workspace, the
+ * Jacobian's intermediates and per-vector buffers); the admission test. */
+int cc3_serve_footprint(const cc3_request *req, size_t *bytes);
+/* Copies the request's inputs (host pointers) at submit and queues it;
+ * returns a ticket.  CC3_ERR_BUSY if its footprint exceeds the budget (it
+ * could never be admitted), CC3_ERR_ARG for an invalid request.  Admission is
+ * first fit in arrival order, as slots and budget free up; a request that has
+ * waited more than 10 s blocks later arrivals from overtaking it. */
 int cc3_serve_submit(cc3_server *srv, const cc3_request *req, uint64_t *ticket);
+/* *done = 1 once the request has completed, failed or been cancelled. */
 int cc3_serve_poll(cc3_server *srv, uint64_t ticket, int *done);
 /* Waits up to timeout_s (< 0: forever); writes the outputs into the pointers
- * given at submit and returns the request's status. */
+ * given at submit, releases the ticket and returns the request's status
+ * (CC3_ERR_TIMEOUT if it is still running: the ticket stays valid). */
 int cc3_serve_wait(cc3_server *srv, uint64_t ticket, double timeout_s);
+/* A queued request is dropped; a running one finishes on the device and its
+ * result is discarded (wait then returns CC3_ERR_CANCELLED). */
 int cc3_serve_cancel(cc3_server *srv, uint64_t ticket);
 int cc3_serve_stats(cc3_server *srv, cc3_stats *out);
+/* Cancels the queued requests, lets the running ones finish, joins the
+ * workers and frees the server.  No other call on srv may be in progress or
+ * follow. */
 int cc3_serve_stop(cc3_server *srv);
 
 #ifdef __cplusplus

@@ -36,7 +36,7 @@ EXPORTED = ["cc3_ctx_create", "cc3_ctx_destroy", "cc3_ctx_set_triples",
             "cc3_serve_submit", "cc3_serve_poll", "cc3_serve_wait",
             "cc3_serve_cancel", "cc3_serve_stats", "cc3_serve_stop",
             "cc3_debug_split_gemm", "cc3_last_error", "cc3_ctx_set_tracing",
-            "cc3_ctx_trace", "cc3_omega_triples_noalloc"]
+            "cc3_ctx_trace", "cc3_omega_triples_noalloc", "cc3_serve_footprint"]
 
 
 class CC3Error(RuntimeError):
@@ -59,6 +59,25 @@ class Trace(ctypes.Structure):
 class Counters(ctypes.Structure):
     _fields_ = [("nominal_flop", ctypes.c_double), ("executed_flop", ctypes.c_double),
                 ("launches", ctypes.c_longlong), ("slices", ctypes.c_int)]
+
+
+class Request(ctypes.Structure):
+    """cc3_request: one residual (kind 0) or Jacobian (kind 1) evaluation."""
+    _fields_ = ([("kind", ctypes.c_int), ("prec", ctypes.c_int), ("no", ctypes.c_int),
+                 ("nv", ctypes.c_int), ("naux", ctypes.c_int)]
+                + [(n, ctypes.c_void_p) for n in ("eps_o", "eps_v", "t2", "g_vvvo", "g_ooov",
+                                                  "g_ovov", "F_ov", "chol_L")]
+                + [("nvec", ctypes.c_int)]
+                + [(n, ctypes.c_void_p) for n in ("omega", "R1", "R2", "Omega1", "Omega2",
+                                                  "E_T", "rho1", "rho2")])
+
+
+class Stats(ctypes.Structure):
+    _fields_ = ([(n, ctypes.c_longlong) for n in ("submitted", "admitted", "completed",
+                                                  "rejected", "cancelled")]
+                + [(n, ctypes.c_double) for n in ("p50_ms", "p99_ms", "mean_ms", "busy_s",
+                                                  "wall_s", "nominal_flop")]
+                + [("hbm_in_use", ctypes.c_size_t), ("hbm_peak", ctypes.c_size_t)])
 
 
 def _load():
@@ -89,6 +108,23 @@ def _load():
     L.cc3_ctx_trace.restype = I
     L.cc3_omega_triples_noalloc.argtypes = [I, I] + [P] * 7 + [P, P, P, P]
     L.cc3_omega_triples_noalloc.restype = I
+    RP = ctypes.POINTER(Request)
+    L.cc3_serve_start.argtypes = [ctypes.POINTER(P), ctypes.c_size_t, I]
+    L.cc3_serve_start.restype = I
+    L.cc3_serve_footprint.argtypes = [RP, ctypes.POINTER(ctypes.c_size_t)]
+    L.cc3_serve_footprint.restype = I
+    L.cc3_serve_submit.argtypes = [P, RP, ctypes.POINTER(ctypes.c_uint64)]
+    L.cc3_serve_submit.restype = I
+    L.cc3_serve_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(I)]
+    L.cc3_serve_poll.restype = I
+    L.cc3_serve_wait.argtypes = [P, ctypes.c_uint64, D]
+    L.cc3_serve_wait.restype = I
+    L.cc3_serve_cancel.argtypes = [P, ctypes.c_uint64]
+    L.cc3_serve_cancel.restype = I
+    L.cc3_serve_stats.argtypes = [P, ctypes.POINTER(Stats)]
+    L.cc3_serve_stats.restype = I
+    L.cc3_serve_stop.argtypes = [P]
+    L.cc3_serve_stop.restype = I
     L.cc3_last_error.argtypes = []
     L.cc3_last_error.restype = ctypes.c_char_p
     L.cc3_strerror.argtypes = [I]
@@ -299,3 +335,132 @@ class Context:
         r2 = self._new((nvec, no, no, nv, nv))
         cc3_jacobian_triples(self.ctx, prec, nvec, omega, R1, R2, r1, r2, self.stream)
         return r1, r2
+
+
+# ---- serving ----------------------------------------------------------------
+def cc3_serve_start(hbm_budget_bytes=0, max_slots=4):
+    srv = ctypes.c_void_p()
+    _check(lib.cc3_serve_start(ctypes.byref(srv), int(hbm_budget_bytes), int(max_slots)),
+           "cc3_serve_start")
+    return srv
+
+
+def cc3_serve_footprint(req):
+    b = ctypes.c_size_t(0)
+    _check(lib.cc3_serve_footprint(ctypes.byref(req), ctypes.byref(b)), "cc3_serve_footprint")
+    return int(b.value)
+
+
+def cc3_serve_submit(srv, req):
+    t = ctypes.c_uint64(0)
+    _check(lib.cc3_serve_submit(srv, ctypes.byref(req), ctypes.byref(t)), "cc3_serve_submit")
+    return int(t.value)
+
+
+def cc3_serve_poll(srv, ticket):
+    d = ctypes.c_int(0)
+    _check(lib.cc3_serve_poll(srv, ctypes.c_uint64(ticket), ctypes.byref(d)), "cc3_serve_poll")
+    return bool(d.value)
+
+
+def cc3_serve_wait(srv, ticket, timeout_s=-1.0):
+    """Returns the request's status (raises only for an unknown ticket)."""
+    st = lib.cc3_serve_wait(srv, ctypes.c_uint64(ticket), float(timeout_s))
+    if st == CC3_ERR_NOT_FOUND:
+        _check(st, "cc3_serve_wait")
+    return st
+
+
+def cc3_serve_cancel(srv, ticket):
+    _check(lib.cc3_serve_cancel(srv, ctypes.c_uint64(ticket)), "cc3_serve_cancel")
+
+
+def cc3_serve_stats(srv):
+    st = Stats()
+    _check(lib.cc3_serve_stats(srv, ctypes.byref(st)), "cc3_serve_stats")
+    return {n: getattr(st, n) for n, _ in Stats._fields_}
+
+
+def cc3_serve_stop(srv):
+    _check(lib.cc3_serve_stop(srv), "cc3_serve_stop")
+
+
+def _f64(x):
+    return None if x is None else np.ascontiguousarray(x, dtype=np.float64)
+
+
+class Server:
+    """Owns one cc3_server.  ``submit_omega`` / ``submit_jacobian`` take host
+    inputs with the fields of cc3_inputs.CC3Inputs (copied at submit) and
+    return a ticket; ``wait`` returns (status, outputs)."""
+
+    def __init__(self, hbm_budget_bytes=0, max_slots=4):
+        self.srv = cc3_serve_start(hbm_budget_bytes, max_slots)
+        self._out = {}
+
+    def _request(self, kind, prec, inp, nvec=0, omega=None, R1=None, R2=None):
+        keep = {n: _f64(getattr(inp, n)) for n in ("eps_o", "eps_v", "t2", "g_vvvo", "g_ooov",
+                                                   "g_ovov", "F_ov")}
+        L = getattr(inp, "chol_L", None)
+        keep["chol_L"] = _f64(L)
+        keep["omega"], keep["R1"], keep["R2"] = _f64(omega), _f64(R1), _f64(R2)
+        r = Request()
+        r.kind, r.prec, r.no, r.nv = int(kind), int(prec), int(inp.no), int(inp.nv)
+        r.naux = 0 if L is None else int(L.shape[0])
+        r.nvec = int(nvec)
+        for n, a in keep.items():
+            setattr(r, n, None if a is None else a.ctypes.data)
+        no, nv = int(inp.no), int(inp.nv)
+        if kind == 0:
+            out = (np.empty((no, nv)), np.empty((no, no, nv, nv)), np.empty(1))
+            r.Omega1, r.Omega2, r.E_T = (o.ctypes.data for o in out)
+        else:
+            out = (np.empty((nvec, no, nv)), np.empty((nvec, no, no, nv, nv)))
+            r.rho1, r.rho2 = (o.ctypes.data for o in out)
+        return r, keep, out
+
+    def footprint(self, kind, prec, inp, nvec=0, omega=None, R1=None, R2=None):
+        r, _keep, _out = self._request(kind, prec, inp, nvec, omega, R1, R2)
+        return cc3_serve_footprint(r)
+
+    def submit_omega(self, inp, prec=CC3_FP64):
+        r, keep, out = self._request(0, prec, inp)
+        t = cc3_serve_submit(self.srv, r)
+        self._out[t] = out
+        return t
+
+    def submit_jacobian(self, inp, R1, R2, omega, prec=CC3_FP64):
+        R1 = _f64(R1)
+        nvec = int(R1.shape[0])
+        w = np.broadcast_to(np.asarray(omega, dtype=np.float64), (nvec,))
+        r, keep, out = self._request(1, prec, inp, nvec, w, R1, R2)
+        t = cc3_serve_submit(self.srv, r)
+        self._out[t] = out
+        return t
+
+    def poll(self, ticket):
+        return cc3_serve_poll(self.srv, ticket)
+
+    def wait(self, ticket, timeout_s=-1.0):
+        st = cc3_serve_wait(self.srv, ticket, timeout_s)
+        if st == CC3_ERR_TIMEOUT:
+            return st, None
+        return st, self._out.pop(ticket, None)
+
+    def cancel(self, ticket):
+        cc3_serve_cancel(self.srv, ticket)
+
+    def stats(self):
+        return cc3_serve_stats(self.srv)
+
+    def stop(self):
+        if getattr(self, "srv", None):
+            cc3_serve_stop(self.srv)
+            self.srv = None
+            self._out.clear()
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass

@@ -159,13 +159,7 @@ int default_triples(cc3_ctx *c) {
   return CC3_OK;
 }
 
-int choose_batch(cc3_ctx *c) {
-  const double nv3b = (double)c->nv * c->nv * c->nv * sizeof(double);
-  const double budget = 4.0e9;  // two nv^3 buffers per triple in flight
-  int b = (int)std::max(1.0, std::min(32.0, budget / (2.0 * nv3b)));
-  b = std::min(b, std::max(1, c->ntri));
-  return b;
-}
+int choose_batch(cc3_ctx *c) { return batch_for(c->nv, c->ntri); }
 
 int alloc_workspace(cc3_ctx *c) {
   const size_t nv3 = (size_t)c->nv * c->nv * c->nv;
@@ -180,6 +174,28 @@ int alloc_workspace(cc3_ctx *c) {
 }  // namespace
 
 namespace cc3 {
+// Triples per batch of the FP64 path: two nv^3 buffers per triple in flight,
+// about 4 GB in all, at most 32.
+int batch_for(int nv, int ntri) {
+  const double nv3b = (double)nv * nv * nv * sizeof(double);
+  int b = (int)std::max(1.0, std::min(32.0, 4.0e9 / (2.0 * nv3b)));
+  return std::min(b, std::max(1, ntri));
+}
+
+// Device bytes held by a context after cc3_ctx_create and one FP64 residual
+// call (inputs, the oovo copy, outputs, the FP64 workspace and plan tables).
+size_t ctx_footprint(int no, int nv, int naux, int ntri, bool host_io) {
+  const size_t nt2 = (size_t)no * no * nv * nv, nvvvo = (size_t)nv * nv * nv * no,
+               nooov = (size_t)no * no * no * nv, n = (size_t)no + nv;
+  size_t d = no + nv + nt2 + nvvvo + 2 * nooov + nt2 + (size_t)no * nv;  // inputs + oovo
+  d += (size_t)naux * n * n;
+  d += nt2 + (size_t)no * nv + 257;  // omt, om1, energy scratch
+  if (host_io) d += nt2;             // Omega2 staging
+  d += 2 * (size_t)nv * nv * nv * batch_for(nv, ntri);
+  const size_t plans = (size_t)std::max(1, ntri) * 8 * (sizeof(Job) + 2 * sizeof(Term));
+  return d * sizeof(double) + plans + 4096;
+}
+
 static thread_local char g_last_error[512] = "";
 int record_error(int status, const char *file, int line, const char *what) {
   const char *base = std::strrchr(file, '/');

@@ -178,4 +178,9 @@ double nominal_flop_omega(int no, int nv, int ntri_weighted);
 
 // Jacobian state (jacobian.cu)
 void jacobian_destroy(cc3_ctx *c);
+
+// device footprints for admission control (api.cu, jacobian.cu)
+int batch_for(int nv, int ntri);
+size_t ctx_footprint(int no, int nv, int naux, int ntri, bool host_io);
+size_t jacobian_footprint(int no, int nv, int naux, int nvec, int ntri, bool host_io);
 }  // namespace cc3

@@ -442,6 +442,22 @@ int jacobian_fp64(cc3_ctx *c, int nvec, const double *w, const double *R1d, cons
   return rc;
 }
 
+// Device bytes of the Jacobian's cached blocks, Algorithm 2 intermediates,
+// R3 workspace and per-call buffers (the same arithmetic as the allocations
+// above), for admission control.
+size_t jacobian_footprint(int no, int nv, int naux, int nvec, int ntri, bool host_io) {
+  const size_t nv3 = (size_t)nv * nv * nv, nt2 = (size_t)no * no * nv * nv,
+               n1 = (size_t)no * nv, o4 = (size_t)no * no * no * no;
+  size_t d = o4 + nt2;                               // oooo, oovv
+  d += nv3 * no + (size_t)nv * no * no * no;         // Zv, Zo
+  d += 2 * nv3 * batch_for(nv, ntri);                // R3 workspace
+  d += (size_t)nvec * (nv3 * no + (size_t)no * no * nv * no + n1 + nt2 + n1);  // per vector
+  d += (size_t)naux * nv * no;                       // M^J_ck
+  if (host_io) d += (size_t)nvec * 2 * (n1 + nt2);   // staging of R and rho
+  const size_t plans = (size_t)std::max(1, ntri) * 24 * (sizeof(Job) + 2 * sizeof(Term));
+  return d * sizeof(double) + plans + 4096;
+}
+
 void jacobian_destroy(cc3_ctx *c) {
   JacState *J = reinterpret_cast<JacState *>(c->jac);
   if (!J) return;

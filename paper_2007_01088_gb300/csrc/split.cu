@@ -547,6 +547,32 @@ int split_omega(cc3_ctx *c, cudaStream_t st) {
   return CC3_OK;
 }
 
+// Device bytes of the split path's staged slices and workspace (the same
+// arithmetic as stage()), for admission control.
+size_t split_footprint(int no, int nv, int s, int ntri) {
+  const int vp = rup(nv, 16), op = rup(no, 16);
+  const long long nv2 = (long long)nv * nv;
+  auto sl = [&](long long rows, long long Kp, long long rps) {
+    return arr_elems(Kp, rps, rows / rps, s) * sizeof(__nv_bfloat16);
+  };
+  size_t b = 0;
+  b += sl((long long)no * no * nv, vp, nv);           // T2S
+  b += 2 * sl((long long)no * nv * nv, op, nv);       // T2C, T2R
+  b += 2 * sl((long long)no * nv * nv, vp, nv);       // XS, YS
+  b += sl((long long)no * no * nv, op, nv);           // OS
+  b += 2 * sl((long long)no * nv, (long long)nv * vp, nv);  // Zg, Zh
+  b += sl((long long)no * no * (no + 1), vp, no + 1);  // OO
+  b += (size_t)no * no * (no + 1) * nv * sizeof(double);  // its FP64 staging copy
+  b += sl((long long)no * no, (long long)nv * vp, 1);  // OV
+  const double per_slot = (double)nv2 * nv * 16.0 + 3.0 * s * nv2 * vp * 2.0;
+  int batch = (int)std::max(1.0, std::min(16.0, 6.0e9 / per_slot));
+  batch = std::min(batch, std::max(1, ntri));
+  b += 2 * (size_t)batch * nv2 * nv * sizeof(float2);  // Wdd, TTdd
+  b += 3 * arr_elems((long long)nv * vp, nv, batch, s) * sizeof(__nv_bfloat16);  // V[3]
+  b += (size_t)nv * sizeof(float2) + 4096;
+  return b;
+}
+
 void split_invalidate(cc3_ctx *c) {
   SplitState *S = state(c);
   if (S) S->planned = false;

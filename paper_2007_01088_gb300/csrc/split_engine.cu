@@ -26,6 +26,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include <algorithm>
 
 #include <cuda_bf16.h>
@@ -398,8 +400,14 @@ int s_launch_plan(const SDevPlan &d, const SArrTable &arrs, const VPtrTable &ptr
   if (slices < 3 || slices > S_MAX_SLICES) return CC3_ERR_ARG;
   // at least 120 KB so that one CTA (and one 512-column TMEM allocation) per SM
   const size_t smem = std::max<size_t>(s_smem_bytes(slices, S_NT_MAX), 120 * 1024);
-  static bool attr_set = false;
-  if (!attr_set) {
+  // per device, once; several host threads (serving slots) may get here at once
+  static std::mutex attr_mu;
+  static bool attr_set[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return CC3_FAIL(CC3_ERR_CUDA, "device index");
+  std::lock_guard<std::mutex> attr_lk(attr_mu);
+  if (!attr_set[dev]) {
     const void *fns[] = {(const void *)split_engine_kernel<3>, (const void *)split_engine_kernel<4>,
                          (const void *)split_engine_kernel<5>, (const void *)split_engine_kernel<6>,
                          (const void *)split_engine_kernel<7>};
@@ -413,7 +421,7 @@ int s_launch_plan(const SDevPlan &d, const SArrTable &arrs, const VPtrTable &ptr
       if (e != cudaSuccess || nb < 1)
         return CC3_FAIL(CC3_ERR_CUDA, "split engine kernel does not fit on an SM");
     }
-    attr_set = true;
+    attr_set[dev] = true;
   }
   switch (slices) {
 #define CC3_SPLIT_LAUNCH(S_)                                                              \
