@@ -182,6 +182,109 @@ def per_kernel(traces):
     return out
 
 
+def serve_stream(n_req, rate, no_lo, no_hi, seed=0):
+    """The seeded mixed request stream: Poisson arrivals at `rate` per second,
+    no ~ U{no_lo..no_hi}, nv = round(no * U[6, 10]), a residual or a Jacobian
+    with 1-6 trial vectors (even odds); the inputs of request n use seed n."""
+    from cc3_inputs import make_inputs, make_trial_vectors
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+    t -= t[0]
+    reqs = []
+    for n in range(n_req):
+        r = np.random.default_rng(n)
+        no = int(r.integers(no_lo, no_hi + 1))
+        nv = int(round(no * r.uniform(6.0, 10.0)))
+        kind = "omega" if r.random() < 0.5 else "jacobian"
+        nvec = int(r.integers(1, 7))
+        inp = make_inputs(no, nv, seed=n)
+        R = make_trial_vectors(no, nv, nvec, seed=n) if kind == "jacobian" else None
+        reqs.append(dict(t=float(t[n]), kind=kind, no=no, nv=nv, nvec=nvec, inp=inp, R=R))
+    return reqs
+
+
+def run_serve(args):
+    """Serving: the stream through the continuous-batching server, and the
+    same stream served one request at a time on the FP64 path."""
+    import torch
+    import paper_2007_01088_gb300 as g
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    reqs = serve_stream(args.requests, args.rate, 4, args.max_no)
+    omega_prec = g.CC3_SPLIT_BF16 if args.prec == "split" else g.CC3_FP64
+    jac_prec = g.CC3_FP64
+
+    def submit(srv, q):
+        if q["kind"] == "omega":
+            return srv.submit_omega(q["inp"], omega_prec)
+        R1, R2 = q["R"]
+        return srv.submit_jacobian(q["inp"], R1, R2, [0.25] * q["nvec"], jac_prec)
+
+    # warm-up: the library, the engines' attributes, one small request per kind
+    srv = g.Server(max_slots=args.slots)
+    for q in reqs[:max(args.warmup, 3)]:
+        srv.wait(submit(srv, q))
+    srv.stop()
+    srv = g.Server(max_slots=args.slots)
+    tickets = [None] * len(reqs)
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = time.perf_counter()
+
+    def feeder():
+        for i, q in enumerate(reqs):
+            d = t0 + q["t"] - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tickets[i] = submit(srv, q)
+
+    th = threading.Thread(target=feeder)
+    th.start()
+    th.join()
+    status = [srv.wait(t)[0] for t in tickets]
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    st = srv.stats()
+    srv.stop()
+    # serial one-at-a-time FP64 over the same arrivals
+    service = []
+    for q in reqs:
+        ctx = g.Context(q["inp"])
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        if q["kind"] == "omega":
+            ctx.omega(g.CC3_FP64)
+        else:
+            ctx.jacobian(q["R"][0], q["R"][1], [0.25] * q["nvec"], g.CC3_FP64)
+        service.append(time.perf_counter() - a)
+        ctx.close()
+    done, lat = 0.0, []
+    for q, sv in zip(reqs, service):
+        done = max(done, q["t"]) + sv
+        lat.append(1e3 * (done - q["t"]))
+    flop = st["nominal_flop"]
+    line = {"metric": "CC3 serving throughput (nominal TFLOP/s) with p50/p99 latency",
+            "value": flop / wall / 1e12, "unit": "TFLOP/s", "n_gpus": 1,
+            "steps": 1, "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * wall,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if omega_prec == g.CC3_SPLIT_BF16 else "f64", "data": "synthetic",
+            "config": {"workload": f"serving stream, {len(reqs)} requests, Poisson "
+                                   f"{args.rate}/s, no~U{{4..{args.max_no}}}, nv=round(no*U[6,10]), "
+                                   "residual or Jacobian (1-6 vectors) 50/50",
+                       "slots": args.slots,
+                       "prec": {"omega": args.prec, "jacobian": "fp64"}},
+            "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"], "mean": st["mean_ms"]},
+            "requests": {"completed": st["completed"], "failed": sum(1 for x in status if x != 0),
+                         "rejected": st["rejected"]},
+            "device_busy_frac": st["busy_s"] / wall, "hbm_peak_bytes": st["hbm_peak"],
+            "serial_fp64": {"value": flop / max(done, 1e-9) / 1e12, "unit": "TFLOP/s",
+                            "p50_ms": float(np.percentile(lat, 50)),
+                            "p99_ms": float(np.percentile(lat, 99))},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -193,6 +296,11 @@ def main():
     ap.add_argument("--nv", type=int, default=NV, help="virtual orbitals (profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--workload", default="omega", choices=["omega", "serve"])
+    ap.add_argument("--requests", type=int, default=32, help="serve: requests in the stream")
+    ap.add_argument("--rate", type=float, default=4.0, help="serve: arrivals per second")
+    ap.add_argument("--max-no", type=int, default=12, help="serve: largest no of the stream")
+    ap.add_argument("--slots", type=int, default=4, help="serve: concurrent requests")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = 3 if args.prec == "fp64" else 10
@@ -200,6 +308,8 @@ def main():
         raise SystemExit("--warmup must be at least 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serve":
+        return run_serve(args)
 
     import torch
     ws, rank, local = dist_env()
