@@ -212,7 +212,7 @@ def run_serve(args):
     torch.cuda.set_device(local)
     reqs = serve_stream(args.requests, args.rate, 4, args.max_no)
     omega_prec = g.CC3_SPLIT_BF16 if args.prec == "split" else g.CC3_FP64
-    jac_prec = g.CC3_FP64
+    jac_prec = omega_prec
 
     def submit(srv, q):
         if q["kind"] == "omega":
@@ -272,7 +272,7 @@ def run_serve(args):
                                    f"{args.rate}/s, no~U{{4..{args.max_no}}}, nv=round(no*U[6,10]), "
                                    "residual or Jacobian (1-6 vectors) 50/50",
                        "slots": args.slots,
-                       "prec": {"omega": args.prec, "jacobian": "fp64"}},
+                       "prec": args.prec},
             "latency_ms": {"p50": st["p50_ms"], "p99": st["p99_ms"], "mean": st["mean_ms"]},
             "requests": {"completed": st["completed"], "failed": sum(1 for x in status if x != 0),
                          "rejected": st["rejected"]},

@@ -45,6 +45,7 @@ struct JacState {
   double *wsWR = nullptr, *wsTTR = nullptr;
   int wsb = 0;
   bool blocks = false;
+  int prep_prec = -1;  // precision the cached Z~v, Z~o were built in
 };
 
 JacState *jst(cc3_ctx *c) {
@@ -179,7 +180,7 @@ int tau_batch(cc3_ctx *c, const PtrTable &pt, int t0, int t1, const std::vector<
 // Algorithm 2: Zv[a][b][i][d] -= sum_c tau~^{abc}_{ijk} (jd|kc),
 //              Zo[a][j][i][l] += sum_bc tau~^{abc}_{ijk} (lb|kc)
 int ensure_prep(cc3_ctx *c, JacState *J, const std::vector<double> &eo, cudaStream_t s) {
-  if (c->prep_valid) return CC3_OK;
+  if (c->prep_valid && J->prep_prec == CC3_FP64) return CC3_OK;
   const int no = c->no, nv = c->nv;
   const long long nv2 = (long long)nv * nv, nv3 = nv2 * nv;
   if (!J->Zv) TRY(dalloc(&J->Zv, (size_t)nv3 * no));
@@ -224,6 +225,7 @@ int ensure_prep(cc3_ctx *c, JacState *J, const std::vector<double> &eo, cudaStre
     TRY(run_plan(c, po, 1, pt, s));
   }
   c->prep_valid = true;
+  J->prep_prec = CC3_FP64;
   return CC3_OK;
 }
 
@@ -322,6 +324,90 @@ int dress(cc3_ctx *c, const PtrTable &pt, cudaStream_t s) {
 
 }  // namespace
 
+int jac_blocks(cc3_ctx *c, cudaStream_t s) {
+  JacState *J = jst(c);
+  if (!J) return CC3_ERR_OOM;
+  return ensure_blocks(c, J, s);
+}
+
+int jac_dress(cc3_ctx *c, const double *R1v, double *hv, double *ho, double *hf, double *mj,
+              cudaStream_t s) {
+  JacState *J = jst(c);
+  if (!J) return CC3_ERR_OOM;
+  PtrTable pt;
+  fill_base(c, J, &pt);
+  pt.p[B_R1] = const_cast<double *>(R1v);
+  pt.p[B_MJ] = mj;
+  pt.p[B_HVVVO] = hv;
+  pt.p[B_HOOVO] = ho;
+  pt.p[B_HF] = hf;
+  return dress(c, pt, s);
+}
+
+int jac_z_buffers(cc3_ctx *c, double **Zv, double **Zo, bool zero, cudaStream_t s) {
+  JacState *J = jst(c);
+  if (!J) return CC3_ERR_OOM;
+  const size_t nzv = (size_t)c->nv * c->nv * c->nv * c->no,
+               nzo = (size_t)c->nv * c->no * c->no * c->no;
+  if (!J->Zv) TRY(dalloc(&J->Zv, nzv));
+  if (!J->Zo) TRY(dalloc(&J->Zo, nzo));
+  if (zero) {
+    TRY(launch_zero(J->Zv, nzv, s));
+    TRY(launch_zero(J->Zo, nzo, s));
+  }
+  *Zv = J->Zv;
+  *Zo = J->Zo;
+  return CC3_OK;
+}
+
+void jac_set_prep(cc3_ctx *c, int prec) {
+  JacState *J = jst(c);
+  if (J) J->prep_prec = prec;
+  c->prep_valid = prec >= 0;
+}
+
+int jac_prep_prec(cc3_ctx *c) {
+  JacState *J = jst(c);
+  return (J && c->prep_valid) ? J->prep_prec : -1;
+}
+
+// rho~[p][l][a][b] += sum_d Z~v[a][b][p][d] R1[l][d];
+// rho~[p][q][a][d] -= sum_l Z~o[a][q][p][l] R1[l][d]
+int jac_z_terms(cc3_ctx *c, const double *R1v, double *rtv, cudaStream_t s) {
+  JacState *J = jst(c);
+  if (!J) return CC3_ERR_OOM;
+  const int no = c->no, nv = c->nv;
+  const long long nv2 = (long long)nv * nv;
+  PtrTable pt;
+  fill_base(c, J, &pt);
+  pt.p[B_R1] = const_cast<double *>(R1v);
+  pt.p[B_RHOT] = rtv;
+  Plan pz1, pz0;
+  for (int p = 0; p < no; ++p) {
+    int jb = new_job(pz1, 1, (int)nv2, no, no, 1, 1, EPI_ATOMIC);
+    add_term(pz1, jb, with_m2(op(B_ZV, (long long)p * nv, (long long)nv * no, 1), nv, nv2 * no),
+             op(B_R1, 0, nv, 1), nv);
+    OutD o = out(B_RHOT, (long long)p * no * nv2, 1, nv2);
+    o.m_in = nv;
+    o.sm1 = nv;
+    pz1.jobs[jb].C = o;
+    pz1.jobs[jb].Ct = o;
+    jb = new_job(pz0, 0, nv * no, nv, nv, 1, 1, EPI_ATOMIC);
+    add_term(pz0, jb,
+             with_m2(op(B_ZO, (long long)p * no, (long long)no * no, 1, 0, 1), no,
+                     (long long)no * no * no),
+             op(B_R1, 0, 1, nv), no);
+    o = out(B_RHOT, (long long)p * no * nv2, nv2, 1);
+    o.m_in = no;
+    o.sm1 = nv;
+    pz0.jobs[jb].C = o;
+    pz0.jobs[jb].Ct = o;
+  }
+  TRY(run_plan(c, pz1, 1, pt, s));
+  TRY(run_plan(c, pz0, 0, pt, s));
+  return CC3_OK;
+}
+
 int jacobian_fp64(cc3_ctx *c, int nvec, const double *w, const double *R1d, const double *R2d,
                   double *rho1d, double *rho2d, cudaStream_t s) {
   const int no = c->no, nv = c->nv;
@@ -408,32 +494,9 @@ int jacobian_fp64(cc3_ctx *c, int nvec, const double *w, const double *R1d, cons
       TRY(run_plan(c, pth, 1, pt, s));
     }
   }
-  // Z~v . R1 and Z~o . R1 (outside the triple loop)
+  // Z~v . R1 and Z~o . R1 (outside the triple loop), back-transform
   for (int v = 0; v < nvec; ++v) {
-    const PtrTable pt = vec_ptrs(v);
-    Plan pz1, pz0;
-    for (int p = 0; p < no; ++p) {
-      int jb = new_job(pz1, 1, (int)nv2, no, no, 1, 1, EPI_ATOMIC);
-      add_term(pz1, jb, with_m2(op(B_ZV, (long long)p * nv, (long long)nv * no, 1), nv, nv2 * no),
-               op(B_R1, 0, nv, 1), nv);
-      OutD o = out(B_RHOT, (long long)p * no * nv2, 1, nv2);
-      o.m_in = nv;
-      o.sm1 = nv;
-      pz1.jobs[jb].C = o;
-      pz1.jobs[jb].Ct = o;
-      jb = new_job(pz0, 0, nv * no, nv, nv, 1, 1, EPI_ATOMIC);
-      add_term(pz0, jb,
-               with_m2(op(B_ZO, (long long)p * no, (long long)no * no, 1, 0, 1), no,
-                       (long long)no * no * no),
-               op(B_R1, 0, 1, nv), no);
-      o = out(B_RHOT, (long long)p * no * nv2, nv2, 1);
-      o.m_in = no;
-      o.sm1 = nv;
-      pz0.jobs[jb].C = o;
-      pz0.jobs[jb].Ct = o;
-    }
-    TRY(run_plan(c, pz1, 1, pt, s));
-    TRY(run_plan(c, pz0, 0, pt, s));
+    TRY(jac_z_terms(c, R1d + v * n1, rt + v * nt2, s));
     TRY(launch_back_transform(rt + v * nt2, rho2d + v * nt2, no, nv, s));
     CU(cudaMemcpyAsync(rho1d + v * n1, r1a + v * n1, sizeof(double) * n1,
                        cudaMemcpyDeviceToDevice, s));
@@ -519,7 +582,7 @@ extern "C" int cc3_jacobian_triples(cc3_ctx *c, cc3_prec prec, int nvec, const d
     if (prec == CC3_FP64)
       rc = jacobian_fp64(c, nvec, omega, dR1, dR2, dr1, dr2, s);
     else
-      rc = CC3_ERR_UNSUPPORTED;
+      rc = split_jacobian(c, nvec, omega, dR1, dR2, dr1, dr2, s);
   }
   if (rc == CC3_OK && !dev) {
     if (cudaMemcpyAsync(rho1, dr1, sizeof(double) * n1 * nvec, cudaMemcpyDeviceToHost, s) !=

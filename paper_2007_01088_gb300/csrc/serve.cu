@@ -62,6 +62,8 @@ size_t request_footprint(const cc3_request &q) {
   size_t b = cc3::ctx_footprint(q.no, q.nv, q.naux, ntri, true);
   if (q.prec == CC3_SPLIT_BF16) b += cc3::split_footprint(q.no, q.nv, 6, ntri);
   if (q.kind == 1) b += cc3::jacobian_footprint(q.no, q.nv, q.naux, q.nvec, ntri, true);
+  if (q.kind == 1 && q.prec == CC3_SPLIT_BF16)
+    b += cc3::split_jacobian_footprint(q.no, q.nv, 6, q.nvec);
   return b + kMargin;
 }
 

@@ -78,7 +78,11 @@ int ntile_for(int N) {
 
 enum MapId {
   MA_T2S = 0, MA_T2C, MA_T2R, MA_XS, MA_YS, MA_OS, MA_V0, MA_V1, MA_V2, MA_V0K, MA_V1K, MA_V2K,
-  MB_T2S, MB_T2C, MB_T2R, MB_XS, MB_YS, MB_OS, MB_ZG, MB_ZH, MB_OO, MB_OV, MAP_COUNT
+  MB_T2S, MB_T2C, MB_T2R, MB_XS, MB_YS, MB_OS, MB_ZG, MB_ZH, MB_OO, MB_OV,
+  // Jacobian: per trial vector (R2 in the t2 layouts, g^ in the integral
+  // layouts), F^ of all vectors, and ovov in the layouts of Algorithm 2
+  MJ_R2S, MJ_R2C, MJ_R2R, MJ_XH, MJ_YH, MJ_OH, MJ_FH, MJ_OVD, MJ_OVZA, MJ_OVZB,
+  MAP_COUNT
 };
 static_assert(MAP_COUNT <= SMAX_MAPS, "map table");
 
@@ -87,6 +91,9 @@ struct SplitState {
   int Nab = 0, N3 = 0, N1 = 16;
   __nv_bfloat16 *T2S = nullptr, *T2C = nullptr, *T2R = nullptr, *XS = nullptr, *YS = nullptr,
                 *OS = nullptr, *Zg = nullptr, *Zh = nullptr, *OO = nullptr, *OV = nullptr;
+  // Jacobian (Algorithm 2 layouts of ovov), staged on first use
+  __nv_bfloat16 *OVD = nullptr, *OVZA = nullptr, *OVZB = nullptr;
+  int ks4 = 1;  // K split of the rows-x contractions
   float2 *evdd = nullptr;
   int batch = 0;
   float2 *Wdd = nullptr, *TTdd = nullptr;
@@ -116,7 +123,7 @@ int alloc(T **p, size_t n) {
 
 void free_state_buffers(SplitState *S) {
   void *bufs[] = {S->T2S, S->T2C, S->T2R, S->XS, S->YS, S->OS, S->Zg, S->Zh, S->OO, S->OV,
-                  S->evdd, S->Wdd, S->TTdd, S->V[0], S->V[1], S->V[2], S->vptr, S->maxbits,
+                  S->OVD, S->OVZA, S->OVZB, S->evdd, S->Wdd, S->TTdd, S->V[0], S->V[1], S->V[2], S->vptr, S->maxbits,
                   S->slot_ex, S->status};
   for (void *p : bufs)
     if (p) cudaFree(p);
@@ -341,27 +348,54 @@ void add_sterm(SPlan &P, int job, SOpnd A, SOpnd B, int K, int negA, double &exe
   P.slice_flop += useful * (slices * (slices + 1) / 2);
 }
 
-void plan_w_split(SPlan &pab, SPlan &pc, SplitState *S, int no, int nv, const int ijk[3],
-                  int slot, const float *eo_dd, double &ex) {
-  const int i = ijk[0], j = ijk[1], k = ijk[2], s = S->s;
-  const int vp = S->vp, op = S->op;
+// Slice arrays that play t2 and the (vvvo, oovo) integrals in the W build
+// (the same descriptor serves as A or B operand).
+struct WMaps {
+  int aT2S, bT2S, aT2C, bT2C, aT2R, bT2R, aXS, bXS, aYS, bYS, aOS, bOS;
+};
+const WMaps kStdMaps = {MA_T2S, MB_T2S, MA_T2C, MB_T2C, MA_T2R, MB_T2R,
+                        MA_XS,  MB_XS,  MA_YS,  MB_YS,  MA_OS,  MB_OS};
+
+// phase AB terms of triple (i,j,k): tile (a, b) at fixed c (batch index)
+void w_terms_ab(SPlan &P, int jb, const WMaps &m, int no, int nv, int vp, int op,
+                const int ijk[3], double &ex, int s) {
+  const int i = ijk[0], j = ijk[1], k = ijk[2];
+  add_sterm(P, jb, opd(m.aT2S, i * no + j), opd(m.bXS, k * nv, 1), vp, 0, ex, s);
+  add_sterm(P, jb, opd(m.aT2S, i * no + k), opd(m.bYS, j * nv, 1), vp, 0, ex, s);
+  add_sterm(P, jb, opd(m.aXS, k * nv, 1), opd(m.bT2S, j * no + i), vp, 0, ex, s);
+  add_sterm(P, jb, opd(m.aYS, i * nv, 1), opd(m.bT2S, j * no + k), vp, 0, ex, s);
+  add_sterm(P, jb, opd(m.aOS, k * no + i), opd(m.bT2C, j * nv, 1), op, 1, ex, s);
+  add_sterm(P, jb, opd(m.aOS, j * no + i), opd(m.bT2R, k * nv, 1), op, 1, ex, s);
+  add_sterm(P, jb, opd(m.aT2R, k * nv, 1), opd(m.bOS, i * no + j), op, 1, ex, s);
+  add_sterm(P, jb, opd(m.aT2C, i * nv, 1), opd(m.bOS, k * no + j), op, 1, ex, s);
+}
+// phase C terms: tile (c, b) at fixed a (batch index)
+void w_terms_c(SPlan &P, int jc, const WMaps &m, int no, int nv, int vp, int op,
+               const int ijk[3], double &ex, int s) {
+  const int i = ijk[0], j = ijk[1], k = ijk[2];
+  // (k,i,j): sum_d t_ki[c][d] (ad|bj) -> YS slab (j, a) rows b
+  add_sterm(P, jc, opd(m.aT2S, k * no + i), opd(m.bYS, j * nv, 1), vp, 0, ex, s);
+  // (k,j,i): sum_d t_kj[c][d] (bd|ai) -> XS slab (i, a) rows b
+  add_sterm(P, jc, opd(m.aT2S, k * no + j), opd(m.bXS, i * nv, 1), vp, 0, ex, s);
+  // (i,j,k) occupied: - sum_l (lj|ck) t^{ab}_{il} -> T2R slab (i, a) rows b
+  add_sterm(P, jc, opd(m.aOS, j * no + k), opd(m.bT2R, i * nv, 1), op, 1, ex, s);
+  // (j,i,k) occupied: - sum_l (li|ck) t^{ba}_{jl} -> T2C slab (j, a) rows b
+  add_sterm(P, jc, opd(m.aOS, i * no + k), opd(m.bT2C, j * nv, 1), op, 1, ex, s);
+}
+
+int w_job_ab(SPlan &pab, int nv, int Nab, int slot, int E, double &ex, int s) {
   const long long nv2 = (long long)nv * nv, nv3 = nv2 * nv;
-  const int E = S->Et + S->Eg - 14;
-  // phase AB: tile (a, b) at fixed c (batch index)
-  int jb = new_sjob(pab, nv, nv, S->Nab, nv, 1, SEPI_DD_STORE, E, ex, s);
+  int jb = new_sjob(pab, nv, nv, Nab, nv, 1, SEPI_DD_STORE, E, ex, s);
   pab.jobs[jb].C = outd(B_WS_W, slot * nv3, nv, 1, nv2);
   pab.jobs[jb].Ct = pab.jobs[jb].C;
   pab.jobs[jb].nv = nv;
-  add_sterm(pab, jb, opd(MA_T2S, i * no + j), opd(MB_XS, k * nv, 1), vp, 0, ex, s);
-  add_sterm(pab, jb, opd(MA_T2S, i * no + k), opd(MB_YS, j * nv, 1), vp, 0, ex, s);
-  add_sterm(pab, jb, opd(MA_XS, k * nv, 1), opd(MB_T2S, j * no + i), vp, 0, ex, s);
-  add_sterm(pab, jb, opd(MA_YS, i * nv, 1), opd(MB_T2S, j * no + k), vp, 0, ex, s);
-  add_sterm(pab, jb, opd(MA_OS, k * no + i), opd(MB_T2C, j * nv, 1), op, 1, ex, s);
-  add_sterm(pab, jb, opd(MA_OS, j * no + i), opd(MB_T2R, k * nv, 1), op, 1, ex, s);
-  add_sterm(pab, jb, opd(MA_T2R, k * nv, 1), opd(MB_OS, i * no + j), op, 1, ex, s);
-  add_sterm(pab, jb, opd(MA_T2C, i * nv, 1), opd(MB_OS, k * no + j), op, 1, ex, s);
-  // phase C: tile (c, b) at fixed a (batch index), epilogue tau = W / (w - eps)
-  int jc = new_sjob(pc, nv, nv, S->Nab, nv, 1, SEPI_DD_TAU, E, ex, s);
+  return jb;
+}
+// the C job's epilogue forms W / (w - eps) in double-float
+int w_job_c(SPlan &pc, int nv, int Nab, int slot, int E, const float *eo_dd, double w,
+            double &ex, int s) {
+  const long long nv2 = (long long)nv * nv, nv3 = nv2 * nv;
+  int jc = new_sjob(pc, nv, nv, Nab, nv, 1, SEPI_DD_TAU, E, ex, s);
   OutD C = outd(B_WS_W, slot * nv3, nv2, 1, nv);  // W[c][a][b]: m = c, n = b, batch a
   pc.jobs[jc].C = C;
   pc.jobs[jc].Ct = C;
@@ -369,16 +403,19 @@ void plan_w_split(SPlan &pab, SPlan &pc, SplitState *S, int no, int nv, const in
   pc.jobs[jc].nv = nv;
   pc.jobs[jc].eo_hi = eo_dd[0];
   pc.jobs[jc].eo_lo = eo_dd[1];
-  pc.jobs[jc].w_hi = 0.f;
-  pc.jobs[jc].w_lo = 0.f;
-  // (k,i,j): sum_d t_ki[c][d] (ad|bj) -> YS slab (j, a) rows b
-  add_sterm(pc, jc, opd(MA_T2S, k * no + i), opd(MB_YS, j * nv, 1), vp, 0, ex, s);
-  // (k,j,i): sum_d t_kj[c][d] (bd|ai) -> XS slab (i, a) rows b
-  add_sterm(pc, jc, opd(MA_T2S, k * no + j), opd(MB_XS, i * nv, 1), vp, 0, ex, s);
-  // (i,j,k) occupied: - sum_l (lj|ck) t^{ab}_{il} -> T2R slab (i, a) rows b
-  add_sterm(pc, jc, opd(MA_OS, j * no + k), opd(MB_T2R, i * nv, 1), op, 1, ex, s);
-  // (j,i,k) occupied: - sum_l (li|ck) t^{ba}_{jl} -> T2C slab (j, a) rows b
-  add_sterm(pc, jc, opd(MA_OS, i * no + k), opd(MB_T2C, j * nv, 1), op, 1, ex, s);
+  const dd::df wd = dd::from_double_host(w);
+  pc.jobs[jc].w_hi = wd.hi;
+  pc.jobs[jc].w_lo = wd.lo;
+  return jc;
+}
+
+void plan_w_split(SPlan &pab, SPlan &pc, SplitState *S, int no, int nv, const int ijk[3],
+                  int slot, const float *eo_dd, double &ex) {
+  const int s = S->s, E = S->Et + S->Eg - 14;
+  const int jb = w_job_ab(pab, nv, S->Nab, slot, E, ex, s);
+  w_terms_ab(pab, jb, kStdMaps, no, nv, S->vp, S->op, ijk, ex, s);
+  const int jc = w_job_c(pc, nv, S->Nab, slot, E, eo_dd, 0.0, ex, s);
+  w_terms_c(pc, jc, kStdMaps, no, nv, S->vp, S->op, ijk, ex, s);
 }
 
 // residual contractions of one triple (every distinct permutation)
@@ -462,6 +499,7 @@ int build_plans(cc3_ctx *c, SplitState *S, cudaStream_t st) {
   const int tiles4 = ((nv + S_BM - 1) / S_BM) * ((nv8 + 1 + ntile_for(nv8 + 1) - 1) / ntile_for(nv8 + 1)) * 6 * S->batch;
   const int kst = nv * S->vp / S_BK;
   int ks4 = std::max(1, std::min(kst / 64, (2 * sms + tiles4 - 1) / std::max(1, tiles4)));
+  S->ks4 = ks4;
   for (int t0 = 0; t0 < c->ntri; t0 += S->batch) {
     const int t1 = std::min(c->ntri, t0 + S->batch);
     SPlan pab, pc, pom;
@@ -497,7 +535,9 @@ void fill_vptrs(cc3_ctx *c, SplitState *S, VPtrTable *P) {
 
 }  // namespace
 
-int split_omega(cc3_ctx *c, cudaStream_t st) {
+namespace {
+// The staged slice arrays and residual plans of the context (built on first use).
+int split_ready(cc3_ctx *c, SplitState **out, cudaStream_t st) {
   const int s = c->slices > 0 ? c->slices : 6;
   SplitState *S = state(c);
   if (S && S->s != s) {
@@ -512,6 +552,15 @@ int split_omega(cc3_ctx *c, cudaStream_t st) {
   }
   if (!S->staged) TRY(stage(c, S, st));
   if (!S->planned) TRY(build_plans(c, S, st));
+  *out = S;
+  return CC3_OK;
+}
+}  // namespace
+
+int split_omega(cc3_ctx *c, cudaStream_t st) {
+  SplitState *S = nullptr;
+  TRY(split_ready(c, &S, st));
+  const int s = S->s;
   VPtrTable P;
   fill_vptrs(c, S, &P);
   const int nv = c->nv;
@@ -588,6 +637,343 @@ void split_destroy(cc3_ctx *c) {
   free_state_buffers(S);
   delete S;
   c->split = nullptr;
+}
+
+
+// ---- right Jacobian transformation (eq. "jcc3", Algorithm 2) -------------------
+namespace {
+
+// one slice array from an FP64 tensor through a strided gather (allocates)
+int slice_array(SplitState *S, __nv_bfloat16 **dst, const double *src, long long rows, int Kp,
+                int E, const Gather &g, int rps, cudaStream_t st) {
+  const size_t n = arr_elems(Kp, rps, rows / rps, S->s);
+  TRY(alloc(dst, n));
+  CU(cudaMemsetAsync(*dst, 0, n * sizeof(__nv_bfloat16), st));
+  return launch_slice_gather(src, *dst, S->s, E, g, rows, Kp, rps, st);
+}
+
+// ovov in the layouts of Algorithm 2 (once per context):
+//   OVD[(q,r)][d][z] = (qd|rz)                  (Z~v: rows d, K = z)
+//   OVZA[r][l][(u,w)] = (lu|rw), OVZB[r][l][(u,w)] = (lw|ru)   (Z~o: rows l, K = (zb, u, zz))
+int stage_jac_static(cc3_ctx *c, SplitState *S, cudaStream_t st) {
+  if (S->OVD) return CC3_OK;
+  const int no = c->no, nv = c->nv, vp = S->vp;
+  const long long nvo = (long long)nv * no, ovl = (long long)nv * no * nv;
+  Gather g;
+  g = {0, ovl, nv, nvo, 0, 1, no, nv, vp, nv, 1};
+  TRY(slice_array(S, &S->OVD, c->ovov, (long long)no * no * nv, vp, S->Eg, g, nv, st));
+  g = {0, 0, nv, ovl, nvo, 1, no, no, nv, nv, nv, 1};
+  TRY(slice_array(S, &S->OVZA, c->ovov, (long long)no * no, nv * vp, S->Eg, g, no, st));
+  g = {0, 0, nv, ovl, 1, nvo, no, no, nv, nv, nv, 1};
+  TRY(slice_array(S, &S->OVZB, c->ovov, (long long)no * no, nv * vp, S->Eg, g, no, st));
+  SArr *M = S->arrs.a;
+  M[MJ_OVD] = make_arr(S->OVD, vp, nv, (long long)no * no);
+  M[MJ_OVZA] = make_arr(S->OVZA, (long long)nv * vp, no, no);
+  M[MJ_OVZB] = make_arr(S->OVZB, (long long)nv * vp, no, no);
+  return CC3_OK;
+}
+
+// Jobs of one distinct permutation (p,q,r) = (ijk[m0], ijk[m1], ijk[m2]) of a
+// triple whose tau~ sits in `slot` of the V layouts:
+//   F^ term:  rho~_v[p][q][x][y] += sum_z tau~[x][y][z] F^_v[r][z]   (column v)
+//   Z~v:      Z~v[x][y][p][d]    -= sum_z tau~[x][y][z] (qd|rz)
+//   Z~o:      Z~o[x][q][p][l]    += sum_yz tau~[x][y][z] (ly|rz)
+void plan_jac_tau(SPlan *pf, SPlan *pz, SplitState *S, int no, int nv, int nvec, int EF,
+                  const int ijk[3], int slot, double &ex) {
+  static const int PERM6[6][3] = {{0, 1, 2}, {1, 0, 2}, {2, 1, 0},
+                                  {0, 2, 1}, {1, 2, 0}, {2, 0, 1}};
+  const int s = S->s, vp = S->vp, nv8 = (nv + 7) / 8 * 8;
+  const long long nv2 = (long long)nv * nv, nt2 = (long long)no * no * nv2;
+  int seen[6][3], nseen = 0;
+  if (ijk[0] == ijk[1] && ijk[1] == ijk[2]) return;
+  for (int u = 0; u < 6; ++u) {
+    const int *m = PERM6[u];
+    const int p = ijk[m[0]], q = ijk[m[1]], r = ijk[m[2]];
+    bool dup = false;
+    for (int w = 0; w < nseen; ++w)
+      if (seen[w][0] == p && seen[w][1] == q && seen[w][2] == r) dup = true;
+    if (dup) continue;
+    seen[nseen][0] = p;
+    seen[nseen][1] = q;
+    seen[nseen][2] = r;
+    ++nseen;
+    // rows (y_L, x_L) of the z-innermost layout Lz (see plan_omega_split)
+    const int Lz = (m[2] + 1) % 3;
+    const bool xouter = (m[0] == Lz);
+    if (pf) {
+      int jb = new_sjob(*pf, nv * nv8, nvec, ntile_for(nvec), 1, 1, SEPI_F64_ATOMIC, EF - 14,
+                        ex, s);
+      SJob &J = pf->jobs[jb];
+      J.expo_slot = slot;
+      J.m_pad = nv8;
+      J.m_valid = nv;
+      OutD c = outd(B_OMT, ((long long)p * no + q) * nv2, xouter ? nv : 1, nt2);
+      c.m_in = nv8;
+      c.sm1 = xouter ? 1 : nv;
+      J.C = c;
+      J.Ct = c;
+      add_sterm(*pf, jb, opd(MA_V0K + Lz, slot), opd(MJ_FH, r), vp, 0, ex, s);
+    }
+    if (pz) {
+      const long long sx = nv2 * no, sy = (long long)no * nv;  // Z~v strides of x, y
+      int jb = new_sjob(*pz, nv * nv8, nv, S->Nab, 1, 1, SEPI_F64_ATOMIC, S->Eg - 14, ex, s);
+      SJob &J = pz->jobs[jb];
+      J.expo_slot = slot;
+      J.m_pad = nv8;
+      J.m_valid = nv;
+      OutD c = outd(B_ZV, (long long)p * nv, xouter ? sx : sy, 1);
+      c.m_in = nv8;
+      c.sm1 = xouter ? sy : sx;
+      J.C = c;
+      J.Ct = c;
+      add_sterm(*pz, jb, opd(MA_V0K + Lz, slot), opd(MJ_OVD, q * no + r), vp, 1, ex, s);
+      // rows x of layout L = m0, K = (slot L+1, slot L+2) in (zb, u, zz) order
+      const int L = m[0];
+      const bool yz = (m[1] == (L + 1) % 3);
+      jb = new_sjob(*pz, nv, no, ntile_for(no), 1, S->ks4, SEPI_F64_ATOMIC, S->Eg - 14, ex, s);
+      SJob &K = pz->jobs[jb];
+      K.expo_slot = slot;
+      K.C = outd(B_ZO, ((long long)q * no + p) * no, (long long)no * no * no, 1);
+      K.Ct = K.C;
+      add_sterm(*pz, jb, opd(MA_V0 + L, slot), opd(yz ? MJ_OVZA : MJ_OVZB, r), nv * vp, 0, ex,
+                s);
+    }
+  }
+}
+
+struct JacBufs {
+  std::vector<void *> p;
+  ~JacBufs() {
+    for (void *x : p)
+      if (x) cudaFree(x);
+  }
+  template <class T>
+  int get(T **out, size_t n) {
+    TRY(alloc(out, n));
+    p.push_back(*out);
+    return CC3_OK;
+  }
+};
+
+struct JacPlans {
+  std::vector<SDevPlan> v;
+  ~JacPlans() {
+    for (auto &d : v) s_free_plan(&d);
+  }
+};
+
+}  // namespace
+
+int split_jacobian(cc3_ctx *c, int nvec, const double *w, const double *R1d, const double *R2d,
+                   double *rho1d, double *rho2d, cudaStream_t st) {
+  SplitState *S = nullptr;
+  TRY(split_ready(c, &S, st));
+  TRY(jac_blocks(c, st));
+  TRY(stage_jac_static(c, S, st));
+  const int no = c->no, nv = c->nv, s = S->s, vp = S->vp, op = S->op;
+  const long long nv2 = (long long)nv * nv, nvo = (long long)nv * no;
+  const size_t n1 = (size_t)no * nv, nt2 = n1 * no * nv, nvvvo = (size_t)nv2 * nv * no,
+               noovo = (size_t)no * no * nv * no;
+  JacBufs B;
+  double *hv = nullptr, *ho = nullptr, *hf = nullptr, *mj = nullptr, *rt = nullptr, *r1a = nullptr;
+  TRY(B.get(&hv, nvvvo * nvec));
+  TRY(B.get(&ho, noovo * nvec));
+  TRY(B.get(&hf, n1 * nvec));
+  TRY(B.get(&mj, (size_t)c->naux * nv * no));
+  TRY(B.get(&rt, nt2 * nvec));
+  TRY(B.get(&r1a, n1 * nvec));
+  TRY(launch_zero(rt, nt2 * nvec, st));
+  TRY(launch_zero(r1a, n1 * nvec, st));
+  // R1-dressed integrals of every vector (FP64 engine)
+  for (int v = 0; v < nvec; ++v)
+    TRY(jac_dress(c, R1d + v * n1, hv + v * nvvvo, ho + v * noovo, hf + v * n1, mj, st));
+  // exponents: one for all R2 . g and t2 . g^ products, one for F^
+  unsigned long long *mx = nullptr;
+  TRY(B.get(&mx, 2 * (size_t)nvec + 1));
+  CU(cudaMemsetAsync(mx, 0, sizeof(unsigned long long) * (2 * nvec + 1), st));
+  for (int v = 0; v < nvec; ++v) {
+    TRY(launch_maxabs(R2d + v * nt2, (long long)nt2, mx + v, st));
+    TRY(launch_maxabs(hv + v * nvvvo, (long long)nvvvo, mx + nvec + v, st));
+    TRY(launch_maxabs(ho + v * noovo, (long long)noovo, mx + nvec + v, st));
+  }
+  TRY(launch_maxabs(hf, (long long)n1 * nvec, mx + 2 * nvec, st));
+  std::vector<unsigned long long> hm(2 * nvec + 1);
+  CU(cudaMemcpyAsync(hm.data(), mx, sizeof(unsigned long long) * hm.size(),
+                     cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  auto ex_of = [&](int i, int dflt) {
+    double x;
+    std::memcpy(&x, &hm[i], 8);
+    return x > 0.0 ? exponent_of(x) : dflt;
+  };
+  int Ec = -100000;
+  for (int v = 0; v < nvec; ++v) {
+    Ec = std::max(Ec, ex_of(v, -100000) + S->Eg);
+    Ec = std::max(Ec, S->Et + ex_of(nvec + v, -100000));
+  }
+  if (Ec < -50000) Ec = S->Et + S->Eg;  // R2 = 0 and R1 = 0: the result is 0
+  const int ER = Ec - S->Eg, EH = Ec - S->Et, EF = ex_of(2 * nvec, 0);
+  // slices of R2 (t2 layouts), g^ (vvvo / oovo layouts) and F^
+  std::vector<SArrTable> arrs(nvec, S->arrs);
+  for (int v = 0; v < nvec; ++v) {
+    __nv_bfloat16 *a = nullptr;
+    const double *r2 = R2d + v * nt2, *gv = hv + v * nvvvo, *go = ho + v * noovo;
+    Gather g;
+    SArr *M = arrs[v].a;
+    g = {0, (long long)no * nv2, nv2, nv, 0, 1, no, nv, vp, nv, 1};
+    TRY(slice_array(S, &a, r2, (long long)no * no * nv, vp, ER, g, nv, st));
+    B.p.push_back(a);
+    M[MJ_R2S] = make_arr(a, vp, nv, (long long)no * no);
+    g = {0, (long long)no * nv2, 1, nv, 0, nv2, nv, nv, op, no, 1};
+    TRY(slice_array(S, &a, r2, (long long)no * nv * nv, op, ER, g, nv, st));
+    B.p.push_back(a);
+    M[MJ_R2C] = make_arr(a, op, nv, (long long)no * nv);
+    g = {0, (long long)no * nv2, nv, 1, 0, nv2, nv, nv, op, no, 1};
+    TRY(slice_array(S, &a, r2, (long long)no * nv * nv, op, ER, g, nv, st));
+    B.p.push_back(a);
+    M[MJ_R2R] = make_arr(a, op, nv, (long long)no * nv);
+    g = {0, 1, no, nv2 * no, 0, nvo, nv, nv, vp, nv, 1};
+    TRY(slice_array(S, &a, gv, (long long)no * nv * nv, vp, EH, g, nv, st));
+    B.p.push_back(a);
+    M[MJ_XH] = make_arr(a, vp, nv, (long long)no * nv);
+    g = {0, 1, nv2 * no, no, 0, nvo, nv, nv, vp, nv, 1};
+    TRY(slice_array(S, &a, gv, (long long)no * nv * nv, vp, EH, g, nv, st));
+    B.p.push_back(a);
+    M[MJ_YH] = make_arr(a, vp, nv, (long long)no * nv);
+    g = {0, nvo, 1, no, 0, (long long)no * nv * no, no, nv, op, no, 1};
+    TRY(slice_array(S, &a, go, (long long)no * no * nv, op, EH, g, nv, st));
+    B.p.push_back(a);
+    M[MJ_OH] = make_arr(a, op, nv, (long long)no * no);
+  }
+  {
+    __nv_bfloat16 *a = nullptr;
+    Gather g = {0, 0, nv, nvo, 0, 1, no, nvec, vp, nv, 1};
+    TRY(slice_array(S, &a, hf, (long long)no * nvec, vp, EF, g, nvec, st));
+    B.p.push_back(a);
+    for (int v = 0; v < nvec; ++v) arrs[v].a[MJ_FH] = make_arr(a, vp, nvec, no);
+    S->arrs.a[MJ_FH] = arrs[0].a[MJ_FH];
+  }
+  // plans per batch: R3 phase AB (shared by the vectors), phase C per vector
+  // (its frequency), the tau~ . F^ jobs and, when the cache is cold, Z~v, Z~o
+  const bool prep = jac_prep_prec(c) < 0;
+  double *Zv = nullptr, *Zo = nullptr;
+  TRY(jac_z_buffers(c, &Zv, &Zo, prep, st));
+  std::vector<double> eo(no);
+  CU(cudaMemcpyAsync(eo.data(), c->eps_o, sizeof(double) * no, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  const WMaps set1 = {MJ_R2S, MJ_R2S, MJ_R2C, MJ_R2C, MJ_R2R, MJ_R2R,
+                      MA_XS,  MB_XS,  MA_YS,  MB_YS,  MA_OS,  MB_OS};
+  const WMaps set2 = {MA_T2S, MB_T2S, MA_T2C, MB_T2C, MA_T2R, MB_T2R,
+                      MJ_XH,  MJ_XH,  MJ_YH,  MJ_YH,  MJ_OH,  MJ_OH};
+  const int nb = (int)S->ab.size();
+  JacPlans pAB, pC, pF, pZ;
+  pAB.v.resize(nb);
+  pC.v.resize((size_t)nb * nvec);
+  pF.v.resize(nb);
+  pZ.v.resize(nb);
+  double ex = 0.0;
+  for (int b = 0, t0 = 0; b < nb; ++b) {
+    const int t1 = t0 + S->nslot[b];
+    SPlan ab, f, z;
+    std::vector<SPlan> cv(nvec);
+    for (int t = t0; t < t1; ++t) {
+      const int *ijk = &c->tri_host[3 * t];
+      const double e = eo[ijk[0]] + eo[ijk[1]] + eo[ijk[2]];
+      const dd::df ed = dd::from_double_host(e);
+      const float eod[2] = {ed.hi, ed.lo};
+      const int jb = w_job_ab(ab, nv, S->Nab, t - t0, Ec - 14, ex, s);
+      w_terms_ab(ab, jb, set1, no, nv, vp, op, ijk, ex, s);
+      w_terms_ab(ab, jb, set2, no, nv, vp, op, ijk, ex, s);
+      for (int v = 0; v < nvec; ++v) {
+        const int jc = w_job_c(cv[v], nv, S->Nab, t - t0, Ec - 14, eod, w[v], ex, s);
+        w_terms_c(cv[v], jc, set1, no, nv, vp, op, ijk, ex, s);
+        w_terms_c(cv[v], jc, set2, no, nv, vp, op, ijk, ex, s);
+      }
+      plan_jac_tau(&f, prep ? &z : nullptr, S, no, nv, nvec, EF, ijk, t - t0, ex);
+    }
+    TRY(s_upload_plan(ab, &pAB.v[b], st));
+    for (int v = 0; v < nvec; ++v) TRY(s_upload_plan(cv[v], &pC.v[(size_t)b * nvec + v], st));
+    TRY(s_upload_plan(f, &pF.v[b], st));
+    if (prep) TRY(s_upload_plan(z, &pZ.v[b], st));
+    t0 = t1;
+  }
+  // the loop: tau~ once per batch, then R3 and its contractions per vector
+  VPtrTable P;
+  fill_vptrs(c, S, &P);
+  P.p[B_ZV] = Zv;
+  P.p[B_ZO] = Zo;
+  const int kd = S_DRAIN_STEPS;
+  long long *L = &c->counters.launches;
+  auto elem = [&](int ns) -> int {
+    trace_begin(c, TR_SPLIT_ELEM, st);
+    CU(cudaMemsetAsync(S->maxbits, 0, sizeof(unsigned int) * ns, st));
+    TRY(launch_contravariant_dd(S->Wdd, S->TTdd, nv, ns, S->maxbits, st));
+    TRY(launch_slot_exponent(S->maxbits, S->slot_ex, ns, st));
+    TRY(launch_slice_tt(S->TTdd, S->vptr, nv, vp, s, S->slot_ex, ns, S->batch, st));
+    trace_end(c, TR_SPLIT_ELEM, st, 0.0, 0.0);
+    *L += 3;
+    return CC3_OK;
+  };
+  auto run = [&](const SDevPlan &d, const SArrTable &a, const VPtrTable &pt, int cls) -> int {
+    trace_begin(c, cls, st);
+    TRY(s_launch_plan(d, a, pt, s, kd, S->status, st, L));
+    trace_end(c, cls, st, d.flop, d.slice_flop);
+    return CC3_OK;
+  };
+  for (int b = 0; b < nb; ++b) {
+    const int ns = S->nslot[b];
+    P.p[B_OMT] = rt;
+    P.p[B_OM1] = r1a;
+    TRY(run(S->ab[b], S->arrs, P, TR_SPLIT_W));
+    TRY(run(S->cc[b], S->arrs, P, TR_SPLIT_W));
+    TRY(elem(ns));
+    if (prep) TRY(run(pZ.v[b], S->arrs, P, TR_SPLIT_OMEGA));
+    TRY(run(pF.v[b], S->arrs, P, TR_SPLIT_OMEGA));
+    for (int v = 0; v < nvec; ++v) {
+      TRY(run(pAB.v[b], arrs[v], P, TR_SPLIT_W));
+      TRY(run(pC.v[(size_t)b * nvec + v], arrs[v], P, TR_SPLIT_W));
+      TRY(elem(ns));
+      VPtrTable Pv = P;
+      Pv.p[B_OMT] = rt + v * nt2;
+      Pv.p[B_OM1] = r1a + v * n1;
+      TRY(run(S->om[b], S->arrs, Pv, TR_SPLIT_OMEGA));
+    }
+  }
+  int hs = 0;
+  CU(cudaMemcpyAsync(&hs, S->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  if (hs != 0) {
+    cudaMemsetAsync(S->status, 0, sizeof(int), st);
+    return hs == 2 ? CC3_FAIL(CC3_ERR_ARG, "a Jacobian plan addressed outside a slice array")
+                   : CC3_FAIL(CC3_ERR_TIMEOUT, "split engine wait gave up");
+  }
+  if (prep) jac_set_prep(c, CC3_SPLIT_BF16);
+  // Z~ . R1 (FP64), back-transform, singles
+  for (int v = 0; v < nvec; ++v) {
+    TRY(jac_z_terms(c, R1d + v * n1, rt + v * nt2, st));
+    TRY(launch_back_transform(rt + v * nt2, rho2d + v * nt2, no, nv, st));
+    CU(cudaMemcpyAsync(rho1d + v * n1, r1a + v * n1, sizeof(double) * n1,
+                       cudaMemcpyDeviceToDevice, st));
+  }
+  CU(cudaStreamSynchronize(st));
+  c->counters.executed_flop = ex + (double)nvec * S->executed;
+  c->counters.slices = s;
+  return CC3_OK;
+}
+
+// Device bytes of one split Jacobian call beyond the residual's state: the
+// Algorithm 2 layouts of ovov, FP64 dressed blocks and the slices of R2 and
+// g^ of every vector.
+size_t split_jacobian_footprint(int no, int nv, int s, int nvec) {
+  const int vp = rup(nv, 16), op = rup(no, 16);
+  auto sl = [&](long long rows, long long Kp, long long rps) {
+    return arr_elems(Kp, rps, rows / rps, s) * sizeof(__nv_bfloat16);
+  };
+  size_t b = sl((long long)no * no * nv, vp, nv) + 2 * sl((long long)no * no, (long long)nv * vp, no);
+  size_t per = sl((long long)no * no * nv, vp, nv) + 2 * sl((long long)no * nv * nv, op, nv) +
+               2 * sl((long long)no * nv * nv, vp, nv) + sl((long long)no * no * nv, op, nv);
+  b += (size_t)nvec * per + sl((long long)no * nvec, vp, nvec);
+  return b + 65536;
 }
 
 // ---- diagnostic: one plain GEMM C[m][n] = sum_k A[m][k] B[n][k] ------------------

@@ -7,4 +7,8 @@ int split_omega(cc3_ctx *c, cudaStream_t s);
 void split_invalidate(cc3_ctx *c);
 void split_destroy(cc3_ctx *c);
 size_t split_footprint(int no, int nv, int slices, int ntri);
+// right Jacobian transformation of nvec trial vectors (device pointers)
+int split_jacobian(cc3_ctx *c, int nvec, const double *w, const double *R1, const double *R2,
+                   double *rho1, double *rho2, cudaStream_t s);
+size_t split_jacobian_footprint(int no, int nv, int slices, int nvec);
 }  // namespace cc3

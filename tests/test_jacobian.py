@@ -93,3 +93,36 @@ def test_jacobian_needs_cholesky_vectors(g):
     with pytest.raises(g.CC3Error) as e:
         ctx.jacobian(R1, R2, [0.0], g.CC3_FP64)
     assert e.value.status == g.CC3_ERR_ARG
+
+
+# split path: Omega-scale absolute targets (the trial vectors are normalised)
+SPLIT_TOL = 1e-9
+
+
+@pytest.mark.parametrize("no,nv", [(3, 9), (4, 20), (5, 33), (3, 40)])
+def test_jacobian_split_matches_oracle(g, no, nv):
+    inp = make_inputs(no, nv, seed=300 + no * nv)
+    R1, R2 = make_trial_vectors(no, nv, 3, seed=no * nv)
+    w = [0.25, 0.0, -0.1]
+    ref = oracle.jacobian(inp, R1, R2, w)
+    ctx = g.Context(inp)
+    r1, r2 = ctx.jacobian(R1, R2, w, g.CC3_SPLIT_BF16)
+    assert np.abs(r1 - ref["rho1"]).max() <= SPLIT_TOL
+    assert np.abs(r2 - ref["rho2"]).max() <= SPLIT_TOL
+    c = ctx.counters()
+    assert c["slices"] == 6 and c["executed_flop"] > 0
+
+
+def test_jacobian_split_and_fp64_share_the_context(g):
+    no, nv = 4, 24
+    inp = make_inputs(no, nv, seed=17)
+    R1, R2 = make_trial_vectors(no, nv, 2, seed=2)
+    w = [0.2, 0.05]
+    ref = oracle.jacobian(inp, R1, R2, w)
+    ctx = g.Context(inp)
+    s1, s2 = ctx.jacobian(R1, R2, w, g.CC3_SPLIT_BF16)  # builds the Z~ cache in split
+    f1, f2 = ctx.jacobian(R1, R2, w, g.CC3_FP64)        # rebuilds it in FP64
+    assert _close(f2, ref["rho2"], 1e-11) and _close(f1, ref["rho1"], 1e-11)
+    t1, t2 = ctx.jacobian(R1, R2, w, g.CC3_SPLIT_BF16)  # reuses the FP64 cache
+    for x, y in ((s1, ref["rho1"]), (s2, ref["rho2"]), (t1, ref["rho1"]), (t2, ref["rho2"])):
+        assert np.abs(x - y).max() <= SPLIT_TOL
