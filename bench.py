@@ -44,7 +44,7 @@ WORKLOAD = "CC3 triples residual, no=16 nv=160, seeded synthetic (Cholesky-like 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
 # the dominant kernel from one ncu capture of the same workload; None where no
 # capture of the current kernel exists.
-TRAFFIC = {("split_engine_kernel", 16, 160): 6.39e9}
+TRAFFIC = {}
 
 
 def peaks():
@@ -285,6 +285,113 @@ def run_serve(args):
     return 0
 
 
+def run_jacobian(args):
+    """Batched right Jacobian transformation: 8 trial vectors at w = 0.25 on
+    the no=20 nv=200 problem, split and FP64 side by side, each on the same
+    seeded triple sample (the rate per weighted triple does not depend on the
+    sample; the sample keeps a step within seconds)."""
+    import torch
+    import paper_2007_01088_gb300 as g
+    from cc3_inputs import make_inputs, make_trial_vectors, unique_triples
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    no, nv, nvec = args.jno, args.jnv, args.nvec
+    inp = make_inputs(no, nv, seed=rank)
+    R1, R2 = make_trial_vectors(no, nv, nvec, seed=1 + rank)
+    tr = unique_triples(no)
+    rng = np.random.default_rng(7)
+    pick = sorted(rng.choice(len(tr), size=max(1, int(round(args.sample * len(tr)))),
+                             replace=False))
+    sel = [tr[i][:3] for i in pick]
+    wsum = sum(tr[i][3] for i in pick)
+    w = torch.full((nvec,), 0.25, dtype=torch.float64).numpy()
+    stream = torch.cuda.Stream(device=dev)
+    sub = sel[:max(1, len(sel) // 8)]  # the FP64 comparison runs on a sub-sample
+
+    def measure(prec, triples, steps, warm):
+        with torch.cuda.stream(stream):
+            ctx = g.Context(inp, device=True, stream=stream)
+            ctx.set_triples(triples)
+            r1 = torch.from_numpy(R1).to(dev)
+            r2 = torch.from_numpy(R2).to(dev)
+            ctx.set_tracing(True)
+            for _ in range(warm):
+                out = ctx.jacobian(r1, r2, w, prec)
+            clocks = ClockSampler(local)
+            clocks.start()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            launches, traces = 0, {}
+            for _ in range(steps):
+                out = ctx.jacobian(r1, r2, w, prec)
+                launches += ctx.counters()["launches"]
+                for k, v in ctx.trace().items():
+                    a = traces.setdefault(k, dict(launches=0, ms=0.0, flop=0.0, slice_flop=0.0))
+                    for f in a:
+                        a[f] += v[f]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            clk = clocks.stop()
+        res = dict(ms=e0.elapsed_time(e1) / steps, flop=ctx.counters()["nominal_flop"],
+                   out=[x.cpu().numpy() for x in out], clk=clk, launches=launches,
+                   traces=traces, steps=steps, executed=ctx.counters()["executed_flop"])
+        ctx.close()
+        return res
+
+    res = {}
+    if args.prec == "split":
+        res[g.CC3_SPLIT_BF16] = measure(g.CC3_SPLIT_BF16, sel, args.steps, args.warmup)
+        res["split_sub"] = measure(g.CC3_SPLIT_BF16, sub, 1, 1)
+        res[g.CC3_FP64] = measure(g.CC3_FP64, sub, 1, 1)
+    else:
+        res[g.CC3_FP64] = measure(g.CC3_FP64, sel, args.steps, args.warmup)
+    main_p = g.CC3_SPLIT_BF16 if args.prec == "split" else g.CC3_FP64
+    r = res[main_p]
+    value = r["flop"] / (r["ms"] * 1e-3) / 1e12
+    pk, src = peaks()
+    kern = per_kernel(r["traces"])
+    dom_name, d = max(kern.items(), key=lambda kv: kv[1]["ms"])
+    if dom_name == "fp64_engine_kernel":
+        roof = {"bound": "tensor", "achieved": d["flop"] / (d["ms"] * 1e-3) / 1e12,
+                "peak": pk["bf16_tflops"] * 1.25 / 2250.0, "unit": "TFLOP/s",
+                "peak_source": f"FP64: {src} bf16 burst x nominal FP64/BF16 ratio (1.25/2250)"}
+    else:
+        roof = {"bound": "tensor", "achieved": d["slice_flop"] / (d["ms"] * 1e-3) / 1e12,
+                "peak": pk["bf16_tflops"], "unit": "TFLOP/s", "peak_source": f"{src} bf16 burst",
+                "fp64_equivalent_tflops": d["flop"] / (d["ms"] * 1e-3) / 1e12}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = dom_name
+    roof["kernels"] = {k: {"ms_per_step": v["ms"] / r["steps"],
+                           "launches_per_step": v["launches"] / r["steps"]}
+                       for k, v in kern.items() if v["launches"]}
+    line = {"metric": "CC3 triples Jacobian TFLOP/s (8 nv^4 no^3 per trial vector)",
+            "value": value, "unit": "TFLOP/s", "n_gpus": 1, "steps": r["steps"],
+            "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if main_p == g.CC3_SPLIT_BF16 else "f64", "data": "synthetic",
+            "config": {"workload": f"batched right Jacobian, no={no} nv={nv}, {nvec} trial "
+                                   f"vectors at w=0.25, seeded sample of {len(sel)} of "
+                                   f"{len(tr)} triples (weight {wsum} of {no ** 3 - no})",
+                       "prec": args.prec},
+            "roofline": roof, "gpu_launches": r["launches"], "clocks": r["clk"],
+            "executed_flop_per_step": r["executed"]}
+    if args.prec == "split":
+        f = res[g.CC3_FP64]
+        fval = f["flop"] / (f["ms"] * 1e-3) / 1e12
+        q = res["split_sub"]
+        line["fp64"] = {"value": fval, "unit": "TFLOP/s", "ms_per_step": f["ms"],
+                        "triples": len(sub),
+                        "max_abs_drho1": float(np.abs(q["out"][0] - f["out"][0]).max()),
+                        "max_abs_drho2": float(np.abs(q["out"][1] - f["out"][1]).max()),
+                        "split_speedup": value / fval}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -296,7 +403,12 @@ def main():
     ap.add_argument("--nv", type=int, default=NV, help="virtual orbitals (profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
-    ap.add_argument("--workload", default="omega", choices=["omega", "serve"])
+    ap.add_argument("--workload", default="omega", choices=["omega", "serve", "jacobian"])
+    ap.add_argument("--jno", type=int, default=20, help="jacobian: occupied orbitals")
+    ap.add_argument("--jnv", type=int, default=200, help="jacobian: virtual orbitals")
+    ap.add_argument("--nvec", type=int, default=8, help="jacobian: trial vectors")
+    ap.add_argument("--sample", type=float, default=0.125,
+                    help="jacobian: fraction of the triples evaluated per step")
     ap.add_argument("--requests", type=int, default=32, help="serve: requests in the stream")
     ap.add_argument("--rate", type=float, default=4.0, help="serve: arrivals per second")
     ap.add_argument("--max-no", type=int, default=12, help="serve: largest no of the stream")
@@ -310,6 +422,10 @@ def main():
         return run_reference(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "jacobian":
+        if args.steps is None or args.steps > 3:
+            args.steps = 3
+        return run_jacobian(args)
 
     import torch
     ws, rank, local = dist_env()

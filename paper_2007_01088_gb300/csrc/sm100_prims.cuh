@@ -225,6 +225,18 @@ __device__ __forceinline__ uint64_t smem_desc_noswz(uint32_t saddr) {
   return d;                                         // layout type 0: no swizzle
 }
 
+// Shared-memory matrix descriptor, canonical K-major layout without swizzle:
+// core matrices of 8 rows x 16 bytes, the two K halves 128 bytes apart and
+// consecutive 8-row groups `sbo` bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_kmajor(uint32_t saddr, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);          // start address
+  d |= (uint64_t)((128 >> 4) & 0x3FFF) << 16;       // leading byte offset (K direction)
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;       // stride byte offset (M/N direction)
+  d |= (uint64_t)1 << 46;                           // descriptor version (sm100)
+  return d;                                         // layout type 0: no swizzle
+}
+
 // Instruction descriptor: BF16 x BF16 -> FP32, K-major A and B, M x N.
 __host__ __device__ __forceinline__ uint32_t idesc_bf16(int M, int N, int negA) {
   return (1u << 4)                         // D format F32

@@ -2,9 +2,10 @@
 // tensor cores: staging of BF16 slice arrays, job plans and the
 // per-batch launch sequence.
 //
-// Layouts (bf16, every array K-blocked as [slice][slab][K/16][row][16] so that
-// each 16 x R tile read by the tensor cores is one contiguous block; K zero
-// padded to a multiple of 16; vp = nv rounded up, op = no rounded up):
+// Layouts (bf16, every array K-blocked as [slab][K/16][row group][slice][8 x 16]
+// so that the slices of each 16 x R tile read by the tensor cores are one
+// contiguous block; K zero padded to a multiple of 16; vp = nv rounded up,
+// op = no rounded up):
 //   T2S[(p,q)][x][d]  = t^{xd}_{pq}          T2C[(p,y)][x][l] = t^{xy}_{pl}
 //   T2R[(p,x)][y][l]  = t^{xy}_{pl}          OS[(q,r)][z][l]  = (lq|zr)
 //   XS[(r,z)][y][d]   = (yd|zr)              YS[(r,y)][z][d]  = (yd|zr)
@@ -46,15 +47,15 @@ namespace cc3 {
 
 namespace {
 
-// Slice-array descriptor: [slice][slab][K/16][rows8 x 16 core-matrix block]
-SArr make_arr(const void *base, long long K, long long rps, long long slabs) {
+// Slice-array descriptor: [slab][K/16][row group][slice][8 x 16 core-matrix pair]
+SArr make_arr(const void *base, long long K, long long rps, long long slabs, int slices) {
   SArr a;
   a.base = reinterpret_cast<unsigned long long>(base);
   a.kblocks = (int)(K / 16);
   a.rows = (int)((rps + 7) / 8 * 8);
   a.slabs = (int)slabs;
-  a.slab_stride = (long long)a.kblocks * a.rows * 16;
-  a.slice_stride = slabs * a.slab_stride;
+  a.kb_stride = (long long)a.rows * 16 * slices;
+  a.slab_stride = (long long)a.kblocks * a.kb_stride;
   return a;
 }
 size_t arr_elems(long long K, long long rps, long long slabs, int slices) {
@@ -259,21 +260,21 @@ int stage(cc3_ctx *c, SplitState *S, cudaStream_t st) {
   SArr *M = S->arrs.a;
   std::memset(&S->arrs, 0, sizeof(S->arrs));
   const long long n_o = no, n_v = nv;
-  M[MA_T2S] = M[MB_T2S] = make_arr(S->T2S, vp, n_v, n_o * n_o);
-  M[MA_T2C] = M[MB_T2C] = make_arr(S->T2C, op, n_v, n_o * n_v);
-  M[MA_T2R] = M[MB_T2R] = make_arr(S->T2R, op, n_v, n_o * n_v);
-  M[MA_XS] = M[MB_XS] = make_arr(S->XS, vp, n_v, n_o * n_v);
-  M[MA_YS] = M[MB_YS] = make_arr(S->YS, vp, n_v, n_o * n_v);
-  M[MA_OS] = M[MB_OS] = make_arr(S->OS, op, n_v, n_o * n_o);
+  M[MA_T2S] = M[MB_T2S] = make_arr(S->T2S, vp, n_v, n_o * n_o, s);
+  M[MA_T2C] = M[MB_T2C] = make_arr(S->T2C, op, n_v, n_o * n_v, s);
+  M[MA_T2R] = M[MB_T2R] = make_arr(S->T2R, op, n_v, n_o * n_v, s);
+  M[MA_XS] = M[MB_XS] = make_arr(S->XS, vp, n_v, n_o * n_v, s);
+  M[MA_YS] = M[MB_YS] = make_arr(S->YS, vp, n_v, n_o * n_v, s);
+  M[MA_OS] = M[MB_OS] = make_arr(S->OS, op, n_v, n_o * n_o, s);
   const long long nv8 = (n_v + 7) / 8 * 8;
   for (int L = 0; L < 3; ++L) {
-    M[MA_V0 + L] = make_arr(S->V[L], n_v * vp, n_v, (long long)nb);        // rows x, K = (zb, y, zz)
-    M[MA_V0K + L] = make_arr(S->V[L], vp, n_v * nv8, (long long)nb);       // rows (y, x), K = z
+    M[MA_V0 + L] = make_arr(S->V[L], n_v * vp, n_v, (long long)nb, s);        // rows x, K = (zb, y, zz)
+    M[MA_V0K + L] = make_arr(S->V[L], vp, n_v * nv8, (long long)nb, s);       // rows (y, x), K = z
   }
-  M[MB_ZG] = make_arr(S->Zg, n_v * vp, n_v, n_o);
-  M[MB_ZH] = make_arr(S->Zh, n_v * vp, n_v, n_o);
-  M[MB_OO] = make_arr(S->OO, vp, n_o + 1, n_o * n_o);
-  M[MB_OV] = make_arr(S->OV, n_v * vp, 1, n_o * n_o);
+  M[MB_ZG] = make_arr(S->Zg, n_v * vp, n_v, n_o, s);
+  M[MB_ZH] = make_arr(S->Zh, n_v * vp, n_v, n_o, s);
+  M[MB_OO] = make_arr(S->OO, vp, n_o + 1, n_o * n_o, s);
+  M[MB_OV] = make_arr(S->OV, n_v * vp, 1, n_o * n_o, s);
   CU(cudaStreamSynchronize(st));
   S->staged = true;
   return CC3_OK;
@@ -418,9 +419,24 @@ void plan_w_split(SPlan &pab, SPlan &pc, SplitState *S, int no, int nv, const in
   w_terms_c(pc, jc, kStdMaps, no, nv, S->vp, S->op, ijk, ex, s);
 }
 
-// residual contractions of one triple (every distinct permutation)
+// Appends the jobs of src to dst (one launch runs dst's jobs in order).
+void append_plan(SPlan &dst, const SPlan &src) {
+  const int t0 = (int)dst.terms.size();
+  for (SJob j : src.jobs) {
+    j.term0 += t0;
+    j.tile_base += dst.tiles;
+    dst.jobs.push_back(j);
+  }
+  dst.terms.insert(dst.terms.end(), src.terms.begin(), src.terms.end());
+  dst.tiles += src.tiles;
+  dst.flop += src.flop;
+  dst.slice_flop += src.slice_flop;
+}
+
+// residual contractions of one triple (every distinct permutation); which:
+// bit 0 the vvov + singles jobs (long K), bit 1 the ooov + F jobs (short K)
 void plan_omega_split(SPlan &P, SplitState *S, int no, int nv, const int ijk[3], int slot,
-                      int ksplit4, double &ex) {
+                      int ksplit4, double &ex, int which = 3) {
   static const int PERM6[6][3] = {{0, 1, 2}, {1, 0, 2}, {2, 1, 0},
                                   {0, 2, 1}, {1, 2, 0}, {2, 0, 1}};
   const int s = S->s, vp = S->vp;
@@ -442,7 +458,7 @@ void plan_omega_split(SPlan &P, SplitState *S, int no, int nv, const int ijk[3],
     // layout with x slot outermost: K order (slot m0+1, slot m0+2)
     const int L = m[0];
     const bool yz = (m[1] == (L + 1) % 3);
-    {  // Omega~^{ad}_{pq} += sum_{yz} V[x][y][z] (dy|rz)   columns d < nv
+    if (which & 1) {  // Omega~^{ad}_{pq} += sum_{yz} V[x][y][z] (dy|rz)   columns d < nv
        // Omega1^x_p       += sum_{yz} V[x][y][z] (qy|rz)   tail column nv8
       const int nv8 = (nv + 7) / 8 * 8;
       int jb = new_sjob(P, nv, nv8 + 1, ntile_for(nv8 + 1), 1, ksplit4, SEPI_F64_ATOMIC, E, ex, s);
@@ -455,7 +471,7 @@ void plan_omega_split(SPlan &P, SplitState *S, int no, int nv, const int ijk[3],
       add_sterm(P, jb, opd(MA_V0 + L, slot), opd(yz ? MB_ZG : MB_ZH, r), nv * vp, 0, ex, s,
                 &tail, nv8);
     }
-    {  // Omega~^{xy}_{pl} -= sum_z V (ql|rz);  Omega~^{xy}_{pq} += sum_z V F_rz
+    if (which & 2) {  // Omega~^{xy}_{pl} -= sum_z V (ql|rz);  Omega~^{xy}_{pq} += sum_z V F_rz
       // layout Lz has z innermost; its rows (y_L, x_L) are the perm's (y, x) when
       // the perm's x slot is Lz, else (x, y); row m = y_L * nv8 + x_L
       const int Lz = (m[2] + 1) % 3;
@@ -492,25 +508,25 @@ int build_plans(cc3_ctx *c, SplitState *S, cudaStream_t st) {
   CU(cudaMemcpyAsync(eo.data(), c->eps_o, sizeof(double) * no, cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
   double ex = 0.0;
-  // K split of the vvov contraction: enough CTAs for two waves per batch
-  int sms = 152;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-  const int nv8 = (nv + 7) / 8 * 8;
-  const int tiles4 = ((nv + S_BM - 1) / S_BM) * ((nv8 + 1 + ntile_for(nv8 + 1) - 1) / ntile_for(nv8 + 1)) * 6 * S->batch;
+  // K split of the vvov contraction: tiles of about 400 K steps, so that the
+  // persistent engine balances them over the SMs (partial sums add in FP64)
   const int kst = nv * S->vp / S_BK;
-  int ks4 = std::max(1, std::min(kst / 64, (2 * sms + tiles4 - 1) / std::max(1, tiles4)));
+  int ks4 = std::max(1, (kst + 399) / 400);
   S->ks4 = ks4;
   for (int t0 = 0; t0 < c->ntri; t0 += S->batch) {
     const int t1 = std::min(c->ntri, t0 + S->batch);
-    SPlan pab, pc, pom;
+    SPlan pab, pc, pom, pom3;
     for (int t = t0; t < t1; ++t) {
       const int *ijk = &c->tri_host[3 * t];
       const double e = eo[ijk[0]] + eo[ijk[1]] + eo[ijk[2]];
       const dd::df ed = dd::from_double_host(e);
       const float eod[2] = {ed.hi, ed.lo};
       plan_w_split(pab, pc, S, no, nv, ijk, t - t0, eod, ex);
-      plan_omega_split(pom, S, no, nv, ijk, t - t0, ks4, ex);
+      // the long-K tiles first: the persistent engine hands tiles out in order
+      plan_omega_split(pom, S, no, nv, ijk, t - t0, ks4, ex, 1);
+      plan_omega_split(pom3, S, no, nv, ijk, t - t0, ks4, ex, 2);
     }
+    append_plan(pom, pom3);
     S->ab.emplace_back();
     S->cc.emplace_back();
     S->om.emplace_back();
@@ -667,9 +683,9 @@ int stage_jac_static(cc3_ctx *c, SplitState *S, cudaStream_t st) {
   g = {0, 0, nv, ovl, 1, nvo, no, no, nv, nv, nv, 1};
   TRY(slice_array(S, &S->OVZB, c->ovov, (long long)no * no, nv * vp, S->Eg, g, no, st));
   SArr *M = S->arrs.a;
-  M[MJ_OVD] = make_arr(S->OVD, vp, nv, (long long)no * no);
-  M[MJ_OVZA] = make_arr(S->OVZA, (long long)nv * vp, no, no);
-  M[MJ_OVZB] = make_arr(S->OVZB, (long long)nv * vp, no, no);
+  M[MJ_OVD] = make_arr(S->OVD, vp, nv, (long long)no * no, S->s);
+  M[MJ_OVZA] = make_arr(S->OVZA, (long long)nv * vp, no, no, S->s);
+  M[MJ_OVZB] = make_arr(S->OVZB, (long long)nv * vp, no, no, S->s);
   return CC3_OK;
 }
 
@@ -823,34 +839,34 @@ int split_jacobian(cc3_ctx *c, int nvec, const double *w, const double *R1d, con
     g = {0, (long long)no * nv2, nv2, nv, 0, 1, no, nv, vp, nv, 1};
     TRY(slice_array(S, &a, r2, (long long)no * no * nv, vp, ER, g, nv, st));
     B.p.push_back(a);
-    M[MJ_R2S] = make_arr(a, vp, nv, (long long)no * no);
+    M[MJ_R2S] = make_arr(a, vp, nv, (long long)no * no, s);
     g = {0, (long long)no * nv2, 1, nv, 0, nv2, nv, nv, op, no, 1};
     TRY(slice_array(S, &a, r2, (long long)no * nv * nv, op, ER, g, nv, st));
     B.p.push_back(a);
-    M[MJ_R2C] = make_arr(a, op, nv, (long long)no * nv);
+    M[MJ_R2C] = make_arr(a, op, nv, (long long)no * nv, s);
     g = {0, (long long)no * nv2, nv, 1, 0, nv2, nv, nv, op, no, 1};
     TRY(slice_array(S, &a, r2, (long long)no * nv * nv, op, ER, g, nv, st));
     B.p.push_back(a);
-    M[MJ_R2R] = make_arr(a, op, nv, (long long)no * nv);
+    M[MJ_R2R] = make_arr(a, op, nv, (long long)no * nv, s);
     g = {0, 1, no, nv2 * no, 0, nvo, nv, nv, vp, nv, 1};
     TRY(slice_array(S, &a, gv, (long long)no * nv * nv, vp, EH, g, nv, st));
     B.p.push_back(a);
-    M[MJ_XH] = make_arr(a, vp, nv, (long long)no * nv);
+    M[MJ_XH] = make_arr(a, vp, nv, (long long)no * nv, s);
     g = {0, 1, nv2 * no, no, 0, nvo, nv, nv, vp, nv, 1};
     TRY(slice_array(S, &a, gv, (long long)no * nv * nv, vp, EH, g, nv, st));
     B.p.push_back(a);
-    M[MJ_YH] = make_arr(a, vp, nv, (long long)no * nv);
+    M[MJ_YH] = make_arr(a, vp, nv, (long long)no * nv, s);
     g = {0, nvo, 1, no, 0, (long long)no * nv * no, no, nv, op, no, 1};
     TRY(slice_array(S, &a, go, (long long)no * no * nv, op, EH, g, nv, st));
     B.p.push_back(a);
-    M[MJ_OH] = make_arr(a, op, nv, (long long)no * no);
+    M[MJ_OH] = make_arr(a, op, nv, (long long)no * no, s);
   }
   {
     __nv_bfloat16 *a = nullptr;
     Gather g = {0, 0, nv, nvo, 0, 1, no, nvec, vp, nv, 1};
     TRY(slice_array(S, &a, hf, (long long)no * nvec, vp, EF, g, nvec, st));
     B.p.push_back(a);
-    for (int v = 0; v < nvec; ++v) arrs[v].a[MJ_FH] = make_arr(a, vp, nvec, no);
+    for (int v = 0; v < nvec; ++v) arrs[v].a[MJ_FH] = make_arr(a, vp, nvec, no, s);
     S->arrs.a[MJ_FH] = arrs[0].a[MJ_FH];
   }
   // plans per batch: R3 phase AB (shared by the vectors), phase C per vector
@@ -1033,8 +1049,8 @@ int debug_split_gemm(int M, int N, int K, const double *A, const double *B, doub
     gB = gA;
     CK(launch_slice_gather(dA, sA, s, eA, gA, M, Kp, M, st));
     CK(launch_slice_gather(dB, sB, s, eB, gB, N, Kp, N, st));
-    arrs.a[0] = make_arr(sA, Kp, M, 1);
-    arrs.a[1] = make_arr(sB, Kp, N, 1);
+    arrs.a[0] = make_arr(sA, Kp, M, 1, s);
+    arrs.a[1] = make_arr(sB, Kp, N, 1, s);
     int jb = new_sjob(P, M, N, Nt, 1, 1, SEPI_F64_ATOMIC, eA + eB - 14, ex, s);
     P.jobs[jb].C = outd(0, 0, N, 1);
     P.jobs[jb].Ct = P.jobs[jb].C;

@@ -13,9 +13,10 @@
 // 4 products of |d d'| <= 2^14 per K); the levels >= 4 share a fifth,
 // rounded accumulator (its error stays below 2^-50 of the result).
 //
-// Warp roles (576 threads): warp 0 issues one bulk copy per slice tile into a
-// 3-stage ring of (s A-slices, s B-slices) tiles of 128 x 16 and Ntile x 16
-// BF16 (pre-tiled in global memory in the canonical no-swizzle order); one thread of warp 1 issues tcgen05.mma (M = 128, N = Ntile <= 96,
+// Warp roles (576 threads): warp 0 issues one bulk copy per operand tile (all
+// s slices of a 128 x 16 A tile, resp. an Ntile x 16 B tile, pre-tiled in
+// global memory in the canonical no-swizzle order with the slices interleaved
+// per row group) into a ring of stages; one thread of warp 1 issues tcgen05.mma (M = 128, N = Ntile <= 96,
 // K = 16, FP32 accumulate) and owns the tensor-memory allocation (5 x Ntile
 // columns); warps 2-17 drain and finish the accumulators (each quadrant of 32
 // TMEM lanes is read by four warps, one per column quarter, 4 columns per
@@ -68,13 +69,57 @@ __device__ __forceinline__ void issue_products(uint32_t tmem, uint64_t dA, uint6
   }
 }
 
+// Position of one tile within its job: batch index, K-split part, M/N tile
+// and its K-step range [g0, g1) over the concatenated terms.
+struct TileInfo {
+  int j, bi, m0, n0, Nt, g0, g1;
+};
+
+// jhint: the job of this CTA's previous tile (tiles are taken in increasing
+// order, so the search only moves forward).
+__device__ __forceinline__ TileInfo decode_tile(const SJob *__restrict__ jobs, int njobs,
+                                                const STerm *__restrict__ terms, long long tile,
+                                                int &jhint) {
+  int j = jhint;
+  if (j >= njobs || jobs[j].tile_base > tile) j = 0;
+  while (j + 1 < njobs && jobs[j + 1].tile_base <= tile) ++j;
+  jhint = j;
+  const SJob &J = jobs[j];
+  TileInfo t;
+  t.j = j;
+  const long long local = tile - J.tile_base;
+  const int per_batch = J.tiles_m * J.tiles_n * J.ksplit;
+  t.bi = (int)(local / per_batch);
+  int r = (int)(local % per_batch);
+  const int ks = r % J.ksplit;
+  r /= J.ksplit;
+  const int tn = r % J.tiles_n, tm = r / J.tiles_n;
+  t.m0 = tm * S_BM;
+  t.Nt = J.Ntile;
+  t.n0 = tn * J.Ntile;
+  int total = 0;
+  for (int q = 0; q < J.nterm; ++q) total += terms[J.term0 + q].ksteps;
+  const int per = (total + J.ksplit - 1) / J.ksplit;
+  t.g0 = min(total, ks * per);
+  t.g1 = min(total, t.g0 + per);
+  return t;
+}
+
+// Persistent: one CTA per SM takes tiles from a launch-wide counter (the plan
+// lists long tiles first) and keeps the stage ring, the TMEM allocation and
+// the barriers across tiles.  The producer fetches each tile index and hands
+// it to the MMA thread and the epilogue warps through a small ring in shared
+// memory; the epilogue releases the accumulators as soon as it has read them,
+// so the next tile's products start while it finishes the previous outputs.
 template <int S>
 __global__ void __maxnreg__(96)
 split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__restrict__ terms,
                     const __grid_constant__ SArrTable arrs, VPtrTable P,
-                    int kdrain_steps, int *status) {
+                    int kdrain_steps, int *status, unsigned long long *tile_ctr,
+                    long long ntiles) {
   constexpr int s = S;
   constexpr int S_STAGES = s_stages(S);
+  constexpr int TQ = 4;  // depth of the tile hand-off ring
   // accumulators that receive products: level L <= 3 exists iff L <= S-1,
   // the shared one (levels >= 4) iff S >= 5
   constexpr int NLOW = S < 4 ? S : 4;
@@ -83,43 +128,24 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t full[S_STAGES], empty[S_STAGES];
-  __shared__ __align__(8) uint64_t accfull, drainfull, drainempty;
+  __shared__ __align__(8) uint64_t accfull, accempty, drainfull, drainempty;
+  __shared__ __align__(8) uint64_t tfull[TQ], tempty[TQ];
+  __shared__ long long tq[TQ];
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int err;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long cta = blockIdx.x;
-  int lo = 0, hi = njobs - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (jobs[mid].tile_base <= cta) lo = mid; else hi = mid - 1;
-  }
-  const SJob &J = jobs[lo];
-  long long local = cta - J.tile_base;
-  const int per_batch = J.tiles_m * J.tiles_n * J.ksplit;
-  const int bi = (int)(local / per_batch);
-  int r = (int)(local % per_batch);
-  const int ks = r % J.ksplit;
-  r /= J.ksplit;
-  const int tn = r % J.tiles_n, tm = r / J.tiles_n;
-  const int m0 = tm * S_BM, n0 = tn * J.Ntile;
-  const int Nt = J.Ntile;
-  const uint32_t a_bytes = S_BM * 32, b_bytes = (uint32_t)Nt * 32;
-  const uint32_t stage_bytes = (uint32_t)s * (a_bytes + b_bytes);
-
-  int total = 0;
-  for (int t = 0; t < J.nterm; ++t) total += terms[J.term0 + t].ksteps;
-  const int per = (total + J.ksplit - 1) / J.ksplit;
-  const int g0 = min(total, ks * per), g1 = min(total, g0 + per);
-  const int nsteps = g1 - g0;
-  const int ndrains = nsteps > 0 ? (nsteps - 1) / kdrain_steps : 0;
-
   if (threadIdx.x == 0) {
     for (int i = 0; i < S_STAGES; ++i) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
     }
+    for (int i = 0; i < TQ; ++i) {
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], 1 + S_EPI_WARPS);
+    }
     mbar_init(&accfull, 1);
+    mbar_init(&accempty, S_EPI_WARPS);
     mbar_init(&drainfull, 1);
     mbar_init(&drainempty, S_EPI_WARPS);
     err = 0;
@@ -130,196 +156,247 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base_sh;
+  const uint32_t a_bytes = S_BM * 32;
 
   if (warp == 0) {
-    if (lane == 0 && nsteps > 0) {
-      // producer
-      int t = 0, kbase = 0;
-      while (t < J.nterm && kbase + terms[J.term0 + t].ksteps <= g0) {
-        kbase += terms[J.term0 + t].ksteps;
-        ++t;
-      }
-      int issued = 0;
-      for (int g = g0; g < g1; ++g) {
-        while (g - kbase >= terms[J.term0 + t].ksteps) {
+    if (lane == 0) {
+      // producer: tile indices, then the operand tiles of every K step
+      int issued = 0, jh = 0;
+      for (int i = 0;; ++i) {
+        const int q = i % TQ;
+        if (!mbar_wait(&tempty[q], ((i / TQ) & 1) ^ 1, &err)) break;
+        const long long tile = (long long)atomicAdd(tile_ctr, 1ull);
+        tq[q] = tile < ntiles ? tile : -1;
+        mbar_arrive(&tfull[q]);
+        if (tile >= ntiles) break;
+        const TileInfo ti = decode_tile(jobs, njobs, terms, tile, jh);
+        const SJob &J = jobs[ti.j];
+        const int Nt = ti.Nt, bi = ti.bi, m0 = ti.m0, n0 = ti.n0;
+        int t = 0, kbase = 0;
+        while (t < J.nterm && kbase + terms[J.term0 + t].ksteps <= ti.g0) {
           kbase += terms[J.term0 + t].ksteps;
           ++t;
         }
-        const STerm &T = terms[J.term0 + t];
-        const int kb = g - kbase;
-        const int st = issued % S_STAGES, ph = (issued / S_STAGES) & 1;
-        if (!mbar_wait(&empty[st], ph ^ 1, &err)) break;
-        const SArr &XA = arrs.a[T.A.map], &XB = arrs.a[T.B.map], &XT = arrs.a[T.Bt.map];
-        const int ar = T.A.row0 + bi * T.A.row_b + m0, as = T.A.slab0 + bi * T.A.slab_b;
-        const int bs = T.B.slab0 + bi * T.B.slab_b, ts = T.Bt.slab0 + bi * T.Bt.slab_b;
-        // B tile rows [n0, n0 + Nt): main rows from B, rows >= nbm from the tail Bt
-        const int nbm = T.nbm > 0 ? T.nbm : (1 << 30);
-        const int br = T.B.row0 + bi * T.B.row_b + n0;
-        const int nmain = max(0, min(min(Nt, nbm - n0), XB.rows - br));
-        const int tfirst = max(n0, nbm);                  // first tail row of the tile
-        const int tr = T.Bt.row0 + tfirst - nbm;          // its row in Bt
-        const int ntail = T.nbm > 0 ? max(0, min(n0 + Nt - tfirst, XT.rows - tr)) : 0;
-        if (as < 0 || as >= XA.slabs || kb >= XA.kblocks || ar < 0 || ar >= XA.rows ||
-            (nmain > 0 && (bs < 0 || bs >= XB.slabs || kb >= XB.kblocks || br < 0)) ||
-            (ntail > 0 && (ts < 0 || ts >= XT.slabs || kb >= XT.kblocks || tr < 0 ||
-                           ((tfirst - n0) & 7) != 0))) {
-          err = 2;  // a plan addressed outside its slice array: stop, report
-          break;
+        bool bad = false;
+        for (int g = ti.g0; g < ti.g1; ++g) {
+          while (g - kbase >= terms[J.term0 + t].ksteps) {
+            kbase += terms[J.term0 + t].ksteps;
+            ++t;
+          }
+          const STerm &T = terms[J.term0 + t];
+          const int kb = g - kbase;
+          const int st = issued % S_STAGES, ph = (issued / S_STAGES) & 1;
+          if (!mbar_wait(&empty[st], ph ^ 1, &err)) { bad = true; break; }
+          const SArr &XA = arrs.a[T.A.map], &XB = arrs.a[T.B.map], &XT = arrs.a[T.Bt.map];
+          const int ar = T.A.row0 + bi * T.A.row_b + m0, as = T.A.slab0 + bi * T.A.slab_b;
+          const int bs = T.B.slab0 + bi * T.B.slab_b, ts = T.Bt.slab0 + bi * T.Bt.slab_b;
+          // B tile rows [n0, n0 + Nt): main rows from B, rows >= nbm from the tail Bt
+          const int nbm = T.nbm > 0 ? T.nbm : (1 << 30);
+          const int br = T.B.row0 + bi * T.B.row_b + n0;
+          const int nmain = max(0, min(min(Nt, nbm - n0), XB.rows - br));
+          const int tfirst = max(n0, nbm);                  // first tail row of the tile
+          const int tr = T.Bt.row0 + tfirst - nbm;          // its row in Bt
+          const int ntail = T.nbm > 0 ? max(0, min(n0 + Nt - tfirst, XT.rows - tr)) : 0;
+          if (as < 0 || as >= XA.slabs || kb >= XA.kblocks || ar < 0 || ar >= XA.rows ||
+              (nmain > 0 && (bs < 0 || bs >= XB.slabs || kb >= XB.kblocks || br < 0)) ||
+              (ntail > 0 && (ts < 0 || ts >= XT.slabs || kb >= XT.kblocks || tr < 0 ||
+                             ((tfirst - n0) & 7) != 0))) {
+            err = 2;  // a plan addressed outside its slice array: stop, report
+            bad = true;
+            break;
+          }
+          const int ra = min(S_BM, XA.rows - ar);
+          const uint32_t abytes = (uint32_t)ra * 32u;
+          const uint32_t mbytes = (uint32_t)nmain * 32u, tbytes = (uint32_t)ntail * 32u;
+          mbar_arrive_expect_tx(&full[st], (uint32_t)s * (abytes + mbytes + tbytes));
+          // stage layout: s A slices (128 rows) then s B slices (S_NT_MAX rows)
+          uint8_t *sa = smem + (size_t)st * ((size_t)s * (a_bytes + S_NT_MAX * 32));
+          uint8_t *sb = sa + (size_t)s * a_bytes;
+          // one bulk copy per operand tile: its s slices are contiguous
+          const __nv_bfloat16 *ga = reinterpret_cast<const __nv_bfloat16 *>(XA.base) +
+                                    (long long)as * XA.slab_stride + (long long)kb * XA.kb_stride +
+                                    (long long)ar * 16 * s;
+          bulk_load(sa, ga, (uint32_t)s * abytes, &full[st]);
+          if (mbytes) {
+            const __nv_bfloat16 *gb = reinterpret_cast<const __nv_bfloat16 *>(XB.base) +
+                                      (long long)bs * XB.slab_stride +
+                                      (long long)kb * XB.kb_stride + (long long)br * 16 * s;
+            bulk_load(sb, gb, (uint32_t)s * mbytes, &full[st]);
+          }
+          if (tbytes) {
+            const __nv_bfloat16 *gt = reinterpret_cast<const __nv_bfloat16 *>(XT.base) +
+                                      (long long)ts * XT.slab_stride +
+                                      (long long)kb * XT.kb_stride + (long long)tr * 16 * s;
+            bulk_load(sb + (size_t)(tfirst - n0) * 32 * s, gt, (uint32_t)s * tbytes, &full[st]);
+          }
+          ++issued;
         }
-        const int ra = min(S_BM, XA.rows - ar);
-        const uint32_t abytes = (uint32_t)ra * 32u;
-        const uint32_t mbytes = (uint32_t)nmain * 32u, tbytes = (uint32_t)ntail * 32u;
-        mbar_arrive_expect_tx(&full[st], (uint32_t)s * (abytes + mbytes + tbytes));
-        uint8_t *sa = smem + (size_t)st * stage_bytes;
-        uint8_t *sb = sa + (size_t)s * a_bytes;
-        const __nv_bfloat16 *ga = reinterpret_cast<const __nv_bfloat16 *>(XA.base) +
-                                  (long long)as * XA.slab_stride +
-                                  ((long long)kb * XA.rows + ar) * 16;
-        for (int p = 0; p < s; ++p)
-          bulk_load(sa + p * a_bytes, ga + p * XA.slice_stride, abytes, &full[st]);
-        if (mbytes) {
-          const __nv_bfloat16 *gb = reinterpret_cast<const __nv_bfloat16 *>(XB.base) +
-                                    (long long)bs * XB.slab_stride +
-                                    ((long long)kb * XB.rows + br) * 16;
-          for (int q = 0; q < s; ++q)
-            bulk_load(sb + q * b_bytes, gb + q * XB.slice_stride, mbytes, &full[st]);
-        }
-        if (tbytes) {
-          const __nv_bfloat16 *gt = reinterpret_cast<const __nv_bfloat16 *>(XT.base) +
-                                    (long long)ts * XT.slab_stride +
-                                    ((long long)kb * XT.rows + tr) * 16;
-          for (int q = 0; q < s; ++q)
-            bulk_load(sb + q * b_bytes + (tfirst - n0) * 32, gt + q * XT.slice_stride, tbytes,
-                      &full[st]);
-        }
-        ++issued;
+        if (bad) break;
       }
       // let every issued copy land before the CTA may exit (bounded)
       for (int i = (issued > S_STAGES ? issued - S_STAGES : 0); i < issued; ++i)
         mbar_wait(&full[i % S_STAGES], (i / S_STAGES) & 1, &err, 500000000ull);
     }
   } else if (warp == 1) {
-    if (lane == 0 && nsteps > 0) {
+    if (lane == 0) {
       // MMA issuer
-      const uint32_t id_pos = idesc_bf16(S_BM, Nt, 0), id_neg = idesc_bf16(S_BM, Nt, 1);
-      int t = 0, kbase = 0;
-      while (t < J.nterm && kbase + terms[J.term0 + t].ksteps <= g0) {
-        kbase += terms[J.term0 + t].ksteps;
-        ++t;
-      }
-      uint32_t fresh = (1u << S_NACC) - 1;
-      int since = 0, nd = 0;
-      bool pending = false;
-      for (int g = g0, it = 0; g < g1; ++g, ++it) {
-        while (g - kbase >= terms[J.term0 + t].ksteps) {
+      int it = 0, nd = 0, jh = 0;
+      bool ok = true;
+      for (int i = 0; ok; ++i) {
+        const int q = i % TQ;
+        if (!mbar_wait(&tfull[q], (i / TQ) & 1, &err)) break;
+        const long long tile = tq[q];
+        mbar_arrive(&tempty[q]);
+        if (tile < 0) break;
+        const TileInfo ti = decode_tile(jobs, njobs, terms, tile, jh);
+        const SJob &J = jobs[ti.j];
+        const int Nt = ti.Nt;
+        const uint32_t id_pos = idesc_bf16(S_BM, Nt, 0), id_neg = idesc_bf16(S_BM, Nt, 1);
+        // the epilogue has read the previous tile's accumulators
+        if (i > 0) {
+          if (!mbar_wait(&accempty, (i - 1) & 1, &err)) break;
+          tc_fence_after();
+        }
+        int t = 0, kbase = 0;
+        while (t < J.nterm && kbase + terms[J.term0 + t].ksteps <= ti.g0) {
           kbase += terms[J.term0 + t].ksteps;
           ++t;
         }
-        const uint32_t idesc = terms[J.term0 + t].negA ? id_neg : id_pos;
-        const int st = it % S_STAGES, ph = (it / S_STAGES) & 1;
-        if (!mbar_wait(&full[st], ph, &err)) break;
-        tc_fence_after();
-        const uint32_t sa = smem_u32(smem + (size_t)st * stage_bytes);
-        const uint64_t dA = smem_desc_noswz(sa), dB = smem_desc_noswz(sa + (uint32_t)s * a_bytes);
-        // levels >= 4 first (they never wait for a drain), then levels 0..3
-        issue_products<S, true>(tmem, dA, dB, a_bytes >> 4, b_bytes >> 4, (uint32_t)Nt, idesc, fresh);
-        if (pending) {
-          if (!mbar_wait(&drainempty, nd & 1, &err)) break;
+        uint32_t fresh = (1u << S_NACC) - 1;
+        int since = 0;
+        bool pending = false;
+        for (int g = ti.g0; g < ti.g1; ++g, ++it) {
+          while (g - kbase >= terms[J.term0 + t].ksteps) {
+            kbase += terms[J.term0 + t].ksteps;
+            ++t;
+          }
+          const uint32_t idesc = terms[J.term0 + t].negA ? id_neg : id_pos;
+          const int st = it % S_STAGES, ph = (it / S_STAGES) & 1;
+          if (!mbar_wait(&full[st], ph, &err)) { ok = false; break; }
           tc_fence_after();
-          ++nd;
-          pending = false;
-          fresh |= 0xFu;
+          const uint32_t sa = smem_u32(smem + (size_t)st * ((size_t)s * (a_bytes + S_NT_MAX * 32)));
+          // slice p of a tile starts 256 p bytes in; row groups are 256 s bytes apart
+          const uint64_t dA = smem_desc_kmajor(sa, 256u * s),
+                         dB = smem_desc_kmajor(sa + (uint32_t)s * a_bytes, 256u * s);
+          // levels >= 4 first (they never wait for a drain), then levels 0..3
+          issue_products<S, true>(tmem, dA, dB, 16u, 16u, (uint32_t)Nt, idesc, fresh);
+          if (pending) {
+            if (!mbar_wait(&drainempty, nd & 1, &err)) { ok = false; break; }
+            tc_fence_after();
+            ++nd;
+            pending = false;
+            fresh |= 0xFu;
+          }
+          issue_products<S, false>(tmem, dA, dB, 16u, 16u, (uint32_t)Nt, idesc, fresh);
+          umma_commit(&empty[st]);
+          if (++since == kdrain_steps && g + 1 < ti.g1) {
+            umma_commit(&drainfull);
+            pending = true;
+            since = 0;
+          }
         }
-        issue_products<S, false>(tmem, dA, dB, a_bytes >> 4, b_bytes >> 4, (uint32_t)Nt, idesc, fresh);
-        umma_commit(&empty[st]);
-        if (++since == kdrain_steps && g + 1 < g1) {
-          umma_commit(&drainfull);
-          pending = true;
-          since = 0;
-        }
+        if (!ok) break;
+        umma_commit(&accfull);
       }
-      umma_commit(&accfull);
     }
   } else {
     // epilogue: warps 2..17
     const int ew = warp - 2, quad = warp & 3, part = ew >> 2;
     const int row = quad * 32 + lane;
-    const int m = m0 + row;
-    const int qc = Nt >> 2;        // columns per quarter (multiple of 4, <= 24)
-    const int nch = qc >> 2;       // 4-column chunks (<= 6)
-    const uint32_t tb = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(part * qc);
-    dd::df acc[6][4];
+    int nd = 0, jh = 0;
+    for (int i = 0;; ++i) {
+      const int q = i % TQ;
+      if (!mbar_wait_sleep(&tfull[q], (i / TQ) & 1, &err)) break;
+      const long long tile = tq[q];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[q]);
+      if (tile < 0) break;
+      const TileInfo ti = decode_tile(jobs, njobs, terms, tile, jh);
+      const SJob &J = jobs[ti.j];
+      const int Nt = ti.Nt, bi = ti.bi, n0 = ti.n0;
+      const int m = ti.m0 + row;
+      const int nsteps = ti.g1 - ti.g0;
+      const int ndrains = nsteps > 0 ? (nsteps - 1) / kdrain_steps : 0;
+      const int qc = Nt >> 2;   // columns per quarter (multiple of 4, <= 24)
+      const int nch = qc >> 2;  // 4-column chunks (<= 6)
+      const uint32_t tb = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(part * qc);
+      dd::df acc[6][4];
 #pragma unroll
-    for (int c = 0; c < 6; ++c)
+      for (int c = 0; c < 6; ++c)
 #pragma unroll
-      for (int i = 0; i < 4; ++i) acc[c][i] = {0.f, 0.f};
-    bool ok = true;
-    for (int d = 0; d < ndrains && ok; ++d) {
-      ok = mbar_wait_sleep(&drainfull, d & 1, &err);
+        for (int k = 0; k < 4; ++k) acc[c][k] = {0.f, 0.f};
+      bool ok = true;
+      for (int d = 0; d < ndrains && ok; ++d, ++nd) {
+        ok = mbar_wait_sleep(&drainfull, nd & 1, &err);
+        if (!ok) break;
+        tc_fence_after();
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          if (c < nch) {
+            float v[4][4];
+#pragma unroll
+            for (int L = 0; L < 4; ++L) {
+              if (L < NLOW) {
+                tmem_ld4(tb + L * Nt + c * 4, v[L]);
+              } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) v[L][k] = 0.f;
+              }
+            }
+            tmem_wait_ld();
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              dd::df x = dd::two_sum(v[0][k], v[1][k]);
+              x = dd::add_f(x, v[2][k]);
+              x = dd::add_f(x, v[3][k]);
+              acc[c][k] = dd::add(acc[c][k], x);
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&drainempty);
+      }
       if (!ok) break;
+      if (!mbar_wait_sleep(&accfull, i & 1, &err)) break;
       tc_fence_after();
+      // fold the final partial sums into acc, then hand the accumulators back
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
-        if (c < nch) {
-          float v[4][4];
+        if (c < nch && nsteps > 0) {
+          float v[5][4];
 #pragma unroll
-          for (int L = 0; L < 4; ++L) {
-            if (L < NLOW) {
+          for (int L = 0; L < 5; ++L) {
+            if (L < NLOW || (L == 4 && HAS_HIGH)) {
               tmem_ld4(tb + L * Nt + c * 4, v[L]);
             } else {
 #pragma unroll
-              for (int i = 0; i < 4; ++i) v[L][i] = 0.f;
+              for (int k = 0; k < 4; ++k) v[L][k] = 0.f;
             }
           }
           tmem_wait_ld();
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            dd::df x = dd::two_sum(v[0][i], v[1][i]);
-            x = dd::add_f(x, v[2][i]);
-            x = dd::add_f(x, v[3][i]);
-            acc[c][i] = dd::add(acc[c][i], x);
+          for (int k = 0; k < 4; ++k) {
+            dd::df x = dd::two_sum(v[0][k], v[1][k]);
+            x = dd::add_f(x, v[2][k]);
+            x = dd::add_f(x, v[3][k]);
+            x = dd::add(acc[c][k], x);
+            acc[c][k] = dd::add_f(x, v[4][k]);
           }
         }
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&drainempty);
-    }
-    if (ok && nsteps > 0) ok = mbar_wait_sleep(&accfull, 0, &err);
-    if (ok) {
-      tc_fence_after();
+      if (lane == 0) mbar_arrive(&accempty);
       const int ex = J.expo + (J.expo_slot >= 0 ? reinterpret_cast<const int *>(P.p[B_SLOTEXP])[J.expo_slot] : 0);
       const float sc = ldexpf(J.mult, ex);
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
         if (c < nch) {
-          float v[5][4];
-          if (nsteps > 0) {
 #pragma unroll
-            for (int L = 0; L < 5; ++L) {
-              if (L < NLOW || (L == 4 && HAS_HIGH)) {
-                tmem_ld4(tb + L * Nt + c * 4, v[L]);
-              } else {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) v[L][i] = 0.f;
-              }
-            }
-            tmem_wait_ld();
-          } else {
-#pragma unroll
-            for (int L = 0; L < 5; ++L)
-#pragma unroll
-              for (int i = 0; i < 4; ++i) v[L][i] = 0.f;
-          }
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            dd::df x = dd::two_sum(v[0][i], v[1][i]);
-            x = dd::add_f(x, v[2][i]);
-            x = dd::add_f(x, v[3][i]);
-            x = dd::add(acc[c][i], x);
-            x = dd::add_f(x, v[4][i]);
-            x = dd::scale(x, sc);
-            const int n = n0 + part * qc + c * 4 + i;
+          for (int k = 0; k < 4; ++k) {
+            const dd::df x = dd::scale(acc[c][k], sc);
+            const int n = n0 + part * qc + c * 4 + k;
             if (m >= J.M || n >= J.N || (J.m_pad > 0 && (m % J.m_pad) >= J.m_valid) ||
                 (n < J.Nm && n >= J.n_valid))
               continue;
@@ -364,6 +441,7 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
 
 int s_upload_plan(const SPlan &p, SDevPlan *d, cudaStream_t s) {
   s_free_plan(d);
+  if (cudaMalloc(&d->counter, sizeof(unsigned long long)) != cudaSuccess) return CC3_ERR_OOM;
   d->njobs = (int)p.jobs.size();
   d->tiles = p.tiles;
   d->flop = p.flop;
@@ -384,6 +462,8 @@ int s_upload_plan(const SPlan &p, SDevPlan *d, cudaStream_t s) {
 }
 
 void s_free_plan(SDevPlan *d) {
+  if (d->counter) cudaFree(d->counter);
+  d->counter = nullptr;
   if (d->jobs) cudaFree(d->jobs);
   if (d->terms) cudaFree(d->terms);
   d->jobs = nullptr;
@@ -423,11 +503,16 @@ int s_launch_plan(const SDevPlan &d, const SArrTable &arrs, const VPtrTable &ptr
     }
     attr_set[dev] = true;
   }
+  static int sms[64] = {0};
+  if (!sms[dev]) cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+  const unsigned grid = (unsigned)std::min<long long>(d.tiles, std::max(1, sms[dev]));
+  const cudaError_t me = cudaMemsetAsync(d.counter, 0, sizeof(unsigned long long), s);
+  if (me != cudaSuccess) return CC3_FAIL(CC3_ERR_CUDA, cudaGetErrorString(me));
   switch (slices) {
 #define CC3_SPLIT_LAUNCH(S_)                                                              \
   case S_:                                                                                \
-    split_engine_kernel<S_><<<(unsigned)d.tiles, S_THREADS, smem, s>>>(                   \
-        d.jobs, d.njobs, d.terms, arrs, ptrs, kdrain_steps, status);                      \
+    split_engine_kernel<S_><<<grid, S_THREADS, smem, s>>>(                                \
+        d.jobs, d.njobs, d.terms, arrs, ptrs, kdrain_steps, status, d.counter, d.tiles);  \
     break;
     CC3_SPLIT_LAUNCH(3)
     CC3_SPLIT_LAUNCH(4)

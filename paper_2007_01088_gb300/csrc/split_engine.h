@@ -9,10 +9,12 @@ namespace cc3 {
 enum { SMAX_MAPS = 32, S_BM = 128, S_BK = 16, S_STAGES_MAX = 6, S_MAX_SLICES = 7,
        S_NT_MAX = 96, S_NACC = 5, S_DRAIN_STEPS = 16, S_EPI_WARPS = 16, S_THREADS = 64 + 32 * S_EPI_WARPS };
 
-// A BF16 slice array in the tensor cores' canonical no-swizzle K-major order:
-// [slice][slab][K/16][row groups of 8][2 K halves][8 rows][8 elements].  Each
-// 16 x R tile (R rows from a multiple of 8) is then one contiguous block of
-// 32 R bytes, moved by a single bulk copy.
+// A BF16 slice array in the tensor cores' canonical no-swizzle K-major order
+// with the slices interleaved per core-matrix row group:
+// [slab][K/16][row groups of 8][slice][2 K halves][8 rows][8 elements].  The
+// s slices of any 16 x R tile (R rows from a multiple of 8) are then one
+// contiguous block of 32 s R bytes, moved by a single bulk copy; slice p of
+// the tile starts 256 p bytes in and its row groups are 256 s bytes apart.
 // Pipeline depth for S slices: as many (A, B) stages of 128 + 96 rows as fit
 // in ~216 KB of shared memory, at most S_STAGES_MAX.
 __host__ __device__ constexpr int s_stages(int S) {
@@ -23,8 +25,8 @@ __host__ __device__ constexpr int s_stages(int S) {
 
 struct SArr {
   unsigned long long base;  // device address
-  long long slab_stride;    // elements
-  long long slice_stride;   // elements
+  long long slab_stride;    // elements (all slices)
+  long long kb_stride;      // elements of one 16-wide K block (all slices, all rows)
   int rows;                 // rows per slab, padded to a multiple of 8
   int kblocks;              // K / 16
   int slabs;                // number of slabs (bounds check)
@@ -81,6 +83,7 @@ struct SPlan {
 };
 
 struct SDevPlan {
+  unsigned long long *counter = nullptr;  // tiles handed out in the current launch
   SJob *jobs = nullptr;
   STerm *terms = nullptr;
   int njobs = 0;

@@ -66,26 +66,26 @@ __device__ __forceinline__ void store_digits(long long T, int s, __nv_bfloat16 *
     if (p < s) dst[p * slice_stride] = __float2bfloat16_rn(ldexpf(d[p], -8 * p));
 }
 
-// Offset of (row r, k in 0..15) inside one 16-column K block of R8 rows, in
-// the tensor cores' canonical no-swizzle K-major order: core matrices of
-// 8 rows x 8 elements (128 contiguous bytes), the two K halves 64 elements
-// apart, 8-row groups 128 elements apart.
-__device__ __forceinline__ long long cm_off(long long r, int k) {
-  return (r >> 3) * 128 + (k >> 3) * 64 + (r & 7) * 8 + (k & 7);
+// Offset of slice 0 of (row r, k in 0..15) inside one 16-column K block of
+// rows, in the tensor cores' canonical no-swizzle K-major order with the s
+// slices interleaved per row group: each group of 8 rows holds, for slice
+// 0..s-1 in turn, two 8 x 8 core matrices (the K halves, 64 elements apart);
+// slice p is 128 p elements further, the next row group 128 s elements.
+__device__ __forceinline__ long long cm_off(long long r, int k, int s) {
+  return (r >> 3) * (128LL * s) + (k >> 3) * 64 + (r & 7) * 8 + (k & 7);
 }
 
 // Slices of an FP64 tensor read through a strided gather
 //   row = (r2, r1, r0), k = (k1, k0); value 0 outside (k0 < k0v, k1 < k1v),
-// stored K-blocked: [p][slab][K/16][rps8 rows, core-matrix order], row =
-// slab * rps + r, rps8 = rps rounded up to 8.  Every 16 x R tile the tensor
-// cores read is one contiguous block.
+// stored K-blocked: [slab][K/16][row groups][slice][8 x 16], row =
+// slab * rps + r, rows per slab rounded up to 8.  The slices of every 16 x R
+// tile the tensor cores read are one contiguous block.
 __global__ void slice_gather_kernel(const double *__restrict__ src, __nv_bfloat16 *__restrict__ dst,
                                     int s, int e, Gather g, long long nrows, int Kp, int rps) {
   const long long n = nrows * Kp;
   const int sh = 7 + 8 * (s - 1) - e;
   const long long KB = Kp / 16;
   const long long rps8 = (rps + 7) / 8 * 8;
-  const long long sstride = (nrows / rps) * KB * rps8 * 16;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
        idx += (long long)gridDim.x * blockDim.x) {
     const long long row = idx / Kp;
@@ -105,8 +105,8 @@ __global__ void slice_gather_kernel(const double *__restrict__ src, __nv_bfloat1
       T = fixed_from_double(src[off], sh);
     }
     const long long slab = row / rps, r = row % rps;
-    const long long o = (slab * KB + k / 16) * rps8 * 16 + cm_off(r, k % 16);
-    store_digits(T, s, dst + o, sstride);
+    const long long o = (slab * KB + k / 16) * rps8 * 16 * s + cm_off(r, k % 16, s);
+    store_digits(T, s, dst + o, 128);
   }
 }
 
@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(256)
 slice_tt_kernel(const float2 *__restrict__ tt, __nv_bfloat16 *const *__restrict__ v, int nv,
                 int vp, int s, const int *__restrict__ ex, int nslot_alloc) {
   __shared__ float2 cube[16][16][17];  // [x][y][z] (+1 pad)
+  (void)nslot_alloc;
   const int nx = (nv + 15) / 16, nzb = vp / 16;
   int b = blockIdx.x;
   const int zb = b % nzb; b /= nzb;
@@ -217,8 +218,7 @@ slice_tt_kernel(const float2 *__restrict__ tt, __nv_bfloat16 *const *__restrict_
   if (gx >= nv || gy >= nv) return;
   const long long nv8 = (nv + 7) / 8 * 8;
   const long long KB = (long long)nzb * nv;
-  const long long sstride = (long long)nslot_alloc * KB * nv8 * 16;
-  const long long blk = ((long long)slot * KB + (long long)zb * nv + gy) * nv8 * 16;
+  const long long blk = ((long long)slot * KB + (long long)zb * nv + gy) * nv8 * 16 * s;
   const int sh = 7 + 8 * (s - 1) - ex[slot];
   __nv_bfloat16 *dst = v[L];
 #pragma unroll 1
@@ -247,14 +247,14 @@ slice_tt_kernel(const float2 *__restrict__ tt, __nv_bfloat16 *const *__restrict_
         }
       }
     }
-    const long long o = blk + cm_off(gx, h * 8);
+    const long long o = blk + cm_off(gx, h * 8, s);
 #pragma unroll
     for (int p = 0; p < S_MAX_SLICES_K; ++p) {
       if (p < s) {
         __align__(16) __nv_bfloat16 out[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) out[e] = __float2bfloat16_rn(ldexpf(d[p][e], -8 * p));
-        *reinterpret_cast<uint4 *>(dst + p * sstride + o) = *reinterpret_cast<const uint4 *>(out);
+        *reinterpret_cast<uint4 *>(dst + p * 128 + o) = *reinterpret_cast<const uint4 *>(out);
       }
     }
   }
