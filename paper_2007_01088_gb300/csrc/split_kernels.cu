@@ -4,6 +4,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "dd.cuh"
 #include "split_kernels.h"
 
@@ -127,30 +129,50 @@ __global__ void maxabs_kernel(const double *__restrict__ x, long long n,
 
 // tau~ = 4 tau^{abc} - 2 tau^{acb} - 2 tau^{cba} - 2 tau^{bac} + tau^{bca} + tau^{cab}
 // from tau stored as T[slot][c][a][b] (dd); writes TT[slot][a][b][c] (dd) and
-// the max |tau~| of each slot (float bits, atomic max).
-__global__ void contravariant_dd_kernel(const float2 *__restrict__ tau, float2 *__restrict__ tt,
-                                        int nv, unsigned int *__restrict__ maxbits) {
+// the max |tau~| of each slot (float bits, atomic max).  One CTA makes an 8^3
+// cube of tau~: it stages the six permuted 8^3 cubes of tau it needs in
+// shared memory, each read along the innermost index of T.
+__global__ void __launch_bounds__(512)
+contravariant_dd_kernel(const float2 *__restrict__ tau, float2 *__restrict__ tt, int nv,
+                        unsigned int *__restrict__ maxbits) {
+  __shared__ float2 cub[6][8][8][9];  // cube q: [i][j][k] = TAU(X0+i, Y0+j, Z0+k)
   const long long nv2 = (long long)nv * nv, nv3 = nv2 * nv;
+  const int nb = (nv + 7) / 8;
+  int blk = blockIdx.x;
+  const int C0 = (blk % nb) * 8;
+  blk /= nb;
+  const int B0 = (blk % nb) * 8;
+  const int A0 = (blk / nb) * 8;
   const float2 *T = tau + blockIdx.y * nv3;
   float2 *O = tt + blockIdx.y * nv3;
+  // block origins (X0, Y0, Z0) of the six cubes: (a,b,c) (a,c,b) (c,b,a) (b,a,c) (b,c,a) (c,a,b)
+  const int org[6][3] = {{A0, B0, C0}, {A0, C0, B0}, {C0, B0, A0},
+                         {B0, A0, C0}, {B0, C0, A0}, {C0, A0, B0}};
+  const int t = threadIdx.x;
+  const int j = t & 7, i = (t >> 3) & 7, k = t >> 6;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const int x = org[q][0] + i, y = org[q][1] + j, z = org[q][2] + k;
+    float2 v = make_float2(0.f, 0.f);
+    if (x < nv && y < nv && z < nv) v = T[(long long)z * nv2 + (long long)x * nv + y];  // TAU(x,y,z)
+    cub[q][i][j][k] = v;
+  }
+  __syncthreads();
+  // output element (a, b, c) = (A0 + oi, B0 + oj, C0 + ok), ok fastest
+  const int ok = t & 7, oj = (t >> 3) & 7, oi = t >> 6;
+  const float2 t0 = cub[0][oi][oj][ok], t1 = cub[1][oi][ok][oj], t2 = cub[2][ok][oj][oi];
+  const float2 t3 = cub[3][oj][oi][ok], t4 = cub[4][oj][ok][oi], t5 = cub[5][ok][oi][oj];
+  dd::df r = dd::scale(dd::df{t0.x, t0.y}, 4.f);
+  r = dd::add(r, dd::scale(dd::df{t1.x, t1.y}, -2.f));
+  r = dd::add(r, dd::scale(dd::df{t2.x, t2.y}, -2.f));
+  r = dd::add(r, dd::scale(dd::df{t3.x, t3.y}, -2.f));
+  r = dd::add(r, dd::df{t4.x, t4.y});
+  r = dd::add(r, dd::df{t5.x, t5.y});
+  const int a = A0 + oi, b = B0 + oj, c = C0 + ok;
   float mx = 0.f;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nv3;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(e % nv);
-    const int b = (int)((e / nv) % nv);
-    const int a = (int)(e / nv2);
-#define TAU(x, y, z) T[(long long)(z) * nv2 + (long long)(x) * nv + (y)]
-    const float2 t0 = TAU(a, b, c), t1 = TAU(a, c, b), t2 = TAU(c, b, a);
-    const float2 t3 = TAU(b, a, c), t4 = TAU(b, c, a), t5 = TAU(c, a, b);
-#undef TAU
-    dd::df r = dd::scale(dd::df{t0.x, t0.y}, 4.f);
-    r = dd::add(r, dd::scale(dd::df{t1.x, t1.y}, -2.f));
-    r = dd::add(r, dd::scale(dd::df{t2.x, t2.y}, -2.f));
-    r = dd::add(r, dd::scale(dd::df{t3.x, t3.y}, -2.f));
-    r = dd::add(r, dd::df{t4.x, t4.y});
-    r = dd::add(r, dd::df{t5.x, t5.y});
-    O[e] = make_float2(r.hi, r.lo);
-    mx = fmaxf(mx, fabsf(r.hi));
+  if (a < nv && b < nv && c < nv) {
+    O[(long long)a * nv2 + (long long)b * nv + c] = make_float2(r.hi, r.lo);
+    mx = fabsf(r.hi);
   }
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0) atomicMax(maxbits + blockIdx.y, __float_as_uint(mx));
@@ -172,88 +194,87 @@ __global__ void slot_exponent_kernel(const unsigned int *__restrict__ maxbits, i
 // Slices of tau~ in the three cyclic layouts used by the residual
 // contractions.  Layout L puts slot L outermost (rows x), then slot L+1 (y),
 // then slot L+2 (z, padded to vp):
-//   V_L[p][slot][kb = zb*nv + y][x (nv8 rows)][16 (zz)],  z = 16 zb + zz,
+//   V_L[slot][kb = zb*nv + y][row group of x][slice][8 x 16 (zz)],  z = 16 zb + zz,
 // core-matrix order inside every 16-column block.  Read as rows x with
 // K = (zb, y, zz) it serves the vvov and singles contractions; read as rows
 // (y, x) with K = z (the nv blocks of one zb are consecutive) it serves the
-// ooov and F contractions.  One CTA stages a 16^3 cube of tau~ in shared
-// memory (coalesced along the innermost index of tt for every rotation) and
-// writes each slice as whole 16-byte core rows.
+// ooov and F contractions.  One CTA converts a 16^3 cube of tau~ (read along
+// its innermost index) into digits once, keeps them in shared memory, and
+// writes the cube into all three layouts as whole 16-byte core rows.
+constexpr int TT_PAD = 18;  // row length (bf16) of the digit cube in shared memory
 __global__ void __launch_bounds__(256)
 slice_tt_kernel(const float2 *__restrict__ tt, __nv_bfloat16 *const *__restrict__ v, int nv,
                 int vp, int s, const int *__restrict__ ex, int nslot_alloc) {
-  __shared__ float2 cube[16][16][17];  // [x][y][z] (+1 pad)
+  extern __shared__ __nv_bfloat16 dig[];  // [p][a][b][c] (c padded to TT_PAD)
   (void)nslot_alloc;
   const int nx = (nv + 15) / 16, nzb = vp / 16;
-  int b = blockIdx.x;
-  const int zb = b % nzb; b /= nzb;
-  const int yb = b % nx; b /= nx;
-  const int xb = b % nx; b /= nx;
-  const int L = b;  // 0..2
+  int blk = blockIdx.x;
+  const int cb = blk % nx;
+  blk /= nx;
+  const int bb = blk % nx;
+  const int ab = blk / nx;
   const int slot = blockIdx.y;
   const long long nv2 = (long long)nv * nv;
   const float2 *T = tt + (long long)slot * nv2 * nv;
-  // load: element (x, y, z) of layout L sits at slots (L, L+1, L+2) of (a,b,c);
-  // the thread index runs fastest along the cube axis that is c
-  for (int e = threadIdx.x; e < 4096; e += 256) {
-    const int i0 = e & 15, i1 = (e >> 4) & 15, i2 = e >> 8;
-    int x, y, z;  // cube axes chosen so that c varies fastest
-    if (L == 0) { z = i0; y = i1; x = i2; }       // (a,b,c) = (x,y,z)
-    else if (L == 1) { y = i0; x = i1; z = i2; }  // (a,b,c) = (z,x,y)
-    else { x = i0; z = i1; y = i2; }              // (a,b,c) = (y,z,x)
-    const int gx = xb * 16 + x, gy = yb * 16 + y, gz = zb * 16 + z;
-    float2 val = make_float2(0.f, 0.f);
-    if (gx < nv && gy < nv && gz < nv) {
-      int vv[3];
-      vv[L] = gx;
-      vv[(L + 1) % 3] = gy;
-      vv[(L + 2) % 3] = gz;
-      val = T[(long long)vv[0] * nv2 + (long long)vv[1] * nv + vv[2]];
-    }
-    cube[x][y][z] = val;
-  }
-  __syncthreads();
-  const int x = threadIdx.x & 15, y = threadIdx.x >> 4;
-  const int gx = xb * 16 + x, gy = yb * 16 + y;
-  if (gx >= nv || gy >= nv) return;
-  const long long nv8 = (nv + 7) / 8 * 8;
-  const long long KB = (long long)nzb * nv;
-  const long long blk = ((long long)slot * KB + (long long)zb * nv + gy) * nv8 * 16 * s;
   const int sh = 7 + 8 * (s - 1) - ex[slot];
-  __nv_bfloat16 *dst = v[L];
-#pragma unroll 1
-  for (int h = 0; h < 2; ++h) {
-    long long Tv[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const float2 t = cube[x][y][h * 8 + e];
-      Tv[e] = fixed_from_float(t.x, sh) + fixed_from_float(t.y, sh);
+  const int plane = 16 * 16 * TT_PAD;
+  for (int e = threadIdx.x; e < 4096; e += 256) {
+    const int c = e & 15, b = (e >> 4) & 15, a = e >> 8;
+    const int ga = ab * 16 + a, gb = bb * 16 + b, gc = cb * 16 + c;
+    long long Tt = 0;
+    if (ga < nv && gb < nv && gc < nv) {
+      const float2 t = T[(long long)ga * nv2 + (long long)gb * nv + gc];
+      Tt = fixed_from_float(t.x, sh) + fixed_from_float(t.y, sh);
     }
-    // balanced base-256 digits of the 8 values, slice by slice
-    float d[S_MAX_SLICES_K][8];
+    // balanced base-256 digits, slice p stores d_p 2^(-8p)
+    float d[S_MAX_SLICES_K];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      long long Tt = Tv[e];
-#pragma unroll
-      for (int p = S_MAX_SLICES_K - 1; p >= 0; --p) {
-        if (p < s) {
-          if (p > 0) {
-            const long long r = ((Tt + 128) & 255) - 128;
-            d[p][e] = (float)r;
-            Tt = (Tt - r) >> 8;
-          } else {
-            d[0][e] = (float)Tt;
-          }
+    for (int p = S_MAX_SLICES_K - 1; p >= 0; --p) {
+      if (p < s) {
+        if (p > 0) {
+          const long long r = ((Tt + 128) & 255) - 128;
+          d[p] = (float)r;
+          Tt = (Tt - r) >> 8;
+        } else {
+          d[0] = (float)Tt;
         }
       }
     }
-    const long long o = blk + cm_off(gx, h * 8, s);
+    const int o = (a * 16 + b) * TT_PAD + c;
 #pragma unroll
-    for (int p = 0; p < S_MAX_SLICES_K; ++p) {
-      if (p < s) {
+    for (int p = 0; p < S_MAX_SLICES_K; ++p)
+      if (p < s) dig[p * plane + o] = __float2bfloat16_rn(ldexpf(d[p], -8 * p));
+  }
+  __syncthreads();
+  const long long nv8 = (nv + 7) / 8 * 8;
+  const long long KB = (long long)nzb * nv;
+  const int x = threadIdx.x & 15, y = threadIdx.x >> 4;
+#pragma unroll 1
+  for (int L = 0; L < 3; ++L) {
+    // block indices of this layout's (x, y, z) roles: (a,b,c), (b,c,a), (c,a,b)
+    const int xb = L == 0 ? ab : (L == 1 ? bb : cb);
+    const int yb = L == 0 ? bb : (L == 1 ? cb : ab);
+    const int zb = L == 0 ? cb : (L == 1 ? ab : bb);
+    const int gx = xb * 16 + x, gy = yb * 16 + y;
+    if (gx >= nv || gy >= nv) continue;
+    const long long blk0 = ((long long)slot * KB + (long long)zb * nv + gy) * nv8 * 16 * s;
+    __nv_bfloat16 *dst = v[L];
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+      const long long o = blk0 + cm_off(gx, h * 8, s);
+#pragma unroll 1
+      for (int p = 0; p < s; ++p) {
+        const __nv_bfloat16 *D = dig + p * plane;
         __align__(16) __nv_bfloat16 out[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) out[e] = __float2bfloat16_rn(ldexpf(d[p][e], -8 * p));
+        for (int e = 0; e < 8; ++e) {
+          const int z = h * 8 + e;
+          // (a, b, c) of the element with local (x, y, z) in layout L
+          const int a = L == 0 ? x : (L == 1 ? z : y);
+          const int b = L == 0 ? y : (L == 1 ? x : z);
+          const int c = L == 0 ? z : (L == 1 ? y : x);
+          out[e] = D[(a * 16 + b) * TT_PAD + c];
+        }
         *reinterpret_cast<uint4 *>(dst + p * 128 + o) = *reinterpret_cast<const uint4 *>(out);
       }
     }
@@ -279,10 +300,8 @@ int launch_maxabs(const double *x, long long n, unsigned long long *out, cudaStr
 }
 int launch_contravariant_dd(const float2 *tau, float2 *tt, int nv, int nslot,
                             unsigned int *maxbits, cudaStream_t st) {
-  const long long nv3 = (long long)nv * nv * nv;
-  int bx = (int)((nv3 + 255) / 256);
-  if (bx > 2048) bx = 2048;
-  contravariant_dd_kernel<<<dim3(bx, nslot), 256, 0, st>>>(tau, tt, nv, maxbits);
+  const int nb = (nv + 7) / 8;
+  contravariant_dd_kernel<<<dim3(nb * nb * nb, nslot), 512, 0, st>>>(tau, tt, nv, maxbits);
   return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_FAIL(CC3_ERR_CUDA, "split element-wise kernel launch");
 }
 int launch_slot_exponent(const unsigned int *maxbits, int *ex, int nslot, cudaStream_t st) {
@@ -291,9 +310,26 @@ int launch_slot_exponent(const unsigned int *maxbits, int *ex, int nslot, cudaSt
 }
 int launch_slice_tt(const float2 *tt, __nv_bfloat16 *const *v, int nv, int vp, int s,
                     const int *ex, int nslot, int nslot_alloc, cudaStream_t st) {
+  if (vp / 16 != (nv + 15) / 16 || s < 1 || s > S_MAX_SLICES_K)
+    return CC3_FAIL(CC3_ERR_ARG, "slice_tt layout");
   const int nx = (nv + 15) / 16;
-  dim3 grid(3 * nx * nx * (vp / 16), nslot);
-  slice_tt_kernel<<<grid, 256, 0, st>>>(tt, v, nv, vp, s, ex, nslot_alloc);
+  const size_t smem = (size_t)s * 16 * 16 * TT_PAD * sizeof(__nv_bfloat16);
+  {
+    static std::mutex mu;
+    static bool set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev >= 0 && dev < 64 && !set[dev]) {
+      const size_t mx = (size_t)S_MAX_SLICES_K * 16 * 16 * TT_PAD * sizeof(__nv_bfloat16);
+      if (cudaFuncSetAttribute(slice_tt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)mx) != cudaSuccess)
+        return CC3_FAIL(CC3_ERR_CUDA, "slice_tt shared memory");
+      set[dev] = true;
+    }
+  }
+  dim3 grid(nx * nx * nx, nslot);
+  slice_tt_kernel<<<grid, 256, smem, st>>>(tt, v, nv, vp, s, ex, nslot_alloc);
   return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_FAIL(CC3_ERR_CUDA, "slice_tt launch");
 }
 
