@@ -445,6 +445,7 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         ctx = g.Context(inp, device=True, stream=stream)
+        tuning = ctx.autotune() if prec == g.CC3_SPLIT_BF16 else None
         ctx.set_tracing(True)
         out = (torch.empty((no, nv), dtype=torch.float64, device=dev),
                torch.empty((no, no, nv, nv), dtype=torch.float64, device=dev),
@@ -558,6 +559,9 @@ def main():
             "data": "synthetic",
             "config": {"workload": workload, "no": no, "nv": nv,
                        "prec": args.prec, "parallelism": f"replicas{ws}",
+                       "tiling": None if tuning is None else
+                       {"vvov_ksteps_per_tile": tuning[0], "w_build_ntile": tuning[1],
+                        "source": "autotuner (sample of the triple loop, before warm-up)"},
                        "l2": f"inputs larger than L2 (g_vvvo {nv ** 3 * no * 8 / 1e6:.0f} MB)"},
             "roofline": roof,
             "e2e": {"value": ws * flop / e2e_s / 1e12, "unit": "TFLOP/s",

@@ -179,6 +179,18 @@ int cc3_ctx_trace(const cc3_ctx *ctx, cc3_trace *out);
  * nv = 160 scale).  */
 int cc3_ctx_set_slices(cc3_ctx *ctx, int slices);
 
+/* Autotuner of the split path (no counterpart in the paper, whose CPU code
+ * has no tile shapes to choose): times the residual on a strided sample of
+ * about 32 triples of the context's loop for each candidate tiling (K steps
+ * per tile of the vvov contraction: 200, 400, 800; N tile of the W build:
+ * the default and the next smaller one), keeps the fastest for this context
+ * and for every later context of the same (no, nv, slices) in the process,
+ * and returns it (either output pointer may be NULL).  Runs kernels on
+ * cuda_stream; the context's Omega accumulators are scratch meanwhile. */
+int cc3_ctx_autotune(cc3_ctx *ctx, void *cuda_stream, int *ksteps_per_tile, int *ntile_w);
+/* The split path's current tiling (tuned or default). */
+int cc3_ctx_get_tuning(cc3_ctx *ctx, int *ksteps_per_tile, int *ntile_w);
+
 const char *cc3_strerror(int status);
 
 /* Detail of the most recent failure on the calling thread (the library call

@@ -36,7 +36,8 @@ EXPORTED = ["cc3_ctx_create", "cc3_ctx_destroy", "cc3_ctx_set_triples",
             "cc3_serve_submit", "cc3_serve_poll", "cc3_serve_wait",
             "cc3_serve_cancel", "cc3_serve_stats", "cc3_serve_stop",
             "cc3_debug_split_gemm", "cc3_last_error", "cc3_ctx_set_tracing",
-            "cc3_ctx_trace", "cc3_omega_triples_noalloc", "cc3_serve_footprint"]
+            "cc3_ctx_trace", "cc3_omega_triples_noalloc", "cc3_serve_footprint",
+            "cc3_ctx_autotune", "cc3_ctx_get_tuning"]
 
 
 class CC3Error(RuntimeError):
@@ -108,6 +109,11 @@ def _load():
     L.cc3_ctx_trace.restype = I
     L.cc3_omega_triples_noalloc.argtypes = [I, I] + [P] * 7 + [P, P, P, P]
     L.cc3_omega_triples_noalloc.restype = I
+    IP = ctypes.POINTER(I)
+    L.cc3_ctx_autotune.argtypes = [P, P, IP, IP]
+    L.cc3_ctx_autotune.restype = I
+    L.cc3_ctx_get_tuning.argtypes = [P, IP, IP]
+    L.cc3_ctx_get_tuning.restype = I
     RP = ctypes.POINTER(Request)
     L.cc3_serve_start.argtypes = [ctypes.POINTER(P), ctypes.c_size_t, I]
     L.cc3_serve_start.restype = I
@@ -239,6 +245,20 @@ def cc3_ctx_trace(ctx):
             for i in range(t.n)}
 
 
+def cc3_ctx_autotune(ctx, stream=None):
+    """Tunes the split path's tiling; returns (ksteps_per_tile, ntile_w)."""
+    ks, nt = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib.cc3_ctx_autotune(ctx, _stream(stream), ctypes.byref(ks), ctypes.byref(nt)),
+           "cc3_ctx_autotune")
+    return ks.value, nt.value
+
+
+def cc3_ctx_get_tuning(ctx):
+    ks, nt = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib.cc3_ctx_get_tuning(ctx, ctypes.byref(ks), ctypes.byref(nt)), "cc3_ctx_get_tuning")
+    return ks.value, nt.value
+
+
 def cc3_ctx_set_slices(ctx, slices):
     _check(lib.cc3_ctx_set_slices(ctx, int(slices)), "cc3_ctx_set_slices")
 
@@ -303,6 +323,12 @@ class Context:
 
     def set_slices(self, s):
         cc3_ctx_set_slices(self.ctx, s)
+
+    def autotune(self):
+        return cc3_ctx_autotune(self.ctx, self.stream)
+
+    def tuning(self):
+        return cc3_ctx_get_tuning(self.ctx)
 
     def counters(self):
         return cc3_ctx_counters(self.ctx)

@@ -422,6 +422,19 @@ int cc3_ctx_counters(const cc3_ctx *c, cc3_counters *out) {
   return CC3_OK;
 }
 
+int cc3_ctx_autotune(cc3_ctx *c, void *cuda_stream, int *ksteps_per_tile, int *ntile_w) {
+  if (!c) return CC3_ERR_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (c->ntri == 0) return CC3_OK;
+  return split_autotune(c, (cudaStream_t)cuda_stream, ksteps_per_tile, ntile_w);
+}
+
+int cc3_ctx_get_tuning(cc3_ctx *c, int *ksteps_per_tile, int *ntile_w) {
+  if (!c) return CC3_ERR_ARG;
+  std::lock_guard<std::mutex> lk(c->mu);
+  return split_tuning(c, ksteps_per_tile, ntile_w);
+}
+
 int cc3_ctx_set_slices(cc3_ctx *c, int slices) {
   if (!c || slices < 3 || slices > 7) return CC3_ERR_ARG;
   c->slices = slices;

@@ -22,6 +22,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -95,6 +97,8 @@ struct SplitState {
   // Jacobian (Algorithm 2 layouts of ovov), staged on first use
   __nv_bfloat16 *OVD = nullptr, *OVZA = nullptr, *OVZB = nullptr;
   int ks4 = 1;  // K split of the rows-x contractions
+  // tunables (autotuner): K steps per vvov tile, N tile of the W build (0: default)
+  int ks_target = 400, nt_w = 0;
   float2 *evdd = nullptr;
   int batch = 0;
   float2 *Wdd = nullptr, *TTdd = nullptr;
@@ -254,7 +258,7 @@ int stage(cc3_ctx *c, SplitState *S, cudaStream_t st) {
   CU(cudaMemsetAsync(S->status, 0, 4 * sizeof(int), st));
 
   // slice-array table (the same descriptor serves an array as A or B operand)
-  S->Nab = ntile_for(nv);
+  S->Nab = S->nt_w > 0 ? S->nt_w : ntile_for(nv);
   S->N3 = rup(no + 1, 16);
   if (S->N3 > S_NT_MAX) return CC3_ERR_UNSUPPORTED;
   SArr *M = S->arrs.a;
@@ -511,8 +515,9 @@ int build_plans(cc3_ctx *c, SplitState *S, cudaStream_t st) {
   // K split of the vvov contraction: tiles of about 400 K steps, so that the
   // persistent engine balances them over the SMs (partial sums add in FP64)
   const int kst = nv * S->vp / S_BK;
-  int ks4 = std::max(1, (kst + 399) / 400);
+  int ks4 = std::max(1, (kst + S->ks_target - 1) / std::max(16, S->ks_target));
   S->ks4 = ks4;
+  S->Nab = S->nt_w > 0 ? S->nt_w : ntile_for(nv);
   for (int t0 = 0; t0 < c->ntri; t0 += S->batch) {
     const int t1 = std::min(c->ntri, t0 + S->batch);
     SPlan pab, pc, pom, pom3;
@@ -552,6 +557,16 @@ void fill_vptrs(cc3_ctx *c, SplitState *S, VPtrTable *P) {
 }  // namespace
 
 namespace {
+// Tuned parameters per (no, nv, slices), shared by all contexts of the process.
+struct TuneKey {
+  int no, nv, s;
+  bool operator<(const TuneKey &o) const {
+    return no != o.no ? no < o.no : (nv != o.nv ? nv < o.nv : s < o.s);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tuned;  // -> (ks_target, nt_w)
+
 // The staged slice arrays and residual plans of the context (built on first use).
 int split_ready(cc3_ctx *c, SplitState **out, cudaStream_t st) {
   const int s = c->slices > 0 ? c->slices : 6;
@@ -565,6 +580,12 @@ int split_ready(cc3_ctx *c, SplitState **out, cudaStream_t st) {
     if (!S) return CC3_ERR_OOM;
     S->s = s;
     c->split = S;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(TuneKey{c->no, c->nv, s});
+    if (it != g_tuned.end()) {
+      S->ks_target = it->second.first;
+      S->nt_w = it->second.second;
+    }
   }
   if (!S->staged) TRY(stage(c, S, st));
   if (!S->planned) TRY(build_plans(c, S, st));
@@ -609,6 +630,100 @@ int split_omega(cc3_ctx *c, cudaStream_t st) {
   }
   c->counters.executed_flop = S->executed;
   c->counters.slices = s;
+  return CC3_OK;
+}
+
+// Autotuner of the split path: times the residual on a strided sample of the
+// triple loop (about 32 triples) for each candidate (K steps per vvov tile,
+// N tile of the W build), keeps the fastest for this context and for every
+// later context of the same (no, nv, slices).  Outputs of the sample runs are
+// scratch: cc3_omega_triples clears its accumulators first.
+int split_autotune(cc3_ctx *c, cudaStream_t st, int *ks_out, int *nt_out) {
+  SplitState *S = nullptr;
+  TRY(split_ready(c, &S, st));
+  const int nv = c->nv;
+  std::vector<int> ks_c = {200, 400, 800};
+  std::vector<int> nt_c = {ntile_for(nv)};
+  {
+    const int nt = (nv + S_NT_MAX - 1) / S_NT_MAX + 1;  // one more N tile
+    const int alt = rup((nv + nt - 1) / nt, 16);
+    if (alt != nt_c[0] && alt >= 16) nt_c.push_back(alt);
+  }
+  const std::vector<int> tri_all = c->tri_host;
+  const int ntri_all = c->ntri;
+  const int stride = std::max(1, ntri_all / 32);
+  std::vector<int> sample;
+  for (int t = 0; t < ntri_all; t += stride)
+    sample.insert(sample.end(), &tri_all[3 * t], &tri_all[3 * t] + 3);
+  c->tri_host = sample;
+  c->ntri = (int)(sample.size() / 3);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = CC3_OK;
+  float best = 1e30f;
+  int bks = S->ks_target, bnt = S->nt_w;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    rc = CC3_FAIL(CC3_ERR_CUDA, "autotune events");
+  }
+  const bool tr = c->trace.on;
+  c->trace.on = false;
+  for (int nt : nt_c) {
+    for (int ks : ks_c) {
+      if (rc != CC3_OK) break;
+      S->ks_target = ks;
+      S->nt_w = nt;
+      S->planned = false;
+      if ((rc = build_plans(c, S, st)) != CC3_OK) break;
+      if ((rc = split_omega(c, st)) != CC3_OK) break;  // warm
+      cudaEventRecord(e0, st);
+      if ((rc = split_omega(c, st)) != CC3_OK) break;
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = CC3_FAIL(CC3_ERR_CUDA, "autotune timing");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        bks = ks;
+        bnt = nt;
+      }
+    }
+  }
+  c->trace.on = tr;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  c->tri_host = tri_all;
+  c->ntri = ntri_all;
+  S->ks_target = bks;
+  S->nt_w = bnt;
+  S->planned = false;
+  if (rc != CC3_OK) return rc;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[TuneKey{c->no, c->nv, S->s}] = {bks, bnt};
+  }
+  if (ks_out) *ks_out = bks;
+  if (nt_out) *nt_out = bnt > 0 ? bnt : ntile_for(nv);
+  return CC3_OK;
+}
+
+int split_tuning(cc3_ctx *c, int *ks_out, int *nt_out) {
+  SplitState *S = state(c);
+  int ks = 400, nt = 0;
+  if (S) {
+    ks = S->ks_target;
+    nt = S->nt_w;
+  } else {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(TuneKey{c->no, c->nv, c->slices > 0 ? c->slices : 6});
+    if (it != g_tuned.end()) {
+      ks = it->second.first;
+      nt = it->second.second;
+    }
+  }
+  if (ks_out) *ks_out = ks;
+  if (nt_out) *nt_out = nt > 0 ? nt : ntile_for(c->nv);
   return CC3_OK;
 }
 

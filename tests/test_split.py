@@ -51,3 +51,17 @@ def test_omega_split_matches_oracle(g, no, nv):
     assert abs(e[0] - ref["E_T"]) <= 1e-8
     c = ctx.counters()
     assert c["slices"] == 6 and c["executed_flop"] > c["nominal_flop"]
+
+
+def test_autotune_keeps_parity_and_is_shared(g):
+    inp = make_inputs(6, 40, seed=12)
+    ref = oracle.omega_inputs(inp)
+    ctx = g.Context(inp)
+    ks, nt = ctx.autotune()
+    assert ks in (200, 400, 800) and nt % 16 == 0 and 16 <= nt <= 96
+    o1, o2, e = ctx.omega(g.CC3_SPLIT_BF16)
+    assert np.abs(o1 - ref["omega1"]).max() <= 1e-9
+    assert np.abs(o2 - ref["omega2"]).max() <= 1e-9
+    assert abs(e[0] - ref["E_T"]) <= 1e-8
+    ctx2 = g.Context(inp)  # a later context of the same size starts tuned
+    assert ctx2.tuning() == (ks, nt)
