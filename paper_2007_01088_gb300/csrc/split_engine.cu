@@ -170,65 +170,81 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
         mbar_arrive(&tfull[q]);
         if (tile >= ntiles) break;
         const TileInfo ti = decode_tile(jobs, njobs, terms, tile, jh);
-        const SJob &J = jobs[ti.j];
         const int Nt = ti.Nt, bi = ti.bi, m0 = ti.m0, n0 = ti.n0;
+        const int term0 = jobs[ti.j].term0, nterm = jobs[ti.j].nterm;
+        // term cursor; per-term operand addresses live in registers (the
+        // barrier asm below would otherwise force the term and array
+        // descriptors to be reloaded from memory every K step)
         int t = 0, kbase = 0;
-        while (t < J.nterm && kbase + terms[J.term0 + t].ksteps <= ti.g0) {
-          kbase += terms[J.term0 + t].ksteps;
+        while (t < nterm && kbase + terms[term0 + t].ksteps <= ti.g0) {
+          kbase += terms[term0 + t].ksteps;
           ++t;
         }
+        int kend = -1;
+        const __nv_bfloat16 *ga0 = nullptr, *gb0 = nullptr, *gt0 = nullptr;
+        long long kbsA = 0, kbsB = 0, kbsT = 0;
+        int kmax = 0;
+        uint32_t abytes = 0, mbytes = 0, tbytes = 0, toff = 0;
         bool bad = false;
         for (int g = ti.g0; g < ti.g1; ++g) {
-          while (g - kbase >= terms[J.term0 + t].ksteps) {
-            kbase += terms[J.term0 + t].ksteps;
-            ++t;
+          if (g >= kend) {
+            if (kend >= 0) {
+              kbase = kend;
+              ++t;
+            }
+            const STerm T = terms[term0 + t];
+            kend = kbase + T.ksteps;
+            const SArr XA = arrs.a[T.A.map], XB = arrs.a[T.B.map], XT = arrs.a[T.Bt.map];
+            const int ar = T.A.row0 + bi * T.A.row_b + m0, as = T.A.slab0 + bi * T.A.slab_b;
+            const int bs = T.B.slab0 + bi * T.B.slab_b, ts = T.Bt.slab0 + bi * T.Bt.slab_b;
+            // B tile rows [n0, n0 + Nt): main rows from B, rows >= nbm from the tail Bt
+            const int nbm = T.nbm > 0 ? T.nbm : (1 << 30);
+            const int br = T.B.row0 + bi * T.B.row_b + n0;
+            const int nmain = max(0, min(min(Nt, nbm - n0), XB.rows - br));
+            const int tfirst = max(n0, nbm);                  // first tail row of the tile
+            const int tr = T.Bt.row0 + tfirst - nbm;          // its row in Bt
+            const int ntail = T.nbm > 0 ? max(0, min(n0 + Nt - tfirst, XT.rows - tr)) : 0;
+            kmax = XA.kblocks;
+            if (nmain > 0) kmax = min(kmax, XB.kblocks);
+            if (ntail > 0) kmax = min(kmax, XT.kblocks);
+            if (as < 0 || as >= XA.slabs || ar < 0 || ar >= XA.rows ||
+                (nmain > 0 && (bs < 0 || bs >= XB.slabs || br < 0)) ||
+                (ntail > 0 && (ts < 0 || ts >= XT.slabs || tr < 0 || ((tfirst - n0) & 7) != 0))) {
+              err = 2;  // a plan addressed outside its slice array: stop, report
+              bad = true;
+              break;
+            }
+            abytes = (uint32_t)min(S_BM, XA.rows - ar) * 32u;
+            mbytes = (uint32_t)nmain * 32u;
+            tbytes = (uint32_t)ntail * 32u;
+            toff = (uint32_t)(tfirst - n0) * 32u * s;
+            // one bulk copy per operand tile: its s slices are contiguous
+            ga0 = reinterpret_cast<const __nv_bfloat16 *>(XA.base) + (long long)as * XA.slab_stride +
+                  (long long)ar * 16 * s;
+            gb0 = reinterpret_cast<const __nv_bfloat16 *>(XB.base) + (long long)bs * XB.slab_stride +
+                  (long long)br * 16 * s;
+            gt0 = reinterpret_cast<const __nv_bfloat16 *>(XT.base) + (long long)ts * XT.slab_stride +
+                  (long long)tr * 16 * s;
+            kbsA = XA.kb_stride;
+            kbsB = XB.kb_stride;
+            kbsT = XT.kb_stride;
           }
-          const STerm &T = terms[J.term0 + t];
           const int kb = g - kbase;
-          const int st = issued % S_STAGES, ph = (issued / S_STAGES) & 1;
-          if (!mbar_wait(&empty[st], ph ^ 1, &err)) { bad = true; break; }
-          const SArr &XA = arrs.a[T.A.map], &XB = arrs.a[T.B.map], &XT = arrs.a[T.Bt.map];
-          const int ar = T.A.row0 + bi * T.A.row_b + m0, as = T.A.slab0 + bi * T.A.slab_b;
-          const int bs = T.B.slab0 + bi * T.B.slab_b, ts = T.Bt.slab0 + bi * T.Bt.slab_b;
-          // B tile rows [n0, n0 + Nt): main rows from B, rows >= nbm from the tail Bt
-          const int nbm = T.nbm > 0 ? T.nbm : (1 << 30);
-          const int br = T.B.row0 + bi * T.B.row_b + n0;
-          const int nmain = max(0, min(min(Nt, nbm - n0), XB.rows - br));
-          const int tfirst = max(n0, nbm);                  // first tail row of the tile
-          const int tr = T.Bt.row0 + tfirst - nbm;          // its row in Bt
-          const int ntail = T.nbm > 0 ? max(0, min(n0 + Nt - tfirst, XT.rows - tr)) : 0;
-          if (as < 0 || as >= XA.slabs || kb >= XA.kblocks || ar < 0 || ar >= XA.rows ||
-              (nmain > 0 && (bs < 0 || bs >= XB.slabs || kb >= XB.kblocks || br < 0)) ||
-              (ntail > 0 && (ts < 0 || ts >= XT.slabs || kb >= XT.kblocks || tr < 0 ||
-                             ((tfirst - n0) & 7) != 0))) {
-            err = 2;  // a plan addressed outside its slice array: stop, report
+          if (kb >= kmax) {
+            err = 2;
             bad = true;
             break;
           }
-          const int ra = min(S_BM, XA.rows - ar);
-          const uint32_t abytes = (uint32_t)ra * 32u;
-          const uint32_t mbytes = (uint32_t)nmain * 32u, tbytes = (uint32_t)ntail * 32u;
+          const int st = issued % S_STAGES, ph = (issued / S_STAGES) & 1;
+          if (!mbar_wait(&empty[st], ph ^ 1, &err)) { bad = true; break; }
           mbar_arrive_expect_tx(&full[st], (uint32_t)s * (abytes + mbytes + tbytes));
           // stage layout: s A slices (128 rows) then s B slices (S_NT_MAX rows)
           uint8_t *sa = smem + (size_t)st * ((size_t)s * (a_bytes + S_NT_MAX * 32));
           uint8_t *sb = sa + (size_t)s * a_bytes;
-          // one bulk copy per operand tile: its s slices are contiguous
-          const __nv_bfloat16 *ga = reinterpret_cast<const __nv_bfloat16 *>(XA.base) +
-                                    (long long)as * XA.slab_stride + (long long)kb * XA.kb_stride +
-                                    (long long)ar * 16 * s;
-          bulk_load(sa, ga, (uint32_t)s * abytes, &full[st]);
-          if (mbytes) {
-            const __nv_bfloat16 *gb = reinterpret_cast<const __nv_bfloat16 *>(XB.base) +
-                                      (long long)bs * XB.slab_stride +
-                                      (long long)kb * XB.kb_stride + (long long)br * 16 * s;
-            bulk_load(sb, gb, (uint32_t)s * mbytes, &full[st]);
-          }
-          if (tbytes) {
-            const __nv_bfloat16 *gt = reinterpret_cast<const __nv_bfloat16 *>(XT.base) +
-                                      (long long)ts * XT.slab_stride +
-                                      (long long)kb * XT.kb_stride + (long long)tr * 16 * s;
-            bulk_load(sb + (size_t)(tfirst - n0) * 32 * s, gt, (uint32_t)s * tbytes, &full[st]);
-          }
+          bulk_load(sa, ga0 + (long long)kb * kbsA, (uint32_t)s * abytes, &full[st]);
+          if (mbytes) bulk_load(sb, gb0 + (long long)kb * kbsB, (uint32_t)s * mbytes, &full[st]);
+          if (tbytes)
+            bulk_load(sb + toff, gt0 + (long long)kb * kbsT, (uint32_t)s * tbytes, &full[st]);
           ++issued;
         }
         if (bad) break;
@@ -249,8 +265,8 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
         mbar_arrive(&tempty[q]);
         if (tile < 0) break;
         const TileInfo ti = decode_tile(jobs, njobs, terms, tile, jh);
-        const SJob &J = jobs[ti.j];
         const int Nt = ti.Nt;
+        const int term0 = jobs[ti.j].term0, nterm = jobs[ti.j].nterm;
         const uint32_t id_pos = idesc_bf16(S_BM, Nt, 0), id_neg = idesc_bf16(S_BM, Nt, 1);
         // the epilogue has read the previous tile's accumulators
         if (i > 0) {
@@ -258,19 +274,26 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
           tc_fence_after();
         }
         int t = 0, kbase = 0;
-        while (t < J.nterm && kbase + terms[J.term0 + t].ksteps <= ti.g0) {
-          kbase += terms[J.term0 + t].ksteps;
+        while (t < nterm && kbase + terms[term0 + t].ksteps <= ti.g0) {
+          kbase += terms[term0 + t].ksteps;
           ++t;
+        }
+        int kend = 0;
+        uint32_t idesc = id_pos;
+        if (ti.g0 < ti.g1) {  // then t < nterm
+          kend = kbase + terms[term0 + t].ksteps;
+          idesc = terms[term0 + t].negA ? id_neg : id_pos;
         }
         uint32_t fresh = (1u << S_NACC) - 1;
         int since = 0;
         bool pending = false;
         for (int g = ti.g0; g < ti.g1; ++g, ++it) {
-          while (g - kbase >= terms[J.term0 + t].ksteps) {
-            kbase += terms[J.term0 + t].ksteps;
+          if (g >= kend) {
             ++t;
+            const STerm T = terms[term0 + t];
+            kend += T.ksteps;
+            idesc = T.negA ? id_neg : id_pos;
           }
-          const uint32_t idesc = terms[J.term0 + t].negA ? id_neg : id_pos;
           const int st = it % S_STAGES, ph = (it / S_STAGES) & 1;
           if (!mbar_wait(&full[st], ph, &err)) { ok = false; break; }
           tc_fence_after();
