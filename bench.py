@@ -407,7 +407,7 @@ def main():
     ap.add_argument("--jno", type=int, default=20, help="jacobian: occupied orbitals")
     ap.add_argument("--jnv", type=int, default=200, help="jacobian: virtual orbitals")
     ap.add_argument("--nvec", type=int, default=8, help="jacobian: trial vectors")
-    ap.add_argument("--sample", type=float, default=0.125,
+    ap.add_argument("--sample", type=float, default=0.25,
                     help="jacobian: fraction of the triples evaluated per step")
     ap.add_argument("--requests", type=int, default=32, help="serve: requests in the stream")
     ap.add_argument("--rate", type=float, default=4.0, help="serve: arrivals per second")

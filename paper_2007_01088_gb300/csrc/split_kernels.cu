@@ -129,50 +129,34 @@ __global__ void maxabs_kernel(const double *__restrict__ x, long long n,
 
 // tau~ = 4 tau^{abc} - 2 tau^{acb} - 2 tau^{cba} - 2 tau^{bac} + tau^{bca} + tau^{cab}
 // from tau stored as T[slot][c][a][b] (dd); writes TT[slot][a][b][c] (dd) and
-// the max |tau~| of each slot (float bits, atomic max).  One CTA makes an 8^3
-// cube of tau~: it stages the six permuted 8^3 cubes of tau it needs in
-// shared memory, each read along the innermost index of T.
-__global__ void __launch_bounds__(512)
-contravariant_dd_kernel(const float2 *__restrict__ tau, float2 *__restrict__ tt, int nv,
-                        unsigned int *__restrict__ maxbits) {
-  __shared__ float2 cub[6][8][8][9];  // cube q: [i][j][k] = TAU(X0+i, Y0+j, Z0+k)
+// the max |tau~| of each slot (float bits, atomic max).  Element (a,b,c) per
+// thread, c fastest: two of the six permuted reads are coalesced, the other
+// four hit L2 (one slot of tau, nv^3 dd values, stays L2-resident).  A
+// shared-memory cube transpose was measured slower (latency- and
+// barrier-bound).
+__global__ void contravariant_dd_kernel(const float2 *__restrict__ tau, float2 *__restrict__ tt,
+                                        int nv, unsigned int *__restrict__ maxbits) {
   const long long nv2 = (long long)nv * nv, nv3 = nv2 * nv;
-  const int nb = (nv + 7) / 8;
-  int blk = blockIdx.x;
-  const int C0 = (blk % nb) * 8;
-  blk /= nb;
-  const int B0 = (blk % nb) * 8;
-  const int A0 = (blk / nb) * 8;
   const float2 *T = tau + blockIdx.y * nv3;
   float2 *O = tt + blockIdx.y * nv3;
-  // block origins (X0, Y0, Z0) of the six cubes: (a,b,c) (a,c,b) (c,b,a) (b,a,c) (b,c,a) (c,a,b)
-  const int org[6][3] = {{A0, B0, C0}, {A0, C0, B0}, {C0, B0, A0},
-                         {B0, A0, C0}, {B0, C0, A0}, {C0, A0, B0}};
-  const int t = threadIdx.x;
-  const int j = t & 7, i = (t >> 3) & 7, k = t >> 6;
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    const int x = org[q][0] + i, y = org[q][1] + j, z = org[q][2] + k;
-    float2 v = make_float2(0.f, 0.f);
-    if (x < nv && y < nv && z < nv) v = T[(long long)z * nv2 + (long long)x * nv + y];  // TAU(x,y,z)
-    cub[q][i][j][k] = v;
-  }
-  __syncthreads();
-  // output element (a, b, c) = (A0 + oi, B0 + oj, C0 + ok), ok fastest
-  const int ok = t & 7, oj = (t >> 3) & 7, oi = t >> 6;
-  const float2 t0 = cub[0][oi][oj][ok], t1 = cub[1][oi][ok][oj], t2 = cub[2][ok][oj][oi];
-  const float2 t3 = cub[3][oj][oi][ok], t4 = cub[4][oj][ok][oi], t5 = cub[5][ok][oi][oj];
-  dd::df r = dd::scale(dd::df{t0.x, t0.y}, 4.f);
-  r = dd::add(r, dd::scale(dd::df{t1.x, t1.y}, -2.f));
-  r = dd::add(r, dd::scale(dd::df{t2.x, t2.y}, -2.f));
-  r = dd::add(r, dd::scale(dd::df{t3.x, t3.y}, -2.f));
-  r = dd::add(r, dd::df{t4.x, t4.y});
-  r = dd::add(r, dd::df{t5.x, t5.y});
-  const int a = A0 + oi, b = B0 + oj, c = C0 + ok;
   float mx = 0.f;
-  if (a < nv && b < nv && c < nv) {
-    O[(long long)a * nv2 + (long long)b * nv + c] = make_float2(r.hi, r.lo);
-    mx = fabsf(r.hi);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nv3;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(e % nv);
+    const int b = (int)((e / nv) % nv);
+    const int a = (int)(e / nv2);
+#define TAU(x, y, z) T[(long long)(z) * nv2 + (long long)(x) * nv + (y)]
+    const float2 t0 = TAU(a, b, c), t1 = TAU(a, c, b), t2 = TAU(c, b, a);
+    const float2 t3 = TAU(b, a, c), t4 = TAU(b, c, a), t5 = TAU(c, a, b);
+#undef TAU
+    dd::df r = dd::scale(dd::df{t0.x, t0.y}, 4.f);
+    r = dd::add(r, dd::scale(dd::df{t1.x, t1.y}, -2.f));
+    r = dd::add(r, dd::scale(dd::df{t2.x, t2.y}, -2.f));
+    r = dd::add(r, dd::scale(dd::df{t3.x, t3.y}, -2.f));
+    r = dd::add(r, dd::df{t4.x, t4.y});
+    r = dd::add(r, dd::df{t5.x, t5.y});
+    O[e] = make_float2(r.hi, r.lo);
+    mx = fmaxf(mx, fabsf(r.hi));
   }
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0) atomicMax(maxbits + blockIdx.y, __float_as_uint(mx));
@@ -300,8 +284,10 @@ int launch_maxabs(const double *x, long long n, unsigned long long *out, cudaStr
 }
 int launch_contravariant_dd(const float2 *tau, float2 *tt, int nv, int nslot,
                             unsigned int *maxbits, cudaStream_t st) {
-  const int nb = (nv + 7) / 8;
-  contravariant_dd_kernel<<<dim3(nb * nb * nb, nslot), 512, 0, st>>>(tau, tt, nv, maxbits);
+  const long long nv3 = (long long)nv * nv * nv;
+  int bx = (int)((nv3 + 255) / 256);
+  if (bx > 2048) bx = 2048;
+  contravariant_dd_kernel<<<dim3(bx, nslot), 256, 0, st>>>(tau, tt, nv, maxbits);
   return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_FAIL(CC3_ERR_CUDA, "split element-wise kernel launch");
 }
 int launch_slot_exponent(const unsigned int *maxbits, int *ex, int nslot, cudaStream_t st) {

@@ -65,3 +65,33 @@ def test_autotune_keeps_parity_and_is_shared(g):
     assert abs(e[0] - ref["E_T"]) <= 1e-8
     ctx2 = g.Context(inp)  # a later context of the same size starts tuned
     assert ctx2.tuning() == (ks, nt)
+
+
+def test_split_edge_cases_small_no(g):
+    # no = 1: the loop is empty (i = j = k only); no = 2: only weight-3 triples
+    for no, nv in [(1, 12), (2, 9)]:
+        inp = make_inputs(no, nv, seed=5 + no)
+        ref = oracle.omega_inputs(inp)
+        ctx = g.Context(inp)
+        o1, o2, e = ctx.omega(g.CC3_SPLIT_BF16)
+        assert np.abs(o1 - ref["omega1"]).max() <= 1e-9
+        assert np.abs(o2 - ref["omega2"]).max() <= 1e-9
+        assert abs(e[0] - ref["E_T"]) <= 1e-8
+
+
+def test_split_proline_sized_triple_subset(g):
+    # the L-proline-sized problem (22 active occupied, nv = 250, naux = 700,
+    # near-degenerate virtual cluster): a seeded sample of triples against the
+    # oracle restricted to the same triples
+    inp = make_inputs(22, 250, seed=0, naux=700, nfrozen=9, n_degenerate=10)
+    tr = unique_triples(22)
+    rng = np.random.default_rng(3)
+    sel = [tr[i][:3] for i in sorted(rng.choice(len(tr), size=3, replace=False))]
+    sel.append((21, 21, 20))  # a weight-3 triple at the top of the range
+    ref = oracle.omega_inputs(inp, triples=sel)
+    ctx = g.Context(inp)
+    ctx.set_triples(sel)
+    o1, o2, e = ctx.omega(g.CC3_SPLIT_BF16)
+    assert np.abs(o1 - ref["omega1"]).max() <= 1e-9
+    assert np.abs(o2 - ref["omega2"]).max() <= 1e-9
+    assert abs(e[0] - ref["E_T"]) <= 1e-8
