@@ -78,7 +78,10 @@ enum {
 /* flags of cc3_ctx_create */
 #define CC3_DEVICE_PTRS 1u   /* all pointers of this context are device pointers */
 #define CC3_DETERMINISTIC 2u /* fixed-order cross-triple reductions (bitwise    */
-                             /* reproducible results, somewhat slower)          */
+                             /* reproducible results): not available in this   */
+                             /* build, cc3_ctx_create returns                   */
+                             /* CC3_ERR_UNSUPPORTED; the cross-triple sums use  */
+                             /* FP64 atomics, reproducible to rounding only     */
 
 /* Create a context for one problem (no >= 1, 1 <= nv <= 1024).  Uploads and
  * reorders the inputs (paper: integrals are reordered before the triple loop,

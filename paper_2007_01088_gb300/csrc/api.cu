@@ -329,6 +329,7 @@ int cc3_ctx_create(cc3_ctx **out, int no, int nv, const double *eps_o,
     return CC3_ERR_ARG;
   if (naux < 0 || (naux > 0 && !chol_L)) return CC3_ERR_ARG;
   if (flags & ~(CC3_DEVICE_PTRS | CC3_DETERMINISTIC)) return CC3_ERR_ARG;
+  if (flags & CC3_DETERMINISTIC) return CC3_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   cc3_ctx *c = new (std::nothrow) cc3_ctx();
   if (!c) return CC3_ERR_OOM;

@@ -80,3 +80,11 @@ def test_subsets_add_up(g):
     b = [x.copy() for x in ctx.omega(g.CC3_FP64)]
     assert rel(a[1] + b[1], full[1]) < 1e-13
     assert abs(a[2][0] + b[2][0] - full[2][0]) < 1e-13 * abs(full[2][0])
+
+
+def test_deterministic_flag_is_rejected(g):
+    # bitwise-reproducible reductions are not built: the flag fails loudly
+    inp = make_inputs(3, 8, seed=1)
+    with pytest.raises(g.CC3Error) as e:
+        g.Context(inp, flags=g.CC3_DETERMINISTIC)
+    assert e.value.status == g.CC3_ERR_UNSUPPORTED
