@@ -99,6 +99,11 @@ struct SplitState {
   int ks4 = 1;  // K split of the rows-x contractions
   // tunables (autotuner): K steps per vvov tile, N tile of the W build (0: default)
   int ks_target = 400, nt_w = 0;
+  // the residual's launch sequence as a CUDA graph (captured on the second
+  // untraced call on a non-default stream, replayed afterwards)
+  cudaGraphExec_t gexec = nullptr;
+  long long g_launches = 0;
+  int g_calls = 0;
   float2 *evdd = nullptr;
   int batch = 0;
   float2 *Wdd = nullptr, *TTdd = nullptr;
@@ -126,7 +131,14 @@ int alloc(T **p, size_t n) {
   return CC3_OK;
 }
 
+void drop_graph(SplitState *S) {
+  if (S->gexec) cudaGraphExecDestroy(S->gexec);
+  S->gexec = nullptr;
+  S->g_calls = 0;
+}
+
 void free_state_buffers(SplitState *S) {
+  drop_graph(S);
   void *bufs[] = {S->T2S, S->T2C, S->T2R, S->XS, S->YS, S->OS, S->Zg, S->Zh, S->OO, S->OV,
                   S->OVD, S->OVZA, S->OVZB, S->evdd, S->Wdd, S->TTdd, S->V[0], S->V[1], S->V[2], S->vptr, S->maxbits,
                   S->slot_ex, S->status};
@@ -501,6 +513,7 @@ void plan_omega_split(SPlan &P, SplitState *S, int no, int nv, const int ijk[3],
 }
 
 int build_plans(cc3_ctx *c, SplitState *S, cudaStream_t st) {
+  drop_graph(S);
   for (auto *v : {&S->ab, &S->cc, &S->om})
     for (auto &d : *v) s_free_plan(&d);
   S->ab.clear();
@@ -594,9 +607,10 @@ int split_ready(cc3_ctx *c, SplitState **out, cudaStream_t st) {
 }
 }  // namespace
 
-int split_omega(cc3_ctx *c, cudaStream_t st) {
-  SplitState *S = nullptr;
-  TRY(split_ready(c, &S, st));
+namespace {
+// The residual's launch sequence: per batch of triples the W build (phases AB
+// and C), tau~ and its slices, and the contractions.
+int omega_sequence(cc3_ctx *c, SplitState *S, cudaStream_t st) {
   const int s = S->s;
   VPtrTable P;
   fill_vptrs(c, S, &P);
@@ -620,6 +634,46 @@ int split_omega(cc3_ctx *c, cudaStream_t st) {
     TRY(s_launch_plan(S->om[b], S->arrs, P, s, kdrain, S->status, st, &c->counters.launches));
     trace_end(c, TR_SPLIT_OMEGA, st, S->om[b].flop, S->om[b].slice_flop);
   }
+  return CC3_OK;
+}
+}  // namespace
+
+int split_omega(cc3_ctx *c, cudaStream_t st) {
+  SplitState *S = nullptr;
+  TRY(split_ready(c, &S, st));
+  const int s = S->s;
+  // untraced calls on a stream other than the legacy default one replay a
+  // captured graph of the whole sequence (the plans and buffers it uses are
+  // fixed until the plans are rebuilt)
+  const bool graphable = !c->trace.on && st != nullptr && st != cudaStreamLegacy;
+  if (graphable && S->gexec) {
+    CU(cudaGraphLaunch(S->gexec, st));
+    c->counters.launches += S->g_launches;
+  } else if (graphable && S->g_calls >= 1) {
+    const long long before = c->counters.launches;
+    CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    const int rc = omega_sequence(c, S, st);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+    cudaGraphExec_t exec = nullptr;
+    if (rc == CC3_OK && ec == cudaSuccess && graph &&
+        cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+      S->gexec = exec;
+      S->g_launches = c->counters.launches - before;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    c->counters.launches = before;
+    if (S->gexec) {
+      CU(cudaGraphLaunch(S->gexec, st));
+      c->counters.launches += S->g_launches;
+    } else {
+      TRY(omega_sequence(c, S, st));  // capture failed: run the launches directly
+    }
+  } else {
+    TRY(omega_sequence(c, S, st));
+  }
+  S->g_calls++;
   int hs = 0;
   CU(cudaMemcpyAsync(&hs, S->status, sizeof(int), cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));

@@ -95,3 +95,20 @@ def test_split_proline_sized_triple_subset(g):
     assert np.abs(o1 - ref["omega1"]).max() <= 1e-9
     assert np.abs(o2 - ref["omega2"]).max() <= 1e-9
     assert abs(e[0] - ref["E_T"]) <= 1e-8
+
+
+def test_graph_replay_matches_direct_launches(g):
+    # untraced calls on a non-default stream: the second call captures the
+    # launch sequence as a CUDA graph, later calls replay it
+    import torch
+    inp = make_inputs(5, 40, seed=21)
+    ref = oracle.omega_inputs(inp)
+    st = torch.cuda.Stream()
+    ctx = g.Context(inp, stream=st)
+    outs = [ctx.omega(g.CC3_SPLIT_BF16) for _ in range(4)]
+    for o1, o2, e in outs:
+        assert np.abs(o1 - ref["omega1"]).max() <= 1e-9
+        assert np.abs(o2 - ref["omega2"]).max() <= 1e-9
+        assert abs(e[0] - ref["E_T"]) <= 1e-8
+        assert np.abs(o2 - outs[0][1]).max() <= 1e-12 * np.abs(outs[0][1]).max()
+    assert ctx.counters()["launches"] > 0
