@@ -77,11 +77,13 @@ enum {
 
 /* flags of cc3_ctx_create */
 #define CC3_DEVICE_PTRS 1u   /* all pointers of this context are device pointers */
-#define CC3_DETERMINISTIC 2u /* fixed-order cross-triple reductions (bitwise    */
-                             /* reproducible results): not available in this   */
-                             /* build, cc3_ctx_create returns                   */
-                             /* CC3_ERR_UNSUPPORTED; the cross-triple sums use  */
-                             /* FP64 atomics, reproducible to rounding only     */
+#define CC3_DETERMINISTIC 2u /* order-independent cross-triple sums of the     */
+                             /* residual (128-bit fixed-point accumulation with */
+                             /* integer atomics, 2^-64 resolution): bitwise     */
+                             /* reproducible Omega1/Omega2/E_T on both paths.   */
+                             /* cc3_jacobian_triples then returns               */
+                             /* CC3_ERR_UNSUPPORTED.  Without it the sums use   */
+                             /* FP64 atomics (reproducible to rounding).        */
 
 /* Create a context for one problem (no >= 1, 1 <= nv <= 1024).  Uploads and
  * reorders the inputs (paper: integrals are reordered before the triple loop,

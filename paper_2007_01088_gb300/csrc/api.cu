@@ -97,6 +97,8 @@ void fill_ptrs(cc3_ctx *c, PtrTable *pt) {
   pt->p[B_OMT] = c->omt;
   pt->p[B_OM1] = c->om1;
   pt->p[B_SCRATCH] = c->omt;
+  pt->fx[B_OMT] = c->omt_fx;  // null unless CC3_DETERMINISTIC
+  pt->fx[B_OM1] = c->om1_fx;
 }
 
 int build_omega_plans(cc3_ctx *c, cudaStream_t s) {
@@ -314,6 +316,8 @@ void cc3_ctx_destroy(cc3_ctx *c) {
   for (double *p : bufs)
     if (p) cudaFree(p);
   if (c->status) cudaFree(c->status);
+  if (c->omt_fx) cudaFree(c->omt_fx);
+  if (c->om1_fx) cudaFree(c->om1_fx);
   delete c;
 }
 
@@ -329,7 +333,6 @@ int cc3_ctx_create(cc3_ctx **out, int no, int nv, const double *eps_o,
     return CC3_ERR_ARG;
   if (naux < 0 || (naux > 0 && !chol_L)) return CC3_ERR_ARG;
   if (flags & ~(CC3_DEVICE_PTRS | CC3_DETERMINISTIC)) return CC3_ERR_ARG;
-  if (flags & CC3_DETERMINISTIC) return CC3_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   cc3_ctx *c = new (std::nothrow) cc3_ctx();
   if (!c) return CC3_ERR_OOM;
@@ -367,6 +370,13 @@ int cc3_ctx_create(cc3_ctx **out, int no, int nv, const double *eps_o,
   if ((rc = launch_transpose_ooov_to_oovo(c->ooov, c->oovo, no, nv, s)) != CC3_OK) goto fail;
   if ((rc = dalloc(&c->omt, nt2)) != CC3_OK) goto fail;
   if ((rc = dalloc(&c->om1, (size_t)no * nv)) != CC3_OK) goto fail;
+  if (flags & CC3_DETERMINISTIC) {
+    if (cudaMalloc(&c->omt_fx, sizeof(unsigned long long) * 2 * nt2) != cudaSuccess ||
+        cudaMalloc(&c->om1_fx, sizeof(unsigned long long) * 2 * (size_t)no * nv) != cudaSuccess) {
+      rc = CC3_ERR_OOM;
+      goto fail;
+    }
+  }
   if ((rc = dalloc(&extra(c)->escr, 257)) != CC3_OK) goto fail;
   if (cudaMalloc(&c->status, sizeof(int) * 4) != cudaSuccess) { rc = CC3_ERR_OOM; goto fail; }
   if (cudaMemsetAsync(c->status, 0, sizeof(int) * 4, s) != cudaSuccess) { rc = CC3_ERR_CUDA; goto fail; }
@@ -522,10 +532,19 @@ int cc3_omega_triples(cc3_ctx *c, cc3_prec prec, double *Omega1,
   TRY(launch_zero(c->omt, nt2, s));
   TRY(launch_zero(c->om1, (size_t)no * nv, s));
   c->counters.launches += 2;
+  if (c->omt_fx) {  // deterministic: the sums accumulate in 128-bit fixed point
+    CU(cudaMemsetAsync(c->omt_fx, 0, sizeof(unsigned long long) * 2 * nt2, s));
+    CU(cudaMemsetAsync(c->om1_fx, 0, sizeof(unsigned long long) * 2 * (size_t)no * nv, s));
+  }
   if (prec == CC3_FP64) {
     TRY(omega_fp64(c, s));
   } else {
     TRY(split_omega(c, s));
+  }
+  if (c->omt_fx) {
+    TRY(launch_fx_to_double(c->omt_fx, c->omt, nt2, s));
+    TRY(launch_fx_to_double(c->om1_fx, c->om1, (size_t)no * nv, s));
+    c->counters.launches += 2;
   }
   trace_begin(c, TR_OUTPUT, s);
   const int rc = finish_outputs(c, Omega1, Omega2, E_T, s);

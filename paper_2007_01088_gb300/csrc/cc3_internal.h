@@ -54,6 +54,9 @@ struct Job {
 enum { MAX_BUFS = 32 };
 struct PtrTable {
   double *p[MAX_BUFS];
+  // deterministic mode: accumulating outputs go to 128-bit fixed point
+  // (lo, hi word pairs per element) instead of FP64 atomics when set
+  unsigned long long *fx[MAX_BUFS];
 };
 
 // Buffer ids of the pointer table.
@@ -112,6 +115,7 @@ struct cc3_ctx {
   int batch = 0;  // triples per batch
   double *ws_w = nullptr, *ws_tt = nullptr, *ws_tt2 = nullptr;
   double *omt = nullptr, *om1 = nullptr;
+  unsigned long long *omt_fx = nullptr, *om1_fx = nullptr;  // deterministic mode
   // Jacobian cache (Algorithm 2 intermediates)
   double *Zv = nullptr, *Zo = nullptr;
   bool prep_valid = false;
@@ -157,6 +161,8 @@ int launch_energy(const double *t2, const double *omt, double *E, int no,
 int launch_transpose_ooov_to_oovo(const double *ooov, double *oovo, int no,
                                   int nv, cudaStream_t s);
 int launch_zero(double *p, size_t n, cudaStream_t s);
+// out[i] = the 128-bit fixed-point value fx[2i..2i+1] as a double
+int launch_fx_to_double(const unsigned long long *fx, double *out, size_t n, cudaStream_t s);
 
 // plans (plans.cu): operand / output descriptors and job builders
 Opnd op(int buf, long long off, long long sm0, long long sk0, long long sb = 0, int neg = 0);

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include "cc3_internal.h"
+#include "fx128.cuh"
 
 namespace cc3 {
 
@@ -128,7 +129,11 @@ fp64_engine_kernel(const Job *__restrict__ jobs, int njobs,
       if (J.mode == EPI_STORE) {
         *dst = v;
       } else if (J.mode == EPI_ATOMIC) {
-        atomicAdd(dst, v);
+        unsigned long long *fx = P.fx[C.buf];
+        if (fx)
+          fx_add(fx + 2 * (dst - P.p[C.buf]), v);
+        else
+          atomicAdd(dst, v);
       } else {  // EPI_TAU: m = c, n = a * nv + b
         const double *ev = P.p[B_EPSV];
         const int nvv = C.n_in;

@@ -541,6 +541,8 @@ extern "C" int cc3_jacobian_triples(cc3_ctx *c, cc3_prec prec, int nvec, const d
   if (c->naux < 1 || !c->chol)
     return CC3_FAIL(CC3_ERR_ARG, "the Jacobian needs the Cholesky vectors (chol_L)");
   if (prec == CC3_SPLIT_INT8) return CC3_ERR_UNSUPPORTED;
+  if (c->flags & CC3_DETERMINISTIC)
+    return CC3_FAIL(CC3_ERR_UNSUPPORTED, "deterministic reductions cover the residual only");
   if (prec != CC3_FP64 && prec != CC3_SPLIT_BF16) return CC3_ERR_ARG;
   std::lock_guard<std::mutex> lk(c->mu);
   cudaStream_t s = (cudaStream_t)cuda_stream;

@@ -1,6 +1,8 @@
 // Element-wise and reduction kernels of the FP64 path.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "cc3_internal.h"
 
 namespace cc3 {
@@ -137,6 +139,24 @@ int launch_zero(double *p, size_t n, cudaStream_t s) {
   if (n == 0) return CC3_OK;
   int blocks = (int)std::min<size_t>((n + 255) / 256, 8192);
   zero_kernel<<<blocks, 256, 0, s>>>(p, n);
+  return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_ERR_CUDA;
+}
+
+__global__ void fx_to_double_kernel(const unsigned long long *__restrict__ fx,
+                                    double *__restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const unsigned long long lo = fx[2 * i];
+    const long long hi = (long long)fx[2 * i + 1];
+    // value = hi + lo 2^-64 (lo unsigned)
+    out[i] = (double)hi + ldexp((double)lo, -64);
+  }
+}
+
+int launch_fx_to_double(const unsigned long long *fx, double *out, size_t n, cudaStream_t s) {
+  if (n == 0) return CC3_OK;
+  const size_t b = std::min<size_t>((n + 255) / 256, 8192);
+  fx_to_double_kernel<<<(unsigned)b, 256, 0, s>>>(fx, out, n);
   return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_ERR_CUDA;
 }
 

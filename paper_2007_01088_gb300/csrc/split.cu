@@ -564,6 +564,8 @@ void fill_vptrs(cc3_ctx *c, SplitState *S, VPtrTable *P) {
   P->p[B_EPSV] = S->evdd;
   P->p[B_OMT] = c->omt;
   P->p[B_OM1] = c->om1;
+  P->fx[B_OMT] = c->omt_fx;  // null unless CC3_DETERMINISTIC
+  P->fx[B_OM1] = c->om1_fx;
   P->p[B_SLOTEXP] = S->slot_ex;
 }
 

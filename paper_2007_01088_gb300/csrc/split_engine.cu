@@ -35,6 +35,7 @@
 
 #include "dd.cuh"
 #include "sm100_prims.cuh"
+#include "fx128.cuh"
 #include "split_engine.h"
 
 namespace cc3 {
@@ -446,6 +447,8 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
               const dd::df den = dd::add(dd::df{J.w_hi, J.w_lo}, dd::neg(e));
               const dd::df tau = dd::div(tot, den);
               reinterpret_cast<float2 *>(P.p[C.buf])[off] = make_float2(tau.hi, tau.lo);
+            } else if (P.fx[C.buf]) {
+              fx_add(P.fx[C.buf] + 2 * off, dd::to_double(x));
             } else {
               atomicAdd(reinterpret_cast<double *>(P.p[C.buf]) + off, dd::to_double(x));
             }

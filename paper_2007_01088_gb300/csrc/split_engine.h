@@ -73,6 +73,7 @@ struct SJob {
 
 struct VPtrTable {
   void *p[MAX_BUFS];
+  unsigned long long *fx[MAX_BUFS];  // deterministic mode, as in PtrTable
 };
 
 struct SPlan {

@@ -82,9 +82,30 @@ def test_subsets_add_up(g):
     assert abs(a[2][0] + b[2][0] - full[2][0]) < 1e-13 * abs(full[2][0])
 
 
-def test_deterministic_flag_is_rejected(g):
-    # bitwise-reproducible reductions are not built: the flag fails loudly
-    inp = make_inputs(3, 8, seed=1)
-    with pytest.raises(g.CC3Error) as e:
-        g.Context(inp, flags=g.CC3_DETERMINISTIC)
-    assert e.value.status == g.CC3_ERR_UNSUPPORTED
+@pytest.mark.parametrize("split", [False, True])
+def test_deterministic_mode_is_bitwise_reproducible(g, split):
+    # CC3_DETERMINISTIC: the cross-triple sums accumulate in 128-bit fixed
+    # point, so repeated evaluations agree bit for bit (FP64 atomics would
+    # agree only to rounding)
+    inp = make_inputs(6, 40, seed=31)
+    ref = oracle.omega_inputs(inp)
+    prec = g.CC3_SPLIT_BF16 if split else g.CC3_FP64
+    ctx = g.Context(inp, flags=g.CC3_DETERMINISTIC)
+    runs = [ctx.omega(prec) for _ in range(3)]
+    ctx2 = g.Context(inp, flags=g.CC3_DETERMINISTIC)
+    runs.append(ctx2.omega(prec))
+    for o1, o2, e in runs[1:]:
+        assert np.array_equal(o1, runs[0][0]) and np.array_equal(o2, runs[0][1])
+        assert e[0] == runs[0][2][0]
+    o1, o2, e = runs[0]
+    if split:
+        assert np.abs(o2 - ref["omega2"]).max() <= 1e-9
+        assert abs(e[0] - ref["E_T"]) <= 1e-8
+    else:
+        assert np.abs(o2 - ref["omega2"]).max() <= 1e-12 * np.abs(ref["omega2"]).max()
+        assert abs(e[0] - ref["E_T"]) <= 1e-12 * abs(ref["E_T"])
+    from cc3_inputs import make_trial_vectors
+    R1, R2 = make_trial_vectors(6, 40, 1)
+    with pytest.raises(g.CC3Error) as err:
+        ctx.jacobian(R1, R2, [0.0], prec)
+    assert err.value.status == g.CC3_ERR_UNSUPPORTED
