@@ -220,6 +220,7 @@ typedef struct {
   /* outputs (host pointers; filled by cc3_serve_wait) */
   double *Omega1, *Omega2, *E_T;  /* kind 0 */
   double *rho1, *rho2;            /* kind 1 */
+  unsigned flags;                 /* context flags: 0 or CC3_DETERMINISTIC    */
 } cc3_request;
 
 typedef struct {

@@ -70,7 +70,8 @@ class Request(ctypes.Structure):
                                                   "g_ovov", "F_ov", "chol_L")]
                 + [("nvec", ctypes.c_int)]
                 + [(n, ctypes.c_void_p) for n in ("omega", "R1", "R2", "Omega1", "Omega2",
-                                                  "E_T", "rho1", "rho2")])
+                                                  "E_T", "rho1", "rho2")]
+                + [("flags", ctypes.c_uint)])
 
 
 class Stats(ctypes.Structure):
@@ -424,7 +425,7 @@ class Server:
         self.srv = cc3_serve_start(hbm_budget_bytes, max_slots)
         self._out = {}
 
-    def _request(self, kind, prec, inp, nvec=0, omega=None, R1=None, R2=None):
+    def _request(self, kind, prec, inp, nvec=0, omega=None, R1=None, R2=None, flags=0):
         keep = {n: _f64(getattr(inp, n)) for n in ("eps_o", "eps_v", "t2", "g_vvvo", "g_ooov",
                                                    "g_ovov", "F_ov")}
         L = getattr(inp, "chol_L", None)
@@ -434,6 +435,7 @@ class Server:
         r.kind, r.prec, r.no, r.nv = int(kind), int(prec), int(inp.no), int(inp.nv)
         r.naux = 0 if L is None else int(L.shape[0])
         r.nvec = int(nvec)
+        r.flags = int(flags)
         for n, a in keep.items():
             setattr(r, n, None if a is None else a.ctypes.data)
         no, nv = int(inp.no), int(inp.nv)
@@ -449,8 +451,8 @@ class Server:
         r, _keep, _out = self._request(kind, prec, inp, nvec, omega, R1, R2)
         return cc3_serve_footprint(r)
 
-    def submit_omega(self, inp, prec=CC3_FP64):
-        r, keep, out = self._request(0, prec, inp)
+    def submit_omega(self, inp, prec=CC3_FP64, flags=0):
+        r, keep, out = self._request(0, prec, inp, flags=flags)
         t = cc3_serve_submit(self.srv, r)
         self._out[t] = out
         return t

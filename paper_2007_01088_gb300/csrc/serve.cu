@@ -60,6 +60,7 @@ constexpr size_t kMargin = 64u << 20;  // CUDA plan tables, rounding of allocati
 size_t request_footprint(const cc3_request &q) {
   const int ntri = q.no * (q.no + 1) * (q.no + 2) / 6;
   size_t b = cc3::ctx_footprint(q.no, q.nv, q.naux, ntri, true);
+  if (q.flags & CC3_DETERMINISTIC) b += 16 * ((size_t)q.no * q.nv * (1 + (size_t)q.no * q.nv));
   if (q.prec == CC3_SPLIT_BF16) b += cc3::split_footprint(q.no, q.nv, 6, ntri);
   if (q.kind == 1) b += cc3::jacobian_footprint(q.no, q.nv, q.naux, q.nvec, ntri, true);
   if (q.kind == 1 && q.prec == CC3_SPLIT_BF16)
@@ -78,6 +79,8 @@ int validate(const cc3_request &q) {
   if (q.kind == 1 && (q.nvec < 1 || !q.omega || !q.R1 || !q.R2 || q.naux < 1 || !q.rho1 ||
                       !q.rho2))
     return CC3_ERR_ARG;
+  if (q.flags & ~CC3_DETERMINISTIC) return CC3_ERR_ARG;
+  if ((q.flags & CC3_DETERMINISTIC) && q.kind == 1) return CC3_ERR_UNSUPPORTED;
   return CC3_OK;
 }
 
@@ -131,7 +134,7 @@ int execute(Req *r, cudaStream_t st) {
   cc3_ctx *ctx = nullptr;
   int rc = cc3_ctx_create(&ctx, q.no, q.nv, r->eps_o.data(), r->eps_v.data(), r->t2.data(),
                           r->vvvo.data(), r->ooov.data(), r->ovov.data(), r->F.data(),
-                          q.naux > 0 ? r->chol.data() : nullptr, q.naux, 0, st);
+                          q.naux > 0 ? r->chol.data() : nullptr, q.naux, q.flags, st);
   if (rc != CC3_OK) return rc;
   const size_t n1 = (size_t)q.no * q.nv, nt2 = n1 * q.no * q.nv;
   if (q.kind == 0) {

@@ -162,3 +162,23 @@ def test_footprint_bounds_device_memory(g):
             assert used <= fp, (prec, no, nv, used, fp)
     finally:
         srv.stop()
+
+
+def test_deterministic_requests_are_bitwise_equal_alone_and_in_the_mix(g):
+    probs = [(make_inputs(4 + n, 20 + 6 * n, seed=80 + n),
+              g.CC3_SPLIT_BF16 if n % 2 else g.CC3_FP64) for n in range(5)]
+    alone = []
+    for inp, prec in probs:
+        ctx = g.Context(inp, flags=g.CC3_DETERMINISTIC)
+        alone.append(ctx.omega(prec))
+        ctx.close()
+    srv = g.Server(max_slots=3)
+    try:
+        ts = [srv.submit_omega(inp, prec, flags=g.CC3_DETERMINISTIC) for inp, prec in probs]
+        for t, ref in zip(ts, alone):
+            st, out = srv.wait(t)
+            assert st == g.CC3_OK
+            for x, y in zip(out, ref):
+                assert np.array_equal(x, y)
+    finally:
+        srv.stop()
