@@ -186,8 +186,10 @@ double nominal_flop_omega(int no, int nv, int ntri_weighted);
 void jacobian_destroy(cc3_ctx *c);
 // pieces shared by the FP64 and split Jacobians (jacobian.cu)
 int jac_blocks(cc3_ctx *c, cudaStream_t s);  // (lj|mk), (lj|cd) from the Cholesky vectors
+// g^_vvvo, g^_oovo, F^ and M^J_ck of one trial vector (FP64); chol = false
+// leaves the Cholesky (vvvv) term of g^_vvvo to the caller
 int jac_dress(cc3_ctx *c, const double *R1v, double *hv, double *ho, double *hf, double *mj,
-              cudaStream_t s);  // g^_vvvo, g^_oovo, F^ of one trial vector (FP64)
+              cudaStream_t s, bool chol = true);
 int jac_z_buffers(cc3_ctx *c, double **Zv, double **Zo, bool zero, cudaStream_t s);
 void jac_set_prep(cc3_ctx *c, int prec);  // the cached Z~ are valid, built in prec
 int jac_prep_prec(cc3_ctx *c);            // -1 if the cache is not valid

@@ -231,7 +231,9 @@ int ensure_prep(cc3_ctx *c, JacState *J, const std::vector<double> &eo, cudaStre
 
 // R1-dressed integrals of one trial vector (pointer table: B_R1, B_MJ,
 // B_HVVVO, B_HOOVO, B_HF of that vector)
-int dress(cc3_ctx *c, const PtrTable &pt, cudaStream_t s) {
+// chol = false leaves out the sum_J L^J_bd M^J_ck term of g^_vvvo (the split
+// path adds it on the tensor cores) and starts g^_vvvo from zero instead.
+int dress(cc3_ctx *c, const PtrTable &pt, cudaStream_t s, bool chol = true) {
   const int no = c->no, nv = c->nv, n = no + nv, naux = c->naux;
   const long long n2 = (long long)n * n, nv2 = (long long)nv * nv, nvo = (long long)nv * no;
   const long long ovovl = (long long)nv * no * nv;  // stride of l in ovov[l][d][k][c]
@@ -262,16 +264,20 @@ int dress(cc3_ctx *c, const PtrTable &pt, cudaStream_t s) {
   TRY(run_plan(c, p0, 0, pt, s));
   TRY(run_plan(c, pf, 1, pt, s));
   // g^vvvo: Cholesky term (store), then the two R1 terms (accumulate)
-  jb = new_job(p1, 0, (int)nv2, (int)nvo, (int)nvo, 1, 1, EPI_STORE);
-  add_term(p1, jb, with_m2(op(B_CHOL, (long long)no * n + no, 1, n2), nv, n),
-           with_m2(op(B_MJ, 0, 1, nvo), no, no), naux);
-  o = out(B_HVVVO, 0, nvo, 1);
-  o.m_in = nv;
-  o.sm1 = nv2 * no;
-  o.n_in = no;
-  o.sn1 = no;
-  p1.jobs[jb].C = o;
-  p1.jobs[jb].Ct = o;
+  if (chol) {
+    jb = new_job(p1, 0, (int)nv2, (int)nvo, (int)nvo, 1, 1, EPI_STORE);
+    add_term(p1, jb, with_m2(op(B_CHOL, (long long)no * n + no, 1, n2), nv, n),
+             with_m2(op(B_MJ, 0, 1, nvo), no, no), naux);
+    o = out(B_HVVVO, 0, nvo, 1);
+    o.m_in = nv;
+    o.sm1 = nv2 * no;
+    o.n_in = no;
+    o.sn1 = no;
+    p1.jobs[jb].C = o;
+    p1.jobs[jb].Ct = o;
+  } else {
+    TRY(launch_zero(pt.p[B_HVVVO], (size_t)nv2 * nv * no, s));
+  }
   // g^oovo: first term (store)
   jb = new_job(p1, 0, no, (int)nvo, (int)nvo, no, 1, EPI_STORE);
   add_term(p1, jb, op(B_R1, 0, nv, 1),
@@ -331,7 +337,7 @@ int jac_blocks(cc3_ctx *c, cudaStream_t s) {
 }
 
 int jac_dress(cc3_ctx *c, const double *R1v, double *hv, double *ho, double *hf, double *mj,
-              cudaStream_t s) {
+              cudaStream_t s, bool chol) {
   JacState *J = jst(c);
   if (!J) return CC3_ERR_OOM;
   PtrTable pt;
@@ -341,7 +347,7 @@ int jac_dress(cc3_ctx *c, const double *R1v, double *hv, double *ho, double *hf,
   pt.p[B_HVVVO] = hv;
   pt.p[B_HOOVO] = ho;
   pt.p[B_HF] = hf;
-  return dress(c, pt, s);
+  return dress(c, pt, s, chol);
 }
 
 int jac_z_buffers(cc3_ctx *c, double **Zv, double **Zo, bool zero, cudaStream_t s) {

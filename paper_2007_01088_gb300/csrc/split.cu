@@ -96,6 +96,9 @@ struct SplitState {
                 *OS = nullptr, *Zg = nullptr, *Zh = nullptr, *OO = nullptr, *OV = nullptr;
   // Jacobian (Algorithm 2 layouts of ovov), staged on first use
   __nv_bfloat16 *OVD = nullptr, *OVZA = nullptr, *OVZB = nullptr;
+  // Jacobian: the vv block of the Cholesky vectors, rows (b,d), K = J
+  __nv_bfloat16 *LVV = nullptr;
+  int EL = 0;
   int ks4 = 1;  // K split of the rows-x contractions
   // tunables (autotuner): K steps per vvov tile, N tile of the W build (0: default)
   int ks_target = 400, nt_w = 0;
@@ -140,7 +143,7 @@ void drop_graph(SplitState *S) {
 void free_state_buffers(SplitState *S) {
   drop_graph(S);
   void *bufs[] = {S->T2S, S->T2C, S->T2R, S->XS, S->YS, S->OS, S->Zg, S->Zh, S->OO, S->OV,
-                  S->OVD, S->OVZA, S->OVZB, S->evdd, S->Wdd, S->TTdd, S->V[0], S->V[1], S->V[2], S->vptr, S->maxbits,
+                  S->OVD, S->OVZA, S->OVZB, S->LVV, S->evdd, S->Wdd, S->TTdd, S->V[0], S->V[1], S->V[2], S->vptr, S->maxbits,
                   S->slot_ex, S->status};
   for (void *p : bufs)
     if (p) cudaFree(p);
@@ -971,9 +974,69 @@ int split_jacobian(cc3_ctx *c, int nvec, const double *w, const double *R1d, con
   TRY(B.get(&r1a, n1 * nvec));
   TRY(launch_zero(rt, nt2 * nvec, st));
   TRY(launch_zero(r1a, n1 * nvec, st));
-  // R1-dressed integrals of every vector (FP64 engine)
-  for (int v = 0; v < nvec; ++v)
-    TRY(jac_dress(c, R1d + v * n1, hv + v * nvvvo, ho + v * noovo, hf + v * n1, mj, st));
+  // R1-dressed integrals of every vector: FP64 engine, except the Cholesky
+  // (vvvv) term sum_J L^J_bd M^J_ck of g^_vvvo, a plain nv^2 x nv no x naux
+  // contraction done here on the tensor cores
+  const int Kj = rup(c->naux, 16);
+  if (!S->LVV) {
+    const int n = no + nv;
+    unsigned long long *ml = nullptr;
+    TRY(B.get(&ml, 1));
+    CU(cudaMemsetAsync(ml, 0, sizeof(unsigned long long), st));
+    TRY(launch_maxabs(c->chol, (long long)c->naux * n * n, ml, st));
+    unsigned long long hb = 0;
+    CU(cudaMemcpyAsync(&hb, ml, sizeof(hb), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    double mxl;
+    std::memcpy(&mxl, &hb, 8);
+    S->EL = exponent_of(mxl);
+    const Gather g = {(long long)no * n + no, 0, n, 1, 0, (long long)n * n, nv, nv, Kj, c->naux, 1};
+    TRY(slice_array(S, &S->LVV, c->chol, nv2, Kj, S->EL, g, (int)nv2, st));
+  }
+  {
+    __nv_bfloat16 *mjs = nullptr;
+    unsigned long long *mm = nullptr;
+    TRY(B.get(&mjs, arr_elems(Kj, nvo, 1, s)));
+    TRY(B.get(&mm, 1));
+    SArrTable la;
+    std::memset(&la, 0, sizeof(la));
+    la.a[0] = make_arr(S->LVV, Kj, nv2, 1, s);
+    la.a[1] = make_arr(mjs, Kj, nvo, 1, s);
+    for (int v = 0; v < nvec; ++v) {
+      TRY(jac_dress(c, R1d + v * n1, hv + v * nvvvo, ho + v * noovo, hf + v * n1, mj, st, false));
+      CU(cudaMemsetAsync(mm, 0, sizeof(unsigned long long), st));
+      TRY(launch_maxabs(mj, (long long)c->naux * nvo, mm, st));
+      unsigned long long hb = 0;
+      CU(cudaMemcpyAsync(&hb, mm, sizeof(hb), cudaMemcpyDeviceToHost, st));
+      CU(cudaStreamSynchronize(st));
+      double mxm;
+      std::memcpy(&mxm, &hb, 8);
+      if (!(mxm > 0.0)) continue;  // R1 = 0: no vvvv term
+      const int EM = exponent_of(mxm);
+      CU(cudaMemsetAsync(mjs, 0, arr_elems(Kj, nvo, 1, s) * sizeof(__nv_bfloat16), st));
+      const Gather g = {0, 0, no, 1, 0, nvo, nv, no, Kj, c->naux, 1};
+      TRY(launch_slice_gather(mj, mjs, s, EM, g, nvo, Kj, (int)nvo, st));
+      SPlan P;
+      double exc = 0.0;
+      const int jb = new_sjob(P, (int)nv2, (int)nvo, ntile_for((int)nvo), 1, 1, SEPI_F64_ATOMIC,
+                              S->EL + EM - 14, exc, s);
+      P.jobs[jb].C = outd(0, 0, nvo, 1);
+      P.jobs[jb].Ct = P.jobs[jb].C;
+      add_sterm(P, jb, opd(0, 0), opd(1, 0), Kj, 0, exc, s);
+      SDevPlan D;
+      TRY(s_upload_plan(P, &D, st));
+      VPtrTable vp2;
+      std::memset(&vp2, 0, sizeof(vp2));
+      vp2.p[0] = hv + v * nvvvo;
+      trace_begin(c, TR_SPLIT_W, st);
+      const int lrc = s_launch_plan(D, la, vp2, s, S_DRAIN_STEPS, S->status, st,
+                                    &c->counters.launches);
+      trace_end(c, TR_SPLIT_W, st, D.flop, D.slice_flop);
+      CU(cudaStreamSynchronize(st));
+      s_free_plan(&D);
+      TRY(lrc);
+    }
+  }
   // exponents: one for all R2 . g and t2 . g^ products, one for F^
   unsigned long long *mx = nullptr;
   TRY(B.get(&mx, 2 * (size_t)nvec + 1));
