@@ -102,6 +102,7 @@ struct SplitState {
   int ks4 = 1;  // K split of the rows-x contractions
   // tunables (autotuner): K steps per vvov tile, N tile of the W build (0: default)
   int ks_target = 400, nt_w = 0;
+  bool stack_vvov = true;  // stack permutations along M in the vvov contraction
   // the residual's launch sequence as a CUDA graph (captured on the second
   // untraced call on a non-default stream, replayed afterwards)
   cudaGraphExec_t gexec = nullptr;
@@ -337,6 +338,7 @@ int new_sjob(SPlan &P, int M, int N, int Ntile, int batch, int ksplit, int mode,
   j.mode = mode;
   j.expo = expo;
   j.expo_slot = -1;
+  j.expo_slot2 = -1;
   j.mult = 1.0f;
   j.tiles_m = (M + S_BM - 1) / S_BM;
   j.tiles_n = (N + Ntile - 1) / Ntile;
@@ -352,6 +354,7 @@ int new_sjob(SPlan &P, int M, int N, int Ntile, int batch, int ksplit, int mode,
 void add_sterm(SPlan &P, int job, SOpnd A, SOpnd B, int K, int negA, double &executed,
                int slices, const SOpnd *Bt = nullptr, int nbm = 0) {
   STerm t;
+  std::memset(&t, 0, sizeof(t));
   t.A = A;
   t.B = B;
   t.Bt = Bt ? *Bt : B;
@@ -515,6 +518,90 @@ void plan_omega_split(SPlan &P, SplitState *S, int no, int nv, const int ijk[3],
   }
 }
 
+// One distinct permutation of a triple in flight, as the vvov contraction
+// sees it: the tau~ layout L whose rows are x, the K order flag and the
+// output / integral indices.
+struct VvovPerm {
+  int slot, L, yz, p, q, r;
+};
+
+void collect_vvov_perms(std::vector<VvovPerm> &out, const int ijk[3], int slot) {
+  static const int PERM6[6][3] = {{0, 1, 2}, {1, 0, 2}, {2, 1, 0},
+                                  {0, 2, 1}, {1, 2, 0}, {2, 0, 1}};
+  int seen[6][3], nseen = 0;
+  if (ijk[0] == ijk[1] && ijk[1] == ijk[2]) return;
+  for (int u = 0; u < 6; ++u) {
+    const int *m = PERM6[u];
+    const int p = ijk[m[0]], q = ijk[m[1]], r = ijk[m[2]];
+    bool dup = false;
+    for (int w = 0; w < nseen; ++w)
+      if (seen[w][0] == p && seen[w][1] == q && seen[w][2] == r) dup = true;
+    if (dup) continue;
+    seen[nseen][0] = p;
+    seen[nseen][1] = q;
+    seen[nseen][2] = r;
+    ++nseen;
+    const int L = m[0];
+    out.push_back(VvovPerm{slot, L, m[1] == (L + 1) % 3 ? 1 : 0, p, q, r});
+  }
+}
+
+// The vvov + singles contraction of a batch with the permutations that share
+// the integral operand (same r and K order) stacked along M: their x rows
+// (nv each) are laid end to end and cut into 128-row tiles, so a tile may hold
+// the last rows of one permutation and the first rows of the next (two A
+// segments, two output row ranges, one singles tail column each).  Without
+// stacking nv = 160 costs two 128-row tiles per permutation, 96 rows of
+// padding in the second; with it, 1.25.  Needs nv a multiple of 8 and >= 128
+// (a tile then spans at most two permutations).
+void plan_vvov_stacked(SPlan &P, SplitState *S, int no, int nv, std::vector<VvovPerm> perms,
+                       int ksplit4, double &ex) {
+  const int s = S->s, vp = S->vp;
+  const long long nv2 = (long long)nv * nv;
+  std::stable_sort(perms.begin(), perms.end(), [](const VvovPerm &a, const VvovPerm &b) {
+    return a.r != b.r ? a.r < b.r : a.yz < b.yz;
+  });
+  size_t g0 = 0;
+  while (g0 < perms.size()) {
+    size_t g1 = g0;
+    while (g1 < perms.size() && perms[g1].r == perms[g0].r && perms[g1].yz == perms[g0].yz) ++g1;
+    const long long total = (long long)(g1 - g0) * nv;
+    for (long long R = 0; R < total; R += S_BM) {
+      const size_t k = g0 + (size_t)(R / nv);
+      const int x0 = (int)(R % nv);
+      const int rows0 = (int)std::min<long long>(std::min<long long>(nv - x0, S_BM), total - R);
+      const int rows1 = (rows0 < S_BM && k + 1 < g1) ? std::min(S_BM - rows0, nv) : 0;
+      const VvovPerm &u = perms[k];
+      const int N = rows1 > 0 ? nv + 9 : nv + 1;
+      int jb = new_sjob(P, rows0 + rows1, N, ntile_for(N), 1, ksplit4, SEPI_F64_ATOMIC,
+                        S->Eg - 14, ex, s);
+      SJob &J = P.jobs[jb];
+      J.expo_slot = u.slot;
+      J.Nm = nv;
+      J.n_valid = nv;
+      J.C = outd(B_OMT, (((long long)u.p * no + u.q) * nv + x0) * nv, nv, 1);
+      J.Ct = outd(B_OM1, (long long)u.p * nv + x0, 1, 0);
+      const SOpnd tail = opd(MB_OV, u.yz ? u.q * no + u.r : u.r * no + u.q);
+      add_sterm(P, jb, opd(MA_V0 + u.L, u.slot, 0, x0, 0), opd(u.yz ? MB_ZG : MB_ZH, u.r), nv * vp,
+                0, ex, s, &tail, nv);
+      if (rows1 > 0) {
+        const VvovPerm &w = perms[k + 1];
+        J.msplit = rows0;
+        J.Nm2 = nv + 8;
+        J.expo_slot2 = w.slot;
+        J.C2 = outd(B_OMT, ((long long)w.p * no + w.q) * nv2, nv, 1);
+        J.Ct2 = outd(B_OM1, (long long)w.p * nv, 1, 0);
+        STerm &T = P.terms.back();
+        T.A2 = opd(MA_V0 + w.L, w.slot);
+        T.asplit = rows0;
+        T.Bt2 = opd(MB_OV, w.yz ? w.q * no + w.r : w.r * no + w.q);
+        T.nbm2 = nv + 8;
+      }
+    }
+    g0 = g1;
+  }
+}
+
 int build_plans(cc3_ctx *c, SplitState *S, cudaStream_t st) {
   drop_graph(S);
   for (auto *v : {&S->ab, &S->cc, &S->om})
@@ -534,9 +621,12 @@ int build_plans(cc3_ctx *c, SplitState *S, cudaStream_t st) {
   int ks4 = std::max(1, (kst + S->ks_target - 1) / std::max(16, S->ks_target));
   S->ks4 = ks4;
   S->Nab = S->nt_w > 0 ? S->nt_w : ntile_for(nv);
+  // stacked vvov tiles (see plan_vvov_stacked) where they save padding rows
+  const bool stack = S->stack_vvov && nv >= S_BM && nv % 8 == 0 && nv % S_BM != 0;
   for (int t0 = 0; t0 < c->ntri; t0 += S->batch) {
     const int t1 = std::min(c->ntri, t0 + S->batch);
     SPlan pab, pc, pom, pom3;
+    std::vector<VvovPerm> vperms;
     for (int t = t0; t < t1; ++t) {
       const int *ijk = &c->tri_host[3 * t];
       const double e = eo[ijk[0]] + eo[ijk[1]] + eo[ijk[2]];
@@ -544,9 +634,14 @@ int build_plans(cc3_ctx *c, SplitState *S, cudaStream_t st) {
       const float eod[2] = {ed.hi, ed.lo};
       plan_w_split(pab, pc, S, no, nv, ijk, t - t0, eod, ex);
       // the long-K tiles first: the persistent engine hands tiles out in order
-      plan_omega_split(pom, S, no, nv, ijk, t - t0, ks4, ex, 1);
+      if (stack) {
+        collect_vvov_perms(vperms, ijk, t - t0);
+      } else {
+        plan_omega_split(pom, S, no, nv, ijk, t - t0, ks4, ex, 1);
+      }
       plan_omega_split(pom3, S, no, nv, ijk, t - t0, ks4, ex, 2);
     }
+    if (stack) plan_vvov_stacked(pom, S, no, nv, vperms, ks4, ex);
     append_plan(pom, pom3);
     S->ab.emplace_back();
     S->cc.emplace_back();

@@ -182,10 +182,12 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
           ++t;
         }
         int kend = -1;
-        const __nv_bfloat16 *ga0 = nullptr, *gb0 = nullptr, *gt0 = nullptr;
-        long long kbsA = 0, kbsB = 0, kbsT = 0;
+        const __nv_bfloat16 *ga0 = nullptr, *gb0 = nullptr, *gt0 = nullptr, *ga20 = nullptr,
+                            *gt20 = nullptr;
+        long long kbsA = 0, kbsB = 0, kbsT = 0, kbsA2 = 0, kbsT2 = 0;
         int kmax = 0;
-        uint32_t abytes = 0, mbytes = 0, tbytes = 0, toff = 0;
+        uint32_t abytes = 0, mbytes = 0, tbytes = 0, toff = 0, a2bytes = 0, a2off = 0,
+                 t2bytes = 0, t2off = 0;
         bool bad = false;
         for (int g = ti.g0; g < ti.g1; ++g) {
           if (g >= kend) {
@@ -198,13 +200,16 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
             const SArr XA = arrs.a[T.A.map], XB = arrs.a[T.B.map], XT = arrs.a[T.Bt.map];
             const int ar = T.A.row0 + bi * T.A.row_b + m0, as = T.A.slab0 + bi * T.A.slab_b;
             const int bs = T.B.slab0 + bi * T.B.slab_b, ts = T.Bt.slab0 + bi * T.Bt.slab_b;
-            // B tile rows [n0, n0 + Nt): main rows from B, rows >= nbm from the tail Bt
+            // B tile rows [n0, n0 + Nt): main rows from B, rows in [nbm, nbm2) from
+            // the tail Bt, rows >= nbm2 from the second tail Bt2
             const int nbm = T.nbm > 0 ? T.nbm : (1 << 30);
+            const int nbm2 = T.nbm2 > 0 ? T.nbm2 : (1 << 30);
             const int br = T.B.row0 + bi * T.B.row_b + n0;
             const int nmain = max(0, min(min(Nt, nbm - n0), XB.rows - br));
             const int tfirst = max(n0, nbm);                  // first tail row of the tile
             const int tr = T.Bt.row0 + tfirst - nbm;          // its row in Bt
-            const int ntail = T.nbm > 0 ? max(0, min(n0 + Nt - tfirst, XT.rows - tr)) : 0;
+            const int ntail =
+                T.nbm > 0 ? max(0, min(min(n0 + Nt, nbm2) - tfirst, XT.rows - tr)) : 0;
             kmax = XA.kblocks;
             if (nmain > 0) kmax = min(kmax, XB.kblocks);
             if (ntail > 0) kmax = min(kmax, XT.kblocks);
@@ -215,10 +220,49 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
               bad = true;
               break;
             }
-            abytes = (uint32_t)min(S_BM, XA.rows - ar) * 32u;
+            int ra = min(S_BM, XA.rows - ar);
+            if (T.asplit > 0) ra = min(ra, T.asplit);
+            abytes = (uint32_t)ra * 32u;
             mbytes = (uint32_t)nmain * 32u;
             tbytes = (uint32_t)ntail * 32u;
             toff = (uint32_t)(tfirst - n0) * 32u * s;
+            a2bytes = 0;
+            t2bytes = 0;
+            if (T.asplit > 0) {  // second A segment
+              const SArr XA2 = arrs.a[T.A2.map];
+              const int ar2 = T.A2.row0 + bi * T.A2.row_b, as2 = T.A2.slab0 + bi * T.A2.slab_b;
+              const int ra2 = min(S_BM - T.asplit, XA2.rows - ar2);
+              if (as2 < 0 || as2 >= XA2.slabs || ar2 < 0 || ra2 <= 0 || (T.asplit & 7) != 0) {
+                err = 2;
+                bad = true;
+                break;
+              }
+              kmax = min(kmax, XA2.kblocks);
+              a2bytes = (uint32_t)ra2 * 32u;
+              a2off = (uint32_t)T.asplit * 32u * s;
+              ga20 = reinterpret_cast<const __nv_bfloat16 *>(XA2.base) +
+                     (long long)as2 * XA2.slab_stride + (long long)ar2 * 16 * s;
+              kbsA2 = XA2.kb_stride;
+            }
+            if (T.nbm2 > 0) {  // second tail
+              const SArr XT2 = arrs.a[T.Bt2.map];
+              const int t2first = max(n0, nbm2), ts2 = T.Bt2.slab0 + bi * T.Bt2.slab_b;
+              const int tr2 = T.Bt2.row0 + t2first - nbm2;
+              const int ntail2 = max(0, min(n0 + Nt - t2first, XT2.rows - tr2));
+              if (ntail2 > 0) {
+                if (ts2 < 0 || ts2 >= XT2.slabs || tr2 < 0 || ((t2first - n0) & 7) != 0) {
+                  err = 2;
+                  bad = true;
+                  break;
+                }
+                kmax = min(kmax, XT2.kblocks);
+                t2bytes = (uint32_t)ntail2 * 32u;
+                t2off = (uint32_t)(t2first - n0) * 32u * s;
+                gt20 = reinterpret_cast<const __nv_bfloat16 *>(XT2.base) +
+                       (long long)ts2 * XT2.slab_stride + (long long)tr2 * 16 * s;
+                kbsT2 = XT2.kb_stride;
+              }
+            }
             // one bulk copy per operand tile: its s slices are contiguous
             ga0 = reinterpret_cast<const __nv_bfloat16 *>(XA.base) + (long long)as * XA.slab_stride +
                   (long long)ar * 16 * s;
@@ -238,14 +282,19 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
           }
           const int st = issued % S_STAGES, ph = (issued / S_STAGES) & 1;
           if (!mbar_wait(&empty[st], ph ^ 1, &err)) { bad = true; break; }
-          mbar_arrive_expect_tx(&full[st], (uint32_t)s * (abytes + mbytes + tbytes));
+          mbar_arrive_expect_tx(&full[st],
+                                (uint32_t)s * (abytes + a2bytes + mbytes + tbytes + t2bytes));
           // stage layout: s A slices (128 rows) then s B slices (S_NT_MAX rows)
           uint8_t *sa = smem + (size_t)st * ((size_t)s * (a_bytes + S_NT_MAX * 32));
           uint8_t *sb = sa + (size_t)s * a_bytes;
           bulk_load(sa, ga0 + (long long)kb * kbsA, (uint32_t)s * abytes, &full[st]);
+          if (a2bytes)
+            bulk_load(sa + a2off, ga20 + (long long)kb * kbsA2, (uint32_t)s * a2bytes, &full[st]);
           if (mbytes) bulk_load(sb, gb0 + (long long)kb * kbsB, (uint32_t)s * mbytes, &full[st]);
           if (tbytes)
             bulk_load(sb + toff, gt0 + (long long)kb * kbsT, (uint32_t)s * tbytes, &full[st]);
+          if (t2bytes)
+            bulk_load(sb + t2off, gt20 + (long long)kb * kbsT2, (uint32_t)s * t2bytes, &full[st]);
           ++issued;
         }
         if (bad) break;
@@ -412,8 +461,12 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&accempty);
-      const int ex = J.expo + (J.expo_slot >= 0 ? reinterpret_cast<const int *>(P.p[B_SLOTEXP])[J.expo_slot] : 0);
-      const float sc = ldexpf(J.mult, ex);
+      const int *slot_ex = reinterpret_cast<const int *>(P.p[B_SLOTEXP]);
+      const bool seg2 = J.msplit > 0 && m >= J.msplit;  // second row segment
+      // the per-triple exponent table is read only by jobs that name a slot
+      const int es = seg2 ? J.expo_slot2 : J.expo_slot;
+      const float sc = ldexpf(J.mult, J.expo + (es >= 0 ? slot_ex[es] : 0));
+      const int mo = seg2 ? m - J.msplit : m;  // row within its output
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
         if (c < nch) {
@@ -424,10 +477,23 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
             if (m >= J.M || n >= J.N || (J.m_pad > 0 && (m % J.m_pad) >= J.m_valid) ||
                 (n < J.Nm && n >= J.n_valid))
               continue;
-            const OutD &C = n < J.Nm ? J.C : J.Ct;
-            const int nc = n < J.Nm ? n : n - J.Nm;
+            const OutD *Cp;
+            int nc;
+            if (n < J.Nm) {
+              Cp = seg2 ? &J.C2 : &J.C;
+              nc = n;
+            } else if (J.Nm2 > 0 && n >= J.Nm2) {
+              if (!seg2) continue;  // the second tail belongs to the second rows
+              Cp = &J.Ct2;
+              nc = n - J.Nm2;
+            } else {
+              if (seg2) continue;
+              Cp = &J.Ct;
+              nc = n - J.Nm;
+            }
+            const OutD &C = *Cp;
             const long long off = C.off + (long long)bi * C.sb +
-                                  s_rowoff(m, C.m_in, C.sm1, C.sm0) +
+                                  s_rowoff(mo, C.m_in, C.sm1, C.sm0) +
                                   s_rowoff(nc, C.n_in, C.sn1, C.sn0);
             if (J.mode == SEPI_DD_STORE) {
               reinterpret_cast<float2 *>(P.p[C.buf])[off] = make_float2(x.hi, x.lo);

@@ -49,6 +49,11 @@ struct STerm {
   int ksteps;  // K / 16
   int negA;    // the products enter with a minus sign
   int nbm;
+  // optional second A segment: tile rows >= asplit come from A2 (row0 of A2
+  // is its first row); asplit = 0: one segment.  Optional second tail: B rows
+  // n >= nbm2 come from Bt2 (row n - nbm2); nbm2 = 0: none.  Both multiples of 8.
+  SOpnd A2, Bt2;
+  int asplit, nbm2;
 };
 
 enum SEpi { SEPI_DD_STORE = 0, SEPI_DD_TAU = 1, SEPI_F64_ATOMIC = 2 };
@@ -66,6 +71,12 @@ struct SJob {
   OutD C, Ct;  // output element (b, m, n) for n < Nm, resp. (b, m, n - Nm);
                // buffer of float2 (dd) or double
   OutD W;      // tau mode: the dd values of the other W phase
+  // rows m >= msplit (msplit > 0) belong to a second output: main columns to
+  // C2 (row m - msplit), tail columns n >= Nm2 to Ct2 (column n - Nm2), with
+  // the per-triple exponent ex[expo_slot2]; rows below msplit take the tail
+  // columns [Nm, Nm2) only
+  int msplit, Nm2, expo_slot2;
+  OutD C2, Ct2;
   float eo_hi, eo_lo, w_hi, w_lo;
   int nv;
   long long tile_base;

@@ -40,7 +40,9 @@ def test_engine_gemm_exact_integers(g):
     assert np.array_equal(g.cc3_debug_split_gemm(A, B, 4), A @ B.T)
 
 
-@pytest.mark.parametrize("no,nv", [(5, 30), (4, 70), (3, 17), (6, 33)])
+# (3, 160) and (4, 136): nv >= 128 with a remainder, the case where the vvov
+# contraction stacks permutations along M (tiles holding two permutations)
+@pytest.mark.parametrize("no,nv", [(5, 30), (4, 70), (3, 17), (6, 33), (3, 160), (4, 136)])
 def test_omega_split_matches_oracle(g, no, nv):
     inp = make_inputs(no, nv, seed=no * nv)
     ref = oracle.omega_inputs(inp)
