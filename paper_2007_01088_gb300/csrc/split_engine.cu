@@ -467,9 +467,36 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
       const int es = seg2 ? J.expo_slot2 : J.expo_slot;
       const float sc = ldexpf(J.mult, J.expo + (es >= 0 ? slot_ex[es] : 0));
       const int mo = seg2 ? m - J.msplit : m;  // row within its output
+      const bool tau_mode = J.mode == SEPI_DD_TAU;
+      // tau mode: the row's orbital-energy terms once per tile
+      const float2 *ev = reinterpret_cast<const float2 *>(P.p[B_EPSV]);
+      dd::df e_row = {0.f, 0.f};
+      if (tau_mode && m < J.M) {
+        // tile (c = m, b = n) at fixed a = batch index: eps = e_a + e_b + e_c - e_ijk
+        const float2 ea = ev[bi], ec = ev[m];
+        e_row = dd::add(dd::add(dd::df{ea.x, ea.y}, dd::df{ec.x, ec.y}),
+                        dd::df{-J.eo_hi, -J.eo_lo});
+      }
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
         if (c < nch) {
+          // tau mode reads the other phase's partial sums of the four columns
+          // before any of them is overwritten, so the loads overlap
+          float2 wpre[4];
+          if (tau_mode) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const int n = n0 + part * qc + c * 4 + k;
+              wpre[k] = make_float2(0.f, 0.f);
+              if (m < J.M && n < J.N && n < J.n_valid) {
+                const OutD &W = J.W;
+                const long long woff = W.off + (long long)bi * W.sb +
+                                       s_rowoff(m, W.m_in, W.sm1, W.sm0) +
+                                       s_rowoff(n, W.n_in, W.sn1, W.sn0);
+                wpre[k] = reinterpret_cast<const float2 *>(P.p[W.buf])[woff];
+              }
+            }
+          }
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             const dd::df x = dd::scale(acc[c][k], sc);
@@ -497,19 +524,10 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
                                   s_rowoff(nc, C.n_in, C.sn1, C.sn0);
             if (J.mode == SEPI_DD_STORE) {
               reinterpret_cast<float2 *>(P.p[C.buf])[off] = make_float2(x.hi, x.lo);
-            } else if (J.mode == SEPI_DD_TAU) {
-              const OutD &W = J.W;
-              const long long woff = W.off + (long long)bi * W.sb +
-                                     s_rowoff(m, W.m_in, W.sm1, W.sm0) +
-                                     s_rowoff(nc, W.n_in, W.sn1, W.sn0);
-              const float2 wv = reinterpret_cast<const float2 *>(P.p[W.buf])[woff];
-              dd::df tot = dd::add(x, dd::df{wv.x, wv.y});
-              const float2 *ev = reinterpret_cast<const float2 *>(P.p[B_EPSV]);
-              // tile (c = m, b = n) at fixed a = batch index
-              const float2 ea = ev[bi], eb = ev[nc], ec = ev[m];
-              dd::df e = dd::add(dd::add(dd::df{ea.x, ea.y}, dd::df{eb.x, eb.y}),
-                                 dd::df{ec.x, ec.y});
-              e = dd::add(e, dd::df{-J.eo_hi, -J.eo_lo});
+            } else if (tau_mode) {
+              const dd::df tot = dd::add(x, dd::df{wpre[k].x, wpre[k].y});
+              const float2 eb = ev[nc];
+              const dd::df e = dd::add(e_row, dd::df{eb.x, eb.y});
               const dd::df den = dd::add(dd::df{J.w_hi, J.w_lo}, dd::neg(e));
               const dd::df tau = dd::div(tot, den);
               reinterpret_cast<float2 *>(P.p[C.buf])[off] = make_float2(tau.hi, tau.lo);
