@@ -70,6 +70,19 @@ __device__ __forceinline__ void issue_products(uint32_t tmem, uint64_t dA, uint6
   }
 }
 
+// tau = (W_AB + W_C) / (w - eps) in double-float for one element.  Kept out
+// of line: inlined 24 times into the unrolled output loop it made the kernel
+// large enough for instruction-cache misses to stall the MMA-issuing warp.
+__device__ __noinline__ float2 tau_finish(dd::df x, float2 wv, dd::df e_row, float2 eb,
+                                          float w_hi, float w_lo) {
+  const dd::df tot = dd::add(x, dd::df{wv.x, wv.y});
+  const dd::df e = dd::add(e_row, dd::df{eb.x, eb.y});
+  const dd::df den = dd::add(dd::df{w_hi, w_lo}, dd::neg(e));
+  const dd::df tau = dd::div(tot, den);
+  return make_float2(tau.hi, tau.lo);
+}
+__device__ __noinline__ void fx_add_call(unsigned long long *slot, double v) { fx_add(slot, v); }
+
 // Position of one tile within its job: batch index, K-split part, M/N tile
 // and its K-step range [g0, g1) over the concatenated terms.
 struct TileInfo {
@@ -525,14 +538,10 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
             if (J.mode == SEPI_DD_STORE) {
               reinterpret_cast<float2 *>(P.p[C.buf])[off] = make_float2(x.hi, x.lo);
             } else if (tau_mode) {
-              const dd::df tot = dd::add(x, dd::df{wpre[k].x, wpre[k].y});
-              const float2 eb = ev[nc];
-              const dd::df e = dd::add(e_row, dd::df{eb.x, eb.y});
-              const dd::df den = dd::add(dd::df{J.w_hi, J.w_lo}, dd::neg(e));
-              const dd::df tau = dd::div(tot, den);
-              reinterpret_cast<float2 *>(P.p[C.buf])[off] = make_float2(tau.hi, tau.lo);
+              reinterpret_cast<float2 *>(P.p[C.buf])[off] =
+                  tau_finish(x, wpre[k], e_row, ev[nc], J.w_hi, J.w_lo);
             } else if (P.fx[C.buf]) {
-              fx_add(P.fx[C.buf] + 2 * off, dd::to_double(x));
+              fx_add_call(P.fx[C.buf] + 2 * off, dd::to_double(x));
             } else {
               atomicAdd(reinterpret_cast<double *>(P.p[C.buf]) + off, dd::to_double(x));
             }
