@@ -366,7 +366,10 @@ void add_sterm(SPlan &P, int job, SOpnd A, SOpnd B, int K, int negA, double &exe
   j.nterm++;
   executed += 2.0 * j.tiles_m * S_BM * (double)j.tiles_n * j.Ntile * K * j.batch *
               (slices * (slices + 1) / 2);
-  const double useful = 2.0 * j.M * (double)(j.n_valid + (j.N - j.Nm)) * K * j.batch;
+  const double mrows = j.m_pad > 0 ? (double)(j.M / j.m_pad) * j.m_valid +
+                                        std::min(j.M % j.m_pad, j.m_valid)
+                                  : (double)j.M;
+  const double useful = 2.0 * mrows * (double)(j.n_valid + (j.N - j.Nm)) * K * j.batch;
   P.flop += useful;
   P.slice_flop += useful * (slices * (slices + 1) / 2);
 }
@@ -379,66 +382,104 @@ struct WMaps {
 const WMaps kStdMaps = {MA_T2S, MB_T2S, MA_T2C, MB_T2C, MA_T2R, MB_T2R,
                         MA_XS,  MB_XS,  MA_YS,  MB_YS,  MA_OS,  MB_OS};
 
-// phase AB terms of triple (i,j,k): tile (a, b) at fixed c (batch index)
-void w_terms_ab(SPlan &P, int jb, const WMaps &m, int no, int nv, int vp, int op,
-                const int ijk[3], double &ex, int s) {
-  const int i = ijk[0], j = ijk[1], k = ijk[2];
-  add_sterm(P, jb, opd(m.aT2S, i * no + j), opd(m.bXS, k * nv, 1), vp, 0, ex, s);
-  add_sterm(P, jb, opd(m.aT2S, i * no + k), opd(m.bYS, j * nv, 1), vp, 0, ex, s);
-  add_sterm(P, jb, opd(m.aXS, k * nv, 1), opd(m.bT2S, j * no + i), vp, 0, ex, s);
-  add_sterm(P, jb, opd(m.aYS, i * nv, 1), opd(m.bT2S, j * no + k), vp, 0, ex, s);
-  add_sterm(P, jb, opd(m.aOS, k * no + i), opd(m.bT2C, j * nv, 1), op, 1, ex, s);
-  add_sterm(P, jb, opd(m.aOS, j * no + i), opd(m.bT2R, k * nv, 1), op, 1, ex, s);
-  add_sterm(P, jb, opd(m.aT2R, k * nv, 1), opd(m.bOS, i * no + j), op, 1, ex, s);
-  add_sterm(P, jb, opd(m.aT2C, i * nv, 1), opd(m.bOS, k * no + j), op, 1, ex, s);
-}
-// phase C terms: tile (c, b) at fixed a (batch index)
-void w_terms_c(SPlan &P, int jc, const WMaps &m, int no, int nv, int vp, int op,
-               const int ijk[3], double &ex, int s) {
-  const int i = ijk[0], j = ijk[1], k = ijk[2];
-  // (k,i,j): sum_d t_ki[c][d] (ad|bj) -> YS slab (j, a) rows b
-  add_sterm(P, jc, opd(m.aT2S, k * no + i), opd(m.bYS, j * nv, 1), vp, 0, ex, s);
-  // (k,j,i): sum_d t_kj[c][d] (bd|ai) -> XS slab (i, a) rows b
-  add_sterm(P, jc, opd(m.aT2S, k * no + j), opd(m.bXS, i * nv, 1), vp, 0, ex, s);
-  // (i,j,k) occupied: - sum_l (lj|ck) t^{ab}_{il} -> T2R slab (i, a) rows b
-  add_sterm(P, jc, opd(m.aOS, j * no + k), opd(m.bT2R, i * nv, 1), op, 1, ex, s);
-  // (j,i,k) occupied: - sum_l (li|ck) t^{ba}_{jl} -> T2C slab (j, a) rows b
-  add_sterm(P, jc, opd(m.aOS, i * no + k), opd(m.bT2C, j * nv, 1), op, 1, ex, s);
-}
-
-int w_job_ab(SPlan &pab, int nv, int Nab, int slot, int E, double &ex, int s) {
+// W build of triple (i,j,k) in three phases.  Every term has one operand
+// that carries a virtual index besides the tile's two (t2 / integral slabs
+// (x, 0..nv-1)); it is the A operand, its nv slabs read as one array of
+// nv * rows flattened rows (rows: the slab's row count, nv padded to 8), so
+// the tiles cover the nv^2 x nv block of W without M padding.
+//   phase 1: rows (c, a), columns b -> W_1[c][a][b]           (store)
+//   phase 2: rows (c, b), columns a -> W_2[c][a][b]           (store)
+//   phase 3: rows (a, b), columns c -> (W_1 + W_2 + W_3) / (w - eps) into W
+// W_1 and the tau result live in the W workspace, W_2 in the tau~ workspace
+// (free until tau~ is formed from tau).
+int w_job(SPlan &P, int nv, int rows, int Nt, int phase, int slot, int E, double &ex, int s) {
   const long long nv2 = (long long)nv * nv, nv3 = nv2 * nv;
-  int jb = new_sjob(pab, nv, nv, Nab, nv, 1, SEPI_DD_STORE, E, ex, s);
-  pab.jobs[jb].C = outd(B_WS_W, slot * nv3, nv, 1, nv2);
-  pab.jobs[jb].Ct = pab.jobs[jb].C;
-  pab.jobs[jb].nv = nv;
+  const int jb = new_sjob(P, nv * rows, nv, Nt, 1, 1, phase == 3 ? SEPI_DD_TAU : SEPI_DD_STORE,
+                          E, ex, s);
+  SJob &J = P.jobs[jb];
+  OutD C = outd(phase == 2 ? B_WS_TT : B_WS_W, slot * nv3, 0, 0);
+  C.m_in = rows;
+  if (phase == 1) {
+    C.sm1 = nv2, C.sm0 = nv, C.sn0 = 1;
+  } else if (phase == 2) {
+    C.sm1 = nv2, C.sm0 = 1, C.sn0 = nv;
+  } else {
+    C.sm1 = nv, C.sm0 = 1, C.sn0 = nv2;
+  }
+  J.C = C;
+  J.Ct = C;
+  J.m_pad = rows;
+  J.m_valid = nv;
+  J.nv = nv;
+  if (phase == 3) {
+    J.W = C;
+    J.wbuf2 = B_WS_TT;
+    J.erow_in = rows;
+  }
   return jb;
 }
-// the C job's epilogue forms W / (w - eps) in double-float
-int w_job_c(SPlan &pc, int nv, int Nab, int slot, int E, const float *eo_dd, double w,
-            double &ex, int s) {
-  const long long nv2 = (long long)nv * nv, nv3 = nv2 * nv;
-  int jc = new_sjob(pc, nv, nv, Nab, nv, 1, SEPI_DD_TAU, E, ex, s);
-  OutD C = outd(B_WS_W, slot * nv3, nv2, 1, nv);  // W[c][a][b]: m = c, n = b, batch a
-  pc.jobs[jc].C = C;
-  pc.jobs[jc].Ct = C;
-  pc.jobs[jc].W = C;
-  pc.jobs[jc].nv = nv;
-  pc.jobs[jc].eo_hi = eo_dd[0];
-  pc.jobs[jc].eo_lo = eo_dd[1];
+// the tau job's energies: e_ijk and the frequency w (0 for the residual)
+int w_job_tau(SPlan &P, int nv, int rows, int Nt, int slot, int E, const float *eo_dd,
+              double w, double &ex, int s) {
+  const int jc = w_job(P, nv, rows, Nt, 3, slot, E, ex, s);
+  SJob &J = P.jobs[jc];
+  J.eo_hi = eo_dd[0];
+  J.eo_lo = eo_dd[1];
   const dd::df wd = dd::from_double_host(w);
-  pc.jobs[jc].w_hi = wd.hi;
-  pc.jobs[jc].w_lo = wd.lo;
+  J.w_hi = wd.hi;
+  J.w_lo = wd.lo;
   return jc;
 }
+// A: slabs (x, 0..nv-1) of map `am` flattened; B: slab `bslab` of map `bm`
+void w_term(SPlan &P, int jb, int am, int x, int bm, int bslab, int K, int neg, int nv,
+            int rows, double &ex, int s) {
+  add_sterm(P, jb, opd(am, x * nv), opd(bm, bslab), K, neg, ex, s);
+  P.terms.back().aflat = nv * rows;
+}
+// phase 1, rows (c, a), columns b:
+//   sum_d (ad|ck) t^{bd}_{ji} [X_k],  sum_d (cd|ai) t^{bd}_{jk} [Y_i],
+//   -sum_l t^{ca}_{kl} (li|bj) [T2R_k],  -sum_l t^{ac}_{il} (lk|bj) [T2C_i]
+void w_terms_1(SPlan &P, int jb, const WMaps &m, int no, int nv, int rows, int vp, int op,
+               const int ijk[3], double &ex, int s) {
+  const int i = ijk[0], j = ijk[1], k = ijk[2];
+  w_term(P, jb, m.aXS, k, m.bT2S, j * no + i, vp, 0, nv, rows, ex, s);
+  w_term(P, jb, m.aYS, i, m.bT2S, j * no + k, vp, 0, nv, rows, ex, s);
+  w_term(P, jb, m.aT2R, k, m.bOS, i * no + j, op, 1, nv, rows, ex, s);
+  w_term(P, jb, m.aT2C, i, m.bOS, k * no + j, op, 1, nv, rows, ex, s);
+}
+// phase 2, rows (c, b), columns a: the terms whose t2 / oovo factor carries a
+void w_terms_2(SPlan &P, int jb, const WMaps &m, int no, int nv, int rows, int vp, int op,
+               const int ijk[3], double &ex, int s) {
+  const int i = ijk[0], j = ijk[1], k = ijk[2];
+  w_term(P, jb, m.aXS, k, m.bT2S, i * no + j, vp, 0, nv, rows, ex, s);
+  w_term(P, jb, m.aYS, j, m.bT2S, i * no + k, vp, 0, nv, rows, ex, s);
+  w_term(P, jb, m.aT2C, j, m.bOS, k * no + i, op, 1, nv, rows, ex, s);
+  w_term(P, jb, m.aT2R, k, m.bOS, j * no + i, op, 1, nv, rows, ex, s);
+}
+// phase 3, rows (a, b), columns c: the terms whose t2 / oovo factor carries c
+void w_terms_3(SPlan &P, int jc, const WMaps &m, int no, int nv, int rows, int vp, int op,
+               const int ijk[3], double &ex, int s) {
+  const int i = ijk[0], j = ijk[1], k = ijk[2];
+  // (k,i,j): sum_d t_ki[c][d] (ad|bj) -> YS slabs (j, a) rows b
+  w_term(P, jc, m.aYS, j, m.bT2S, k * no + i, vp, 0, nv, rows, ex, s);
+  // (k,j,i): sum_d t_kj[c][d] (bd|ai) -> XS slabs (i, a) rows b
+  w_term(P, jc, m.aXS, i, m.bT2S, k * no + j, vp, 0, nv, rows, ex, s);
+  // (i,j,k) occupied: - sum_l (lj|ck) t^{ab}_{il} -> T2R slabs (i, a) rows b
+  w_term(P, jc, m.aT2R, i, m.bOS, j * no + k, op, 1, nv, rows, ex, s);
+  // (j,i,k) occupied: - sum_l (li|ck) t^{ba}_{jl} -> T2C slabs (j, a) rows b
+  w_term(P, jc, m.aT2C, j, m.bOS, i * no + k, op, 1, nv, rows, ex, s);
+}
 
+// phases 1 and 2 (one launch, pab) and phase 3 (pc) of one triple
 void plan_w_split(SPlan &pab, SPlan &pc, SplitState *S, int no, int nv, const int ijk[3],
                   int slot, const float *eo_dd, double &ex) {
-  const int s = S->s, E = S->Et + S->Eg - 14;
-  const int jb = w_job_ab(pab, nv, S->Nab, slot, E, ex, s);
-  w_terms_ab(pab, jb, kStdMaps, no, nv, S->vp, S->op, ijk, ex, s);
-  const int jc = w_job_c(pc, nv, S->Nab, slot, E, eo_dd, 0.0, ex, s);
-  w_terms_c(pc, jc, kStdMaps, no, nv, S->vp, S->op, ijk, ex, s);
+  const int s = S->s, E = S->Et + S->Eg - 14, rows = (nv + 7) / 8 * 8;
+  const int j1 = w_job(pab, nv, rows, S->Nab, 1, slot, E, ex, s);
+  w_terms_1(pab, j1, kStdMaps, no, nv, rows, S->vp, S->op, ijk, ex, s);
+  const int j2 = w_job(pab, nv, rows, S->Nab, 2, slot, E, ex, s);
+  w_terms_2(pab, j2, kStdMaps, no, nv, rows, S->vp, S->op, ijk, ex, s);
+  const int jc = w_job_tau(pc, nv, rows, S->Nab, slot, E, eo_dd, 0.0, ex, s);
+  w_terms_3(pc, jc, kStdMaps, no, nv, rows, S->vp, S->op, ijk, ex, s);
 }
 
 // Appends the jobs of src to dst (one launch runs dst's jobs in order).
@@ -659,6 +700,7 @@ int build_plans(cc3_ctx *c, SplitState *S, cudaStream_t st) {
 void fill_vptrs(cc3_ctx *c, SplitState *S, VPtrTable *P) {
   std::memset(P, 0, sizeof(*P));
   P->p[B_WS_W] = S->Wdd;
+  P->p[B_WS_TT] = S->TTdd;  // W_2 of the W build until tau~ overwrites it
   P->p[B_EPSV] = S->evdd;
   P->p[B_OMT] = c->omt;
   P->p[B_OM1] = c->om1;
@@ -1206,6 +1248,7 @@ int split_jacobian(cc3_ctx *c, int nvec, const double *w, const double *R1d, con
   std::vector<double> eo(no);
   CU(cudaMemcpyAsync(eo.data(), c->eps_o, sizeof(double) * no, cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
+  const int rows = (nv + 7) / 8 * 8;
   const WMaps set1 = {MJ_R2S, MJ_R2S, MJ_R2C, MJ_R2C, MJ_R2R, MJ_R2R,
                       MA_XS,  MB_XS,  MA_YS,  MB_YS,  MA_OS,  MB_OS};
   const WMaps set2 = {MA_T2S, MB_T2S, MA_T2C, MB_T2C, MA_T2R, MB_T2R,
@@ -1226,13 +1269,16 @@ int split_jacobian(cc3_ctx *c, int nvec, const double *w, const double *R1d, con
       const double e = eo[ijk[0]] + eo[ijk[1]] + eo[ijk[2]];
       const dd::df ed = dd::from_double_host(e);
       const float eod[2] = {ed.hi, ed.lo};
-      const int jb = w_job_ab(ab, nv, S->Nab, t - t0, Ec - 14, ex, s);
-      w_terms_ab(ab, jb, set1, no, nv, vp, op, ijk, ex, s);
-      w_terms_ab(ab, jb, set2, no, nv, vp, op, ijk, ex, s);
+      const int j1 = w_job(ab, nv, rows, S->Nab, 1, t - t0, Ec - 14, ex, s);
+      w_terms_1(ab, j1, set1, no, nv, rows, vp, op, ijk, ex, s);
+      w_terms_1(ab, j1, set2, no, nv, rows, vp, op, ijk, ex, s);
+      const int j2 = w_job(ab, nv, rows, S->Nab, 2, t - t0, Ec - 14, ex, s);
+      w_terms_2(ab, j2, set1, no, nv, rows, vp, op, ijk, ex, s);
+      w_terms_2(ab, j2, set2, no, nv, rows, vp, op, ijk, ex, s);
       for (int v = 0; v < nvec; ++v) {
-        const int jc = w_job_c(cv[v], nv, S->Nab, t - t0, Ec - 14, eod, w[v], ex, s);
-        w_terms_c(cv[v], jc, set1, no, nv, vp, op, ijk, ex, s);
-        w_terms_c(cv[v], jc, set2, no, nv, vp, op, ijk, ex, s);
+        const int jc = w_job_tau(cv[v], nv, rows, S->Nab, t - t0, Ec - 14, eod, w[v], ex, s);
+        w_terms_3(cv[v], jc, set1, no, nv, rows, vp, op, ijk, ex, s);
+        w_terms_3(cv[v], jc, set2, no, nv, rows, vp, op, ijk, ex, s);
       }
       plan_jac_tau(&f, prep ? &z : nullptr, S, no, nv, nvec, EF, ijk, t - t0, ex);
     }

@@ -70,9 +70,10 @@ __device__ __forceinline__ void issue_products(uint32_t tmem, uint64_t dA, uint6
   }
 }
 
-// tau = (W_AB + W_C) / (w - eps) in double-float for one element.  Kept out
-// of line: inlined 24 times into the unrolled output loop it made the kernel
-// large enough for instruction-cache misses to stall the MMA-issuing warp.
+// tau = (W_12 + W_3) / (w - eps) in double-float for one element (the
+// partial sums of the earlier phases and this tile's).  Kept out of line:
+// inlined 24 times into the unrolled output loop it made the kernel large
+// enough for instruction-cache misses to stall the MMA-issuing warp.
 __device__ __noinline__ float2 tau_finish(dd::df x, float2 wv, dd::df e_row, float2 eb,
                                           float w_hi, float w_lo) {
   const dd::df tot = dd::add(x, dd::df{wv.x, wv.y});
@@ -125,6 +126,7 @@ __device__ __forceinline__ TileInfo decode_tile(const SJob *__restrict__ jobs, i
 // it to the MMA thread and the epilogue warps through a small ring in shared
 // memory; the epilogue releases the accumulators as soon as it has read them,
 // so the next tile's products start while it finishes the previous outputs.
+// 96 registers: the 18 warps sit 5 to a sub-partition of 16,384 registers.
 template <int S>
 __global__ void __maxnreg__(96)
 split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__restrict__ terms,
@@ -201,6 +203,11 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
         int kmax = 0;
         uint32_t abytes = 0, mbytes = 0, tbytes = 0, toff = 0, a2bytes = 0, a2off = 0,
                  t2bytes = 0, t2off = 0;
+        // flattened A rows: rows to load (0: not flattened), rows in the first
+        // slab, rows per slab, slab stride and row 0 of the first slab
+        int fra = 0, fseg = 0, frows = 0;
+        long long fstride = 0;
+        const __nv_bfloat16 *gaf = nullptr;
         bool bad = false;
         for (int g = ti.g0; g < ti.g1; ++g) {
           if (g >= kend) {
@@ -226,16 +233,31 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
             kmax = XA.kblocks;
             if (nmain > 0) kmax = min(kmax, XB.kblocks);
             if (ntail > 0) kmax = min(kmax, XT.kblocks);
-            if (as < 0 || as >= XA.slabs || ar < 0 || ar >= XA.rows ||
-                (nmain > 0 && (bs < 0 || bs >= XB.slabs || br < 0)) ||
+            // A rows: [ar, ar + ra) of slab as, or flattened over slabs as, as + 1, ...
+            int ra = 0, fs = as, fr = ar;
+            bool abad = as < 0 || ar < 0;
+            if (!abad && T.aflat > 0) {
+              ra = min(S_BM, T.aflat - ar);
+              fs = as + ar / XA.rows;
+              fr = ar % XA.rows;
+              abad = ra <= 0 || as + (ar + ra - 1) / XA.rows >= XA.slabs || T.asplit > 0;
+            } else if (!abad) {
+              abad = as >= XA.slabs || ar >= XA.rows;
+              ra = min(S_BM, XA.rows - ar);
+              if (T.asplit > 0) ra = min(ra, T.asplit);
+            }
+            if (abad || (nmain > 0 && (bs < 0 || bs >= XB.slabs || br < 0)) ||
                 (ntail > 0 && (ts < 0 || ts >= XT.slabs || tr < 0 || ((tfirst - n0) & 7) != 0))) {
               err = 2;  // a plan addressed outside its slice array: stop, report
               bad = true;
               break;
             }
-            int ra = min(S_BM, XA.rows - ar);
-            if (T.asplit > 0) ra = min(ra, T.asplit);
             abytes = (uint32_t)ra * 32u;
+            fra = T.aflat > 0 ? ra : 0;
+            fseg = min(ra, XA.rows - fr);
+            frows = XA.rows;
+            fstride = XA.slab_stride;
+            gaf = reinterpret_cast<const __nv_bfloat16 *>(XA.base) + (long long)fs * XA.slab_stride;
             mbytes = (uint32_t)nmain * 32u;
             tbytes = (uint32_t)ntail * 32u;
             toff = (uint32_t)(tfirst - n0) * 32u * s;
@@ -277,8 +299,7 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
               }
             }
             // one bulk copy per operand tile: its s slices are contiguous
-            ga0 = reinterpret_cast<const __nv_bfloat16 *>(XA.base) + (long long)as * XA.slab_stride +
-                  (long long)ar * 16 * s;
+            ga0 = gaf + (long long)fr * 16 * s;
             gb0 = reinterpret_cast<const __nv_bfloat16 *>(XB.base) + (long long)bs * XB.slab_stride +
                   (long long)br * 16 * s;
             gt0 = reinterpret_cast<const __nv_bfloat16 *>(XT.base) + (long long)ts * XT.slab_stride +
@@ -300,7 +321,20 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
           // stage layout: s A slices (128 rows) then s B slices (S_NT_MAX rows)
           uint8_t *sa = smem + (size_t)st * ((size_t)s * (a_bytes + S_NT_MAX * 32));
           uint8_t *sb = sa + (size_t)s * a_bytes;
-          bulk_load(sa, ga0 + (long long)kb * kbsA, (uint32_t)s * abytes, &full[st]);
+          if (fra > 0) {  // one copy per slab the tile's rows touch
+            const __nv_bfloat16 *src = ga0 + (long long)kb * kbsA, *sp = gaf + (long long)kb * kbsA;
+            int r = 0, cnt = fseg;
+            for (;;) {
+              bulk_load(sa + (uint32_t)r * 32u * s, src, (uint32_t)cnt * 32u * s, &full[st]);
+              r += cnt;
+              if (r >= fra) break;
+              sp += fstride;
+              src = sp;
+              cnt = min(fra - r, frows);
+            }
+          } else {
+            bulk_load(sa, ga0 + (long long)kb * kbsA, (uint32_t)s * abytes, &full[st]);
+          }
           if (a2bytes)
             bulk_load(sa + a2off, ga20 + (long long)kb * kbsA2, (uint32_t)s * a2bytes, &full[st]);
           if (mbytes) bulk_load(sb, gb0 + (long long)kb * kbsB, (uint32_t)s * mbytes, &full[st]);
@@ -481,12 +515,15 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
       const float sc = ldexpf(J.mult, J.expo + (es >= 0 ? slot_ex[es] : 0));
       const int mo = seg2 ? m - J.msplit : m;  // row within its output
       const bool tau_mode = J.mode == SEPI_DD_TAU;
+      const bool row_ok = m < J.M && !(J.m_pad > 0 && (m % J.m_pad) >= J.m_valid);
       // tau mode: the row's orbital-energy terms once per tile
       const float2 *ev = reinterpret_cast<const float2 *>(P.p[B_EPSV]);
       dd::df e_row = {0.f, 0.f};
-      if (tau_mode && m < J.M) {
-        // tile (c = m, b = n) at fixed a = batch index: eps = e_a + e_b + e_c - e_ijk
-        const float2 ea = ev[bi], ec = ev[m];
+      if (tau_mode && row_ok) {
+        // eps = e_a + e_b + e_c - e_ijk; the row is (a, b) with the column c,
+        // or c at a fixed a = batch index with the column b
+        const float2 ea = J.erow_in > 0 ? ev[m / J.erow_in] : ev[bi];
+        const float2 ec = J.erow_in > 0 ? ev[m % J.erow_in] : ev[m];
         e_row = dd::add(dd::add(dd::df{ea.x, ea.y}, dd::df{ec.x, ec.y}),
                         dd::df{-J.eo_hi, -J.eo_lo});
       }
@@ -501,12 +538,17 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
             for (int k = 0; k < 4; ++k) {
               const int n = n0 + part * qc + c * 4 + k;
               wpre[k] = make_float2(0.f, 0.f);
-              if (m < J.M && n < J.N && n < J.n_valid) {
+              if (row_ok && n < J.N && n < J.n_valid) {
                 const OutD &W = J.W;
                 const long long woff = W.off + (long long)bi * W.sb +
                                        s_rowoff(m, W.m_in, W.sm1, W.sm0) +
                                        s_rowoff(n, W.n_in, W.sn1, W.sn0);
                 wpre[k] = reinterpret_cast<const float2 *>(P.p[W.buf])[woff];
+                if (J.wbuf2 > 0) {  // the other partial sum, folded in at once
+                  const float2 w2 = reinterpret_cast<const float2 *>(P.p[J.wbuf2])[woff];
+                  const dd::df ws = dd::add(dd::df{wpre[k].x, wpre[k].y}, dd::df{w2.x, w2.y});
+                  wpre[k] = make_float2(ws.hi, ws.lo);
+                }
               }
             }
           }
@@ -514,8 +556,7 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
           for (int k = 0; k < 4; ++k) {
             const dd::df x = dd::scale(acc[c][k], sc);
             const int n = n0 + part * qc + c * 4 + k;
-            if (m >= J.M || n >= J.N || (J.m_pad > 0 && (m % J.m_pad) >= J.m_valid) ||
-                (n < J.Nm && n >= J.n_valid))
+            if (!row_ok || n >= J.N || (n < J.Nm && n >= J.n_valid))
               continue;
             const OutD *Cp;
             int nc;

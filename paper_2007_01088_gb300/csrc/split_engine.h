@@ -54,6 +54,11 @@ struct STerm {
   // n >= nbm2 come from Bt2 (row n - nbm2); nbm2 = 0: none.  Both multiples of 8.
   SOpnd A2, Bt2;
   int asplit, nbm2;
+  // aflat > 0: the A rows are flattened over consecutive slabs: tile row r
+  // is row (f % rows) of slab A.slab0 + f / rows, f = A.row0 + b*A.row_b +
+  // m0 + r, for f < aflat (the rows that exist); rows is the array's padded
+  // row count.  Loaded as one bulk copy per slab the tile touches.
+  int aflat;
 };
 
 enum SEpi { SEPI_DD_STORE = 0, SEPI_DD_TAU = 1, SEPI_F64_ATOMIC = 2 };
@@ -79,6 +84,11 @@ struct SJob {
   OutD C2, Ct2;
   float eo_hi, eo_lo, w_hi, w_lo;
   int nv;
+  // tau mode: erow_in > 0: row m stands for (a, b) = (m / erow_in,
+  // m % erow_in) and column n for c; 0: the batch index is a, row m is c and
+  // column n is b.  wbuf2 > 0: a second partial sum of W at W's offsets in
+  // buffer wbuf2 (0: none; buffer 0 never holds one).
+  int erow_in, wbuf2;
   long long tile_base;
 };
 
