@@ -129,37 +129,120 @@ __global__ void maxabs_kernel(const double *__restrict__ x, long long n,
 
 // tau~ = 4 tau^{abc} - 2 tau^{acb} - 2 tau^{cba} - 2 tau^{bac} + tau^{bca} + tau^{cab}
 // from tau stored as T[slot][c][a][b] (dd); writes TT[slot][a][b][c] (dd) and
-// the max |tau~| of each slot (float bits, atomic max).  Element (a,b,c) per
-// thread, c fastest: two of the six permuted reads are coalesced, the other
-// four hit L2 (one slot of tau, nv^3 dd values, stays L2-resident).  A
-// shared-memory cube transpose was measured slower (latency- and
-// barrier-bound).
-__global__ void contravariant_dd_kernel(const float2 *__restrict__ tau, float2 *__restrict__ tt,
-                                        int nv, unsigned int *__restrict__ maxbits) {
+// the max |tau~| of each slot (float bits, atomic max).
+//
+// The six values tau^{pi(a,b,c)} over the permutations pi are the same set
+// for every permutation of (a,b,c), and tau~ at each of the six points is a
+// combination of that set: with E = tau^{abc} + tau^{bca} + tau^{cab} and
+// O = tau^{acb} + tau^{cba} + tau^{bac},
+//   tau~ at an even permutation (abc, bca, cab) = 3 tau^{itself} + E - 2 O,
+//   tau~ at an odd one (acb, cba, bac)           = 3 tau^{itself} + O - 2 E.
+// A block takes one triple of 8-cube indices A >= B >= C, stages the (up to
+// six distinct) tau cubes whose index triples permute it in shared memory
+// with coalesced row reads, forms all six outputs of each of its points from
+// the six staged values, and writes the output cubes back row by row: every
+// tau element is read once and every tau~ element written once.  When cube
+// indices coincide, only points with a >= b (A = B) and b >= c (B = C) are
+// formed, so that each output is produced by one thread.
+constexpr int CV_SX = 8, CV_SZ = 65, CV_SLOT = 8 * CV_SZ;  // padded cube strides (float2)
+__global__ void __launch_bounds__(256)
+contravariant_dd_kernel(const float2 *__restrict__ tau, float2 *__restrict__ tt, int nv,
+                        unsigned int *__restrict__ maxbits) {
+  __shared__ float2 sm[6][CV_SLOT];
   const long long nv2 = (long long)nv * nv, nv3 = nv2 * nv;
   const float2 *T = tau + blockIdx.y * nv3;
   float2 *O = tt + blockIdx.y * nv3;
+  // block -> (A, B, C), A >= B >= C, in lexicographic order
+  int r = blockIdx.x, A = 0;
+  while (r >= (A + 1) * (A + 2) / 2) {
+    r -= (A + 1) * (A + 2) / 2;
+    ++A;
+  }
+  int B = 0;
+  while (r >= B + 1) {
+    r -= B + 1;
+    ++B;
+  }
+  const int C = r;
+  // cube of term q, order abc, acb, cba, bac, bca, cab (cube indices of the
+  // tau superscripts); the same triple indexes the output cube of point q
+  const int cx[6] = {A, A, C, B, B, C}, cy[6] = {B, C, B, A, C, A}, cz[6] = {C, B, A, C, A, B};
+  int slot[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    slot[q] = q;
+#pragma unroll
+    for (int u = 0; u < q; ++u)
+      if (slot[q] == q && cx[u] == cx[q] && cy[u] == cy[q] && cz[u] == cz[q]) slot[q] = u;
+  }
+  const int t = threadIdx.x;
+  // stage tau^{xyz} of cube (X, Y, Z) at [z][x][y] (y contiguous in memory)
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    if (slot[q] != q) continue;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int e = t + 256 * h, y = e & 7, x = (e >> 3) & 7, z = e >> 6;
+      const int gx = cx[q] * 8 + x, gy = cy[q] * 8 + y, gz = cz[q] * 8 + z;
+      float2 v = make_float2(0.f, 0.f);
+      if (gx < nv && gy < nv && gz < nv) v = T[(long long)gz * nv2 + (long long)gx * nv + gy];
+      sm[q][z * CV_SZ + x * CV_SX + y] = v;
+    }
+  }
+  __syncthreads();
+  dd::df v[2][6];
+  bool own[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int p = t + 256 * h, a = p >> 6, b = (p >> 3) & 7, c = p & 7;
+    const int ga = A * 8 + a, gb = B * 8 + b, gc = C * 8 + c;
+    own[h] = ga < nv && gb < nv && gc < nv && !(A == B && ga < gb) && !(B == C && gb < gc);
+    // term q's element sits at its cube's [z][x][y] with (x, y, z) the
+    // permuted (a, b, c)
+    const int off[6] = {c * CV_SZ + a * CV_SX + b, b * CV_SZ + a * CV_SX + c,
+                        a * CV_SZ + c * CV_SX + b, c * CV_SZ + b * CV_SX + a,
+                        a * CV_SZ + b * CV_SX + c, b * CV_SZ + c * CV_SX + a};
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const float2 w = sm[slot[q]][off[q]];
+      v[h][q] = dd::df{w.x, w.y};
+    }
+  }
+  __syncthreads();  // every staged value read: the cubes now take the outputs
   float mx = 0.f;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nv3;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(e % nv);
-    const int b = (int)((e / nv) % nv);
-    const int a = (int)(e / nv2);
-#define TAU(x, y, z) T[(long long)(z) * nv2 + (long long)(x) * nv + (y)]
-    const float2 t0 = TAU(a, b, c), t1 = TAU(a, c, b), t2 = TAU(c, b, a);
-    const float2 t3 = TAU(b, a, c), t4 = TAU(b, c, a), t5 = TAU(c, a, b);
-#undef TAU
-    dd::df r = dd::scale(dd::df{t0.x, t0.y}, 4.f);
-    r = dd::add(r, dd::scale(dd::df{t1.x, t1.y}, -2.f));
-    r = dd::add(r, dd::scale(dd::df{t2.x, t2.y}, -2.f));
-    r = dd::add(r, dd::scale(dd::df{t3.x, t3.y}, -2.f));
-    r = dd::add(r, dd::df{t4.x, t4.y});
-    r = dd::add(r, dd::df{t5.x, t5.y});
-    O[e] = make_float2(r.hi, r.lo);
-    mx = fmaxf(mx, fabsf(r.hi));
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    if (!own[h]) continue;
+    const int p = t + 256 * h, a = p >> 6, b = (p >> 3) & 7, c = p & 7;
+    const dd::df E = dd::add(dd::add(v[h][0], v[h][4]), v[h][5]);
+    const dd::df Od = dd::add(dd::add(v[h][1], v[h][2]), v[h][3]);
+    const dd::df ke = dd::add(E, dd::scale(Od, -2.f)), ko = dd::add(Od, dd::scale(E, -2.f));
+    // output point of term q in its cube, stored [i][j][k] (k contiguous)
+    const int off[6] = {a * CV_SZ + b * CV_SX + c, a * CV_SZ + c * CV_SX + b,
+                        c * CV_SZ + b * CV_SX + a, b * CV_SZ + a * CV_SX + c,
+                        b * CV_SZ + c * CV_SX + a, c * CV_SZ + a * CV_SX + b};
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const bool even = q == 0 || q == 4 || q == 5;
+      const dd::df o = dd::add(dd::mul_f(v[h][q], 3.f), even ? ke : ko);
+      sm[slot[q]][off[q]] = make_float2(o.hi, o.lo);
+      mx = fmaxf(mx, fabsf(o.hi));
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    if (slot[q] != q) continue;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int e = t + 256 * h, k = e & 7, j = (e >> 3) & 7, i = e >> 6;
+      const int gi = cx[q] * 8 + i, gj = cy[q] * 8 + j, gk = cz[q] * 8 + k;
+      if (gi < nv && gj < nv && gk < nv)
+        O[(long long)gi * nv2 + (long long)gj * nv + gk] = sm[q][i * CV_SZ + j * CV_SX + k];
+    }
   }
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(maxbits + blockIdx.y, __float_as_uint(mx));
+  if ((t & 31) == 0) atomicMax(maxbits + blockIdx.y, __float_as_uint(mx));
 }
 
 // exponent e with max < 2^e (max slightly enlarged to cover the dd low part)
@@ -284,10 +367,10 @@ int launch_maxabs(const double *x, long long n, unsigned long long *out, cudaStr
 }
 int launch_contravariant_dd(const float2 *tau, float2 *tt, int nv, int nslot,
                             unsigned int *maxbits, cudaStream_t st) {
-  const long long nv3 = (long long)nv * nv * nv;
-  int bx = (int)((nv3 + 255) / 256);
-  if (bx > 2048) bx = 2048;
-  contravariant_dd_kernel<<<dim3(bx, nslot), 256, 0, st>>>(tau, tt, nv, maxbits);
+  const long long nx = (nv + 7) / 8, ncube = nx * (nx + 1) * (nx + 2) / 6;  // A >= B >= C
+  if (ncube > 0x7fffffffLL || nslot > 65535)
+    return CC3_FAIL(CC3_ERR_ARG, "contravariant_dd grid");
+  contravariant_dd_kernel<<<dim3((unsigned)ncube, nslot), 256, 0, st>>>(tau, tt, nv, maxbits);
   return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_FAIL(CC3_ERR_CUDA, "split element-wise kernel launch");
 }
 int launch_slot_exponent(const unsigned int *maxbits, int *ex, int nslot, cudaStream_t st) {
