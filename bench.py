@@ -573,6 +573,11 @@ def main():
     roof["kernels"] = {k: {"ms_per_step": v["ms"] / args.steps,
                            "launches_per_step": v["launches"] / args.steps}
                        for k, v in kern.items() if v["launches"]}
+    # the same time by step of the path (W build, contractions, element-wise)
+    roof["phases"] = {k: {"ms_per_step": v["ms"] / args.steps,
+                          "slice_tflops": (v["slice_flop"] / (v["ms"] * 1e-3) / 1e12
+                                           if v["ms"] > 0 and v["slice_flop"] else None)}
+                      for k, v in traces.items() if v["launches"]}
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

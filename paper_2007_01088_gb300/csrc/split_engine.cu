@@ -147,8 +147,17 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
   __shared__ __align__(8) uint64_t accfull, accempty, drainfull, drainempty;
   __shared__ __align__(8) uint64_t tfull[TQ], tempty[TQ];
   __shared__ long long tq[TQ];
+  // the producer decodes each tile once for everyone (tinfo, with tq) and
+  // marks each stage with the sign of its term, so that the MMA thread and
+  // the epilogue read no job or term tables
+  __shared__ TileInfo tinfo[TQ];
+  __shared__ int sneg[S_STAGES];
   __shared__ uint32_t tmem_base_sh;
   __shared__ volatile int err;
+  // each epilogue warp's copy of its current tile's job: the output loop reads
+  // its fields for every element, and global reads of them (L1 is small next
+  // to 216 KB of shared memory) put an L2 round trip on each element's path
+  __shared__ SJob ejob[S_EPI_WARPS];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -182,10 +191,14 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
         const int q = i % TQ;
         if (!mbar_wait(&tempty[q], ((i / TQ) & 1) ^ 1, &err)) break;
         const long long tile = (long long)atomicAdd(tile_ctr, 1ull);
+        TileInfo ti;
+        if (tile < ntiles) {
+          ti = decode_tile(jobs, njobs, terms, tile, jh);
+          tinfo[q] = ti;
+        }
         tq[q] = tile < ntiles ? tile : -1;
         mbar_arrive(&tfull[q]);
         if (tile >= ntiles) break;
-        const TileInfo ti = decode_tile(jobs, njobs, terms, tile, jh);
         const int Nt = ti.Nt, bi = ti.bi, m0 = ti.m0, n0 = ti.n0;
         const int term0 = jobs[ti.j].term0, nterm = jobs[ti.j].nterm;
         // term cursor; per-term operand addresses live in registers (the
@@ -196,7 +209,7 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
           kbase += terms[term0 + t].ksteps;
           ++t;
         }
-        int kend = -1;
+        int kend = -1, neg = 0;
         const __nv_bfloat16 *ga0 = nullptr, *gb0 = nullptr, *gt0 = nullptr, *ga20 = nullptr,
                             *gt20 = nullptr;
         long long kbsA = 0, kbsB = 0, kbsT = 0, kbsA2 = 0, kbsT2 = 0;
@@ -216,6 +229,7 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
               ++t;
             }
             const STerm T = terms[term0 + t];
+            neg = T.negA;
             kend = kbase + T.ksteps;
             const SArr XA = arrs.a[T.A.map], XB = arrs.a[T.B.map], XT = arrs.a[T.Bt.map];
             const int ar = T.A.row0 + bi * T.A.row_b + m0, as = T.A.slab0 + bi * T.A.slab_b;
@@ -316,6 +330,7 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
           }
           const int st = issued % S_STAGES, ph = (issued / S_STAGES) & 1;
           if (!mbar_wait(&empty[st], ph ^ 1, &err)) { bad = true; break; }
+          sneg[st] = neg;
           mbar_arrive_expect_tx(&full[st],
                                 (uint32_t)s * (abytes + a2bytes + mbytes + tbytes + t2bytes));
           // stage layout: s A slices (128 rows) then s B slices (S_NT_MAX rows)
@@ -353,47 +368,30 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
   } else if (warp == 1) {
     if (lane == 0) {
       // MMA issuer
-      int it = 0, nd = 0, jh = 0;
+      int it = 0, nd = 0;
       bool ok = true;
       for (int i = 0; ok; ++i) {
         const int q = i % TQ;
         if (!mbar_wait(&tfull[q], (i / TQ) & 1, &err)) break;
         const long long tile = tq[q];
+        const TileInfo ti = tinfo[q];  // read before the slot is handed back
         mbar_arrive(&tempty[q]);
         if (tile < 0) break;
-        const TileInfo ti = decode_tile(jobs, njobs, terms, tile, jh);
         const int Nt = ti.Nt;
-        const int term0 = jobs[ti.j].term0, nterm = jobs[ti.j].nterm;
         const uint32_t id_pos = idesc_bf16(S_BM, Nt, 0), id_neg = idesc_bf16(S_BM, Nt, 1);
         // the epilogue has read the previous tile's accumulators
         if (i > 0) {
           if (!mbar_wait(&accempty, (i - 1) & 1, &err)) break;
           tc_fence_after();
         }
-        int t = 0, kbase = 0;
-        while (t < nterm && kbase + terms[term0 + t].ksteps <= ti.g0) {
-          kbase += terms[term0 + t].ksteps;
-          ++t;
-        }
-        int kend = 0;
-        uint32_t idesc = id_pos;
-        if (ti.g0 < ti.g1) {  // then t < nterm
-          kend = kbase + terms[term0 + t].ksteps;
-          idesc = terms[term0 + t].negA ? id_neg : id_pos;
-        }
         uint32_t fresh = (1u << S_NACC) - 1;
         int since = 0;
         bool pending = false;
         for (int g = ti.g0; g < ti.g1; ++g, ++it) {
-          if (g >= kend) {
-            ++t;
-            const STerm T = terms[term0 + t];
-            kend += T.ksteps;
-            idesc = T.negA ? id_neg : id_pos;
-          }
           const int st = it % S_STAGES, ph = (it / S_STAGES) & 1;
           if (!mbar_wait(&full[st], ph, &err)) { ok = false; break; }
           tc_fence_after();
+          const uint32_t idesc = sneg[st] ? id_neg : id_pos;
           const uint32_t sa = smem_u32(smem + (size_t)st * ((size_t)s * (a_bytes + S_NT_MAX * 32)));
           // slice p of a tile starts 256 p bytes in; row groups are 256 s bytes apart
           const uint64_t dA = smem_desc_kmajor(sa, 256u * s),
@@ -431,10 +429,18 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[q]);
       if (tile < 0) break;
+      // decoded again from the (read-only) tables: the compiler may reload
+      // these values instead of holding them in registers across the asm
       const TileInfo ti = decode_tile(jobs, njobs, terms, tile, jh);
-      const SJob &J = jobs[ti.j];
-      const int Nt = ti.Nt, bi = ti.bi, n0 = ti.n0;
-      const int m = ti.m0 + row;
+      __syncwarp();  // every lane is done with the previous tile's job
+      {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(jobs + ti.j);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&ejob[ew]);
+        for (int w = lane; w < (int)(sizeof(SJob) / 4); w += 32) dst[w] = src[w];
+      }
+      __syncwarp();
+      const SJob &J = ejob[ew];
+      const int Nt = ti.Nt;
       const int nsteps = ti.g1 - ti.g0;
       const int ndrains = nsteps > 0 ? (nsteps - 1) / kdrain_steps : 0;
       const int qc = Nt >> 2;   // columns per quarter (multiple of 4, <= 24)
@@ -508,6 +514,7 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&accempty);
+      const int bi = ti.bi, n0 = ti.n0, m = ti.m0 + row;
       const int *slot_ex = reinterpret_cast<const int *>(P.p[B_SLOTEXP]);
       const bool seg2 = J.msplit > 0 && m >= J.msplit;  // second row segment
       // the per-triple exponent table is read only by jobs that name a slot
@@ -516,6 +523,13 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
       const int mo = seg2 ? m - J.msplit : m;  // row within its output
       const bool tau_mode = J.mode == SEPI_DD_TAU;
       const bool row_ok = m < J.M && !(J.m_pad > 0 && (m % J.m_pad) >= J.m_valid);
+      // the thread's row is fixed for the tile: its output row offsets once.
+      // Main columns n < Nm go to C (C2 for second-segment rows), tail
+      // columns n in [tlo, thi) to Ct (Ct2); columns map linearly (n_in >= N,
+      // checked when the plan is uploaded)
+      const OutD &Cm = seg2 ? J.C2 : J.C;
+      const long long rowM =
+          row_ok ? Cm.off + (long long)bi * Cm.sb + s_rowoff(mo, Cm.m_in, Cm.sm1, Cm.sm0) : 0;
       // tau mode: the row's orbital-energy terms once per tile
       const float2 *ev = reinterpret_cast<const float2 *>(P.p[B_EPSV]);
       dd::df e_row = {0.f, 0.f};
@@ -530,7 +544,7 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
         if (c < nch) {
-          // tau mode reads the other phase's partial sums of the four columns
+          // tau mode reads the other phases' partial sums of the four columns
           // before any of them is overwritten, so the loads overlap
           float2 wpre[4];
           if (tau_mode) {
@@ -539,11 +553,8 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
               const int n = n0 + part * qc + c * 4 + k;
               wpre[k] = make_float2(0.f, 0.f);
               if (row_ok && n < J.N && n < J.n_valid) {
-                const OutD &W = J.W;
-                const long long woff = W.off + (long long)bi * W.sb +
-                                       s_rowoff(m, W.m_in, W.sm1, W.sm0) +
-                                       s_rowoff(n, W.n_in, W.sn1, W.sn0);
-                wpre[k] = reinterpret_cast<const float2 *>(P.p[W.buf])[woff];
+                const long long woff = rowM + (long long)n * Cm.sn0;  // W at C's offsets
+                wpre[k] = reinterpret_cast<const float2 *>(P.p[J.W.buf])[woff];
                 if (J.wbuf2 > 0) {  // the other partial sum, folded in at once
                   const float2 w2 = reinterpret_cast<const float2 *>(P.p[J.wbuf2])[woff];
                   const dd::df ws = dd::add(dd::df{wpre[k].x, wpre[k].y}, dd::df{w2.x, w2.y});
@@ -556,35 +567,33 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
           for (int k = 0; k < 4; ++k) {
             const dd::df x = dd::scale(acc[c][k], sc);
             const int n = n0 + part * qc + c * 4 + k;
-            if (!row_ok || n >= J.N || (n < J.Nm && n >= J.n_valid))
-              continue;
-            const OutD *Cp;
-            int nc;
+            if (!row_ok || n >= J.N) continue;
+            long long off;
+            int buf, nc;
             if (n < J.Nm) {
-              Cp = seg2 ? &J.C2 : &J.C;
+              if (n >= J.n_valid) continue;
+              off = rowM + (long long)n * Cm.sn0;
+              buf = Cm.buf;
               nc = n;
-            } else if (J.Nm2 > 0 && n >= J.Nm2) {
-              if (!seg2) continue;  // the second tail belongs to the second rows
-              Cp = &J.Ct2;
-              nc = n - J.Nm2;
-            } else {
-              if (seg2) continue;
-              Cp = &J.Ct;
-              nc = n - J.Nm;
+            } else {  // tail columns are few: their offsets on the fly
+              const OutD &Ctl = seg2 ? J.Ct2 : J.Ct;
+              const int tlo = seg2 ? (J.Nm2 > 0 ? J.Nm2 : J.N) : J.Nm;
+              const int thi = seg2 ? J.N : (J.Nm2 > 0 ? J.Nm2 : J.N);
+              if (n < tlo || n >= thi) continue;
+              nc = n - tlo;
+              off = Ctl.off + (long long)bi * Ctl.sb + s_rowoff(mo, Ctl.m_in, Ctl.sm1, Ctl.sm0) +
+                    (long long)nc * Ctl.sn0;
+              buf = Ctl.buf;
             }
-            const OutD &C = *Cp;
-            const long long off = C.off + (long long)bi * C.sb +
-                                  s_rowoff(mo, C.m_in, C.sm1, C.sm0) +
-                                  s_rowoff(nc, C.n_in, C.sn1, C.sn0);
             if (J.mode == SEPI_DD_STORE) {
-              reinterpret_cast<float2 *>(P.p[C.buf])[off] = make_float2(x.hi, x.lo);
+              reinterpret_cast<float2 *>(P.p[buf])[off] = make_float2(x.hi, x.lo);
             } else if (tau_mode) {
-              reinterpret_cast<float2 *>(P.p[C.buf])[off] =
+              reinterpret_cast<float2 *>(P.p[buf])[off] =
                   tau_finish(x, wpre[k], e_row, ev[nc], J.w_hi, J.w_lo);
-            } else if (P.fx[C.buf]) {
-              fx_add_call(P.fx[C.buf] + 2 * off, dd::to_double(x));
+            } else if (P.fx[buf]) {
+              fx_add_call(P.fx[buf] + 2 * off, dd::to_double(x));
             } else {
-              atomicAdd(reinterpret_cast<double *>(P.p[C.buf]) + off, dd::to_double(x));
+              atomicAdd(reinterpret_cast<double *>(P.p[buf]) + off, dd::to_double(x));
             }
           }
         }
@@ -601,6 +610,19 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
 
 int s_upload_plan(const SPlan &p, SDevPlan *d, cudaStream_t s) {
   s_free_plan(d);
+  // the epilogue maps output columns linearly (n * sn0): no output may split
+  // its columns (n_in >= N)
+  for (const SJob &j : p.jobs) {
+    const bool two = j.msplit > 0;
+    const OutD *outs[4] = {&j.C, &j.Ct, two ? &j.C2 : nullptr, two ? &j.Ct2 : nullptr};
+    for (const OutD *o : outs)
+      if (o && o->n_in < j.N) return CC3_ERR_ARG;
+    // tau mode reads the partial sums of W at C's element offsets (buffer W.buf)
+    if (j.mode == SEPI_DD_TAU &&
+        (j.W.off != j.C.off || j.W.sb != j.C.sb || j.W.m_in != j.C.m_in || j.W.sm1 != j.C.sm1 ||
+         j.W.sm0 != j.C.sm0 || j.W.sn0 != j.C.sn0 || two || j.Nm != j.N))
+      return CC3_ERR_ARG;
+  }
   if (cudaMalloc(&d->counter, sizeof(unsigned long long)) != cudaSuccess) return CC3_ERR_OOM;
   d->njobs = (int)p.jobs.size();
   d->tiles = p.tiles;
