@@ -51,16 +51,27 @@ __device__ __forceinline__ df mul(df a, df b) {
   e = __fmaf_rn(a.lo, b.hi, e);
   return fast_two_sum(p, e);
 }
-// a / b with one Newton correction on the quotient (~2^-44 relative)
+// a / b by long division on the quotient: three partial quotients, each
+// from the remainder of the previous ones (formed in dd arithmetic) times an
+// approximate reciprocal of b.hi.  Each step shrinks the remainder by the
+// reciprocal's relative error (~2^-22 for the hardware approximation), so
+// the quotient is accurate to the dd arithmetic (~2^-46 relative); the
+// reciprocal's last bits do not matter.  |b.hi| must be a normal number.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ df div(df a, df b) {
-  float q1 = __fdiv_rn(a.hi, b.hi);
+  const float rb = rcp_approx(b.hi);
+  const float q1 = a.hi * rb;
   df p = mul_f(b, q1);
   df r = add(a, df{-p.hi, -p.lo});
-  float q2 = __fdiv_rn(r.hi, b.hi);
-  df p2 = mul_f(b, q2);
-  r = add(r, df{-p2.hi, -p2.lo});
-  float q3 = __fdiv_rn(r.hi, b.hi);
-  df q = fast_two_sum(q1, q2);
+  const float q2 = r.hi * rb;
+  p = mul_f(b, q2);
+  r = add(r, df{-p.hi, -p.lo});
+  const float q3 = r.hi * rb;
+  const df q = fast_two_sum(q1, q2);
   return add_f(q, q3);
 }
 __device__ __forceinline__ df scale(df a, float s) {  // s a power of two
