@@ -65,7 +65,7 @@ enum BufId {
   B_WS_W, B_WS_TT, B_OMT, B_OM1,
   B_R2, B_HVVVO, B_HOOVO, B_HF, B_ZV, B_ZO, B_VVOO, B_OOOO,
   B_RHOT, B_RHO1, B_TT_TAU, B_SCRATCH, B_SLOTEXP,
-  B_WS_WR, B_WS_TTR, B_MJ, B_CHOL, B_R1,
+  B_WS_WR, B_WS_TTR, B_MJ, B_CHOL, B_R1, B_WS_W3,
   B_COUNT
 };
 

@@ -110,14 +110,16 @@ struct SplitState {
   int g_calls = 0;
   float2 *evdd = nullptr;
   int batch = 0;
-  float2 *Wdd = nullptr, *TTdd = nullptr;
+  // per slot: the W build's partial sums (Wdd, TTdd, W3dd; tau~ replaces the
+  // second), and e_i + e_j + e_k of every triple (dd) for the denominators
+  float2 *Wdd = nullptr, *TTdd = nullptr, *W3dd = nullptr, *eo_tri = nullptr;
   __nv_bfloat16 *V[3] = {nullptr, nullptr, nullptr};
   __nv_bfloat16 **vptr = nullptr;  // device copy of {V[0..2]}
   unsigned int *maxbits = nullptr;
   int *slot_ex = nullptr;
   int *status = nullptr;
   SArrTable arrs;
-  std::vector<SDevPlan> ab, cc, om;
+  std::vector<SDevPlan> ab, om;
   std::vector<int> nslot;
   double executed = 0.0;
   bool staged = false, planned = false;
@@ -144,11 +146,11 @@ void drop_graph(SplitState *S) {
 void free_state_buffers(SplitState *S) {
   drop_graph(S);
   void *bufs[] = {S->T2S, S->T2C, S->T2R, S->XS, S->YS, S->OS, S->Zg, S->Zh, S->OO, S->OV,
-                  S->OVD, S->OVZA, S->OVZB, S->LVV, S->evdd, S->Wdd, S->TTdd, S->V[0], S->V[1], S->V[2], S->vptr, S->maxbits,
+                  S->OVD, S->OVZA, S->OVZB, S->LVV, S->evdd, S->Wdd, S->TTdd, S->W3dd, S->eo_tri, S->V[0], S->V[1], S->V[2], S->vptr, S->maxbits,
                   S->slot_ex, S->status};
   for (void *p : bufs)
     if (p) cudaFree(p);
-  for (auto *v : {&S->ab, &S->cc, &S->om})
+  for (auto *v : {&S->ab, &S->om})
     for (auto &d : *v) s_free_plan(&d);
 }
 
@@ -252,12 +254,13 @@ int stage(cc3_ctx *c, SplitState *S, cudaStream_t st) {
     CU(cudaMemcpyAsync(S->evdd, evd.data(), sizeof(float2) * nv, cudaMemcpyHostToDevice, st));
   }
   // per-batch workspace
-  const double per_slot = (double)nv2 * nv * 16.0 + 3.0 * s * nv2 * vp * 2.0;
+  const double per_slot = (double)nv2 * nv * 24.0 + 3.0 * s * nv2 * vp * 2.0;
   S->batch = (int)std::max(1.0, std::min(16.0, 6.0e9 / per_slot));
   S->batch = std::min(S->batch, std::max(1, c->ntri));
   const size_t nb = (size_t)S->batch;
   TRY(alloc(&S->Wdd, nb * nv2 * nv));
   TRY(alloc(&S->TTdd, nb * nv2 * nv));
+  TRY(alloc(&S->W3dd, nb * nv2 * nv));
   for (int L = 0; L < 3; ++L) {
     const size_t n4 = arr_elems((long long)nv * vp, nv, (long long)nb, s);
     TRY(alloc(&S->V[L], n4));
@@ -387,17 +390,17 @@ const WMaps kStdMaps = {MA_T2S, MB_T2S, MA_T2C, MB_T2C, MA_T2R, MB_T2R,
 // (x, 0..nv-1)); it is the A operand, its nv slabs read as one array of
 // nv * rows flattened rows (rows: the slab's row count, nv padded to 8), so
 // the tiles cover the nv^2 x nv block of W without M padding.
-//   phase 1: rows (c, a), columns b -> W_1[c][a][b]           (store)
-//   phase 2: rows (c, b), columns a -> W_2[c][a][b]           (store)
-//   phase 3: rows (a, b), columns c -> (W_1 + W_2 + W_3) / (w - eps) into W
-// W_1 and the tau result live in the W workspace, W_2 in the tau~ workspace
-// (free until tau~ is formed from tau).
+//   phase 1: rows (c, a), columns b -> W_1[c][a][b]
+//   phase 2: rows (c, b), columns a -> W_2[c][a][b]
+//   phase 3: rows (a, b), columns c -> W_3[c][a][b]
+// The three phases write separate buffers (W_2 in the tau~ workspace), so one
+// launch runs them all; the element-wise step forms tau = (W_1 + W_2 + W_3) /
+// (w - eps) and tau~ from the three.
 int w_job(SPlan &P, int nv, int rows, int Nt, int phase, int slot, int E, double &ex, int s) {
   const long long nv2 = (long long)nv * nv, nv3 = nv2 * nv;
-  const int jb = new_sjob(P, nv * rows, nv, Nt, 1, 1, phase == 3 ? SEPI_DD_TAU : SEPI_DD_STORE,
-                          E, ex, s);
+  const int jb = new_sjob(P, nv * rows, nv, Nt, 1, 1, SEPI_DD_STORE, E, ex, s);
   SJob &J = P.jobs[jb];
-  OutD C = outd(phase == 2 ? B_WS_TT : B_WS_W, slot * nv3, 0, 0);
+  OutD C = outd(phase == 1 ? B_WS_W : (phase == 2 ? B_WS_TT : B_WS_W3), slot * nv3, 0, 0);
   C.m_in = rows;
   if (phase == 1) {
     C.sm1 = nv2, C.sm0 = nv, C.sn0 = 1;
@@ -411,24 +414,7 @@ int w_job(SPlan &P, int nv, int rows, int Nt, int phase, int slot, int E, double
   J.m_pad = rows;
   J.m_valid = nv;
   J.nv = nv;
-  if (phase == 3) {
-    J.W = C;
-    J.wbuf2 = B_WS_TT;
-    J.erow_in = rows;
-  }
   return jb;
-}
-// the tau job's energies: e_ijk and the frequency w (0 for the residual)
-int w_job_tau(SPlan &P, int nv, int rows, int Nt, int slot, int E, const float *eo_dd,
-              double w, double &ex, int s) {
-  const int jc = w_job(P, nv, rows, Nt, 3, slot, E, ex, s);
-  SJob &J = P.jobs[jc];
-  J.eo_hi = eo_dd[0];
-  J.eo_lo = eo_dd[1];
-  const dd::df wd = dd::from_double_host(w);
-  J.w_hi = wd.hi;
-  J.w_lo = wd.lo;
-  return jc;
 }
 // A: slabs (x, 0..nv-1) of map `am` flattened; B: slab `bslab` of map `bm`
 void w_term(SPlan &P, int jb, int am, int x, int bm, int bslab, int K, int neg, int nv,
@@ -470,16 +456,16 @@ void w_terms_3(SPlan &P, int jc, const WMaps &m, int no, int nv, int rows, int v
   w_term(P, jc, m.aT2C, j, m.bOS, i * no + k, op, 1, nv, rows, ex, s);
 }
 
-// phases 1 and 2 (one launch, pab) and phase 3 (pc) of one triple
-void plan_w_split(SPlan &pab, SPlan &pc, SplitState *S, int no, int nv, const int ijk[3],
-                  int slot, const float *eo_dd, double &ex) {
+// the three W build phases of one triple (one launch)
+void plan_w_split(SPlan &pab, SplitState *S, int no, int nv, const int ijk[3], int slot,
+                  double &ex) {
   const int s = S->s, E = S->Et + S->Eg - 14, rows = (nv + 7) / 8 * 8;
   const int j1 = w_job(pab, nv, rows, S->Nab, 1, slot, E, ex, s);
   w_terms_1(pab, j1, kStdMaps, no, nv, rows, S->vp, S->op, ijk, ex, s);
   const int j2 = w_job(pab, nv, rows, S->Nab, 2, slot, E, ex, s);
   w_terms_2(pab, j2, kStdMaps, no, nv, rows, S->vp, S->op, ijk, ex, s);
-  const int jc = w_job_tau(pc, nv, rows, S->Nab, slot, E, eo_dd, 0.0, ex, s);
-  w_terms_3(pc, jc, kStdMaps, no, nv, rows, S->vp, S->op, ijk, ex, s);
+  const int j3 = w_job(pab, nv, rows, S->Nab, 3, slot, E, ex, s);
+  w_terms_3(pab, j3, kStdMaps, no, nv, rows, S->vp, S->op, ijk, ex, s);
 }
 
 // Appends the jobs of src to dst (one launch runs dst's jobs in order).
@@ -645,16 +631,29 @@ void plan_vvov_stacked(SPlan &P, SplitState *S, int no, int nv, std::vector<Vvov
 
 int build_plans(cc3_ctx *c, SplitState *S, cudaStream_t st) {
   drop_graph(S);
-  for (auto *v : {&S->ab, &S->cc, &S->om})
+  for (auto *v : {&S->ab, &S->om})
     for (auto &d : *v) s_free_plan(&d);
   S->ab.clear();
-  S->cc.clear();
   S->om.clear();
   S->nslot.clear();
   const int no = c->no, nv = c->nv;
   std::vector<double> eo(no);
   CU(cudaMemcpyAsync(eo.data(), c->eps_o, sizeof(double) * no, cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
+  {  // e_i + e_j + e_k of every triple (dd), read by the element-wise step
+    std::vector<float2> eot(std::max(1, c->ntri));
+    for (int t = 0; t < c->ntri; ++t) {
+      const int *ijk = &c->tri_host[3 * t];
+      const dd::df ed = dd::from_double_host(eo[ijk[0]] + eo[ijk[1]] + eo[ijk[2]]);
+      eot[t] = make_float2(ed.hi, ed.lo);
+    }
+    if (S->eo_tri) cudaFree(S->eo_tri);
+    S->eo_tri = nullptr;
+    TRY(alloc(&S->eo_tri, eot.size()));
+    CU(cudaMemcpyAsync(S->eo_tri, eot.data(), sizeof(float2) * eot.size(),
+                       cudaMemcpyHostToDevice, st));
+    CU(cudaStreamSynchronize(st));
+  }
   double ex = 0.0;
   // K split of the vvov contraction: tiles of about 400 K steps, so that the
   // persistent engine balances them over the SMs (partial sums add in FP64)
@@ -666,14 +665,11 @@ int build_plans(cc3_ctx *c, SplitState *S, cudaStream_t st) {
   const bool stack = S->stack_vvov && nv >= S_BM && nv % 8 == 0 && nv % S_BM != 0;
   for (int t0 = 0; t0 < c->ntri; t0 += S->batch) {
     const int t1 = std::min(c->ntri, t0 + S->batch);
-    SPlan pab, pc, pom, pom3;
+    SPlan pab, pom, pom3;
     std::vector<VvovPerm> vperms;
     for (int t = t0; t < t1; ++t) {
       const int *ijk = &c->tri_host[3 * t];
-      const double e = eo[ijk[0]] + eo[ijk[1]] + eo[ijk[2]];
-      const dd::df ed = dd::from_double_host(e);
-      const float eod[2] = {ed.hi, ed.lo};
-      plan_w_split(pab, pc, S, no, nv, ijk, t - t0, eod, ex);
+      plan_w_split(pab, S, no, nv, ijk, t - t0, ex);
       // the long-K tiles first: the persistent engine hands tiles out in order
       if (stack) {
         collect_vvov_perms(vperms, ijk, t - t0);
@@ -685,10 +681,8 @@ int build_plans(cc3_ctx *c, SplitState *S, cudaStream_t st) {
     if (stack) plan_vvov_stacked(pom, S, no, nv, vperms, ks4, ex);
     append_plan(pom, pom3);
     S->ab.emplace_back();
-    S->cc.emplace_back();
     S->om.emplace_back();
     TRY(s_upload_plan(pab, &S->ab.back(), st));
-    TRY(s_upload_plan(pc, &S->cc.back(), st));
     TRY(s_upload_plan(pom, &S->om.back(), st));
     S->nslot.push_back(t1 - t0);
   }
@@ -701,6 +695,7 @@ void fill_vptrs(cc3_ctx *c, SplitState *S, VPtrTable *P) {
   std::memset(P, 0, sizeof(*P));
   P->p[B_WS_W] = S->Wdd;
   P->p[B_WS_TT] = S->TTdd;  // W_2 of the W build until tau~ overwrites it
+  P->p[B_WS_W3] = S->W3dd;
   P->p[B_EPSV] = S->evdd;
   P->p[B_OMT] = c->omt;
   P->p[B_OM1] = c->om1;
@@ -758,16 +753,15 @@ int omega_sequence(cc3_ctx *c, SplitState *S, cudaStream_t st) {
   fill_vptrs(c, S, &P);
   const int nv = c->nv;
   const int kdrain = S_DRAIN_STEPS;
-  for (size_t b = 0; b < S->ab.size(); ++b) {
+  for (size_t b = 0, t0 = 0; b < S->ab.size(); t0 += S->nslot[b], ++b) {
     const int ns = S->nslot[b];
-    for (const SDevPlan *d : {&S->ab[b], &S->cc[b]}) {
-      trace_begin(c, TR_SPLIT_W, st);
-      TRY(s_launch_plan(*d, S->arrs, P, s, kdrain, S->status, st, &c->counters.launches));
-      trace_end(c, TR_SPLIT_W, st, d->flop, d->slice_flop);
-    }
+    trace_begin(c, TR_SPLIT_W, st);
+    TRY(s_launch_plan(S->ab[b], S->arrs, P, s, kdrain, S->status, st, &c->counters.launches));
+    trace_end(c, TR_SPLIT_W, st, S->ab[b].flop, S->ab[b].slice_flop);
     trace_begin(c, TR_SPLIT_ELEM, st);
     CU(cudaMemsetAsync(S->maxbits, 0, sizeof(unsigned int) * ns, st));
-    TRY(launch_contravariant_dd(S->Wdd, S->TTdd, nv, ns, S->maxbits, st));
+    TRY(launch_tau_contravariant_dd(S->Wdd, S->TTdd, S->W3dd, S->TTdd, S->evdd, S->eo_tri + t0,
+                                    0.f, 0.f, nv, ns, S->maxbits, st));
     TRY(launch_slot_exponent(S->maxbits, S->slot_ex, ns, st));
     TRY(launch_slice_tt(S->TTdd, S->vptr, nv, S->vp, s, S->slot_ex, ns, S->batch, st));
     trace_end(c, TR_SPLIT_ELEM, st, 0.0, 0.0);
@@ -940,10 +934,11 @@ size_t split_footprint(int no, int nv, int s, int ntri) {
   b += sl((long long)no * no * (no + 1), vp, no + 1);  // OO
   b += (size_t)no * no * (no + 1) * nv * sizeof(double);  // its FP64 staging copy
   b += sl((long long)no * no, (long long)nv * vp, 1);  // OV
-  const double per_slot = (double)nv2 * nv * 16.0 + 3.0 * s * nv2 * vp * 2.0;
+  const double per_slot = (double)nv2 * nv * 24.0 + 3.0 * s * nv2 * vp * 2.0;
   int batch = (int)std::max(1.0, std::min(16.0, 6.0e9 / per_slot));
   batch = std::min(batch, std::max(1, ntri));
-  b += 2 * (size_t)batch * nv2 * nv * sizeof(float2);  // Wdd, TTdd
+  b += 3 * (size_t)batch * nv2 * nv * sizeof(float2);  // Wdd, TTdd, W3dd
+  b += (size_t)std::max(1, ntri) * sizeof(float2);       // eo_tri
   b += 3 * arr_elems((long long)nv * vp, nv, batch, s) * sizeof(__nv_bfloat16);  // V[3]
   b += (size_t)nv * sizeof(float2) + 4096;
   return b;
@@ -1240,50 +1235,40 @@ int split_jacobian(cc3_ctx *c, int nvec, const double *w, const double *R1d, con
     for (int v = 0; v < nvec; ++v) arrs[v].a[MJ_FH] = make_arr(a, vp, nvec, no, s);
     S->arrs.a[MJ_FH] = arrs[0].a[MJ_FH];
   }
-  // plans per batch: R3 phase AB (shared by the vectors), phase C per vector
-  // (its frequency), the tau~ . F^ jobs and, when the cache is cold, Z~v, Z~o
+  // plans per batch: the R3 W build (one plan, run with each vector's slice
+  // arrays; the frequency enters in the element-wise step), the tau~ . F^
+  // jobs and, when the cache is cold, Z~v, Z~o
   const bool prep = jac_prep_prec(c) < 0;
   double *Zv = nullptr, *Zo = nullptr;
   TRY(jac_z_buffers(c, &Zv, &Zo, prep, st));
-  std::vector<double> eo(no);
-  CU(cudaMemcpyAsync(eo.data(), c->eps_o, sizeof(double) * no, cudaMemcpyDeviceToHost, st));
-  CU(cudaStreamSynchronize(st));
   const int rows = (nv + 7) / 8 * 8;
   const WMaps set1 = {MJ_R2S, MJ_R2S, MJ_R2C, MJ_R2C, MJ_R2R, MJ_R2R,
                       MA_XS,  MB_XS,  MA_YS,  MB_YS,  MA_OS,  MB_OS};
   const WMaps set2 = {MA_T2S, MB_T2S, MA_T2C, MB_T2C, MA_T2R, MB_T2R,
                       MJ_XH,  MJ_XH,  MJ_YH,  MJ_YH,  MJ_OH,  MJ_OH};
   const int nb = (int)S->ab.size();
-  JacPlans pAB, pC, pF, pZ;
+  JacPlans pAB, pF, pZ;
   pAB.v.resize(nb);
-  pC.v.resize((size_t)nb * nvec);
   pF.v.resize(nb);
   pZ.v.resize(nb);
   double ex = 0.0;
   for (int b = 0, t0 = 0; b < nb; ++b) {
     const int t1 = t0 + S->nslot[b];
     SPlan ab, f, z;
-    std::vector<SPlan> cv(nvec);
     for (int t = t0; t < t1; ++t) {
       const int *ijk = &c->tri_host[3 * t];
-      const double e = eo[ijk[0]] + eo[ijk[1]] + eo[ijk[2]];
-      const dd::df ed = dd::from_double_host(e);
-      const float eod[2] = {ed.hi, ed.lo};
       const int j1 = w_job(ab, nv, rows, S->Nab, 1, t - t0, Ec - 14, ex, s);
       w_terms_1(ab, j1, set1, no, nv, rows, vp, op, ijk, ex, s);
       w_terms_1(ab, j1, set2, no, nv, rows, vp, op, ijk, ex, s);
       const int j2 = w_job(ab, nv, rows, S->Nab, 2, t - t0, Ec - 14, ex, s);
       w_terms_2(ab, j2, set1, no, nv, rows, vp, op, ijk, ex, s);
       w_terms_2(ab, j2, set2, no, nv, rows, vp, op, ijk, ex, s);
-      for (int v = 0; v < nvec; ++v) {
-        const int jc = w_job_tau(cv[v], nv, rows, S->Nab, t - t0, Ec - 14, eod, w[v], ex, s);
-        w_terms_3(cv[v], jc, set1, no, nv, rows, vp, op, ijk, ex, s);
-        w_terms_3(cv[v], jc, set2, no, nv, rows, vp, op, ijk, ex, s);
-      }
+      const int j3 = w_job(ab, nv, rows, S->Nab, 3, t - t0, Ec - 14, ex, s);
+      w_terms_3(ab, j3, set1, no, nv, rows, vp, op, ijk, ex, s);
+      w_terms_3(ab, j3, set2, no, nv, rows, vp, op, ijk, ex, s);
       plan_jac_tau(&f, prep ? &z : nullptr, S, no, nv, nvec, EF, ijk, t - t0, ex);
     }
     TRY(s_upload_plan(ab, &pAB.v[b], st));
-    for (int v = 0; v < nvec; ++v) TRY(s_upload_plan(cv[v], &pC.v[(size_t)b * nvec + v], st));
     TRY(s_upload_plan(f, &pF.v[b], st));
     if (prep) TRY(s_upload_plan(z, &pZ.v[b], st));
     t0 = t1;
@@ -1295,10 +1280,13 @@ int split_jacobian(cc3_ctx *c, int nvec, const double *w, const double *R1d, con
   P.p[B_ZO] = Zo;
   const int kd = S_DRAIN_STEPS;
   long long *L = &c->counters.launches;
-  auto elem = [&](int ns) -> int {
+  // tau at frequency wv from the W build's partial sums, tau~ and its slices
+  auto elem = [&](int ns, int t0, double wv) -> int {
     trace_begin(c, TR_SPLIT_ELEM, st);
     CU(cudaMemsetAsync(S->maxbits, 0, sizeof(unsigned int) * ns, st));
-    TRY(launch_contravariant_dd(S->Wdd, S->TTdd, nv, ns, S->maxbits, st));
+    const dd::df wd = dd::from_double_host(wv);
+    TRY(launch_tau_contravariant_dd(S->Wdd, S->TTdd, S->W3dd, S->TTdd, S->evdd, S->eo_tri + t0,
+                                    wd.hi, wd.lo, nv, ns, S->maxbits, st));
     TRY(launch_slot_exponent(S->maxbits, S->slot_ex, ns, st));
     TRY(launch_slice_tt(S->TTdd, S->vptr, nv, vp, s, S->slot_ex, ns, S->batch, st));
     trace_end(c, TR_SPLIT_ELEM, st, 0.0, 0.0);
@@ -1311,19 +1299,17 @@ int split_jacobian(cc3_ctx *c, int nvec, const double *w, const double *R1d, con
     trace_end(c, cls, st, d.flop, d.slice_flop);
     return CC3_OK;
   };
-  for (int b = 0; b < nb; ++b) {
+  for (int b = 0, t0 = 0; b < nb; t0 += S->nslot[b], ++b) {
     const int ns = S->nslot[b];
     P.p[B_OMT] = rt;
     P.p[B_OM1] = r1a;
     TRY(run(S->ab[b], S->arrs, P, TR_SPLIT_W));
-    TRY(run(S->cc[b], S->arrs, P, TR_SPLIT_W));
-    TRY(elem(ns));
+    TRY(elem(ns, t0, 0.0));
     if (prep) TRY(run(pZ.v[b], S->arrs, P, TR_SPLIT_OMEGA));
     TRY(run(pF.v[b], S->arrs, P, TR_SPLIT_OMEGA));
     for (int v = 0; v < nvec; ++v) {
       TRY(run(pAB.v[b], arrs[v], P, TR_SPLIT_W));
-      TRY(run(pC.v[(size_t)b * nvec + v], arrs[v], P, TR_SPLIT_W));
-      TRY(elem(ns));
+      TRY(elem(ns, t0, w[v]));
       VPtrTable Pv = P;
       Pv.p[B_OMT] = rt + v * nt2;
       Pv.p[B_OM1] = r1a + v * n1;

@@ -70,18 +70,8 @@ __device__ __forceinline__ void issue_products(uint32_t tmem, uint64_t dA, uint6
   }
 }
 
-// tau = (W_12 + W_3) / (w - eps) in double-float for one element (the
-// partial sums of the earlier phases and this tile's).  Kept out of line:
-// inlined 24 times into the unrolled output loop it made the kernel large
-// enough for instruction-cache misses to stall the MMA-issuing warp.
-__device__ __noinline__ float2 tau_finish(dd::df x, float2 wv, dd::df e_row, float2 eb,
-                                          float w_hi, float w_lo) {
-  const dd::df tot = dd::add(x, dd::df{wv.x, wv.y});
-  const dd::df e = dd::add(e_row, dd::df{eb.x, eb.y});
-  const dd::df den = dd::add(dd::df{w_hi, w_lo}, dd::neg(e));
-  const dd::df tau = dd::div(tot, den);
-  return make_float2(tau.hi, tau.lo);
-}
+// Kept out of line: inlined into the unrolled output loop it would make the
+// kernel large enough for instruction-cache misses to stall the MMA warp.
 __device__ __noinline__ void fx_add_call(unsigned long long *slot, double v) { fx_add(slot, v); }
 
 // Position of one tile within its job: batch index, K-split part, M/N tile
@@ -521,7 +511,6 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
       const int es = seg2 ? J.expo_slot2 : J.expo_slot;
       const float sc = ldexpf(J.mult, J.expo + (es >= 0 ? slot_ex[es] : 0));
       const int mo = seg2 ? m - J.msplit : m;  // row within its output
-      const bool tau_mode = J.mode == SEPI_DD_TAU;
       const bool row_ok = m < J.M && !(J.m_pad > 0 && (m % J.m_pad) >= J.m_valid);
       // the thread's row is fixed for the tile: its output row offsets once.
       // Main columns n < Nm go to C (C2 for second-segment rows), tail
@@ -530,66 +519,31 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
       const OutD &Cm = seg2 ? J.C2 : J.C;
       const long long rowM =
           row_ok ? Cm.off + (long long)bi * Cm.sb + s_rowoff(mo, Cm.m_in, Cm.sm1, Cm.sm0) : 0;
-      // tau mode: the row's orbital-energy terms once per tile
-      const float2 *ev = reinterpret_cast<const float2 *>(P.p[B_EPSV]);
-      dd::df e_row = {0.f, 0.f};
-      if (tau_mode && row_ok) {
-        // eps = e_a + e_b + e_c - e_ijk; the row is (a, b) with the column c,
-        // or c at a fixed a = batch index with the column b
-        const float2 ea = J.erow_in > 0 ? ev[m / J.erow_in] : ev[bi];
-        const float2 ec = J.erow_in > 0 ? ev[m % J.erow_in] : ev[m];
-        e_row = dd::add(dd::add(dd::df{ea.x, ea.y}, dd::df{ec.x, ec.y}),
-                        dd::df{-J.eo_hi, -J.eo_lo});
-      }
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
         if (c < nch) {
-          // tau mode reads the other phases' partial sums of the four columns
-          // before any of them is overwritten, so the loads overlap
-          float2 wpre[4];
-          if (tau_mode) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              const int n = n0 + part * qc + c * 4 + k;
-              wpre[k] = make_float2(0.f, 0.f);
-              if (row_ok && n < J.N && n < J.n_valid) {
-                const long long woff = rowM + (long long)n * Cm.sn0;  // W at C's offsets
-                wpre[k] = reinterpret_cast<const float2 *>(P.p[J.W.buf])[woff];
-                if (J.wbuf2 > 0) {  // the other partial sum, folded in at once
-                  const float2 w2 = reinterpret_cast<const float2 *>(P.p[J.wbuf2])[woff];
-                  const dd::df ws = dd::add(dd::df{wpre[k].x, wpre[k].y}, dd::df{w2.x, w2.y});
-                  wpre[k] = make_float2(ws.hi, ws.lo);
-                }
-              }
-            }
-          }
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             const dd::df x = dd::scale(acc[c][k], sc);
             const int n = n0 + part * qc + c * 4 + k;
             if (!row_ok || n >= J.N) continue;
             long long off;
-            int buf, nc;
+            int buf;
             if (n < J.Nm) {
               if (n >= J.n_valid) continue;
               off = rowM + (long long)n * Cm.sn0;
               buf = Cm.buf;
-              nc = n;
             } else {  // tail columns are few: their offsets on the fly
               const OutD &Ctl = seg2 ? J.Ct2 : J.Ct;
               const int tlo = seg2 ? (J.Nm2 > 0 ? J.Nm2 : J.N) : J.Nm;
               const int thi = seg2 ? J.N : (J.Nm2 > 0 ? J.Nm2 : J.N);
               if (n < tlo || n >= thi) continue;
-              nc = n - tlo;
               off = Ctl.off + (long long)bi * Ctl.sb + s_rowoff(mo, Ctl.m_in, Ctl.sm1, Ctl.sm0) +
-                    (long long)nc * Ctl.sn0;
+                    (long long)(n - tlo) * Ctl.sn0;
               buf = Ctl.buf;
             }
             if (J.mode == SEPI_DD_STORE) {
               reinterpret_cast<float2 *>(P.p[buf])[off] = make_float2(x.hi, x.lo);
-            } else if (tau_mode) {
-              reinterpret_cast<float2 *>(P.p[buf])[off] =
-                  tau_finish(x, wpre[k], e_row, ev[nc], J.w_hi, J.w_lo);
             } else if (P.fx[buf]) {
               fx_add_call(P.fx[buf] + 2 * off, dd::to_double(x));
             } else {
@@ -617,11 +571,6 @@ int s_upload_plan(const SPlan &p, SDevPlan *d, cudaStream_t s) {
     const OutD *outs[4] = {&j.C, &j.Ct, two ? &j.C2 : nullptr, two ? &j.Ct2 : nullptr};
     for (const OutD *o : outs)
       if (o && o->n_in < j.N) return CC3_ERR_ARG;
-    // tau mode reads the partial sums of W at C's element offsets (buffer W.buf)
-    if (j.mode == SEPI_DD_TAU &&
-        (j.W.off != j.C.off || j.W.sb != j.C.sb || j.W.m_in != j.C.m_in || j.W.sm1 != j.C.sm1 ||
-         j.W.sm0 != j.C.sm0 || j.W.sn0 != j.C.sn0 || two || j.Nm != j.N))
-      return CC3_ERR_ARG;
   }
   if (cudaMalloc(&d->counter, sizeof(unsigned long long)) != cudaSuccess) return CC3_ERR_OOM;
   d->njobs = (int)p.jobs.size();

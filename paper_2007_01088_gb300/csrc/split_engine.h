@@ -61,7 +61,7 @@ struct STerm {
   int aflat;
 };
 
-enum SEpi { SEPI_DD_STORE = 0, SEPI_DD_TAU = 1, SEPI_F64_ATOMIC = 2 };
+enum SEpi { SEPI_DD_STORE = 0, SEPI_F64_ATOMIC = 2 };
 
 struct SJob {
   int M, N, Nm, Ntile, batch;
@@ -75,20 +75,13 @@ struct SJob {
   float mult;  // +-1 or 2 (exact)
   OutD C, Ct;  // output element (b, m, n) for n < Nm, resp. (b, m, n - Nm);
                // buffer of float2 (dd) or double
-  OutD W;      // tau mode: the dd values of the other W phase
   // rows m >= msplit (msplit > 0) belong to a second output: main columns to
   // C2 (row m - msplit), tail columns n >= Nm2 to Ct2 (column n - Nm2), with
   // the per-triple exponent ex[expo_slot2]; rows below msplit take the tail
   // columns [Nm, Nm2) only
   int msplit, Nm2, expo_slot2;
   OutD C2, Ct2;
-  float eo_hi, eo_lo, w_hi, w_lo;
   int nv;
-  // tau mode: erow_in > 0: row m stands for (a, b) = (m / erow_in,
-  // m % erow_in) and column n for c; 0: the batch index is a, row m is c and
-  // column n is b.  wbuf2 > 0: a second partial sum of W at W's offsets in
-  // buffer wbuf2 (0: none; buffer 0 never holds one).
-  int erow_in, wbuf2;
   long long tile_base;
 };
 

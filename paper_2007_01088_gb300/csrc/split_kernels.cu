@@ -127,9 +127,12 @@ __global__ void maxabs_kernel(const double *__restrict__ x, long long n,
   if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
-// tau~ = 4 tau^{abc} - 2 tau^{acb} - 2 tau^{cba} - 2 tau^{bac} + tau^{bca} + tau^{cab}
-// from tau stored as T[slot][c][a][b] (dd); writes TT[slot][a][b][c] (dd) and
-// the max |tau~| of each slot (float bits, atomic max).
+// tau = (W_1 + W_2 + W_3) / (w - e_a - e_b - e_c + e_ijk) from the three
+// partial sums of the W build, then
+// tau~ = 4 tau^{abc} - 2 tau^{acb} - 2 tau^{cba} - 2 tau^{bac} + tau^{bca} + tau^{cab},
+// all in double-float.  The partial sums are stored as W[slot][c][a][b]; tau~
+// is written as TT[slot][a][b][c], together with the max |tau~| of each slot
+// (float bits, atomic max).  TT may be the buffer of W_2 (see below).
 //
 // The six values tau^{pi(a,b,c)} over the permutations pi are the same set
 // for every permutation of (a,b,c), and tau~ at each of the six points is a
@@ -137,21 +140,28 @@ __global__ void maxabs_kernel(const double *__restrict__ x, long long n,
 // O = tau^{acb} + tau^{cba} + tau^{bac},
 //   tau~ at an even permutation (abc, bca, cab) = 3 tau^{itself} + E - 2 O,
 //   tau~ at an odd one (acb, cba, bac)           = 3 tau^{itself} + O - 2 E.
-// A block takes one triple of 8-cube indices A >= B >= C, stages the (up to
-// six distinct) tau cubes whose index triples permute it in shared memory
-// with coalesced row reads, forms all six outputs of each of its points from
-// the six staged values, and writes the output cubes back row by row: every
-// tau element is read once and every tau~ element written once.  When cube
-// indices coincide, only points with a >= b (A = B) and b >= c (B = C) are
-// formed, so that each output is produced by one thread.
+// A block takes one triple of 8-cube indices A >= B >= C, forms tau for the
+// (up to six distinct) cubes whose index triples permute it and stages them
+// in shared memory (coalesced row reads), forms all six outputs of each of
+// its points from the six staged values, and writes the output cubes back
+// row by row: every partial sum is read once and every tau~ element written
+// once.  The locations a block reads are exactly those it writes (the cubes
+// of one permutation orbit, in either layout), so TT may alias W_2: each
+// block reads all of its locations before it writes any.  When cube indices
+// coincide, only points with a >= b (A = B) and b >= c (B = C) are formed,
+// so that each output is produced by one thread.
 constexpr int CV_SX = 8, CV_SZ = 65, CV_SLOT = 8 * CV_SZ;  // padded cube strides (float2)
 __global__ void __launch_bounds__(256)
-contravariant_dd_kernel(const float2 *__restrict__ tau, float2 *__restrict__ tt, int nv,
-                        unsigned int *__restrict__ maxbits) {
+tau_contravariant_dd_kernel(const float2 *__restrict__ W1, const float2 *W2,
+                            const float2 *__restrict__ W3, float2 *tt,
+                            const float2 *__restrict__ ev, const float2 *__restrict__ eo,
+                            float w_hi, float w_lo, int nv, unsigned int *__restrict__ maxbits) {
   __shared__ float2 sm[6][CV_SLOT];
   const long long nv2 = (long long)nv * nv, nv3 = nv2 * nv;
-  const float2 *T = tau + blockIdx.y * nv3;
-  float2 *O = tt + blockIdx.y * nv3;
+  const long long sbase = blockIdx.y * nv3;
+  // w - ... + e_ijk of this slot
+  const float2 eos = eo[blockIdx.y];
+  const dd::df wo = dd::add(dd::df{w_hi, w_lo}, dd::df{eos.x, eos.y});
   // block -> (A, B, C), A >= B >= C, in lexicographic order
   int r = blockIdx.x, A = 0;
   while (r >= (A + 1) * (A + 2) / 2) {
@@ -185,7 +195,18 @@ contravariant_dd_kernel(const float2 *__restrict__ tau, float2 *__restrict__ tt,
       const int e = t + 256 * h, y = e & 7, x = (e >> 3) & 7, z = e >> 6;
       const int gx = cx[q] * 8 + x, gy = cy[q] * 8 + y, gz = cz[q] * 8 + z;
       float2 v = make_float2(0.f, 0.f);
-      if (gx < nv && gy < nv && gz < nv) v = T[(long long)gz * nv2 + (long long)gx * nv + gy];
+      if (gx < nv && gy < nv && gz < nv) {
+        const long long i = sbase + (long long)gz * nv2 + (long long)gx * nv + gy;
+        const float2 a1 = W1[i], a2 = W2[i], a3 = W3[i];
+        const dd::df sum =
+            dd::add(dd::add(dd::df{a1.x, a1.y}, dd::df{a2.x, a2.y}), dd::df{a3.x, a3.y});
+        const float2 ex = ev[gx], ey = ev[gy], ez = ev[gz];
+        dd::df den = dd::add(wo, dd::df{-ex.x, -ex.y});
+        den = dd::add(den, dd::df{-ey.x, -ey.y});
+        den = dd::add(den, dd::df{-ez.x, -ez.y});
+        const dd::df tau = dd::div(sum, den);
+        v = make_float2(tau.hi, tau.lo);
+      }
       sm[q][z * CV_SZ + x * CV_SX + y] = v;
     }
   }
@@ -238,7 +259,7 @@ contravariant_dd_kernel(const float2 *__restrict__ tau, float2 *__restrict__ tt,
       const int e = t + 256 * h, k = e & 7, j = (e >> 3) & 7, i = e >> 6;
       const int gi = cx[q] * 8 + i, gj = cy[q] * 8 + j, gk = cz[q] * 8 + k;
       if (gi < nv && gj < nv && gk < nv)
-        O[(long long)gi * nv2 + (long long)gj * nv + gk] = sm[q][i * CV_SZ + j * CV_SX + k];
+        tt[sbase + (long long)gi * nv2 + (long long)gj * nv + gk] = sm[q][i * CV_SZ + j * CV_SX + k];
     }
   }
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -365,12 +386,16 @@ int launch_maxabs(const double *x, long long n, unsigned long long *out, cudaStr
   maxabs_kernel<<<grid_for(n), 256, 0, st>>>(x, n, out);
   return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_FAIL(CC3_ERR_CUDA, "split element-wise kernel launch");
 }
-int launch_contravariant_dd(const float2 *tau, float2 *tt, int nv, int nslot,
-                            unsigned int *maxbits, cudaStream_t st) {
+int launch_tau_contravariant_dd(const float2 *W1, const float2 *W2, const float2 *W3,
+                                float2 *tt, const float2 *ev, const float2 *eo, float w_hi,
+                                float w_lo, int nv, int nslot, unsigned int *maxbits,
+                                cudaStream_t st) {
+  if (nslot <= 0) return CC3_OK;
   const long long nx = (nv + 7) / 8, ncube = nx * (nx + 1) * (nx + 2) / 6;  // A >= B >= C
   if (ncube > 0x7fffffffLL || nslot > 65535)
-    return CC3_FAIL(CC3_ERR_ARG, "contravariant_dd grid");
-  contravariant_dd_kernel<<<dim3((unsigned)ncube, nslot), 256, 0, st>>>(tau, tt, nv, maxbits);
+    return CC3_FAIL(CC3_ERR_ARG, "tau_contravariant_dd grid");
+  tau_contravariant_dd_kernel<<<dim3((unsigned)ncube, nslot), 256, 0, st>>>(
+      W1, W2, W3, tt, ev, eo, w_hi, w_lo, nv, maxbits);
   return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_FAIL(CC3_ERR_CUDA, "split element-wise kernel launch");
 }
 int launch_slot_exponent(const unsigned int *maxbits, int *ex, int nslot, cudaStream_t st) {

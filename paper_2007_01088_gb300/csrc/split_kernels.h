@@ -27,8 +27,13 @@ struct Gather {
 int launch_slice_gather(const double *src, __nv_bfloat16 *dst, int s, int e, const Gather &g,
                         long long nrows, int Kp, int rps, cudaStream_t st);
 int launch_maxabs(const double *x, long long n, unsigned long long *out, cudaStream_t st);
-int launch_contravariant_dd(const float2 *tau, float2 *tt, int nv, int nslot,
-                            unsigned int *maxbits, cudaStream_t st);
+// tau from the W build's three partial sums W1 + W2 + W3 (dd, [slot][c][a][b])
+// over (w - eps), and tau~ (dd, [slot][a][b][c]) into tt, which may be W2;
+// ev: dd virtual orbital energies, eo: dd e_i + e_j + e_k of each slot
+int launch_tau_contravariant_dd(const float2 *W1, const float2 *W2, const float2 *W3,
+                                float2 *tt, const float2 *ev, const float2 *eo, float w_hi,
+                                float w_lo, int nv, int nslot, unsigned int *maxbits,
+                                cudaStream_t st);
 int launch_slot_exponent(const unsigned int *maxbits, int *ex, int nslot, cudaStream_t st);
 // v: device array of 3 pointers (one per cyclic layout)
 int launch_slice_tt(const float2 *tt, __nv_bfloat16 *const *v, int nv, int vp, int s,
