@@ -103,6 +103,7 @@ struct SplitState {
   // tunables (autotuner): K steps per vvov tile, N tile of the W build (0: default)
   int ks_target = 400, nt_w = 0;
   bool stack_vvov = true;  // stack permutations along M in the vvov contraction
+  bool pair_ooov = true;   // one ooov job for the two permutations of a z slot
   // the residual's launch sequence as a CUDA graph (captured on the second
   // untraced call on a non-default stream, replayed afterwards)
   cudaGraphExec_t gexec = nullptr;
@@ -372,7 +373,8 @@ void add_sterm(SPlan &P, int job, SOpnd A, SOpnd B, int K, int negA, double &exe
   const double mrows = j.m_pad > 0 ? (double)(j.M / j.m_pad) * j.m_valid +
                                         std::min(j.M % j.m_pad, j.m_valid)
                                   : (double)j.M;
-  const double useful = 2.0 * mrows * (double)(j.n_valid + (j.N - j.Nm)) * K * j.batch;
+  const double ncols = j.route == 1 ? 2.0 * (j.Nm + j.tw) : (double)(j.n_valid + (j.N - j.Nm));
+  const double useful = 2.0 * mrows * ncols * K * j.batch;
   P.flop += useful;
   P.slice_flop += useful * (slices * (slices + 1) / 2);
 }
@@ -492,6 +494,7 @@ void plan_omega_split(SPlan &P, SplitState *S, int no, int nv, const int ijk[3],
   const long long nv2 = (long long)nv * nv;
   const int E = S->Eg - 14;  // + slot exponent of tau~
   int seen[6][3], nseen = 0;
+  int ooov[6][5], nooov = 0;  // (p, q, r, Lz, xouter) of the ooov / F jobs
   if (ijk[0] == ijk[1] && ijk[1] == ijk[2]) return;
   for (int u = 0; u < 6; ++u) {
     const int *m = PERM6[u];
@@ -520,28 +523,72 @@ void plan_omega_split(SPlan &P, SplitState *S, int no, int nv, const int ijk[3],
       add_sterm(P, jb, opd(MA_V0 + L, slot), opd(yz ? MB_ZG : MB_ZH, r), nv * vp, 0, ex, s,
                 &tail, nv8);
     }
-    if (which & 2) {  // Omega~^{xy}_{pl} -= sum_z V (ql|rz);  Omega~^{xy}_{pq} += sum_z V F_rz
-      // layout Lz has z innermost; its rows (y_L, x_L) are the perm's (y, x) when
-      // the perm's x slot is Lz, else (x, y); row m = y_L * nv8 + x_L
-      const int Lz = (m[2] + 1) % 3;
-      const bool xouter = (m[0] == Lz);
-      const int nv8 = (nv + 7) / 8 * 8;
-      int jb = new_sjob(P, nv * nv8, no + 1, S->N3, 1, 1, SEPI_F64_ATOMIC, E, ex, s);
-      P.jobs[jb].expo_slot = slot;
-      P.jobs[jb].Nm = no;
-      P.jobs[jb].m_pad = nv8;
-      P.jobs[jb].m_valid = nv;
-      // m / nv8 = y_L, m % nv8 = x_L;  Omega~[p][l][x][y] at x*nv + y
-      OutD c = outd(B_OMT, (long long)p * no * nv2, xouter ? nv : 1, nv2);
-      c.m_in = nv8;
-      c.sm1 = xouter ? 1 : nv;
-      P.jobs[jb].C = c;
-      OutD ct = outd(B_OMT, ((long long)p * no + q) * nv2, xouter ? nv : 1, 0);
-      ct.m_in = nv8;
-      ct.sm1 = xouter ? 1 : nv;
-      P.jobs[jb].Ct = ct;
-      add_sterm(P, jb, opd(MA_V0K + Lz, slot), opd(MB_OO, q * no + r), vp, 1, ex, s);
+    if (which & 2) {  // the ooov / F job, formed below
+      ooov[nooov][0] = p;
+      ooov[nooov][1] = q;
+      ooov[nooov][2] = r;
+      ooov[nooov][3] = (m[2] + 1) % 3;  // Lz
+      ooov[nooov][4] = m[0] == (m[2] + 1) % 3 ? 1 : 0;  // xouter
+      ++nooov;
     }
+  }
+  // Omega~^{xy}_{pl} -= sum_z V (ql|rz);  Omega~^{xy}_{pq} += sum_z V F_rz.
+  // Layout Lz has z innermost; its rows (y_L, x_L) are the perm's (y, x) when
+  // the perm's x slot is Lz (xouter), else (x, y); row m = y_L * nv8 + x_L.
+  // The two permutations with the same z slot read the same tau~ rows (layout
+  // Lz): when the columns allow, one job takes both, B rows [0, cs) from the
+  // first permutation's OO block and [cs, 2 cs) from the second's.
+  const int nv8 = (nv + 7) / 8 * 8, cs = (no + 1 + 7) / 8 * 8;
+  const bool pair_ok = S->pair_ooov && (cs + no + 1 + 15) / 16 * 16 <= S_NT_MAX;
+  auto ooov_out = [&](int p, int xo, int l0, OutD *c, OutD *ct) {
+    // Omega~[p][l][x][y] at x*nv + y; the tail column is l = l0
+    *c = outd(B_OMT, (long long)p * no * nv2, xo ? nv : 1, nv2);
+    c->m_in = nv8;
+    c->sm1 = xo ? 1 : nv;
+    *ct = outd(B_OMT, ((long long)p * no + l0) * nv2, xo ? nv : 1, 0);
+    ct->m_in = nv8;
+    ct->sm1 = xo ? 1 : nv;
+  };
+  bool used[6] = {false, false, false, false, false, false};
+  for (int a = 0; a < nooov; ++a) {
+    if (used[a]) continue;
+    used[a] = true;
+    int b = -1;
+    for (int u = a + 1; u < nooov && pair_ok; ++u)
+      if (!used[u] && ooov[u][3] == ooov[a][3]) {
+        b = u;
+        break;
+      }
+    const int Lz = ooov[a][3];
+    if (b < 0) {
+      int jb = new_sjob(P, nv * nv8, no + 1, S->N3, 1, 1, SEPI_F64_ATOMIC, E, ex, s);
+      SJob &J = P.jobs[jb];
+      J.expo_slot = slot;
+      J.Nm = no;
+      J.m_pad = nv8;
+      J.m_valid = nv;
+      ooov_out(ooov[a][0], ooov[a][4], ooov[a][1], &J.C, &J.Ct);
+      add_sterm(P, jb, opd(MA_V0K + Lz, slot), opd(MB_OO, ooov[a][1] * no + ooov[a][2]), vp, 1,
+                ex, s);
+      continue;
+    }
+    used[b] = true;
+    const int N = cs + no + 1;
+    int jb = new_sjob(P, nv * nv8, N, (N + 15) / 16 * 16, 1, 1, SEPI_F64_ATOMIC, E, ex, s);
+    SJob &J = P.jobs[jb];
+    J.expo_slot = slot;
+    J.Nm = no;
+    J.n_valid = N;
+    J.route = 1;  // columns [0, cs): first permutation, [cs, N): second
+    J.Nm2 = cs;
+    J.tw = 1;
+    J.m_pad = nv8;
+    J.m_valid = nv;
+    ooov_out(ooov[a][0], ooov[a][4], ooov[a][1], &J.C, &J.Ct);
+    ooov_out(ooov[b][0], ooov[b][4], ooov[b][1], &J.C2, &J.Ct2);
+    const SOpnd tail = opd(MB_OO, ooov[b][1] * no + ooov[b][2]);
+    add_sterm(P, jb, opd(MA_V0K + Lz, slot), opd(MB_OO, ooov[a][1] * no + ooov[a][2]), vp, 1,
+              ex, s, &tail, cs);
   }
 }
 

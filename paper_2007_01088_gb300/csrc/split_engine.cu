@@ -519,6 +519,7 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
       const OutD &Cm = seg2 ? J.C2 : J.C;
       const long long rowM =
           row_ok ? Cm.off + (long long)bi * Cm.sb + s_rowoff(mo, Cm.m_in, Cm.sm1, Cm.sm0) : 0;
+      const int mq = mo / Cm.m_in, mr = mo % Cm.m_in;  // route 1: shared by its outputs
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
         if (c < nch) {
@@ -529,7 +530,15 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
             if (!row_ok || n >= J.N) continue;
             long long off;
             int buf;
-            if (n < J.Nm) {
+            if (J.route == 1) {  // two column segments (see SJob)
+              const bool sg = n >= J.Nm2;
+              const int jc = sg ? n - J.Nm2 : n;
+              if (jc >= J.Nm + J.tw) continue;
+              const OutD &O = jc < J.Nm ? (sg ? J.C2 : J.C) : (sg ? J.Ct2 : J.Ct);
+              off = O.off + (long long)bi * O.sb + (long long)mq * O.sm1 + (long long)mr * O.sm0 +
+                    (long long)(jc < J.Nm ? jc : jc - J.Nm) * O.sn0;
+              buf = O.buf;
+            } else if (n < J.Nm) {
               if (n >= J.n_valid) continue;
               off = rowM + (long long)n * Cm.sn0;
               buf = Cm.buf;
@@ -568,9 +577,11 @@ int s_upload_plan(const SPlan &p, SDevPlan *d, cudaStream_t s) {
   // its columns (n_in >= N)
   for (const SJob &j : p.jobs) {
     const bool two = j.msplit > 0;
-    const OutD *outs[4] = {&j.C, &j.Ct, two ? &j.C2 : nullptr, two ? &j.Ct2 : nullptr};
+    const bool r1 = j.route == 1;
+    const OutD *outs[4] = {&j.C, &j.Ct, two || r1 ? &j.C2 : nullptr, two || r1 ? &j.Ct2 : nullptr};
     for (const OutD *o : outs)
-      if (o && o->n_in < j.N) return CC3_ERR_ARG;
+      if (o && (o->n_in < j.N || (r1 && o->m_in != j.C.m_in))) return CC3_ERR_ARG;
+    if (r1 && (two || j.Nm2 <= 0 || j.Nm + j.tw > j.Nm2)) return CC3_ERR_ARG;
   }
   if (cudaMalloc(&d->counter, sizeof(unsigned long long)) != cudaSuccess) return CC3_ERR_OOM;
   d->njobs = (int)p.jobs.size();

@@ -81,6 +81,11 @@ struct SJob {
   // columns [Nm, Nm2) only
   int msplit, Nm2, expo_slot2;
   OutD C2, Ct2;
+  // route 1 (column pairs): columns [0, Nm2) and [Nm2, N) are two segments;
+  // column j of a segment goes to C / C2 (j < Nm) or Ct / Ct2 (column j - Nm,
+  // Nm <= j < Nm + tw); other columns are padding.  All four outputs share
+  // m_in.  route 0: the row segments above.
+  int route, tw;
   int nv;
   long long tile_base;
 };

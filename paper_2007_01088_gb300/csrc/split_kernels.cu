@@ -46,6 +46,11 @@ __device__ __forceinline__ long long fixed_from_float(float x, int sh) {
   return (b >> 31) ? -v : v;
 }
 
+// 2^(-8p): the exact scale of slice p (a multiply, not a library call)
+__device__ __forceinline__ float slice_scale(int p) {
+  return __int_as_float((127 - 8 * p) << 23);
+}
+
 // Balanced base-256 digits of T (|T| < 2^(7+8(s-1))): T = sum_p d_p 256^(s-1-p),
 // d_p in [-128, 128]; slice p stores d_p 2^(-8p) as an exact BF16.
 __device__ __forceinline__ void store_digits(long long T, int s, __nv_bfloat16 *dst,
@@ -56,16 +61,16 @@ __device__ __forceinline__ void store_digits(long long T, int s, __nv_bfloat16 *
     if (p < s) {
       if (p > 0) {
         const long long r = ((T + 128) & 255) - 128;
-        d[p] = (float)r;
+        d[p] = (float)(int)r;
         T = (T - r) >> 8;
       } else {
-        d[0] = (float)T;
+        d[0] = (float)(int)T;  // |d_0| <= 128 by the bound on T
       }
     }
   }
 #pragma unroll
   for (int p = 0; p < S_MAX_SLICES_K; ++p)
-    if (p < s) dst[p * slice_stride] = __float2bfloat16_rn(ldexpf(d[p], -8 * p));
+    if (p < s) dst[p * slice_stride] = __float2bfloat16_rn(d[p] * slice_scale(p));
 }
 
 // Offset of slice 0 of (row r, k in 0..15) inside one 16-column K block of
@@ -186,6 +191,17 @@ tau_contravariant_dd_kernel(const float2 *__restrict__ W1, const float2 *W2,
       if (slot[q] == q && cx[u] == cx[q] && cy[u] == cy[q] && cz[u] == cz[q]) slot[q] = u;
   }
   const int t = threadIdx.x;
+  // the denominators' (x, y) parts of every staged cube, w + e_ijk - e_x - e_y
+  __shared__ float2 dxy[6][64];
+  for (int u = t; u < 6 * 64; u += 256) {
+    const int q = u >> 6, x = (u >> 3) & 7, y = u & 7;
+    const int gx = cx[q] * 8 + x, gy = cy[q] * 8 + y;
+    if (slot[q] != q || gx >= nv || gy >= nv) continue;
+    const float2 ex = ev[gx], ey = ev[gy];
+    const dd::df d = dd::add(dd::add(wo, dd::df{-ex.x, -ex.y}), dd::df{-ey.x, -ey.y});
+    dxy[q][u & 63] = make_float2(d.hi, d.lo);
+  }
+  __syncthreads();
   // stage tau^{xyz} of cube (X, Y, Z) at [z][x][y] (y contiguous in memory)
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
@@ -200,10 +216,8 @@ tau_contravariant_dd_kernel(const float2 *__restrict__ W1, const float2 *W2,
         const float2 a1 = W1[i], a2 = W2[i], a3 = W3[i];
         const dd::df sum =
             dd::add(dd::add(dd::df{a1.x, a1.y}, dd::df{a2.x, a2.y}), dd::df{a3.x, a3.y});
-        const float2 ex = ev[gx], ey = ev[gy], ez = ev[gz];
-        dd::df den = dd::add(wo, dd::df{-ex.x, -ex.y});
-        den = dd::add(den, dd::df{-ey.x, -ey.y});
-        den = dd::add(den, dd::df{-ez.x, -ez.y});
+        const float2 dq = dxy[q][x * 8 + y], ez = ev[gz];
+        const dd::df den = dd::add(dd::df{dq.x, dq.y}, dd::df{-ez.x, -ez.y});
         const dd::df tau = dd::div(sum, den);
         v = make_float2(tau.hi, tau.lo);
       }
@@ -321,17 +335,17 @@ slice_tt_kernel(const float2 *__restrict__ tt, __nv_bfloat16 *const *__restrict_
       if (p < s) {
         if (p > 0) {
           const long long r = ((Tt + 128) & 255) - 128;
-          d[p] = (float)r;
+          d[p] = (float)(int)r;
           Tt = (Tt - r) >> 8;
         } else {
-          d[0] = (float)Tt;
+          d[0] = (float)(int)Tt;  // |d_0| <= 128 by the bound on Tt
         }
       }
     }
     const int o = (a * 16 + b) * TT_PAD + c;
 #pragma unroll
     for (int p = 0; p < S_MAX_SLICES_K; ++p)
-      if (p < s) dig[p * plane + o] = __float2bfloat16_rn(ldexpf(d[p], -8 * p));
+      if (p < s) dig[p * plane + o] = __float2bfloat16_rn(d[p] * slice_scale(p));
   }
   __syncthreads();
   const long long nv8 = (nv + 7) / 8 * 8;
