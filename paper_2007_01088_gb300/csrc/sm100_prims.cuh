@@ -152,6 +152,40 @@ __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a_desc, uint6
       "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
 }
 
+// The same with a usage hint for the A operand's collector buffer: U = 1
+// reads A from shared memory and keeps it (fill), U = 2 reuses the kept A
+// (use), U = 3 reuses it for the last time (lastuse), U = 0 reads A and does
+// not keep it (discard, the default).  A run fill, use..., lastuse must pass
+// the same A descriptor and be consecutive MMAs of this thread.
+template <int U>
+__device__ __forceinline__ void umma_f16_a(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                           uint32_t idesc, uint32_t accumulate) {
+  if constexpr (U == 1) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n\t}" ::"r"(
+            d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
+  } else if constexpr (U == 2) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16.collector::a::use [%0], %1, %2, %3, p;\n\t}" ::"r"(
+            d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
+  } else if constexpr (U == 3) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n\t}" ::"r"(
+            d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
+  } else {
+    umma_f16(d_tmem, a_desc, b_desc, idesc, accumulate);
+  }
+}
+
 // arrive on `bar` when every previously issued tcgen05.mma of this thread completes
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
   asm volatile(

@@ -49,6 +49,28 @@ __device__ __forceinline__ long long s_rowoff(int m, int m_in, long long s1, lon
   return (long long)(m / m_in) * s1 + (long long)(m % m_in) * s0;
 }
 
+// One slice product p x q into accumulator min(p + q, 4), as element `i` of
+// a run of `n` products that share A slice p (the run keeps A in the
+// collector buffer instead of reading it from shared memory again).
+template <int S>
+__device__ __forceinline__ void issue_one(uint32_t tmem, uint64_t dA, uint64_t dB, uint32_t a16,
+                                          uint32_t b16, uint32_t Nt, uint32_t idesc,
+                                          uint32_t &fresh, int p, int q, int i, int n) {
+  const int lv = p + q;
+  const int acc = lv < 4 ? lv : 4;
+  const uint32_t d = tmem + (uint32_t)acc * Nt, en = ((fresh >> acc) & 1u) ^ 1u;
+  const uint64_t a = dA + (uint64_t)(p * a16), b = dB + (uint64_t)(q * b16);
+  if (n == 1)
+    umma_f16_a<0>(d, a, b, idesc, en);
+  else if (i == 0)
+    umma_f16_a<1>(d, a, b, idesc, en);
+  else if (i == n - 1)
+    umma_f16_a<3>(d, a, b, idesc, en);
+  else
+    umma_f16_a<2>(d, a, b, idesc, en);
+  fresh &= ~(1u << acc);
+}
+
 // Issues the slice products of one K step whose level is >= 4 (HIGH) or
 // <= 3 (!HIGH), fully unrolled; bit L of `fresh` marks accumulator L as not
 // yet written since its last reset (its first product overwrites it).
@@ -58,16 +80,27 @@ __device__ __forceinline__ void issue_products(uint32_t tmem, uint64_t dA, uint6
                                                uint32_t idesc, uint32_t &fresh) {
 #pragma unroll
   for (int p = 0; p < S; ++p) {
+    // q range of this group for slice p
+    const int qlo = HIGH ? (4 - p > 0 ? 4 - p : 0) : 0;
+    const int qhi = HIGH ? S - 1 - p : (3 - p < S - 1 - p ? 3 - p : S - 1 - p);
 #pragma unroll
-    for (int q = 0; q < S - p; ++q) {
-      const int lv = p + q;
-      if (HIGH != (lv >= 4)) continue;
-      const int acc = lv < 4 ? lv : 4;
-      umma_f16(tmem + (uint32_t)acc * Nt, dA + (uint64_t)(p * a16), dB + (uint64_t)(q * b16),
-               idesc, ((fresh >> acc) & 1u) ^ 1u);
-      fresh &= ~(1u << acc);
-    }
+    for (int q = qlo; q <= qhi; ++q)
+      issue_one<S>(tmem, dA, dB, a16, b16, Nt, idesc, fresh, p, q, q - qlo, qhi - qlo + 1);
   }
+}
+
+// All slice products of one K step, A slice by A slice (the order of a step
+// that does not wait for a drain): A is read from shared memory S times
+// instead of once per product.
+template <int S>
+__device__ __forceinline__ void issue_products_all(uint32_t tmem, uint64_t dA, uint64_t dB,
+                                                   uint32_t a16, uint32_t b16, uint32_t Nt,
+                                                   uint32_t idesc, uint32_t &fresh) {
+#pragma unroll
+  for (int p = 0; p < S; ++p)
+#pragma unroll
+    for (int q = 0; q < S - p; ++q)
+      issue_one<S>(tmem, dA, dB, a16, b16, Nt, idesc, fresh, p, q, q, S - p);
 }
 
 // Kept out of line: inlined into the unrolled output loop it would make the
@@ -386,16 +419,18 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
           // slice p of a tile starts 256 p bytes in; row groups are 256 s bytes apart
           const uint64_t dA = smem_desc_kmajor(sa, 256u * s),
                          dB = smem_desc_kmajor(sa + (uint32_t)s * a_bytes, 256u * s);
-          // levels >= 4 first (they never wait for a drain), then levels 0..3
-          issue_products<S, true>(tmem, dA, dB, 16u, 16u, (uint32_t)Nt, idesc, fresh);
           if (pending) {
+            // levels >= 4 first (they never wait for a drain), then levels 0..3
+            issue_products<S, true>(tmem, dA, dB, 16u, 16u, (uint32_t)Nt, idesc, fresh);
             if (!mbar_wait(&drainempty, nd & 1, &err)) { ok = false; break; }
             tc_fence_after();
             ++nd;
             pending = false;
             fresh |= 0xFu;
+            issue_products<S, false>(tmem, dA, dB, 16u, 16u, (uint32_t)Nt, idesc, fresh);
+          } else {
+            issue_products_all<S>(tmem, dA, dB, 16u, 16u, (uint32_t)Nt, idesc, fresh);
           }
-          issue_products<S, false>(tmem, dA, dB, 16u, 16u, (uint32_t)Nt, idesc, fresh);
           umma_commit(&empty[st]);
           if (++since == kdrain_steps && g + 1 < ti.g1) {
             umma_commit(&drainfull);
