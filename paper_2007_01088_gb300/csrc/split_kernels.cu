@@ -303,7 +303,11 @@ __global__ void slot_exponent_kernel(const unsigned int *__restrict__ maxbits, i
 // ooov and F contractions.  One CTA converts a 16^3 cube of tau~ (read along
 // its innermost index) into digits once, keeps them in shared memory, and
 // writes the cube into all three layouts as whole 16-byte core rows.
-constexpr int TT_PAD = 18;  // row length (bf16) of the digit cube in shared memory
+// Digit cube in shared memory: element (a, b, c) of slice p at
+// p * TT_PLANE + a * TT_APLANE + b * TT_PAD + c (bf16).  The a-plane stride is
+// an odd number of 4-byte words, so that the 16 lanes of a layout-0 read
+// (consecutive a) fall in distinct banks.
+constexpr int TT_PAD = 18, TT_APLANE = 16 * TT_PAD + 2, TT_PLANE = 16 * TT_APLANE;
 __global__ void __launch_bounds__(256)
 slice_tt_kernel(const float2 *__restrict__ tt, __nv_bfloat16 *const *__restrict__ v, int nv,
                 int vp, int s, const int *__restrict__ ex, int nslot_alloc) {
@@ -319,7 +323,7 @@ slice_tt_kernel(const float2 *__restrict__ tt, __nv_bfloat16 *const *__restrict_
   const long long nv2 = (long long)nv * nv;
   const float2 *T = tt + (long long)slot * nv2 * nv;
   const int sh = 7 + 8 * (s - 1) - ex[slot];
-  const int plane = 16 * 16 * TT_PAD;
+  const int plane = TT_PLANE;
   for (int e = threadIdx.x; e < 4096; e += 256) {
     const int c = e & 15, b = (e >> 4) & 15, a = e >> 8;
     const int ga = ab * 16 + a, gb = bb * 16 + b, gc = cb * 16 + c;
@@ -342,7 +346,7 @@ slice_tt_kernel(const float2 *__restrict__ tt, __nv_bfloat16 *const *__restrict_
         }
       }
     }
-    const int o = (a * 16 + b) * TT_PAD + c;
+    const int o = a * TT_APLANE + b * TT_PAD + c;
 #pragma unroll
     for (int p = 0; p < S_MAX_SLICES_K; ++p)
       if (p < s) dig[p * plane + o] = __float2bfloat16_rn(d[p] * slice_scale(p));
@@ -375,7 +379,7 @@ slice_tt_kernel(const float2 *__restrict__ tt, __nv_bfloat16 *const *__restrict_
           const int a = L == 0 ? x : (L == 1 ? z : y);
           const int b = L == 0 ? y : (L == 1 ? x : z);
           const int c = L == 0 ? z : (L == 1 ? y : x);
-          out[e] = D[(a * 16 + b) * TT_PAD + c];
+          out[e] = D[a * TT_APLANE + b * TT_PAD + c];
         }
         *reinterpret_cast<uint4 *>(dst + p * 128 + o) = *reinterpret_cast<const uint4 *>(out);
       }
@@ -421,7 +425,7 @@ int launch_slice_tt(const float2 *tt, __nv_bfloat16 *const *v, int nv, int vp, i
   if (vp / 16 != (nv + 15) / 16 || s < 1 || s > S_MAX_SLICES_K)
     return CC3_FAIL(CC3_ERR_ARG, "slice_tt layout");
   const int nx = (nv + 15) / 16;
-  const size_t smem = (size_t)s * 16 * 16 * TT_PAD * sizeof(__nv_bfloat16);
+  const size_t smem = (size_t)s * TT_PLANE * sizeof(__nv_bfloat16);
   {
     static std::mutex mu;
     static bool set[64] = {false};
@@ -429,7 +433,7 @@ int launch_slice_tt(const float2 *tt, __nv_bfloat16 *const *v, int nv, int vp, i
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(mu);
     if (dev >= 0 && dev < 64 && !set[dev]) {
-      const size_t mx = (size_t)S_MAX_SLICES_K * 16 * 16 * TT_PAD * sizeof(__nv_bfloat16);
+      const size_t mx = (size_t)S_MAX_SLICES_K * TT_PLANE * sizeof(__nv_bfloat16);
       if (cudaFuncSetAttribute(slice_tt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)mx) != cudaSuccess)
         return CC3_FAIL(CC3_ERR_CUDA, "slice_tt shared memory");
