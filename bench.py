@@ -406,6 +406,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--workload", default="omega", choices=["omega", "serve", "jacobian"])
+    ap.add_argument("--config", default=None,
+                    help="omega: a named workload of the input generator (e.g. "
+                         "cfg3_proline_no22_nv250) instead of --no/--nv")
     ap.add_argument("--jno", type=int, default=20, help="jacobian: occupied orbitals")
     ap.add_argument("--jnv", type=int, default=200, help="jacobian: virtual orbitals")
     ap.add_argument("--nvec", type=int, default=8, help="jacobian: trial vectors")
@@ -438,12 +441,17 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     import paper_2007_01088_gb300 as g
-    from cc3_inputs import make_inputs
+    from cc3_inputs import make_inputs, CONFIGS, config_inputs
     no, nv = args.no, args.nv
     workload = WORKLOAD if (no, nv) == (NO, NV) else WORKLOAD.replace(
         f"no={NO} nv={NV}", f"no={no} nv={nv}")
     prec = g.CC3_SPLIT_BF16 if args.prec == "split" else g.CC3_FP64
-    inp = make_inputs(no, nv, seed=rank)
+    if args.config:  # one of the named workloads of the input generator
+        inp = config_inputs(args.config, seed=rank)
+        no, nv = inp.no, inp.nv
+        workload = f"{args.config}: " + ", ".join(f"{k}={v}" for k, v in CONFIGS[args.config].items())
+    else:
+        inp = make_inputs(no, nv, seed=rank)
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         ctx = g.Context(inp, device=True, stream=stream)
