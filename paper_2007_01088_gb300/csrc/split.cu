@@ -792,8 +792,9 @@ int split_ready(cc3_ctx *c, SplitState **out, cudaStream_t st) {
 }  // namespace
 
 namespace {
-// The residual's launch sequence: per batch of triples the W build (phases AB
-// and C), tau~ and its slices, and the contractions.
+// The residual's launch sequence: per batch of triples the W build (one
+// launch, three partial sums), tau and tau~ from them, the slices of tau~,
+// and the contractions.
 int omega_sequence(cc3_ctx *c, SplitState *S, cudaStream_t st) {
   const int s = S->s;
   VPtrTable P;
