@@ -324,32 +324,43 @@ slice_tt_kernel(const float2 *__restrict__ tt, __nv_bfloat16 *const *__restrict_
   const float2 *T = tt + (long long)slot * nv2 * nv;
   const int sh = 7 + 8 * (s - 1) - ex[slot];
   const int plane = TT_PLANE;
-  for (int e = threadIdx.x; e < 4096; e += 256) {
-    const int c = e & 15, b = (e >> 4) & 15, a = e >> 8;
-    const int ga = ab * 16 + a, gb = bb * 16 + b, gc = cb * 16 + c;
-    long long Tt = 0;
-    if (ga < nv && gb < nv && gc < nv) {
-      const float2 t = T[(long long)ga * nv2 + (long long)gb * nv + gc];
-      Tt = fixed_from_float(t.x, sh) + fixed_from_float(t.y, sh);
-    }
-    // balanced base-256 digits, slice p stores d_p 2^(-8p)
-    float d[S_MAX_SLICES_K];
+  // 16 elements per thread, loaded 8 at a time before any is converted (the
+  // loads of a batch are in flight together)
+#pragma unroll 1
+  for (int i0 = 0; i0 < 16; i0 += 8) {
+    float2 tv[8];
 #pragma unroll
-    for (int p = S_MAX_SLICES_K - 1; p >= 0; --p) {
-      if (p < s) {
-        if (p > 0) {
-          const long long r = ((Tt + 128) & 255) - 128;
-          d[p] = (float)(int)r;
-          Tt = (Tt - r) >> 8;
-        } else {
-          d[0] = (float)(int)Tt;  // |d_0| <= 128 by the bound on Tt
+    for (int u = 0; u < 8; ++u) {
+      const int e = threadIdx.x + 256 * (i0 + u);
+      const int c = e & 15, b = (e >> 4) & 15, a = e >> 8;
+      const int ga = ab * 16 + a, gb = bb * 16 + b, gc = cb * 16 + c;
+      tv[u] = make_float2(0.f, 0.f);
+      if (ga < nv && gb < nv && gc < nv) tv[u] = T[(long long)ga * nv2 + (long long)gb * nv + gc];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = threadIdx.x + 256 * (i0 + u);
+      const int c = e & 15, b = (e >> 4) & 15, a = e >> 8;
+      long long Tt = fixed_from_float(tv[u].x, sh) + fixed_from_float(tv[u].y, sh);
+      // balanced base-256 digits, slice p stores d_p 2^(-8p)
+      float d[S_MAX_SLICES_K];
+#pragma unroll
+      for (int p = S_MAX_SLICES_K - 1; p >= 0; --p) {
+        if (p < s) {
+          if (p > 0) {
+            const long long r = ((Tt + 128) & 255) - 128;
+            d[p] = (float)(int)r;
+            Tt = (Tt - r) >> 8;
+          } else {
+            d[0] = (float)(int)Tt;  // |d_0| <= 128 by the bound on Tt
+          }
         }
       }
-    }
-    const int o = a * TT_APLANE + b * TT_PAD + c;
+      const int o = a * TT_APLANE + b * TT_PAD + c;
 #pragma unroll
-    for (int p = 0; p < S_MAX_SLICES_K; ++p)
-      if (p < s) dig[p * plane + o] = __float2bfloat16_rn(d[p] * slice_scale(p));
+      for (int p = 0; p < S_MAX_SLICES_K; ++p)
+        if (p < s) dig[p * plane + o] = __float2bfloat16_rn(d[p] * slice_scale(p));
+    }
   }
   __syncthreads();
   const long long nv8 = (nv + 7) / 8 * 8;
