@@ -55,9 +55,10 @@ typedef struct cc3_server cc3_server;
  * CC3_SPLIT_BF16 the dominant contractions run as exact products of
  *                integer-valued BF16 slices of the FP64 operands on the
  *                tensor cores (FP32 accumulation of exact integer sums),
- *                recombined in extended precision; denominators,
- *                cross-triple accumulation and the energy stay in FP64 or
- *                in double-float arithmetic of equal or better accuracy.
+ *                recombined in extended precision.  The denominators and
+ *                the contravariant combination run in double-float
+ *                arithmetic (pairs of FP32, ~48 significant bits); the
+ *                cross-triple accumulation and the energy stay in FP64.
  * CC3_SPLIT_INT8 reserved (the INT8 tensor rate of this GPU is far below its
  *                BF16 rate); returns CC3_ERR_UNSUPPORTED. */
 typedef enum { CC3_FP64 = 0, CC3_SPLIT_BF16 = 1, CC3_SPLIT_INT8 = 2 } cc3_prec;
