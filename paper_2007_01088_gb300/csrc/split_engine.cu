@@ -16,14 +16,18 @@
 // Warp roles (576 threads): warp 0 issues one bulk copy per operand tile (all
 // s slices of a 128 x 16 A tile, resp. an Ntile x 16 B tile, pre-tiled in
 // global memory in the canonical no-swizzle order with the slices interleaved
-// per row group) into a ring of stages; one thread of warp 1 issues tcgen05.mma (M = 128, N = Ntile <= 96,
-// K = 16, FP32 accumulate) and owns the tensor-memory allocation (5 x Ntile
-// columns); warps 2-17 drain and finish the accumulators (each quadrant of 32
-// TMEM lanes is read by four warps, one per column quarter, 4 columns per
-// load).  At a drain point the issuer queues the next step's level >= 4
-// products before it waits for the drain, so the drain overlaps tensor work.
-// Every wait is bounded: on timeout the CTA sets an error word that the host
-// turns into CC3_ERR_TIMEOUT.
+// per row group; one copy per slab when the A rows are flattened over slabs)
+// into a ring of stages; one thread of warp 1 issues tcgen05.mma (M = 128,
+// N = Ntile <= 96, K = 16, FP32 accumulate, A kept in the collector buffer
+// across the products of one A slice) and owns the tensor-memory allocation
+// (5 x Ntile columns); warps 2-17 drain and finish the accumulators (each
+// quadrant of 32 TMEM lanes is read by four warps, one per column quarter, 4
+// columns per load) and write the outputs (double-float stores, FP64 atomics
+// or 128-bit fixed-point atomics) through up to four output descriptors.  At
+// a drain point the issuer queues the next step's level >= 4 products before
+// it waits for the drain, so the drain overlaps tensor work.  Every wait is
+// bounded: on timeout the CTA sets an error word that the host turns into
+// CC3_ERR_TIMEOUT.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
