@@ -106,6 +106,19 @@ void cc3_ctx_destroy(cc3_ctx *ctx);
  * task filters such as core-valence separation). */
 int cc3_ctx_set_triples(cc3_ctx *ctx, int ntri, const int *ijk);
 
+/* Core-valence separation task filter (paper, Introduction and
+ * Applications: the triple loop skips every occupied triple none of whose
+ * indices is a core orbital of interest, which takes the Jacobian from
+ * 8 nv^4 no^3 to 8 nv^4 no^2 per vector for one core orbital).  Host only,
+ * no context needed.  core[ncore]: distinct occupied indices in [0, no).
+ * Enumerates the triples i >= j >= k, not all equal, with at least one index
+ * in core, in loop order (i outermost), and writes the first min(count, max)
+ * of them to ijk[3 * t + 0..2] (ijk may be NULL when max = 0).  Returns the
+ * count (>= 0), or CC3_ERR_ARG for no < 0, ncore < 0 or > no, a NULL core
+ * with ncore > 0, an index outside [0, no) or a repeated index.  Pass the
+ * result to cc3_ctx_set_triples to restrict a context to those tasks. */
+int cc3_cvs_triples(int no, int ncore, const int *core, int max, int *ijk);
+
 /* CC3 triples contribution to the ground-state residual (Algorithm 1):
  * Omega1[no][nv], Omega2[no][no][nv][nv] (covariant, pair symmetric) and
  * E_T = sum_{ijab} t^{ab}_{ij} Omega~^{ab}_{ij} (the contravariant residual

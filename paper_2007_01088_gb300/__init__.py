@@ -22,7 +22,7 @@ __all__ = ["CC3_FP64", "CC3_SPLIT_BF16", "CC3_SPLIT_INT8", "CC3_DEVICE_PTRS",
            "CC3_DETERMINISTIC", "CC3Error", "lib", "cc3_ctx_create",
            "cc3_ctx_destroy", "cc3_ctx_set_triples", "cc3_omega_triples",
            "cc3_jacobian_triples", "cc3_ctx_counters", "cc3_ctx_set_slices",
-           "cc3_strerror", "Context", "EXPORTED"]
+           "cc3_strerror", "cc3_cvs_triples", "Context", "EXPORTED"]
 
 CC3_FP64, CC3_SPLIT_BF16, CC3_SPLIT_INT8 = 0, 1, 2
 CC3_DEVICE_PTRS, CC3_DETERMINISTIC = 1, 2
@@ -37,7 +37,7 @@ EXPORTED = ["cc3_ctx_create", "cc3_ctx_destroy", "cc3_ctx_set_triples",
             "cc3_serve_cancel", "cc3_serve_stats", "cc3_serve_stop",
             "cc3_debug_split_gemm", "cc3_last_error", "cc3_ctx_set_tracing",
             "cc3_ctx_trace", "cc3_omega_triples_noalloc", "cc3_serve_footprint",
-            "cc3_ctx_autotune", "cc3_ctx_get_tuning"]
+            "cc3_ctx_autotune", "cc3_ctx_get_tuning", "cc3_cvs_triples"]
 
 
 class CC3Error(RuntimeError):
@@ -94,6 +94,8 @@ def _load():
     L.cc3_ctx_destroy.restype = None
     L.cc3_ctx_set_triples.argtypes = [P, I, P]
     L.cc3_ctx_set_triples.restype = I
+    L.cc3_cvs_triples.argtypes = [I, I, P, I, P]
+    L.cc3_cvs_triples.restype = I
     L.cc3_omega_triples.argtypes = [P, I, P, P, P, P]
     L.cc3_omega_triples.restype = I
     L.cc3_jacobian_triples.argtypes = [P, I, I, P, P, P, P, P, P]
@@ -203,6 +205,21 @@ def cc3_ctx_set_triples(ctx, triples=None):
     arr = np.ascontiguousarray(np.asarray(triples, dtype=np.int32).reshape(-1, 3))
     _check(lib.cc3_ctx_set_triples(ctx, int(arr.shape[0]), arr.ctypes.data_as(ctypes.c_void_p)),
            "cc3_ctx_set_triples")
+
+
+def cc3_cvs_triples(no, core):
+    """The occupied triples i >= j >= k (not all equal) with at least one index
+    in `core` (core-valence separation), as an (n, 3) int32 array."""
+    c = np.ascontiguousarray(np.asarray(core, dtype=np.int32).reshape(-1))
+    cp = c.ctypes.data_as(ctypes.c_void_p) if c.size else None
+    n = lib.cc3_cvs_triples(int(no), int(c.size), cp, 0, None)
+    if n < 0:
+        _check(n, "cc3_cvs_triples")
+    out = np.zeros((max(n, 1), 3), dtype=np.int32)
+    m = lib.cc3_cvs_triples(int(no), int(c.size), cp, int(n), out.ctypes.data_as(ctypes.c_void_p))
+    if m < 0:
+        _check(m, "cc3_cvs_triples")
+    return out[:n]
 
 
 def cc3_omega_triples(ctx, prec, Omega1, Omega2, E_T, stream=None):
@@ -321,6 +338,15 @@ class Context:
 
     def set_triples(self, triples=None):
         cc3_ctx_set_triples(self.ctx, triples)
+
+    def set_cvs(self, core):
+        """Restrict the context to the triples that contain a core orbital of
+        `core` (core-valence separation); returns those triples."""
+        tr = cc3_cvs_triples(self.no, core)
+        if len(tr) == 0:
+            raise CC3Error(CC3_ERR_ARG, "set_cvs: no triple contains a core index")
+        cc3_ctx_set_triples(self.ctx, tr)
+        return tr
 
     def set_slices(self, s):
         cc3_ctx_set_slices(self.ctx, s)

@@ -427,6 +427,31 @@ int cc3_ctx_set_triples(cc3_ctx *c, int ntri, const int *ijk) {
   return CC3_OK;
 }
 
+int cc3_cvs_triples(int no, int ncore, const int *core, int max, int *ijk) {
+  if (no < 0 || ncore < 0 || ncore > no || (ncore > 0 && !core) || max < 0 ||
+      (max > 0 && !ijk))
+    return CC3_ERR_ARG;
+  std::vector<char> is_core((size_t)no, 0);
+  for (int u = 0; u < ncore; ++u) {
+    if (core[u] < 0 || core[u] >= no || is_core[core[u]]) return CC3_ERR_ARG;
+    is_core[core[u]] = 1;
+  }
+  long long n = 0;
+  for (int i = 0; i < no; ++i)
+    for (int j = 0; j <= i; ++j)
+      for (int k = 0; k <= j; ++k) {
+        if (i == k) continue;  // i = j = k contributes nothing
+        if (!is_core[i] && !is_core[j] && !is_core[k]) continue;
+        if (n < max) {
+          ijk[3 * n] = i;
+          ijk[3 * n + 1] = j;
+          ijk[3 * n + 2] = k;
+        }
+        ++n;
+      }
+  return n > 0x7fffffffLL ? CC3_ERR_ARG : (int)n;
+}
+
 int cc3_ctx_counters(const cc3_ctx *c, cc3_counters *out) {
   if (!c || !out) return CC3_ERR_ARG;
   *out = c->counters;
