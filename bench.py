@@ -112,6 +112,22 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
+def cpu_model():
+    """The host CPU's model name (Linux /proc/cpuinfo; the architecture else)."""
+    import platform
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu model", "hardware"):
+                return line.split(":", 1)[1].strip()
+        for line in open("/proc/cpuinfo"):  # Arm: implementer / part numbers
+            if line.lower().startswith("cpu part"):
+                return f"{platform.machine()} (cpu part {line.split(':', 1)[1].strip()})"
+    except OSError:
+        pass
+    return platform.machine()
+
+
 def oracle_sample(inp, seconds_target=15.0, nthreads=0):
     """Time the FP64 oracle on a bounded, seeded sample of triples."""
     import oracle
@@ -135,7 +151,7 @@ def oracle_sample(inp, seconds_target=15.0, nthreads=0):
     dt = time.perf_counter() - t0
     flop = 4.0 * inp.nv ** 4 * w
     return dict(value=flop / dt / 1e12, unit="TFLOP/s", cores=r["threads"],
-                kind="oracle", seconds=dt,
+                kind="oracle", seconds=dt, cpu=cpu_model(),
                 sample=f"{n} of {len(tr)} triples (weight {w} of {inp.no**3 - inp.no}) "
                        f"of the no={inp.no} nv={inp.nv} residual, FP64 C oracle, "
                        f"{r['threads']} OpenMP threads")
@@ -162,7 +178,8 @@ def run_reference(args):
             "config": {"workload": WORKLOAD.replace(f"no={NO} nv={NV}", f"no={args.no} nv={args.nv}"),
                        "no": args.no, "nv": args.nv, "prec": "fp64-cpu-oracle"},
             "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": vals[-1]["cores"],
-                             "kind": "oracle", "sample": vals[-1]["sample"]},
+                             "kind": "oracle", "sample": vals[-1]["sample"],
+                             "cpu": vals[-1]["cpu"]},
             "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -610,7 +627,7 @@ def main():
         line["graph_replay"] = graph
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = {k: v for k, v in oracle_sample(inp).items()
-                                if k in ("value", "unit", "cores", "kind", "sample")}
+                                if k in ("value", "unit", "cores", "kind", "sample", "cpu")}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
