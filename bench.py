@@ -123,7 +123,7 @@ def cpu_model():
         for line in open("/proc/cpuinfo"):  # Arm: implementer / part numbers
             if line.lower().startswith("cpu part"):
                 return f"{platform.machine()} (cpu part {line.split(':', 1)[1].strip()})"
-    except OSError:
+    except Exception:  # an unreadable cpuinfo only loses the label
         pass
     return platform.machine()
 
