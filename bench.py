@@ -128,22 +128,24 @@ def cpu_model():
     return platform.machine()
 
 
-def oracle_sample(inp, seconds_target=15.0, nthreads=0):
-    """Time the FP64 oracle on a bounded, seeded sample of triples."""
+def oracle_sample(inp, seconds_target=15.0, nthreads=0, n=None):
+    """Time the FP64 oracle on a bounded, seeded sample of triples (n triples,
+    or as many as fill ~seconds_target after a calibration run)."""
     import oracle
     from cc3_inputs import unique_triples
     tr = unique_triples(inp.no)
     rng = np.random.default_rng(11)
     order = rng.permutation(len(tr))
-    # calibrate on one triple per thread, then size the sample to ~seconds_target
-    import os as _os
-    threads = len(_os.sched_getaffinity(0)) if nthreads <= 0 else nthreads
-    ncal = min(len(tr), threads)
-    t0 = time.perf_counter()
-    r = oracle.omega_inputs(inp, triples=[tr[x][:3] for x in order[:ncal]], nthreads=nthreads)
-    dt1 = time.perf_counter() - t0
-    threads = r["threads"]
-    n = int(max(ncal, min(len(tr), ncal * seconds_target / max(dt1, 1e-3))))
+    if n is None:
+        # calibrate on one triple per thread, then size the sample to ~seconds_target
+        import os as _os
+        threads = len(_os.sched_getaffinity(0)) if nthreads <= 0 else nthreads
+        ncal = min(len(tr), threads)
+        t0 = time.perf_counter()
+        oracle.omega_inputs(inp, triples=[tr[x][:3] for x in order[:ncal]], nthreads=nthreads)
+        dt1 = time.perf_counter() - t0
+        n = int(max(ncal, min(len(tr), ncal * seconds_target / max(dt1, 1e-3))))
+    n = max(1, min(int(n), len(tr)))
     sel = [tr[x][:3] for x in order[:n]]
     w = sum(tr[x][3] for x in order[:n])
     t0 = time.perf_counter()
@@ -151,7 +153,7 @@ def oracle_sample(inp, seconds_target=15.0, nthreads=0):
     dt = time.perf_counter() - t0
     flop = 4.0 * inp.nv ** 4 * w
     return dict(value=flop / dt / 1e12, unit="TFLOP/s", cores=r["threads"],
-                kind="oracle", seconds=dt, cpu=cpu_model(),
+                kind="oracle", seconds=dt, cpu=cpu_model(), n=n,
                 sample=f"{n} of {len(tr)} triples (weight {w} of {inp.no**3 - inp.no}) "
                        f"of the no={inp.no} nv={inp.nv} residual, FP64 C oracle, "
                        f"{r['threads']} OpenMP threads")
@@ -165,8 +167,10 @@ def run_reference(args):
     inp = make_inputs(args.no, args.nv, seed=0)
     vals = []
     per_step = max(5.0, 60.0 / max(1, args.steps + args.warmup))
+    n = None  # the sample size is calibrated once, on the first warm-up step
     for s in range(args.warmup + args.steps):
-        r = oracle_sample(inp, seconds_target=per_step)
+        r = oracle_sample(inp, seconds_target=per_step, n=n)
+        n = r["n"]
         if s >= args.warmup:
             vals.append(r)
     v = statistics.median([x["value"] for x in vals])
