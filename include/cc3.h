@@ -51,7 +51,9 @@ typedef struct cc3_ctx cc3_ctx;
 typedef struct cc3_server cc3_server;
 
 /* Arithmetic of the bulk contractions.
- * CC3_FP64       native FP64 (DMMA/DFMA) everywhere.
+ * CC3_FP64       native FP64 everywhere: the contractions run as FP64 fused
+ *                multiply-adds on the FP64 pipe (DFMA), the element-wise
+ *                steps and all sums in FP64.
  * CC3_SPLIT_BF16 the dominant contractions run as exact products of
  *                integer-valued BF16 slices of the FP64 operands on the
  *                tensor cores (FP32 accumulation of exact integer sums),
@@ -69,12 +71,18 @@ enum {
   CC3_ERR_OOM = -2,         /* device or host allocation failed               */
   CC3_ERR_CUDA = -3,        /* a CUDA call or kernel launch failed            */
   CC3_ERR_TIMEOUT = -4,     /* a bounded device wait gave up                  */
-  CC3_ERR_DENOM = -5,       /* |w - eps| too small or eps <= 0 somewhere      */
+  CC3_ERR_DENOM = -5,       /* |w - eps| < CC3_DENOM_MIN or eps <= 0 somewhere */
   CC3_ERR_BUSY = -6,        /* server full / request rejected at admission    */
   CC3_ERR_UNSUPPORTED = -7, /* option not available in this build             */
   CC3_ERR_NOT_FOUND = -8,   /* unknown ticket                                  */
   CC3_ERR_CANCELLED = -9    /* request cancelled / server stopped              */
 };
+
+/* Smallest distance |w - eps^{abc}_{ijk}| (Eh) between a Jacobian frequency
+ * and a triples denominator that cc3_jacobian_triples accepts: closer, the
+ * R3 amplitudes (w - eps)^{-1} <mu3|...> sit on a pole of the effective
+ * Jacobian and the call returns CC3_ERR_DENOM instead. */
+#define CC3_DENOM_MIN 1e-6
 
 /* flags of cc3_ctx_create */
 #define CC3_DEVICE_PTRS 1u   /* all pointers of this context are device pointers */
@@ -89,8 +97,10 @@ enum {
 /* Create a context for one problem (no >= 1, 1 <= nv <= 1024).  Uploads and
  * reorders the inputs (paper: integrals are reordered before the triple loop,
  * "Implementation" section).  chol_L may be NULL (naux = 0): then the
- * Jacobian is unavailable (CC3_ERR_ARG).  On success *out owns device memory
- * of about (5 nv^3 no + 4 no^2 nv^2) * 8 bytes plus per-call workspace. */
+ * Jacobian is unavailable (CC3_ERR_ARG).  Returns CC3_ERR_DENOM when some
+ * ground-state denominator eps^{abc}_{ijk} = e_a + e_b + e_c - e_i - e_j - e_k
+ * could be <= 0 (3 min eps_v <= 3 max eps_o).  On success *out owns device
+ * memory of about (5 nv^3 no + 4 no^2 nv^2) * 8 bytes plus per-call workspace. */
 int cc3_ctx_create(cc3_ctx **out, int no, int nv, const double *eps_o,
                    const double *eps_v, const double *t2, const double *g_vvvo,
                    const double *g_ooov, const double *g_ovov,
@@ -133,11 +143,27 @@ int cc3_omega_triples(cc3_ctx *ctx, cc3_prec prec, double *Omega1,
  * with H the T1-transformed Hamiltonian; the R1 dressing of the integrals
  * needs the Cholesky vectors.  The tau3-dependent intermediates of
  * Algorithm 2 are built on first use and cached in the context.
- * rho1[nvec][no][nv], rho2[nvec][no][no][nv][nv]. */
+ * rho1[nvec][no][nv], rho2[nvec][no][no][nv][nv].  Before any device work the
+ * call checks every frequency against the denominators of the context's
+ * triple loop (cc3_denominator_gap) and returns CC3_ERR_DENOM if one of them
+ * comes within CC3_DENOM_MIN of some eps^{abc}_{ijk} (CC3_ERR_ARG for a
+ * non-finite frequency). */
 int cc3_jacobian_triples(cc3_ctx *ctx, cc3_prec prec, int nvec,
                          const double *omega, const double *R1,
                          const double *R2, double *rho1, double *rho2,
                          void *cuda_stream);
+
+/* Smallest |w - eps^{abc}_{ijk}| over every virtual triple (a, b, c) and the
+ * occupied triples of a loop, eps^{abc}_{ijk} = e_a + e_b + e_c - e_i - e_j -
+ * e_k (the R3 denominator of eq. "jcc3" at frequency w; at w = 0 the tau
+ * denominator of Algorithm 1).  Host only, no context needed: eps_o[no],
+ * eps_v[nv] are host arrays; ntri = 0 (ijk may be NULL) means the full loop
+ * i >= j >= k, not all equal, else ijk[3 t + 0..2] lists the triples
+ * (i >= j >= k).  Writes the distance to *gap (1e300 if the loop is empty).
+ * CC3_ERR_ARG for sizes < 1, NULL pointers, a triple out of order or out of
+ * range, or non-finite energies or frequency. */
+int cc3_denominator_gap(int no, int nv, const double *eps_o, const double *eps_v, int ntri,
+                        const int *ijk, double w, double *gap);
 
 /* Counters of the last call on ctx: nominal FLOP (4 nv^4 no^3 per residual,
  * 8 nv^4 no^3 per trial vector, over the triples in the loop), FLOP executed
@@ -161,11 +187,15 @@ int cc3_ctx_counters(const cc3_ctx *ctx, cc3_counters *out);
  * accumulators, reduction partials and contraction tables) comes from one
  * 16 MiB file-scope device array that every GPU loading the library keeps
  * until process exit; it limits the size to no <= 12, nv <= 64 (larger sizes
- * return CC3_ERR_ARG).  The first call on a device looks the array's address
- * up for that device; make that first call before any stream capture.  Calls
- * share the array: calls that overlap on the GPU race.  The call returns after
- * enqueuing its kernels on cuda_stream (it synchronises cuda_stream once, while
- * uploading its tables). */
+ * return CC3_ERR_ARG).  The first call on a device (and the first after that
+ * device's context was reset) looks the array's address up for it; make that
+ * first call before any stream capture.  Calls share the array: calls that
+ * overlap on the GPU race.  Each call reads eps_o and eps_v back to the host
+ * and returns CC3_ERR_DENOM, with nothing enqueued, when some denominator
+ * could be <= 0 (3 min eps_v <= 3 max eps_o), as cc3_ctx_create does.  It
+ * synchronises cuda_stream twice (after reading the orbital energies and after
+ * uploading its tables into the array) and returns after enqueuing its kernels
+ * on cuda_stream. */
 int cc3_omega_triples_noalloc(int no, int nv, const double *eps_o, const double *eps_v,
                               const double *t2, const double *g_vvvo,
                               const double *g_ooov, const double *g_ovov,

@@ -49,6 +49,19 @@
 #include <omp.h>
 #endif
 
+/* Parallel work split.  The triple loops run one triple per thread when
+ * there are at least as many triples as threads; with fewer triples the loop
+ * runs in one thread and the loops over the first virtual index inside each
+ * step are split over the threads instead (each thread then owns whole rows
+ * of the arrays it writes, so every element is summed in the same order
+ * either way). */
+#ifdef _OPENMP
+#define ORACLE_PRAGMA(x) _Pragma(#x)
+#define ORACLE_INNER_FOR ORACLE_PRAGMA(omp parallel for if (!omp_in_parallel()) schedule(static))
+#else
+#define ORACLE_INNER_FOR
+#endif
+
 typedef struct {
   int no, nv;
   const double *eps_o, *eps_v, *t2;
@@ -78,18 +91,26 @@ static void build_B(int no, int nv, const double *t, const double *gvvvo,
                     const double *goovo, int p, int q, int r, double *Bout,
                     long long *flops) {
   size_t nv2 = (size_t)nv * nv;
+  /* each element B[x][y][z] is the sum over d in increasing order, then the
+   * l terms in increasing order; the z loop is innermost so that the
+   * integral block is read along its rows */
+  ORACLE_INNER_FOR
   for (int x = 0; x < nv; ++x)
-    for (int y = 0; y < nv; ++y)
-      for (int z = 0; z < nv; ++z) {
-        double s = 0.0;
-        const double *tr = t + (((size_t)p * no + q) * nv + x) * nv;
-        for (int d = 0; d < nv; ++d)
-          s += tr[d] * gvvvo[(((size_t)y * nv + d) * nv + z) * no + r];
-        for (int l = 0; l < no; ++l)
-          s -= t[(((size_t)p * no + l) * nv + x) * nv + y] *
-               goovo[(((size_t)l * no + q) * nv + z) * no + r];
-        Bout[(size_t)x * nv2 + (size_t)y * nv + z] = s;
+    for (int y = 0; y < nv; ++y) {
+      double *row = Bout + (size_t)x * nv2 + (size_t)y * nv;
+      const double *tr = t + (((size_t)p * no + q) * nv + x) * nv;
+      for (int z = 0; z < nv; ++z) row[z] = 0.0;
+      for (int d = 0; d < nv; ++d) {
+        const double td = tr[d];
+        const double *g = gvvvo + ((size_t)y * nv + d) * nv * no + r;
+        for (int z = 0; z < nv; ++z) row[z] += td * g[(size_t)z * no];
       }
+      for (int l = 0; l < no; ++l) {
+        const double tl = t[(((size_t)p * no + l) * nv + x) * nv + y];
+        const double *g = goovo + ((size_t)l * no + q) * nv * no + r;
+        for (int z = 0; z < nv; ++z) row[z] -= tl * g[(size_t)z * no];
+      }
+    }
   /* dominant term only: the d-sum is one nv x nv^2 x nv contraction */
   if (flops) *flops += 2LL * nv * nv * nv * nv;
 }
@@ -112,13 +133,16 @@ static void build_W(int no, int nv, const double *t, const double *gvvvo,
         continue;
       done[s2] = 1;
       const int *m = PERM6[s2];
-      int v[3];
-      for (v[0] = 0; v[0] < nv; ++v[0])
+      ORACLE_INNER_FOR
+      for (int v0 = 0; v0 < nv; ++v0) {
+        int v[3];
+        v[0] = v0;
         for (v[1] = 0; v[1] < nv; ++v[1])
           for (v[2] = 0; v[2] < nv; ++v[2]) {
             size_t src = (size_t)v[m[0]] * nv2 + (size_t)v[m[1]] * nv + v[m[2]];
             W[(size_t)v[0] * nv2 + (size_t)v[1] * nv + v[2]] += Bscratch[src];
           }
+      }
     }
   }
 }
@@ -128,6 +152,7 @@ static void build_W(int no, int nv, const double *t, const double *gvvvo,
 static void contravariant(int nv, const double *tau, double *tt) {
   size_t nv2 = (size_t)nv * nv;
 #define TAU(a, b, c) tau[(size_t)(a) * nv2 + (size_t)(b) * nv + (c)]
+  ORACLE_INNER_FOR
   for (int a = 0; a < nv; ++a)
     for (int b = 0; b < nv; ++b)
       for (int c = 0; c < nv; ++c)
@@ -162,10 +187,11 @@ static int distinct_perms(const int ijk[3], int maps[6][3]) {
  * m[0], y in slot m[1], z in slot m[2]. */
 static void permuted_view(int nv, const double *tt, const int m[3], double *V) {
   size_t nv2 = (size_t)nv * nv;
-  int s[3];
+  ORACLE_INNER_FOR
   for (int x = 0; x < nv; ++x)
     for (int y = 0; y < nv; ++y)
       for (int z = 0; z < nv; ++z) {
+        int s[3];
         s[m[0]] = x;
         s[m[1]] = y;
         s[m[2]] = z;
@@ -183,6 +209,7 @@ static void contract_omega(const blocks_t *B, const double *V, int p, int q,
                            int r, double *om1, double *omt, long long *flops) {
   int no = B->no, nv = B->nv;
   size_t nv2 = (size_t)nv * nv;
+  ORACLE_INNER_FOR
   for (int a = 0; a < nv; ++a) {
     double s1 = 0.0;
     for (int b = 0; b < nv; ++b)
@@ -190,6 +217,7 @@ static void contract_omega(const blocks_t *B, const double *V, int p, int q,
         s1 += V[(size_t)a * nv2 + (size_t)b * nv + c] * OVOV(B, q, b, r, c);
     om1[(size_t)p * nv + a] += s1;
   }
+  ORACLE_INNER_FOR
   for (int a = 0; a < nv; ++a)
     for (int b = 0; b < nv; ++b) {
       const double *vr = V + (size_t)a * nv2 + (size_t)b * nv;
@@ -202,6 +230,7 @@ static void contract_omega(const blocks_t *B, const double *V, int p, int q,
         omt[(((size_t)p * no + l) * nv + a) * nv + b] -= so;
       }
     }
+  ORACLE_INNER_FOR
   for (int a = 0; a < nv; ++a)
     for (int d = 0; d < nv; ++d) {
       double s = 0.0;
@@ -220,6 +249,7 @@ static void divide_denominator(const blocks_t *B, const int ijk[3], double w,
   int nv = B->nv;
   size_t nv2 = (size_t)nv * nv;
   double eo = B->eps_o[ijk[0]] + B->eps_o[ijk[1]] + B->eps_o[ijk[2]];
+  ORACLE_INNER_FOR
   for (int a = 0; a < nv; ++a)
     for (int b = 0; b < nv; ++b)
       for (int c = 0; c < nv; ++c) {
@@ -295,7 +325,7 @@ int oracle_omega(int no, int nv, const double *eps_o, const double *eps_v,
   double *om1 = (double *)calloc(n1 ? n1 : 1, sizeof(double));
   double *omt = (double *)calloc(n2 ? n2 : 1, sizeof(double));
   long long fl = 0;
-#pragma omp parallel reduction(+ : fl)
+#pragma omp parallel if (nt >= used) reduction(+ : fl)
   {
     double *W = (double *)malloc(nv3 * sizeof(double));
     double *S = (double *)malloc(nv3 * sizeof(double));
@@ -357,7 +387,7 @@ int oracle_prep(int no, int nv, const double *eps_o, const double *eps_v,
   memset(Zv, 0, nzv * sizeof(double));
   memset(Zo, 0, nzo * sizeof(double));
   long long fl = 0;
-#pragma omp parallel reduction(+ : fl)
+#pragma omp parallel if (nt >= used) reduction(+ : fl)
   {
     double *W = (double *)malloc(nv3 * sizeof(double));
     double *S = (double *)malloc(nv3 * sizeof(double));
@@ -378,6 +408,7 @@ int oracle_prep(int no, int nv, const double *eps_o, const double *eps_v,
       for (int u = 0; u < np; ++u) {
         int p = ijk[maps[u][0]], q = ijk[maps[u][1]], r = ijk[maps[u][2]];
         permuted_view(nv, S, maps[u], V);
+        ORACLE_INNER_FOR
         for (int a = 0; a < nv; ++a)
           for (int b = 0; b < nv; ++b)
             for (int d = 0; d < nv; ++d) {
@@ -386,6 +417,7 @@ int oracle_prep(int no, int nv, const double *eps_o, const double *eps_v,
                 s += V[(size_t)a * nv2 + (size_t)b * nv + c] * OVOV(&B, q, d, r, c);
               zv[(((size_t)a * nv + b) * no + p) * nv + d] -= s;
             }
+        ORACLE_INNER_FOR
         for (int a = 0; a < nv; ++a)
           for (int l = 0; l < no; ++l) {
             double s = 0.0;
@@ -419,6 +451,22 @@ static double eri(const double *L, int naux, int n, int p, int q, int r, int s) 
   return v;
 }
 
+/* One block of integrals G[p][q][r][s] = (p0+p q0+q | r0+r s0+s) for
+ * p < np, q < nq, r < nr, s < ns (orbital offsets p0.. into the n orbitals). */
+static double *eri_block(const double *L, int naux, int n, int p0, int np, int q0, int nq,
+                         int r0, int nr, int s0, int ns) {
+  double *G = (double *)malloc(((size_t)np * nq * nr * ns + 1) * sizeof(double));
+  if (!G) return NULL;
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int p = 0; p < np; ++p)
+    for (int q = 0; q < nq; ++q)
+      for (int r = 0; r < nr; ++r)
+        for (int t = 0; t < ns; ++t)
+          G[(((size_t)p * nq + q) * nr + r) * ns + t] =
+              eri(L, naux, n, p0 + p, q0 + q, r0 + r, s0 + t);
+  return G;
+}
+
 /* R1-dressed blocks from the first-order T1 transformation
  * g^_{pqrs} = -[p in v] sum_l R^p_l g_{lqrs} + [q in o] sum_e R^e_q g_{pers}
  *             -[r in v] sum_l R^r_l g_{pqls} + [s in o] sum_e R^e_s g_{pqre}
@@ -427,8 +475,10 @@ static double eri(const double *L, int naux, int n, int p, int q, int r, int s) 
  *   g^_{ljck} =  sum_d R^d_j (ld|ck) - sum_m R^c_m (lj|mk) + sum_d R^d_k (lj|cd)
  *   g^_{jlkc} =  sum_d R^d_l (jd|kc)        g^_{dbkc} = -sum_l R^d_l (lb|kc)
  *   g^_{jbkc} = 0                           F^_{kc} = sum_ld [2(kc|ld)-(kd|lc)] R^d_l
- * The vvvv integrals of the first line are contracted through the Cholesky
- * vectors: sum_e R^e_k (bd|ce) = sum_J L^J_bd (sum_e L^J_ce R^e_k). */
+ * The integrals (pq|rs) = sum_J L^J_pq L^J_rs of the ovvo, vvoo, oooo, oovv and
+ * ovov kinds are formed once as blocks; the vvvv integrals of the first line
+ * are contracted through the Cholesky vectors instead:
+ * sum_e R^e_k (bd|ce) = sum_J L^J_bd (sum_e L^J_ce R^e_k). */
 static void dressed_blocks(int no, int nv, const double *L, int naux,
                            const double *R1, double *hvvvo, double *hoovo,
                            double *hooov, double *hvvov, double *hF) {
@@ -436,7 +486,21 @@ static void dressed_blocks(int no, int nv, const double *L, int naux,
   size_t n2 = (size_t)n * n;
 #define R(i, a) R1[(size_t)(i) * nv + (a)]
 #define V(p) (no + (p))
+  /* Govvo[l][d][c][k] = (ld|ck), Gvvoo[b][d][l][k] = (bd|lk),
+   * Goooo[l][j][m][k] = (lj|mk), Goovv[l][j][c][d] = (lj|cd),
+   * Govov[j][d][k][c] = (jd|kc) */
+  double *Govvo = eri_block(L, naux, n, 0, no, no, nv, no, nv, 0, no);
+  double *Gvvoo = eri_block(L, naux, n, no, nv, no, nv, 0, no, 0, no);
+  double *Goooo = eri_block(L, naux, n, 0, no, 0, no, 0, no, 0, no);
+  double *Goovv = eri_block(L, naux, n, 0, no, 0, no, no, nv, no, nv);
+  double *Govov = eri_block(L, naux, n, 0, no, no, nv, 0, no, no, nv);
+#define OVVO(l, d, c, k) Govvo[(((size_t)(l) * nv + (d)) * nv + (c)) * no + (k)]
+#define VVOO(b, d, l, k) Gvvoo[(((size_t)(b) * nv + (d)) * no + (l)) * no + (k)]
+#define OOOO(l, j, m, k) Goooo[(((size_t)(l) * no + (j)) * no + (m)) * no + (k)]
+#define OOVV(l, j, c, d) Goovv[(((size_t)(l) * no + (j)) * nv + (c)) * nv + (d)]
+#define GOVOV(j, d, k, c) Govov[(((size_t)(j) * nv + (d)) * no + (k)) * nv + (c)]
   double *M = (double *)calloc((size_t)naux * nv * no + 1, sizeof(double));
+#pragma omp parallel for collapse(2) schedule(static)
   for (int J = 0; J < naux; ++J)
     for (int c = 0; c < nv; ++c)
       for (int k = 0; k < no; ++k) {
@@ -452,34 +516,36 @@ static void dressed_blocks(int no, int nv, const double *L, int naux,
         for (int k = 0; k < no; ++k) {
           double s = 0.0;
           for (int l = 0; l < no; ++l)
-            s -= R(l, b) * eri(L, naux, n, l, V(d), V(c), k);
+            s -= R(l, b) * OVVO(l, d, c, k);
           for (int l = 0; l < no; ++l)
-            s -= R(l, c) * eri(L, naux, n, V(b), V(d), l, k);
+            s -= R(l, c) * VVOO(b, d, l, k);
           for (int J = 0; J < naux; ++J)
             s += L[J * n2 + (size_t)V(b) * n + V(d)] *
                  M[((size_t)J * nv + c) * no + k];
           hvvvo[(((size_t)b * nv + d) * nv + c) * no + k] = s;
         }
+#pragma omp parallel for collapse(2) schedule(static)
   for (int l = 0; l < no; ++l)
     for (int j = 0; j < no; ++j)
       for (int c = 0; c < nv; ++c)
         for (int k = 0; k < no; ++k) {
           double s = 0.0;
           for (int d = 0; d < nv; ++d)
-            s += R(j, d) * eri(L, naux, n, l, V(d), V(c), k);
+            s += R(j, d) * OVVO(l, d, c, k);
           for (int m = 0; m < no; ++m)
-            s -= R(m, c) * eri(L, naux, n, l, j, m, k);
+            s -= R(m, c) * OOOO(l, j, m, k);
           for (int d = 0; d < nv; ++d)
-            s += R(k, d) * eri(L, naux, n, l, j, V(c), V(d));
+            s += R(k, d) * OOVV(l, j, c, d);
           hoovo[(((size_t)l * no + j) * nv + c) * no + k] = s;
         }
+#pragma omp parallel for collapse(2) schedule(static)
   for (int j = 0; j < no; ++j)
     for (int l = 0; l < no; ++l)
       for (int k = 0; k < no; ++k)
         for (int c = 0; c < nv; ++c) {
           double s = 0.0;
           for (int d = 0; d < nv; ++d)
-            s += R(l, d) * eri(L, naux, n, j, V(d), k, V(c));
+            s += R(l, d) * GOVOV(j, d, k, c);
           hooov[(((size_t)j * no + l) * no + k) * nv + c] = s;
         }
 #pragma omp parallel for collapse(2) schedule(static)
@@ -489,7 +555,7 @@ static void dressed_blocks(int no, int nv, const double *L, int naux,
         for (int c = 0; c < nv; ++c) {
           double s = 0.0;
           for (int l = 0; l < no; ++l)
-            s -= R(l, d) * eri(L, naux, n, l, V(b), k, V(c));
+            s -= R(l, d) * GOVOV(l, b, k, c);
           hvvov[(((size_t)d * nv + b) * no + k) * nv + c] = s;
         }
   for (int k = 0; k < no; ++k)
@@ -497,11 +563,16 @@ static void dressed_blocks(int no, int nv, const double *L, int naux,
       double s = 0.0;
       for (int l = 0; l < no; ++l)
         for (int d = 0; d < nv; ++d)
-          s += (2.0 * eri(L, naux, n, k, V(c), l, V(d)) -
-                eri(L, naux, n, k, V(d), l, V(c))) * R(l, d);
+          s += (2.0 * GOVOV(k, c, l, d) - GOVOV(k, d, l, c)) * R(l, d);
       hF[(size_t)k * nv + c] = s;
     }
   free(M);
+  free(Govvo); free(Gvvoo); free(Goooo); free(Goovv); free(Govov);
+#undef OVVO
+#undef VVOO
+#undef OOOO
+#undef OOVV
+#undef GOVOV
 #undef R
 #undef V
 }
@@ -549,7 +620,7 @@ int oracle_jacobian(int no, int nv, const double *eps_o, const double *eps_v,
     double *om1 = (double *)calloc(n1 + 1, sizeof(double));
     double *omt = (double *)calloc(n2 + 1, sizeof(double));
     long long fl = 0;
-#pragma omp parallel reduction(+ : fl)
+#pragma omp parallel if (nt >= used) reduction(+ : fl)
     {
       double *W = (double *)malloc(nv3 * sizeof(double));
       double *W2 = (double *)malloc(nv3 * sizeof(double));

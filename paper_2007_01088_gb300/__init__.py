@@ -22,10 +22,12 @@ __all__ = ["CC3_FP64", "CC3_SPLIT_BF16", "CC3_SPLIT_INT8", "CC3_DEVICE_PTRS",
            "CC3_DETERMINISTIC", "CC3Error", "lib", "cc3_ctx_create",
            "cc3_ctx_destroy", "cc3_ctx_set_triples", "cc3_omega_triples",
            "cc3_jacobian_triples", "cc3_ctx_counters", "cc3_ctx_set_slices",
-           "cc3_strerror", "cc3_cvs_triples", "Context", "EXPORTED"]
+           "cc3_strerror", "cc3_cvs_triples", "cc3_denominator_gap", "CC3_DENOM_MIN",
+           "Context", "EXPORTED"]
 
 CC3_FP64, CC3_SPLIT_BF16, CC3_SPLIT_INT8 = 0, 1, 2
 CC3_DEVICE_PTRS, CC3_DETERMINISTIC = 1, 2
+CC3_DENOM_MIN = 1e-6  # Eh, smallest |w - eps| the Jacobian accepts
 (CC3_OK, CC3_ERR_ARG, CC3_ERR_OOM, CC3_ERR_CUDA, CC3_ERR_TIMEOUT, CC3_ERR_DENOM, CC3_ERR_BUSY,
  CC3_ERR_UNSUPPORTED, CC3_ERR_NOT_FOUND, CC3_ERR_CANCELLED) = range(0, -10, -1)
 
@@ -37,7 +39,8 @@ EXPORTED = ["cc3_ctx_create", "cc3_ctx_destroy", "cc3_ctx_set_triples",
             "cc3_serve_cancel", "cc3_serve_stats", "cc3_serve_stop",
             "cc3_debug_split_gemm", "cc3_last_error", "cc3_ctx_set_tracing",
             "cc3_ctx_trace", "cc3_omega_triples_noalloc", "cc3_serve_footprint",
-            "cc3_ctx_autotune", "cc3_ctx_get_tuning", "cc3_cvs_triples"]
+            "cc3_ctx_autotune", "cc3_ctx_get_tuning", "cc3_cvs_triples",
+            "cc3_denominator_gap"]
 
 
 class CC3Error(RuntimeError):
@@ -96,6 +99,8 @@ def _load():
     L.cc3_ctx_set_triples.restype = I
     L.cc3_cvs_triples.argtypes = [I, I, P, I, P]
     L.cc3_cvs_triples.restype = I
+    L.cc3_denominator_gap.argtypes = [I, I, P, P, I, P, D, ctypes.POINTER(D)]
+    L.cc3_denominator_gap.restype = I
     L.cc3_omega_triples.argtypes = [P, I, P, P, P, P]
     L.cc3_omega_triples.restype = I
     L.cc3_jacobian_triples.argtypes = [P, I, I, P, P, P, P, P, P]
@@ -220,6 +225,23 @@ def cc3_cvs_triples(no, core):
     if m < 0:
         _check(m, "cc3_cvs_triples")
     return out[:n]
+
+
+def cc3_denominator_gap(no, nv, eps_o, eps_v, w, triples=None):
+    """Smallest |w - eps^{abc}_{ijk}| over every virtual triple and the occupied
+    triples of the loop (all i >= j >= k, not all equal, when triples is None).
+    Host only."""
+    eo = np.ascontiguousarray(eps_o, dtype=np.float64)
+    ev = np.ascontiguousarray(eps_v, dtype=np.float64)
+    if triples is None or len(triples) == 0:
+        n, tp = 0, None
+    else:
+        arr = np.ascontiguousarray(np.asarray(triples, dtype=np.int32).reshape(-1, 3))
+        n, tp = int(arr.shape[0]), arr.ctypes.data_as(ctypes.c_void_p)
+    gap = ctypes.c_double(0.0)
+    _check(lib.cc3_denominator_gap(int(no), int(nv), _ptr(eo), _ptr(ev), n, tp, float(w),
+                                   ctypes.byref(gap)), "cc3_denominator_gap")
+    return gap.value
 
 
 def cc3_omega_triples(ctx, prec, Omega1, Omega2, E_T, stream=None):

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -196,6 +197,39 @@ size_t ctx_footprint(int no, int nv, int naux, int ntri, bool host_io) {
   d += 2 * (size_t)nv * nv * nv * batch_for(nv, ntri);
   const size_t plans = (size_t)std::max(1, ntri) * 8 * (sizeof(Job) + 2 * sizeof(Term));
   return d * sizeof(double) + plans + 4096;
+}
+
+// Smallest |w - eps^{abc}_{ijk}| with eps^{abc}_{ijk} = e_a + e_b + e_c - e_i
+// - e_j - e_k, over every virtual triple (a, b, c) (all nv^3 of them enter
+// the division) and the occupied triples of the loop.  The sorted pair sums
+// e_b + e_c (b <= c) turn the search over (a, b, c) into nv binary searches
+// per occupied triple.
+double denominator_gap(int no, int nv, const double *eo, const double *ev, int ntri,
+                       const int *ijk, double w) {
+  std::vector<double> pair;
+  pair.reserve((size_t)nv * (nv + 1) / 2);
+  for (int b = 0; b < nv; ++b)
+    for (int c = b; c < nv; ++c) pair.push_back(ev[b] + ev[c]);
+  std::sort(pair.begin(), pair.end());
+  double gap = 1e300;
+  auto one = [&](int i, int j, int k) {
+    const double T = w + eo[i] + eo[j] + eo[k];  // e_a + e_b + e_c closest to T
+    for (int a = 0; a < nv; ++a) {
+      const double x = T - ev[a];
+      const auto it = std::lower_bound(pair.begin(), pair.end(), x);
+      if (it != pair.end()) gap = std::min(gap, std::fabs(*it - x));
+      if (it != pair.begin()) gap = std::min(gap, std::fabs(*(it - 1) - x));
+    }
+  };
+  if (ntri > 0 && ijk) {
+    for (int t = 0; t < ntri; ++t) one(ijk[3 * t], ijk[3 * t + 1], ijk[3 * t + 2]);
+  } else {
+    for (int i = 0; i < no; ++i)
+      for (int j = 0; j <= i; ++j)
+        for (int k = 0; k <= j; ++k)
+          if (!(i == j && j == k)) one(i, j, k);
+  }
+  return gap;
 }
 
 static thread_local char g_last_error[512] = "";
@@ -392,6 +426,8 @@ int cc3_ctx_create(cc3_ctx **out, int no, int nv, const double *eps_o,
     const double emin = 3.0 * *std::min_element(ev.begin(), ev.end()) -
                         3.0 * *std::max_element(eo.begin(), eo.end());
     if (!(emin > 0.0)) { rc = CC3_ERR_DENOM; goto fail; }
+    c->eo_h = eo;
+    c->ev_h = ev;
   }
   if (cudaStreamSynchronize(s) != cudaSuccess) { rc = CC3_ERR_CUDA; goto fail; }
   *out = c;
@@ -450,6 +486,23 @@ int cc3_cvs_triples(int no, int ncore, const int *core, int max, int *ijk) {
         ++n;
       }
   return n > 0x7fffffffLL ? CC3_ERR_ARG : (int)n;
+}
+
+int cc3_denominator_gap(int no, int nv, const double *eps_o, const double *eps_v, int ntri,
+                        const int *ijk, double w, double *gap) {
+  if (no < 1 || nv < 1 || !eps_o || !eps_v || !gap || ntri < 0 || (ntri > 0 && !ijk) ||
+      !std::isfinite(w))
+    return CC3_ERR_ARG;
+  for (int t = 0; t < ntri; ++t) {
+    const int i = ijk[3 * t], j = ijk[3 * t + 1], k = ijk[3 * t + 2];
+    if (!(i < no && i >= j && j >= k && k >= 0)) return CC3_ERR_ARG;
+  }
+  for (int p = 0; p < no; ++p)
+    if (!std::isfinite(eps_o[p])) return CC3_ERR_ARG;
+  for (int a = 0; a < nv; ++a)
+    if (!std::isfinite(eps_v[a])) return CC3_ERR_ARG;
+  *gap = denominator_gap(no, nv, eps_o, eps_v, ntri, ntri > 0 ? ijk : nullptr, w);
+  return CC3_OK;
 }
 
 int cc3_ctx_counters(const cc3_ctx *c, cc3_counters *out) {

@@ -108,6 +108,8 @@ struct cc3_ctx {
   double *eps_o = nullptr, *eps_v = nullptr, *t2 = nullptr, *vvvo = nullptr,
          *oovo = nullptr, *ooov = nullptr, *ovov = nullptr, *F_ov = nullptr,
          *chol = nullptr, *vvoo = nullptr, *oooo = nullptr;
+  // host copies of the orbital energies (denominator checks, plan epilogues)
+  std::vector<double> eo_h, ev_h;
   // triple list (device and host), weights
   std::vector<int> tri_host;  // 3 per triple
   int ntri = 0;
@@ -194,6 +196,11 @@ int jac_z_buffers(cc3_ctx *c, double **Zv, double **Zo, bool zero, cudaStream_t 
 void jac_set_prep(cc3_ctx *c, int prec);  // the cached Z~ are valid, built in prec
 int jac_prep_prec(cc3_ctx *c);            // -1 if the cache is not valid
 int jac_z_terms(cc3_ctx *c, const double *R1v, double *rtv, cudaStream_t s);
+
+// smallest |w - eps^{abc}_{ijk}| over every (a, b, c) and the ntri triples
+// ijk (host arrays; ntri = 0: the full loop); api.cu
+double denominator_gap(int no, int nv, const double *eo, const double *ev, int ntri,
+                       const int *ijk, double w);
 
 // device footprints for admission control (api.cu, jacobian.cu)
 int batch_for(int nv, int ntri);

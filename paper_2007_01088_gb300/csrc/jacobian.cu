@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -551,6 +552,20 @@ extern "C" int cc3_jacobian_triples(cc3_ctx *c, cc3_prec prec, int nvec, const d
     return CC3_FAIL(CC3_ERR_UNSUPPORTED, "deterministic reductions cover the residual only");
   if (prec != CC3_FP64 && prec != CC3_SPLIT_BF16) return CC3_ERR_ARG;
   std::lock_guard<std::mutex> lk(c->mu);
+  // the R3 denominators (w - eps^{abc}_{ijk}) of every vector stay away from 0
+  // (host check on the context's copies of the orbital energies, before any
+  // device work)
+  for (int v = 0; v < nvec; ++v) {
+    if (!std::isfinite(omega[v])) return CC3_FAIL(CC3_ERR_ARG, "non-finite frequency");
+    bool seen = false;
+    for (int u = 0; u < v; ++u) seen = seen || omega[u] == omega[v];
+    if (seen || c->ntri == 0) continue;
+    const double gap = denominator_gap(c->no, c->nv, c->eo_h.data(), c->ev_h.data(), c->ntri,
+                                       c->tri_host.data(), omega[v]);
+    if (gap < CC3_DENOM_MIN)
+      return CC3_FAIL(CC3_ERR_DENOM, "a frequency lies within CC3_DENOM_MIN of a triples "
+                                     "denominator");
+  }
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const int no = c->no, nv = c->nv;
   const size_t n1 = (size_t)no * nv, nt2 = (size_t)no * no * nv * nv;

@@ -10,12 +10,16 @@
 //
 // The scratch array below is part of the library image: every GPU that loads
 // libcc3 holds it (16 MiB) until the process exits.  Its device address is
-// looked up once per device on the first call (cudaGetSymbolAddress with that
-// device current).  All calls share the array, so calls that overlap on the
-// GPU race; the contents left by the previous call are not relied on (the
-// accumulators are cleared at the start of each call).
+// looked up once per device (cudaGetSymbolAddress with that device current) on
+// the first call, and again only if that device's context has changed since
+// (after a cudaDeviceReset the module is loaded anew and the old address is
+// stale).  All calls share the array, so calls that overlap on the GPU race;
+// the contents left by the previous call are not relied on (the accumulators
+// are cleared at the start of each call).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -30,22 +34,49 @@ constexpr int kMaxNo = 12, kMaxNv = 64;
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
 std::mutex g_mu;
-double *g_scratch_ptr[64] = {nullptr};
+struct ScratchSlot {
+  CUcontext ctx = nullptr;  // the device context the address belongs to
+  double *ptr = nullptr;
+};
+ScratchSlot g_slot[64];
 
-// Device address of the scratch array for the current device (set-up on the
-// first call per device).
+// The calling thread's current driver context (the runtime's primary context
+// of the current device once it is initialised), through the runtime's
+// driver entry point so that the library does not link the driver library.
+CUcontext current_context() {
+  using GetCurrent = CUresult (*)(CUcontext *);
+  static GetCurrent fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<GetCurrent>(f);
+  });
+  CUcontext c = nullptr;
+  if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+  return c;
+}
+
+// Device address of the scratch array for the current device: set up on the
+// first call per device, and again when the device's context changed.
 int scratch_for_current_device(double **out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
     return CC3_FAIL(CC3_ERR_CUDA, "no current device");
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_ptr[dev]) {
+  ScratchSlot &S = g_slot[dev];
+  CUcontext now = current_context();
+  if (!S.ptr || !now || now != S.ctx) {
     void *p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) return CC3_FAIL(CC3_ERR_CUDA, cudaGetErrorString(e));
-    g_scratch_ptr[dev] = static_cast<double *>(p);
+    S.ptr = static_cast<double *>(p);
+    S.ctx = current_context();  // the lookup made the device's context current
   }
-  *out = g_scratch_ptr[dev];
+  *out = S.ptr;
   return CC3_OK;
 }
 
@@ -85,11 +116,17 @@ extern "C" int cc3_omega_triples_noalloc(int no, int nv, const double *eps_o,
           tri.push_back(k);
         }
   const int ntri = (int)(tri.size() / 3);
-  std::vector<double> eo(no);
+  std::vector<double> eo(no), ev(nv);
   if (cudaMemcpyAsync(eo.data(), eps_o, sizeof(double) * no, cudaMemcpyDeviceToHost, s) !=
           cudaSuccess ||
+      cudaMemcpyAsync(ev.data(), eps_v, sizeof(double) * nv, cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
-    return CC3_FAIL(CC3_ERR_CUDA, "reading eps_o");
+    return CC3_FAIL(CC3_ERR_CUDA, "reading the orbital energies");
+  // every denominator eps^{abc}_{ijk} must be > 0 (the rule of cc3_ctx_create)
+  if (!(3.0 * *std::min_element(ev.begin(), ev.end()) -
+            3.0 * *std::max_element(eo.begin(), eo.end()) > 0.0))
+    return CC3_FAIL(CC3_ERR_DENOM, "a triples denominator could be <= 0");
   const TermSet set{B_T2, B_VVVO, B_OOVO};
   Plan P[4];  // AB, C, residual (64x64 tiles), residual (thin tiles); all triples
   std::vector<int> j0[4];

@@ -241,3 +241,44 @@ def test_prep_intermediates_give_dressed_contractions(tiny):
     via_z = (np.einsum("abid,ld->ilab", z["Zv"], R1[0])
              - np.einsum("ajil,ld->ijad", z["Zo"], R1[0]))
     assert rel(via_z, direct) < 1e-12
+
+
+# --- the matrix-product form of the restricted loop -------------------------
+# oracle.matrix_form takes the same steps with numpy tensor products; it serves
+# the GPU tests at the batched-Jacobian shape (nv = 200), where the C loops take
+# minutes per triple.  Pinned here to the C oracle (itself pinned above) on
+# general non-symmetric blocks, triple subsets and non-zero frequencies.
+def test_matrix_form_residual_equals_c_oracle():
+    from oracle import matrix_form as MF
+    inp = make_inputs(4, 7, 3)
+    t1 = np.random.default_rng(4).normal(0, 0.2, size=(4, 7))
+    b = oracle.t1_transform(inp, t1)
+    tr = [t[:3] for t in unique_triples(4)]
+    for sel in (None, tr[::3]):
+        r1 = oracle.omega(4, 7, inp.eps_o, inp.eps_v, inp.t2, b, triples=sel)
+        r2 = MF.omega(4, 7, inp.eps_o, inp.eps_v, inp.t2, b, triples=sel)
+        for k in ("omega1", "omega2", "omega2_tilde"):
+            assert rel(r2[k], r1[k]) < 1e-13, k
+        assert abs(r2["E_T"] - r1["E_T"]) <= 1e-13 * abs(r1["E_T"])
+
+
+def test_matrix_form_dressed_blocks_equal_c_oracle(tiny):
+    from oracle import matrix_form as MF
+    inp, R1, _ = tiny
+    ref = oracle.dressed_blocks(inp, R1[1])
+    mine = MF.dressed_blocks(inp.no, inp.nv, inp.chol_L, R1[1])
+    for k, v in ref.items():
+        assert rel(mine[k], v) < 1e-13, k
+
+
+def test_matrix_form_jacobian_equals_c_oracle():
+    from oracle import matrix_form as MF
+    inp = make_inputs(4, 9, 6)
+    R1, R2 = make_trial_vectors(4, 9, 3, seed=8)
+    w = [0.25, 0.0, -0.1]
+    tr = [t[:3] for t in unique_triples(4)]
+    for sel in (None, [tr[1], tr[-1], tr[4]]):
+        ref = oracle.jacobian(inp, R1, R2, w, triples=sel)
+        mine = MF.jacobian(inp, R1, R2, w, triples=sel)
+        assert rel(mine["rho1"], ref["rho1"]) < 1e-12
+        assert rel(mine["rho2"], ref["rho2"]) < 1e-12
