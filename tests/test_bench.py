@@ -62,8 +62,26 @@ def test_serve_stream_is_seeded():
     b = bench.serve_stream(6, 4.0, 3, 5, seed=3)
     assert len(a) == len(b) == 6
     for x, y in zip(a, b):
-        assert all(x[k] == y[k] for k in ("t", "kind", "no", "nv", "nvec"))
+        assert all(x[k] == y[k] for k in ("t", "kind", "no", "nv", "nvec", "flop", "bytes"))
         assert np.array_equal(x["inp"].t2, y["inp"].t2)
         assert 3 <= x["no"] <= 5 and 6 * x["no"] - 1 <= x["nv"] <= 10 * x["no"] + 1
+        mult = 1 if x["kind"] == "omega" else 2 * x["nvec"]
+        assert x["flop"] == 4.0 * x["nv"] ** 4 * (x["no"] ** 3 - x["no"]) * mult
     times = [x["t"] for x in a]
     assert times[0] == 0.0 and np.all(np.diff(times) >= 0)
+
+
+def test_serving_stream_is_the_mixed_workload():
+    # 256 requests, Poisson 4/s, no ~ U{4..24}, nv = round(no * U[6, 10]),
+    # residual or Jacobian with 1-6 vectors: the sizes are drawn without inputs
+    sys.path.insert(0, ROOT)
+    import bench
+    plan = bench.serve_plan(256, 4.0, 4, 24)
+    assert len(plan) == 256
+    nos = [q["no"] for q in plan]
+    assert min(nos) >= 4 and max(nos) <= 24 and len(set(nos)) > 15
+    kinds = [q["kind"] for q in plan]
+    assert 80 < kinds.count("omega") < 176
+    assert all(1 <= q["nvec"] <= 6 for q in plan)
+    rate = len(plan) / plan[-1]["t"]
+    assert 3.0 < rate < 5.0
