@@ -84,7 +84,7 @@ static const int PERM6[6][3] = {{0, 1, 2}, {1, 0, 2}, {2, 1, 0},
                                 {0, 2, 1}, {1, 2, 0}, {2, 0, 1}};
 
 /* B_{pqr}[x][y][z] = sum_d t^{xd}_{pq} g_{ydzr} - sum_l t^{xy}_{pl} g_{lqzr}
- * (the bracket of the tau line of Algorithms 1 and 2 for one ordered triple).
+ * (the bracket that defines tau in Algorithms 1 and 2, for one ordered triple).
  * t and the two integral blocks are passed separately so that the Jacobian can
  * call the same builder with (R2, g) and (t2, g-hat). */
 static void build_B(int no, int nv, const double *t, const double *gvvvo,
@@ -243,7 +243,7 @@ static void contract_omega(const blocks_t *B, const double *V, int p, int q,
 }
 
 /* Denominator (w - eps^{abc}_{ijk}); tau = W / (w - eps), so w = 0 gives the
- * tau line of Algorithm 1, tau = -W / eps. */
+ * tau of Algorithm 1, tau = -W / eps. */
 static void divide_denominator(const blocks_t *B, const int ijk[3], double w,
                                const double *W, double *tau) {
   int nv = B->nv;

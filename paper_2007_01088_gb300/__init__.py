@@ -40,7 +40,7 @@ EXPORTED = ["cc3_ctx_create", "cc3_ctx_destroy", "cc3_ctx_set_triples",
             "cc3_debug_split_gemm", "cc3_last_error", "cc3_ctx_set_tracing",
             "cc3_ctx_trace", "cc3_omega_triples_noalloc", "cc3_serve_footprint",
             "cc3_ctx_autotune", "cc3_ctx_get_tuning", "cc3_cvs_triples",
-            "cc3_denominator_gap"]
+            "cc3_denominator_gap", "cc3_debug_wait_timeout"]
 
 
 class CC3Error(RuntimeError):
@@ -111,6 +111,8 @@ def _load():
     L.cc3_ctx_set_slices.restype = I
     L.cc3_debug_split_gemm.argtypes = [I, I, I, P, P, P, I]
     L.cc3_debug_split_gemm.restype = I
+    L.cc3_debug_wait_timeout.argtypes = [D]
+    L.cc3_debug_wait_timeout.restype = I
     L.cc3_ctx_set_tracing.argtypes = [P, I]
     L.cc3_ctx_set_tracing.restype = I
     L.cc3_ctx_trace.argtypes = [P, ctypes.POINTER(Trace)]
@@ -301,6 +303,12 @@ def cc3_ctx_get_tuning(ctx):
 
 def cc3_ctx_set_slices(ctx, slices):
     _check(lib.cc3_ctx_set_slices(ctx, int(slices)), "cc3_ctx_set_slices")
+
+
+def cc3_debug_wait_timeout(limit_s=1e-3):
+    """Runs a bounded device wait that cannot succeed; returns its status
+    (CC3_ERR_TIMEOUT expected)."""
+    return lib.cc3_debug_wait_timeout(float(limit_s))
 
 
 def cc3_debug_split_gemm(A, B, slices=6):

@@ -40,7 +40,7 @@ int launch_contravariant(const double *tau_cab, double *tt_abc, int nv,
 }
 
 // Omega2^{ab}_{ij} = (1/3) P^{ab}_{ij} (2 X^{ab}_{ij} + X^{ba}_{ij}),
-// P^{ab}_{ij} Y^{ab}_{ij} = Y^{ab}_{ij} + Y^{ba}_{ji}   (Algorithm 1, last line)
+// P^{ab}_{ij} Y^{ab}_{ij} = Y^{ab}_{ij} + Y^{ba}_{ji}   (Algorithm 1, the back-transform)
 __global__ void back_transform_kernel(const double *__restrict__ X,
                                       double *__restrict__ Om, int no, int nv) {
   const long long nv2 = (long long)nv * nv, n = (long long)no * no * nv2;

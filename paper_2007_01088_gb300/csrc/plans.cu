@@ -1,6 +1,6 @@
 // Host-side construction of contraction job lists for the FP64 engine.
 //
-// Triples amplitudes (paper, Algorithm 1, tau line, and eq. "permutation"):
+// Triples amplitudes (paper, Algorithm 1, the tau amplitudes, and eq. "permutation"):
 //   W^{abc}_{ijk} = P^{abc}_{ijk} B,  B^{xyz}_{pqr} = sum_d t^{xd}_{pq} gv_{ydzr}
 //                                                  - sum_l t^{xy}_{pl} go_{lqzr}
 // with gv[y][d][z][r] the vvvo block and go[l][q][z][r] the oovo block (both

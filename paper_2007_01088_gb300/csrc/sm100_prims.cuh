@@ -1,6 +1,6 @@
 // Inline-PTX primitives for sm_100-family (sm_103a) kernels: mbarriers with
-// bounded waits, TMA tensor loads, tensor-memory allocation and loads, and
-// the shared-memory / instruction descriptors of tcgen05.mma (kind::f16).
+// bounded waits, bulk copies, tensor-memory allocation and loads, and the
+// shared-memory / instruction descriptors of tcgen05.mma (kind::f16).
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -68,17 +68,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
   return true;
 }
 
-// 4-D tiled TMA load into shared memory, completion counted on `bar`.
-__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar,
-                                            int c0, int c1, int c2, int c3) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2),
-      "r"(c3)
-      : "memory");
-}
-
 // Contiguous bulk copy global -> shared (16-byte aligned, size % 16 == 0),
 // completion counted on `bar` (transaction bytes).
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
@@ -87,17 +76,6 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
           smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// 5-D tiled TMA load
-__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, uint64_t *bar,
-                                            int c0, int c1, int c2, int c3, int c4) {
-  asm volatile(
-      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2),
-      "r"(c3), "r"(c4)
       : "memory");
 }
 
@@ -118,8 +96,19 @@ __device__ __forceinline__ bool mbar_wait_sleep(uint64_t *bar, uint32_t parity, 
   return true;
 }
 
-__device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map) {
-  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+// Bounded wait that ignores the error word: for the exit path of a CTA that
+// has given up, which must still let its own bulk copies and tensor-core
+// operations finish (they write shared and tensor memory) before it frees
+// them.  Returns false after about limit_ns.
+__device__ __forceinline__ bool mbar_wait_quiet(uint64_t *bar, uint32_t parity,
+                                                uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    __nanosleep(128);
+    if (globaltimer_ns() - t0 > limit_ns) return false;
+  }
+  return true;
 }
 
 // ---- tensor memory -----------------------------------------------------------
@@ -194,31 +183,6 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
       : "memory");
 }
 
-// 32 lanes x 16 columns of 32 bit: thread t of the warp gets lane (base + t)
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-// 32 lanes x 8 columns of 32 bit
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
-  uint32_t r[8];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
 // 32 lanes x 4 columns of 32 bit
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float *v) {
   uint32_t r[4];
@@ -234,31 +198,6 @@ __device__ __forceinline__ void tmem_wait_ld() {
 }
 
 // ---- descriptors ---------------------------------------------------------------
-// Shared-memory matrix descriptor, K-major operand with 32-byte swizzling: rows
-// of 16 bf16 (32 bytes), 8-row core groups 256 bytes apart.
-__device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFF);          // start address
-  d |= (uint64_t)(1) << 16;                         // leading byte offset (unused)
-  d |= (uint64_t)((256 >> 4) & 0x3FFF) << 32;       // stride byte offset
-  d |= (uint64_t)1 << 46;                           // descriptor version (sm100)
-  d |= (uint64_t)6 << 61;                           // SWIZZLE_32B
-  return d;
-}
-
-// Shared-memory matrix descriptor, K-major operand without swizzling: core
-// matrices of 8 rows x 16 bytes (128 contiguous bytes), the two K halves of a
-// 16-element K step 128 bytes apart (leading byte offset), 8-row groups 256
-// bytes apart (stride byte offset).
-__device__ __forceinline__ uint64_t smem_desc_noswz(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFF);          // start address
-  d |= (uint64_t)((128 >> 4) & 0x3FFF) << 16;       // leading byte offset (K direction)
-  d |= (uint64_t)((256 >> 4) & 0x3FFF) << 32;       // stride byte offset (M/N direction)
-  d |= (uint64_t)1 << 46;                           // descriptor version (sm100)
-  return d;                                         // layout type 0: no swizzle
-}
-
 // Shared-memory matrix descriptor, canonical K-major layout without swizzle:
 // core matrices of 8 rows x 16 bytes, the two K halves 128 bytes apart and
 // consecutive 8-row groups `sbo` bytes apart.

@@ -27,7 +27,9 @@
 // a drain point the issuer queues the next step's level >= 4 products before
 // it waits for the drain, so the drain overlaps tensor work.  Every wait is
 // bounded: on timeout the CTA sets an error word that the host turns into
-// CC3_ERR_TIMEOUT.
+// CC3_ERR_TIMEOUT; before it exits, the CTA waits (bounded again) for its own
+// bulk copies and tensor-core products in flight, then frees its tensor
+// memory.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -171,7 +173,7 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t full[S_STAGES], empty[S_STAGES];
-  __shared__ __align__(8) uint64_t accfull, accempty, drainfull, drainempty;
+  __shared__ __align__(8) uint64_t accfull, accempty, drainfull, drainempty, mmafin;
   __shared__ __align__(8) uint64_t tfull[TQ], tempty[TQ];
   __shared__ long long tq[TQ];
   // the producer decodes each tile once for everyone (tinfo, with tq) and
@@ -200,6 +202,7 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
     mbar_init(&accempty, S_EPI_WARPS);
     mbar_init(&drainfull, 1);
     mbar_init(&drainempty, S_EPI_WARPS);
+    mbar_init(&mmafin, 1);
     err = 0;
     fence_barrier_init();
   }
@@ -388,9 +391,10 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
         }
         if (bad) break;
       }
-      // let every issued copy land before the CTA may exit (bounded)
+      // let every issued copy land before the CTA may exit, also after a
+      // give-up (bounded; the wait ignores the error word)
       for (int i = (issued > S_STAGES ? issued - S_STAGES : 0); i < issued; ++i)
-        mbar_wait(&full[i % S_STAGES], (i / S_STAGES) & 1, &err, 500000000ull);
+        mbar_wait_quiet(&full[i % S_STAGES], (i / S_STAGES) & 1, 500000000ull);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -445,6 +449,10 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
         if (!ok) break;
         umma_commit(&accfull);
       }
+      // every product this thread issued has landed in tensor memory before
+      // the CTA frees it, also after a give-up (bounded)
+      umma_commit(&mmafin);
+      mbar_wait_quiet(&mmafin, 0, 500000000ull);
     }
   } else {
     // epilogue: warps 2..17

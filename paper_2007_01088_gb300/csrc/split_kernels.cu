@@ -1,6 +1,6 @@
 // Element-wise kernels of the split path: exact digit extraction into BF16
 // slices, max-abs reductions, and the per-triple double-float contravariant
-// combination (paper, Algorithm 1, second line of the triple loop).
+// combination (paper, Algorithm 1: tau~ from tau with i, j, k fixed).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 

@@ -39,7 +39,10 @@ def triple_partition(no: int, world: int, rank: int):
 
 def omega_sharded(ctx, prec, out, group=None):
     """Sharded residual: this rank's triples, then a sum all-reduce of
-    (Omega1, Omega2, E_T) over the process group (device tensors in `out`)."""
+    (Omega1, Omega2, E_T) over the process group.  `out` holds torch tensors:
+    on the device for a device-pointer context (NCCL), in host memory for a
+    host-pointer context (gloo).  The context is left restricted to this
+    rank's triples."""
     import torch.distributed as dist
     world = dist.get_world_size(group)
     rank = dist.get_rank(group)
