@@ -7,9 +7,12 @@ seeded input generator in ``cc3_inputs``.
 
 Two independent forms of the same result (Paul, Myhre, Koch, arXiv 2007.01088):
 
-* ``omega`` / ``prep`` / ``jacobian``: the restricted-loop algorithms written
-  out in plain C (``cc3_oracle.c``; Algorithm 1, Algorithm 2 and the right
-  Jacobian transformation reconstructed from eq. "jcc3").
+* ``omega`` / ``prep`` / ``jacobian`` / ``left_jacobian``: the restricted-loop
+  algorithms written out in plain C (``cc3_oracle.c``; Algorithm 1,
+  Algorithm 2, the right Jacobian transformation reconstructed from eq. "jcc3"
+  and its transpose).
+* ``matrix_form``: the same restricted loops with numpy matrix products as
+  steps, for test shapes where the C loops are too slow.
 * ``definition.omega_full``: the plain definition over the full
   nv^3 no^3 tensor (every ordered i,j,k), numpy, tiny sizes only.
 
@@ -60,6 +63,9 @@ def _load():
             lib.oracle_jacobian.argtypes = ([I, I] + [P] * 9 + [P, I, I, P, P, P]
                                             + [I, P, P, P, P, I])
             lib.oracle_jacobian.restype = I
+            lib.oracle_left_jacobian.argtypes = ([I, I] + [P] * 9 + [P, I, I, P, P, P]
+                                                 + [I, P, P, P, P, I])
+            lib.oracle_left_jacobian.restype = I
             lib.oracle_dressed_blocks.argtypes = [I, I, P, I, P, P, P, P, P, P]
             lib.oracle_dressed_blocks.restype = None
             _lib = lib
@@ -167,6 +173,37 @@ def jacobian(inp, R1, R2, w, triples=None, nthreads=0):
     if used < 0:
         raise MemoryError("oracle_jacobian failed")
     return dict(rho1=rho1, rho2=rho2, flops=fl.value, threads=used)
+
+
+def left_jacobian(inp, L1, L2, w, triples=None, nthreads=0):
+    """Left (transpose) Jacobian transformation of left vectors L1[n][i][a],
+    L2[n][i][j][a][b] at frequencies w[n]: the exact transpose of
+    ``jacobian`` under the plain inner product over (R1, R2) elements
+    (sigma2 projected on pair-symmetric tensors).  Returns dict(sigma1,
+    sigma2, flops)."""
+    lib = _load()
+    no, nv = inp.no, inp.nv
+    if inp.chol_L is None:
+        raise ValueError("the Jacobian needs the Cholesky vectors")
+    b = symmetric_blocks(inp)
+    L1 = _c(L1).reshape(-1, no, nv)
+    nvec = L1.shape[0]
+    L2 = _c(L2).reshape(nvec, no, no, nv, nv)
+    w = _c(np.broadcast_to(np.asarray(w, dtype=np.float64), (nvec,)))
+    L = _c(inp.chol_L)
+    s1 = np.zeros((nvec, no, nv))
+    s2 = np.zeros((nvec, no, no, nv, nv))
+    fl = ctypes.c_longlong(0)
+    nt, tri = _triples_arg(triples)
+    used = lib.oracle_left_jacobian(no, nv, _p(_c(inp.eps_o)), _p(_c(inp.eps_v)),
+                                    _p(_c(inp.t2)), _p(b["vvvo"]), _p(b["oovo"]),
+                                    _p(b["ooov"]), _p(b["ovov"]), _p(b["vvov"]),
+                                    _p(b["F_ov"]), _p(L), int(L.shape[0]), nvec,
+                                    _p(w), _p(L1), _p(L2), nt, _p(tri), _p(s1),
+                                    _p(s2), ctypes.byref(fl), int(nthreads))
+    if used < 0:
+        raise MemoryError("oracle_left_jacobian failed")
+    return dict(sigma1=s1, sigma2=s2, flops=fl.value, threads=used)
 
 
 def dressed_blocks(inp, R1):

@@ -15,6 +15,10 @@
  *                     the four contractions for every distinct permutation of
  *                     (i,j,k), and the back-transform (1/3) P^{ab}_{ij}(2X+X^{ba}).
  *   oracle_prep       Algorithm 2 (Z^v and Z^o intermediates).
+ *   oracle_left_jacobian  The left (transpose) Jacobian transformation: the
+ *                     covariant L3 amplitudes, their contravariant form and
+ *                     their contractions, read as the exact transpose of the
+ *                     right transformation below.
  *   oracle_jacobian   The right CC3 Jacobian transformation of trial vectors,
  *                     reconstructed from eq. "jcc3": R3 = (w - eps)^{-1}
  *                     <mu3|[H,R2] + [[H,R1],T2]>, rho = <mu1|[H,R3]> and
@@ -668,6 +672,345 @@ int oracle_jacobian(int no, int nv, const double *eps_o, const double *eps_v,
     fl_total += fl;
     free(om1); free(omt); free(hvvvo); free(hoovo); free(hooov); free(hvvov);
     free(hF); free(zero_ovov);
+  }
+  if (flops) *flops = fl_total;
+  free(T);
+  return used;
+}
+
+/* ------------------------------------------------------------------------
+ * Left (transpose) Jacobian transformation, triples part.
+ *
+ * The paper's transpose-Jacobian paragraph (section "Implementation") builds
+ * the covariant L3 amplitudes with contractions like those of tau3 plus outer
+ * products, takes their contravariant form by eq. "contra_t", and contracts
+ * them back, after a separate loop that contracts tau3; Algorithm 3 gives the
+ * same L3 amplitudes (an outer product of L1 with g_ovov, one of L2 with F,
+ * and two contractions of L2 with integrals, permuted by P and divided by
+ * (w - eps)).  Here the left transformation is read as the exact transpose of the right
+ * one (oracle_jacobian) under the plain inner product over the elements of
+ * (R1, R2): sigma = J(w)^T L, so that sum L.rho(R) = sum sigma(L).R for every
+ * pair-symmetric R2.  With Lt2 = the back-transform applied to L2 (the
+ * back-transform (1/3) P^{ab}_{ij}(2X + X^{ba}) is its own transpose) that
+ * gives, per ordered triple (p,q,r) (a distinct permutation of a loop triple,
+ * V the contravariant amplitudes viewed with x, y, z in the slots of p, q, r):
+ *
+ *   X_pqr[x][y][z] = L1[p][x] g_{qyrz} + Lt2[p][q][x][y] F[r][z]
+ *                  + sum_d Lt2[p][q][x][d] g_{dyrz} - sum_l Lt2[p][l][x][y] g_{qlrz}
+ *   L3 = (w - eps)^{-1} P X,  V = contravariant(L3)
+ *   sigma2[p][q][x][d] += sum_yz V g_{ydzr}      sigma2[p][l][x][y] -= sum_z V g_{lqzr}
+ *   G[y][d][z][r]      += sum_x V t[p][q][x][d]  H[l][q][z][r]      += sum_xy V t[p][l][x][y]
+ *
+ * and, from the tau3 loop (V = contravariant tau3),
+ *   Q[r][z] += sum_xy Lt2[p][q][x][y] V[x][y][z]
+ *   sigma1[l][d] -= sum_xyz Lt2[p][l][x][y] V[x][y][z] (qd|rz)
+ *                 + sum_xyz Lt2[p][q][x][d] V[x][y][z] (ly|rz)
+ * (the transposes of the tau~3 . g^_ooov and tau~3 . g^_vvov terms).  After
+ * the loops the R1 dependence of the dressed integrals is transposed:
+ *   sigma1 += F^(Q) (F^_kc = sum_ld [2(kc|ld) - (kd|lc)] x_ld is symmetric)
+ *   sigma1[l][b] -= sum G[b][d][c][k] (ld|ck)   sigma1[l][c] -= sum G[b][d][c][k] (bd|lk)
+ *   sigma1[k][e] += sum G[b][d][c][k] (bd|ce)   (vvvv through the Cholesky vectors)
+ *   sigma1[j][d] -= sum H[l][j][c][k] (ld|ck)   sigma1[m][c] += sum H[l][j][c][k] (lj|mk)
+ *   sigma1[k][d] -= sum H[l][j][c][k] (lj|cd)
+ *   sigma2 <- (sigma2 + sigma2^{T pair}) / 2.
+ * Cost: 8 nv^4 per distinct permutation (tau3, X, sigma2 and G, 2 nv^4 each).
+ * Symmetric integrals (T1 = 0), as oracle_jacobian.
+ * ---------------------------------------------------------------------- */
+
+/* X_pqr of the L3 amplitudes (see above); lt2 = the back-transformed L2 */
+static void build_X(const blocks_t *B, const double *l1, const double *lt2, int p, int q,
+                    int r, double *Xout, long long *flops) {
+  int no = B->no, nv = B->nv;
+  size_t nv2 = (size_t)nv * nv;
+  ORACLE_INNER_FOR
+  for (int x = 0; x < nv; ++x)
+    for (int y = 0; y < nv; ++y) {
+      double *row = Xout + (size_t)x * nv2 + (size_t)y * nv;
+      const double l1x = l1[(size_t)p * nv + x];
+      const double lxy = lt2[(((size_t)p * no + q) * nv + x) * nv + y];
+      for (int z = 0; z < nv; ++z)
+        row[z] = l1x * OVOV(B, q, y, r, z) + lxy * B->F_ov[(size_t)r * nv + z];
+      for (int d = 0; d < nv; ++d) {
+        const double ld = lt2[(((size_t)p * no + q) * nv + x) * nv + d];
+        for (int z = 0; z < nv; ++z) row[z] += ld * VVOV(B, d, y, r, z);
+      }
+      for (int l = 0; l < no; ++l) {
+        const double ll = lt2[(((size_t)p * no + l) * nv + x) * nv + y];
+        for (int z = 0; z < nv; ++z) row[z] -= ll * OOOV(B, q, l, r, z);
+      }
+    }
+  if (flops) *flops += 2LL * nv * nv * nv * nv;
+}
+
+/* L3 numerator P X for one unique triple (placement as in build_W) */
+static void build_PX(const blocks_t *B, const double *l1, const double *lt2, const int ijk[3],
+                     double *W, double *Xs, long long *flops) {
+  int nv = B->nv;
+  size_t nv2 = (size_t)nv * nv, nv3 = nv2 * nv;
+  memset(W, 0, nv3 * sizeof(double));
+  int done[6] = {0, 0, 0, 0, 0, 0};
+  for (int s = 0; s < 6; ++s) {
+    if (done[s]) continue;
+    int p = ijk[PERM6[s][0]], q = ijk[PERM6[s][1]], r = ijk[PERM6[s][2]];
+    build_X(B, l1, lt2, p, q, r, Xs, flops);
+    for (int s2 = s; s2 < 6; ++s2) {
+      if (ijk[PERM6[s2][0]] != p || ijk[PERM6[s2][1]] != q || ijk[PERM6[s2][2]] != r) continue;
+      done[s2] = 1;
+      const int *m = PERM6[s2];
+      ORACLE_INNER_FOR
+      for (int v0 = 0; v0 < nv; ++v0) {
+        int v[3];
+        v[0] = v0;
+        for (v[1] = 0; v[1] < nv; ++v[1])
+          for (v[2] = 0; v[2] < nv; ++v[2]) {
+            size_t src = (size_t)v[m[0]] * nv2 + (size_t)v[m[1]] * nv + v[m[2]];
+            W[(size_t)v[0] * nv2 + (size_t)v[1] * nv + v[2]] += Xs[src];
+          }
+      }
+    }
+  }
+}
+
+int oracle_left_jacobian(int no, int nv, const double *eps_o, const double *eps_v,
+                         const double *t2, const double *vvvo, const double *oovo,
+                         const double *ooov, const double *ovov, const double *vvov,
+                         const double *F_ov, const double *chol_L, int naux, int nvec,
+                         const double *w, const double *L1, const double *L2, int ntri,
+                         const int *tri, double *sig1, double *sig2, long long *flops,
+                         int nthreads) {
+  size_t nv2 = (size_t)nv * nv, nv3 = nv2 * nv, n1 = (size_t)no * nv,
+         n2 = (size_t)no * no * nv * nv;
+  int n = no + nv;
+  size_t nn = (size_t)n * n;
+  int *T = NULL;
+  int nt = list_triples(no, ntri, tri, &T);
+  if (nt < 0) return -1;
+  int used = set_threads(nthreads);
+  blocks_t B = {no, nv, eps_o, eps_v, t2, vvvo, oovo, ooov, ovov, vvov, F_ov};
+  long long fl_total = 0;
+  for (int vec = 0; vec < nvec; ++vec) {
+    const double *l1 = L1 + vec * n1, *l2 = L2 + vec * n2;
+    double *lt2 = (double *)malloc(n2 * sizeof(double) + 8);
+    back_transform(no, nv, l2, lt2);  /* the back-transform is its own transpose */
+    double *s1 = (double *)calloc(n1 + 1, sizeof(double));
+    double *s2 = (double *)calloc(n2 + 1, sizeof(double));
+    double *Q = (double *)calloc(n1 + 1, sizeof(double));
+    double *G = (double *)calloc(nv3 * no + 1, sizeof(double));
+    double *H = (double *)calloc((size_t)no * no * nv * no + 1, sizeof(double));
+    long long fl = 0;
+    /* loop 1: tau3 and its contractions with Lt2 */
+#pragma omp parallel if (nt >= used) reduction(+ : fl)
+    {
+      double *W = (double *)malloc(nv3 * sizeof(double));
+      double *S = (double *)malloc(nv3 * sizeof(double));
+      double *tau = (double *)malloc(nv3 * sizeof(double));
+      double *V = (double *)malloc(nv3 * sizeof(double));
+      double *q1 = (double *)calloc(n1 + 1, sizeof(double));
+      double *m1 = (double *)calloc(n1 + 1, sizeof(double));
+#pragma omp for schedule(dynamic, 1)
+      for (int t = 0; t < nt; ++t) {
+        const int *ijk = T + 3 * t;
+        int maps[6][3];
+        int np = distinct_perms(ijk, maps);
+        if (np == 0) continue;
+        build_W(no, nv, t2, vvvo, oovo, ijk, W, S, &fl);
+        divide_denominator(&B, ijk, 0.0, W, tau);
+        contravariant(nv, tau, S);
+        for (int u = 0; u < np; ++u) {
+          int p = ijk[maps[u][0]], q = ijk[maps[u][1]], r = ijk[maps[u][2]];
+          permuted_view(nv, S, maps[u], V);
+          for (int x = 0; x < nv; ++x)
+            for (int y = 0; y < nv; ++y) {
+              const double lq = lt2[(((size_t)p * no + q) * nv + x) * nv + y];
+              const double *vr = V + (size_t)x * nv2 + (size_t)y * nv;
+              for (int z = 0; z < nv; ++z) q1[(size_t)r * nv + z] += lq * vr[z];
+            }
+          /* - sum Lt2[p][l][x][y] V[x][y][z] (qd|rz) */
+          for (int x = 0; x < nv; ++x)
+            for (int y = 0; y < nv; ++y) {
+              const double *vr = V + (size_t)x * nv2 + (size_t)y * nv;
+              for (int d = 0; d < nv; ++d) {
+                double s = 0.0;
+                for (int z = 0; z < nv; ++z) s += vr[z] * OVOV(&B, q, d, r, z);
+                for (int l = 0; l < no; ++l)
+                  m1[(size_t)l * nv + d] -= lt2[(((size_t)p * no + l) * nv + x) * nv + y] * s;
+              }
+            }
+          /* - sum Lt2[p][q][x][d] V[x][y][z] (ly|rz) */
+          for (int x = 0; x < nv; ++x)
+            for (int l = 0; l < no; ++l) {
+              double s = 0.0;
+              for (int y = 0; y < nv; ++y)
+                for (int z = 0; z < nv; ++z)
+                  s += V[(size_t)x * nv2 + (size_t)y * nv + z] * OVOV(&B, l, y, r, z);
+              for (int d = 0; d < nv; ++d)
+                m1[(size_t)l * nv + d] -= lt2[(((size_t)p * no + q) * nv + x) * nv + d] * s;
+            }
+        }
+      }
+#pragma omp critical
+      {
+        for (size_t x = 0; x < n1; ++x) Q[x] += q1[x];
+        for (size_t x = 0; x < n1; ++x) s1[x] += m1[x];
+      }
+      free(W); free(S); free(tau); free(V); free(q1); free(m1);
+    }
+    /* loop 2: L3, its contravariant form and its contractions */
+#pragma omp parallel if (nt >= used) reduction(+ : fl)
+    {
+      double *W = (double *)malloc(nv3 * sizeof(double));
+      double *S = (double *)malloc(nv3 * sizeof(double));
+      double *l3 = (double *)malloc(nv3 * sizeof(double));
+      double *V = (double *)malloc(nv3 * sizeof(double));
+      double *m2 = (double *)calloc(n2 + 1, sizeof(double));
+      double *g = (double *)calloc(nv3 * no + 1, sizeof(double));
+      double *h = (double *)calloc((size_t)no * no * nv * no + 1, sizeof(double));
+#pragma omp for schedule(dynamic, 1)
+      for (int t = 0; t < nt; ++t) {
+        const int *ijk = T + 3 * t;
+        int maps[6][3];
+        int np = distinct_perms(ijk, maps);
+        if (np == 0) continue;
+        build_PX(&B, l1, lt2, ijk, W, S, &fl);
+        divide_denominator(&B, ijk, w[vec], W, l3);
+        contravariant(nv, l3, S);
+        for (int u = 0; u < np; ++u) {
+          int p = ijk[maps[u][0]], q = ijk[maps[u][1]], r = ijk[maps[u][2]];
+          permuted_view(nv, S, maps[u], V);
+          ORACLE_INNER_FOR
+          for (int x = 0; x < nv; ++x) {
+            for (int d = 0; d < nv; ++d) {  /* sigma2[p][q][x][d] += sum_yz V g_{ydzr} */
+              double s = 0.0;
+              for (int y = 0; y < nv; ++y)
+                for (int z = 0; z < nv; ++z)
+                  s += V[(size_t)x * nv2 + (size_t)y * nv + z] * VVVO(&B, y, d, z, r);
+              m2[(((size_t)p * no + q) * nv + x) * nv + d] += s;
+            }
+            for (int y = 0; y < nv; ++y)    /* sigma2[p][l][x][y] -= sum_z V g_{lqzr} */
+              for (int l = 0; l < no; ++l) {
+                double s = 0.0;
+                for (int z = 0; z < nv; ++z)
+                  s += V[(size_t)x * nv2 + (size_t)y * nv + z] * OOVO(&B, l, q, z, r);
+                m2[(((size_t)p * no + l) * nv + x) * nv + y] -= s;
+              }
+          }
+          ORACLE_INNER_FOR
+          for (int y = 0; y < nv; ++y)      /* G[y][d][z][r] += sum_x V t[p][q][x][d] */
+            for (int d = 0; d < nv; ++d)
+              for (int z = 0; z < nv; ++z) {
+                double s = 0.0;
+                for (int x = 0; x < nv; ++x)
+                  s += V[(size_t)x * nv2 + (size_t)y * nv + z] * T2(&B, p, q, x, d);
+                g[(((size_t)y * nv + d) * nv + z) * no + r] += s;
+              }
+          for (int z = 0; z < nv; ++z)      /* H[l][q][z][r] += sum_xy V t[p][l][x][y] */
+            for (int l = 0; l < no; ++l) {
+              double s = 0.0;
+              for (int x = 0; x < nv; ++x)
+                for (int y = 0; y < nv; ++y)
+                  s += V[(size_t)x * nv2 + (size_t)y * nv + z] * T2(&B, p, l, x, y);
+              h[(((size_t)l * no + q) * nv + z) * no + r] += s;
+            }
+          fl += 4LL * nv * nv * nv * nv;
+        }
+      }
+#pragma omp critical
+      {
+        for (size_t x = 0; x < n2; ++x) s2[x] += m2[x];
+        for (size_t x = 0; x < nv3 * no; ++x) G[x] += g[x];
+        for (size_t x = 0; x < (size_t)no * no * nv * no; ++x) H[x] += h[x];
+      }
+      free(W); free(S); free(l3); free(V); free(m2); free(g); free(h);
+    }
+    /* the R1 dependence of F^ and of the dressed integrals, transposed */
+    const double *L = chol_L;
+#define V_(p) (no + (p))
+    for (int l = 0; l < no; ++l)
+      for (int d = 0; d < nv; ++d) {
+        double s = 0.0;
+        for (int k = 0; k < no; ++k)
+          for (int c = 0; c < nv; ++c)
+            s += Q[(size_t)k * nv + c] * (2.0 * OVOV(&B, k, c, l, d) - OVOV(&B, k, d, l, c));
+        s1[(size_t)l * nv + d] += s;
+      }
+#pragma omp parallel for schedule(static)
+    for (int l = 0; l < no; ++l) {
+      for (int b = 0; b < nv; ++b) {   /* - sum G[b][d][c][k] (ld|ck) */
+        double s = 0.0;
+        for (int d = 0; d < nv; ++d)
+          for (int c = 0; c < nv; ++c)
+            for (int k = 0; k < no; ++k)
+              s += G[(((size_t)b * nv + d) * nv + c) * no + k] * eri(L, naux, n, l, V_(d), V_(c), k);
+        s1[(size_t)l * nv + b] -= s;
+      }
+      for (int c = 0; c < nv; ++c) {   /* - sum G[b][d][c][k] (bd|lk) */
+        double s = 0.0;
+        for (int b = 0; b < nv; ++b)
+          for (int d = 0; d < nv; ++d)
+            for (int k = 0; k < no; ++k)
+              s += G[(((size_t)b * nv + d) * nv + c) * no + k] * eri(L, naux, n, V_(b), V_(d), l, k);
+        s1[(size_t)l * nv + c] -= s;
+      }
+    }
+    { /* + sum G[b][d][c][k] (bd|ce) = sum_J (sum_bd G L^J_bd) L^J_ce */
+      double *N = (double *)calloc((size_t)naux * nv * no + 1, sizeof(double));
+#pragma omp parallel for schedule(static)
+      for (int J = 0; J < naux; ++J)
+        for (int c = 0; c < nv; ++c)
+          for (int k = 0; k < no; ++k) {
+            double s = 0.0;
+            for (int b = 0; b < nv; ++b)
+              for (int d = 0; d < nv; ++d)
+                s += L[J * nn + (size_t)V_(b) * n + V_(d)] * G[(((size_t)b * nv + d) * nv + c) * no + k];
+            N[((size_t)J * nv + c) * no + k] = s;
+          }
+      for (int k = 0; k < no; ++k)
+        for (int e = 0; e < nv; ++e) {
+          double s = 0.0;
+          for (int J = 0; J < naux; ++J)
+            for (int c = 0; c < nv; ++c)
+              s += N[((size_t)J * nv + c) * no + k] * L[J * nn + (size_t)V_(c) * n + V_(e)];
+          s1[(size_t)k * nv + e] += s;
+        }
+      free(N);
+    }
+#define HH(l, j, c, k) H[(((size_t)(l) * no + (j)) * nv + (c)) * no + (k)]
+    for (int j = 0; j < no; ++j)       /* - sum H[l][j][c][k] (ld|ck) */
+      for (int d = 0; d < nv; ++d) {
+        double s = 0.0;
+        for (int l = 0; l < no; ++l)
+          for (int c = 0; c < nv; ++c)
+            for (int k = 0; k < no; ++k) s += HH(l, j, c, k) * eri(L, naux, n, l, V_(d), V_(c), k);
+        s1[(size_t)j * nv + d] -= s;
+      }
+    for (int m = 0; m < no; ++m)       /* + sum H[l][j][c][k] (lj|mk) */
+      for (int c = 0; c < nv; ++c) {
+        double s = 0.0;
+        for (int l = 0; l < no; ++l)
+          for (int j = 0; j < no; ++j)
+            for (int k = 0; k < no; ++k) s += HH(l, j, c, k) * eri(L, naux, n, l, j, m, k);
+        s1[(size_t)m * nv + c] += s;
+      }
+    for (int k = 0; k < no; ++k)       /* - sum H[l][j][c][k] (lj|cd) */
+      for (int d = 0; d < nv; ++d) {
+        double s = 0.0;
+        for (int l = 0; l < no; ++l)
+          for (int j = 0; j < no; ++j)
+            for (int c = 0; c < nv; ++c) s += HH(l, j, c, k) * eri(L, naux, n, l, j, V_(c), V_(d));
+        s1[(size_t)k * nv + d] -= s;
+      }
+#undef HH
+#undef V_
+    memcpy(sig1 + vec * n1, s1, n1 * sizeof(double));
+    for (int i = 0; i < no; ++i)
+      for (int j = 0; j < no; ++j)
+        for (int a = 0; a < nv; ++a)
+          for (int b = 0; b < nv; ++b)
+            sig2[vec * n2 + (((size_t)i * no + j) * nv + a) * nv + b] =
+                0.5 * (s2[(((size_t)i * no + j) * nv + a) * nv + b] +
+                       s2[(((size_t)j * no + i) * nv + b) * nv + a]);
+    fl_total += fl;
+    free(lt2); free(s1); free(s2); free(Q); free(G); free(H);
   }
   if (flops) *flops = fl_total;
   free(T);

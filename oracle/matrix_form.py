@@ -217,3 +217,93 @@ def jacobian(inp, R1, R2, w, triples=None, blocks=None):
         rho1[n] = om1
         rho2[n] = back_transform(omt)
     return dict(rho1=rho1, rho2=rho2)
+
+
+def left_jacobian(inp, L1, L2, w, triples=None):
+    """Left (transpose) Jacobian transformation, the steps of the C oracle's
+    oracle_left_jacobian with numpy products (symmetric blocks).  Returns
+    dict(sigma1, sigma2)."""
+    from . import symmetric_blocks
+    no, nv = inp.no, inp.nv
+    g = Blocks(symmetric_blocks(inp))
+    L1 = np.asarray(L1).reshape(-1, no, nv)
+    nvec = L1.shape[0]
+    L2 = np.asarray(L2).reshape(nvec, no, no, nv, nv)
+    w = np.broadcast_to(np.asarray(w, dtype=np.float64), (nvec,))
+    triples = all_triples(no) if triples is None else [tuple(int(x) for x in t) for t in triples]
+    eo, ev, t2 = np.asarray(inp.eps_o), np.asarray(inp.eps_v), np.asarray(inp.t2)
+    L = np.asarray(inp.chol_L)
+    ib = integral_blocks(no, nv, L)
+    ovov, vvoo, oooo, oovv = ib["ovov"], ib["vvoo"], ib["oooo"], ib["oovv"]
+    ovvo = ib["ovvo"]
+    vvov_r = g.vvov_r                               # [r][d][y][z] = g_dyrz
+    ooov = g["ooov"]
+    tau_tt = {}
+    for ijk in triples:
+        if distinct_perms(ijk):
+            W = build_W(t2, g.vvvo_r, g["oovo"], ijk)
+            tau_tt[ijk] = contravariant(divide(W, eo, ev, ijk, 0.0))
+    s1 = np.zeros((nvec, no, nv))
+    s2 = np.zeros((nvec, no, no, nv, nv))
+    for n in range(nvec):
+        l1 = L1[n]
+        lt = back_transform(L2[n])                 # the back-transform is symmetric
+        sig1 = np.zeros((no, nv))
+        sig2 = np.zeros((no, no, nv, nv))
+        Q = np.zeros((no, nv))
+        G = np.zeros((nv, nv, nv, no))             # [y][d][z][r]
+        H = np.zeros((no, no, nv, no))             # [l][q][z][r]
+        for ijk in triples:
+            maps = distinct_perms(ijk)
+            if not maps:
+                continue
+            tt = tau_tt[ijk]
+            for m in maps:
+                p, q, r = ijk[m[0]], ijk[m[1]], ijk[m[2]]
+                V = np.ascontiguousarray(tt.transpose(m))
+                Q[r] += np.tensordot(lt[p, q], V, axes=([0, 1], [0, 1]))
+                # - sum_xyz Lt[p][l][x][y] V[x][y][z] (qd|rz)
+                T = V @ ovov[q, :, r, :].T                                   # (x, y, d)
+                sig1 -= np.tensordot(lt[p], T, axes=([1, 2], [0, 1]))       # (l, d)
+                # - sum_xyz Lt[p][q][x][d] V[x][y][z] (ly|rz)
+                U = np.tensordot(V, ovov[:, :, r, :], axes=([1, 2], [1, 2]))  # (x, l)
+                sig1 -= U.T @ lt[p, q]
+            # L3 numerator, P X
+            cache = {}
+            X = None
+            for m in PERM6:
+                key = (ijk[m[0]], ijk[m[1]], ijk[m[2]])
+                if key not in cache:
+                    p, q, r = key
+                    B = (l1[p][:, None, None] * ovov[q, :, r, :][None, :, :]
+                         + lt[p, q][:, :, None] * g["F_ov"][r][None, None, :])
+                    B = B + (lt[p, q] @ vvov_r[r].reshape(nv, nv * nv)).reshape(nv, nv, nv)
+                    B = B - np.tensordot(lt[p], ooov[q, :, r, :], axes=([0], [0]))
+                    cache[key] = B
+                term = np.transpose(cache[key], np.argsort(m))
+                X = term.copy() if X is None else X + term
+            Vt = contravariant(divide(X, eo, ev, ijk, w[n]))
+            for m in maps:
+                p, q, r = ijk[m[0]], ijk[m[1]], ijk[m[2]]
+                V = np.ascontiguousarray(Vt.transpose(m))
+                Vm = V.reshape(nv, nv * nv)
+                # sigma2[p][q][x][d] += sum_yz V g_{ydzr};  g_ydzr = vvvo_r[r][d][y][z]
+                sig2[p, q] += Vm @ g.vvvo_r[r].reshape(nv, nv * nv).T
+                # sigma2[p][l][x][y] -= sum_z V g_{lqzr}
+                sig2[p] -= np.tensordot(V, g["oovo"][:, q, :, r], axes=([2], [1])).transpose(2, 0, 1)
+                # G[y][d][z][r] += sum_x V[x][y][z] t[p][q][x][d]
+                G[:, :, :, r] += np.tensordot(V, t2[p, q], axes=([0], [0])).transpose(0, 2, 1)
+                # H[l][q][z][r] += sum_xy V[x][y][z] t[p][l][x][y]
+                H[:, q, :, r] += np.tensordot(t2[p], V, axes=([1, 2], [0, 1]))
+        sig1 += 2.0 * np.tensordot(Q, ovov, axes=([0, 1], [0, 1])) \
+            - np.tensordot(Q, ovov.transpose(0, 3, 2, 1), axes=([0, 1], [0, 1]))
+        sig1 -= np.tensordot(ovvo, G, axes=([1, 2, 3], [1, 2, 3]))                # (l, b)
+        sig1 -= np.tensordot(vvoo, G, axes=([0, 1, 3], [0, 1, 3]))                 # (l, c)
+        N = np.tensordot(ib["Lvv"], G, axes=([1, 2], [0, 1]))                       # (J, c, k)
+        sig1 += np.tensordot(N, ib["Lvv"], axes=([0, 1], [0, 1]))                   # (k, e)
+        sig1 -= np.tensordot(H, ovvo, axes=([0, 2, 3], [0, 2, 3]))                 # (j, d)
+        sig1 += np.tensordot(oooo, H, axes=([0, 1, 3], [0, 1, 3]))                 # (m, c)
+        sig1 -= np.tensordot(H, oovv, axes=([0, 1, 2], [0, 1, 2]))                 # (k, d)
+        s1[n] = sig1
+        s2[n] = 0.5 * (sig2 + sig2.transpose(1, 0, 3, 2))
+    return dict(sigma1=s1, sigma2=s2)

@@ -282,3 +282,97 @@ def test_matrix_form_jacobian_equals_c_oracle():
         mine = MF.jacobian(inp, R1, R2, w, triples=sel)
         assert rel(mine["rho1"], ref["rho1"]) < 1e-12
         assert rel(mine["rho2"], ref["rho2"]) < 1e-12
+
+
+# --- left (transpose) Jacobian ------------------------------------------------
+# The left transformation is read as the exact transpose of the right one under
+# the plain inner product over the elements of (R1, R2) with pair-symmetric R2.
+# It is pinned to the right Jacobian (itself pinned to the derivative of the
+# residual above) through the bilinear identity sum L.rho(R) = sum sigma(L).R.
+def _pair_sym(x):
+    return 0.5 * (x + np.transpose(x, (0, 2, 1, 4, 3)))
+
+
+def _left_vectors(no, nv, n, seed):
+    rng = np.random.default_rng(seed)
+    return rng.normal(size=(n, no, nv)), _pair_sym(rng.normal(size=(n, no, no, nv, nv)))
+
+
+@pytest.mark.parametrize("no,nv", [(2, 5), (3, 4), (4, 7)])
+def test_left_jacobian_is_the_transpose_of_the_right(no, nv):
+    inp = make_inputs(no, nv, seed=no + nv)
+    R1, R2 = make_trial_vectors(no, nv, 2, seed=3)
+    L1, L2 = _left_vectors(no, nv, 2, seed=5)
+    tr = [t[:3] for t in unique_triples(no)]
+    for w, sel in [(0.0, None), (0.25, None), (-0.1, tr[::2])]:
+        rho = oracle.jacobian(inp, R1, R2, [w, w], triples=sel)
+        sig = oracle.left_jacobian(inp, L1, L2, [w, w], triples=sel)
+        for n in range(2):
+            for m in range(2):
+                a = np.sum(L1[n] * rho["rho1"][m]) + np.sum(L2[n] * rho["rho2"][m])
+                b = np.sum(sig["sigma1"][n] * R1[m]) + np.sum(sig["sigma2"][n] * R2[m])
+                scale = (np.abs(L1[n]).sum() * np.abs(rho["rho1"][m]).max()
+                         + np.abs(L2[n]).sum() * np.abs(rho["rho2"][m]).max())
+                assert abs(a - b) <= 1e-13 * scale, (w, n, m, a, b)
+
+
+def test_left_jacobian_matrix_equals_transposed_right_matrix():
+    # every column of the right Jacobian (unit R) against every row of the left
+    # one (unit L), on a two-orbital, three-virtual problem
+    no, nv = 2, 3
+    inp = make_inputs(no, nv, seed=4)
+    n1 = no * nv
+    basis = []  # unit vectors of (R1, pair-symmetric R2)
+    for k in range(n1):
+        e1 = np.zeros(n1)
+        e1[k] = 1.0
+        basis.append((e1.reshape(no, nv), np.zeros((no, no, nv, nv))))
+    for i in range(no):
+        for j in range(no):
+            for a in range(nv):
+                for b in range(nv):
+                    if (i, a) <= (j, b):
+                        e2 = np.zeros((no, no, nv, nv))
+                        e2[i, j, a, b] = e2[j, i, b, a] = 1.0
+                        basis.append((np.zeros((no, nv)), e2))
+    R1 = np.stack([x[0] for x in basis])
+    R2 = np.stack([x[1] for x in basis])
+    w = [0.2] * len(basis)
+    rho = oracle.jacobian(inp, R1, R2, w)
+    sig = oracle.left_jacobian(inp, R1, R2, w)
+    J = np.array([[np.sum(R1[n] * rho["rho1"][m]) + np.sum(R2[n] * rho["rho2"][m])
+                   for m in range(len(basis))] for n in range(len(basis))])
+    S = np.array([[np.sum(sig["sigma1"][n] * R1[m]) + np.sum(sig["sigma2"][n] * R2[m])
+                   for m in range(len(basis))] for n in range(len(basis))])
+    assert np.abs(J).max() > 1e-6
+    assert np.abs(J - S).max() <= 1e-13 * np.abs(J).max()
+
+
+def test_left_jacobian_linear_zero_symmetric_and_flops():
+    no, nv = 3, 6
+    inp = make_inputs(no, nv, seed=12)
+    L1, L2 = _left_vectors(no, nv, 2, seed=1)
+    a = oracle.left_jacobian(inp, L1[:1], L2[:1], [0.3])
+    b = oracle.left_jacobian(inp, L1[1:], L2[1:], [0.3])
+    c = oracle.left_jacobian(inp, 2 * L1[:1] - 3 * L1[1:], 2 * L2[:1] - 3 * L2[1:], [0.3])
+    for k in ("sigma1", "sigma2"):
+        assert rel(c[k][0], 2 * a[k][0] - 3 * b[k][0]) < 1e-12
+    s2 = a["sigma2"][0]
+    assert np.array_equal(s2, np.transpose(s2, (1, 0, 3, 2)))
+    z = oracle.left_jacobian(inp, np.zeros((1, no, nv)), np.zeros((1, no, no, nv, nv)), [0.3])
+    assert not z["sigma1"].any() and not z["sigma2"].any()
+    # 8 nv^4 per distinct permutation: tau3, the L3 numerator, sigma2 and G
+    assert a["flops"] == 8 * nv ** 4 * (no ** 3 - no)
+
+
+def test_matrix_form_left_jacobian_equals_c_oracle():
+    from oracle import matrix_form as MF
+    inp = make_inputs(4, 9, 6)
+    L1, L2 = _left_vectors(4, 9, 2, seed=9)
+    w = [0.25, -0.1]
+    tr = [t[:3] for t in unique_triples(4)]
+    for sel in (None, [tr[1], tr[-1], tr[4]]):
+        ref = oracle.left_jacobian(inp, L1, L2, w, triples=sel)
+        mine = MF.left_jacobian(inp, L1, L2, w, triples=sel)
+        assert rel(mine["sigma1"], ref["sigma1"]) < 1e-12
+        assert rel(mine["sigma2"], ref["sigma2"]) < 1e-12
