@@ -107,6 +107,27 @@ int cc3_ctx_create(cc3_ctx **out, int no, int nv, const double *eps_o,
                    const double *F_ov, const double *chol_L, int naux,
                    unsigned flags, void *cuda_stream);
 
+/* Context for general integrals, as the T1-transformed Hamiltonian of a CC3
+ * iteration with t1 != 0 gives them (paper, "Implementation": the integrals
+ * are T1 transformed and lose the pq <-> qp symmetry, so no block can be
+ * derived from another).  The five blocks of Algorithm 1 come separately:
+ *   g_vvvo[b][d][c][k] = g_bdck      g_oovo[l][j][c][k] = g_ljck
+ *   g_ooov[j][l][k][c] = g_jlkc      g_ovov[j][b][k][c] = g_jbkc
+ *   g_vvov[d][b][k][c] = g_dbkc      F_ov[k][c] (the T1-transformed Fock block)
+ * The W build reads vvvo and oovo, the contractions vvov, ooov, ovov and F
+ * (for symmetric integrals g_oovo is g_ooov with its last two indices swapped
+ * and g_vvov[d][b][k][c] = g_vvvo[b][d][c][k], which is what cc3_ctx_create
+ * assumes).  eps_o and eps_v are the orbital energies of the denominators.
+ * Other arguments, ownership and errors as cc3_ctx_create; the residual
+ * (cc3_omega_triples) runs on both precision paths, while
+ * cc3_jacobian_triples on such a context returns CC3_ERR_UNSUPPORTED (its
+ * R1 dressing assumes symmetric integrals). */
+int cc3_ctx_create_general(cc3_ctx **out, int no, int nv, const double *eps_o,
+                           const double *eps_v, const double *t2, const double *g_vvvo,
+                           const double *g_oovo, const double *g_ooov, const double *g_ovov,
+                           const double *g_vvov, const double *F_ov, unsigned flags,
+                           void *cuda_stream);
+
 void cc3_ctx_destroy(cc3_ctx *ctx);
 
 /* Restrict the triple loop to ntri unique occupied triples ijk[3*t..3*t+2]
@@ -152,6 +173,27 @@ int cc3_jacobian_triples(cc3_ctx *ctx, cc3_prec prec, int nvec,
                          const double *omega, const double *R1,
                          const double *R2, double *rho1, double *rho2,
                          void *cuda_stream);
+
+/* Left (transpose) CC3 Jacobian transformation (triples part) of nvec left
+ * vectors at frequencies omega[nvec] (host array always), the product needed
+ * for left excited states and for the multipliers (paper, "Implementation",
+ * the transpose-Jacobian paragraph; the L3 amplitudes of Algorithm 3):
+ *   L3 = (w - eps)^{-1} P[ L1 (x) g_ovov + L2~ (x) F + contractions of L2~ with
+ *        g_vvov and g_ooov ],  L2~ = the back-transform applied to L2,
+ * then its contravariant form contracted with the integrals (sigma2) and with
+ * t2 into intermediates that the Cholesky vectors turn into sigma1, after a
+ * loop that contracts tau3 (sharing the Algorithm 2 intermediates with
+ * cc3_jacobian_triples).  The result is the exact transpose of the right
+ * transformation under the plain inner product over the elements of (R1, R2):
+ *   sum L1 . rho1(R) + sum L2 . rho2(R) = sum sigma1(L) . R1 + sum sigma2(L) . R2
+ * for every R with pair-symmetric R2; sigma2 is pair symmetric.
+ * L1[n][i][a], L2[n][i][j][a][b], sigma1[n][i][a], sigma2[n][i][j][a][b]; other
+ * rules (pointers, frequencies, CC3_ERR_DENOM, symmetric integrals, Cholesky
+ * vectors required) as cc3_jacobian_triples.  FP64 path only: CC3_SPLIT_BF16
+ * returns CC3_ERR_UNSUPPORTED. */
+int cc3_left_jacobian_triples(cc3_ctx *ctx, cc3_prec prec, int nvec, const double *omega,
+                              const double *L1, const double *L2, double *sigma1,
+                              double *sigma2, void *cuda_stream);
 
 /* Smallest |w - eps^{abc}_{ijk}| over every virtual triple (a, b, c) and the
  * occupied triples of a loop, eps^{abc}_{ijk} = e_a + e_b + e_c - e_i - e_j -

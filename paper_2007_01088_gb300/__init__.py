@@ -40,7 +40,8 @@ EXPORTED = ["cc3_ctx_create", "cc3_ctx_destroy", "cc3_ctx_set_triples",
             "cc3_debug_split_gemm", "cc3_last_error", "cc3_ctx_set_tracing",
             "cc3_ctx_trace", "cc3_omega_triples_noalloc", "cc3_serve_footprint",
             "cc3_ctx_autotune", "cc3_ctx_get_tuning", "cc3_cvs_triples",
-            "cc3_denominator_gap", "cc3_debug_wait_timeout"]
+            "cc3_denominator_gap", "cc3_debug_wait_timeout", "cc3_ctx_create_general",
+            "cc3_left_jacobian_triples"]
 
 
 class CC3Error(RuntimeError):
@@ -93,6 +94,8 @@ def _load():
     P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
     L.cc3_ctx_create.argtypes = [ctypes.POINTER(P), I, I] + [P] * 8 + [I, ctypes.c_uint, P]
     L.cc3_ctx_create.restype = I
+    L.cc3_ctx_create_general.argtypes = [ctypes.POINTER(P), I, I] + [P] * 9 + [ctypes.c_uint, P]
+    L.cc3_ctx_create_general.restype = I
     L.cc3_ctx_destroy.argtypes = [P]
     L.cc3_ctx_destroy.restype = None
     L.cc3_ctx_set_triples.argtypes = [P, I, P]
@@ -105,6 +108,8 @@ def _load():
     L.cc3_omega_triples.restype = I
     L.cc3_jacobian_triples.argtypes = [P, I, I, P, P, P, P, P, P]
     L.cc3_jacobian_triples.restype = I
+    L.cc3_left_jacobian_triples.argtypes = [P, I, I, P, P, P, P, P, P]
+    L.cc3_left_jacobian_triples.restype = I
     L.cc3_ctx_counters.argtypes = [P, ctypes.POINTER(Counters)]
     L.cc3_ctx_counters.restype = I
     L.cc3_ctx_set_slices.argtypes = [P, I]
@@ -201,6 +206,17 @@ def cc3_ctx_create(no, nv, eps_o, eps_v, t2, g_vvvo, g_ooov, g_ovov, F_ov,
     return ctx
 
 
+def cc3_ctx_create_general(no, nv, eps_o, eps_v, t2, g_vvvo, g_oovo, g_ooov, g_ovov, g_vvov,
+                           F_ov, flags=0, stream=None):
+    ctx = ctypes.c_void_p()
+    st = lib.cc3_ctx_create_general(ctypes.byref(ctx), int(no), int(nv), _ptr(eps_o),
+                                    _ptr(eps_v), _ptr(t2), _ptr(g_vvvo), _ptr(g_oovo),
+                                    _ptr(g_ooov), _ptr(g_ovov), _ptr(g_vvov), _ptr(F_ov),
+                                    int(flags), _stream(stream))
+    _check(st, "cc3_ctx_create_general")
+    return ctx
+
+
 def cc3_ctx_destroy(ctx):
     lib.cc3_ctx_destroy(ctx)
 
@@ -256,6 +272,14 @@ def cc3_jacobian_triples(ctx, prec, nvec, omega, R1, R2, rho1, rho2, stream=None
     _check(lib.cc3_jacobian_triples(ctx, int(prec), int(nvec), w.ctypes.data_as(ctypes.c_void_p),
                                     _ptr(R1), _ptr(R2), _ptr(rho1), _ptr(rho2),
                                     _stream(stream)), "cc3_jacobian_triples")
+
+
+def cc3_left_jacobian_triples(ctx, prec, nvec, omega, L1, L2, sigma1, sigma2, stream=None):
+    w = np.ascontiguousarray(np.asarray(omega, dtype=np.float64).reshape(-1))
+    _check(lib.cc3_left_jacobian_triples(ctx, int(prec), int(nvec),
+                                         w.ctypes.data_as(ctypes.c_void_p), _ptr(L1), _ptr(L2),
+                                         _ptr(sigma1), _ptr(sigma2), _stream(stream)),
+           "cc3_left_jacobian_triples")
 
 
 def cc3_ctx_counters(ctx):
@@ -330,13 +354,25 @@ class Context:
     ``device=True`` the inputs are uploaded through torch CUDA tensors and the
     context works on device pointers."""
 
-    def __init__(self, inputs, device: bool = False, stream=None, flags: int = 0):
+    def __init__(self, inputs, device: bool = False, stream=None, flags: int = 0,
+                 blocks=None):
+        """blocks: the five general (e.g. T1-transformed) integral blocks and
+        F_ov as a dict (vvvo, oovo, ooov, ovov, vvov, F_ov); the context is
+        then created with cc3_ctx_create_general and inputs supplies the
+        sizes, the orbital energies and t2."""
         self.no, self.nv = int(inputs.no), int(inputs.nv)
         self.device = device
         self.stream = stream
-        L = getattr(inputs, "chol_L", None)
+        L = getattr(inputs, "chol_L", None) if blocks is None else None
         names = ["eps_o", "eps_v", "t2", "g_vvvo", "g_ooov", "g_ovov", "F_ov"]
-        arrs = {n: np.ascontiguousarray(getattr(inputs, n), dtype=np.float64) for n in names}
+        if blocks is None:
+            arrs = {n: np.ascontiguousarray(getattr(inputs, n), dtype=np.float64) for n in names}
+        else:
+            arrs = {n: np.ascontiguousarray(getattr(inputs, n), dtype=np.float64)
+                    for n in ("eps_o", "eps_v", "t2")}
+            for k in ("vvvo", "oovo", "ooov", "ovov", "vvov"):
+                arrs["g_" + k] = np.ascontiguousarray(blocks[k], dtype=np.float64)
+            arrs["F_ov"] = np.ascontiguousarray(blocks["F_ov"], dtype=np.float64)
         if L is not None:
             arrs["chol_L"] = np.ascontiguousarray(L, dtype=np.float64)
         if device:
@@ -347,9 +383,15 @@ class Context:
         else:
             src = arrs
         naux = 0 if L is None else int(L.shape[0])
-        self.ctx = cc3_ctx_create(self.no, self.nv, src["eps_o"], src["eps_v"], src["t2"],
-                                  src["g_vvvo"], src["g_ooov"], src["g_ovov"], src["F_ov"],
-                                  src.get("chol_L"), naux, flags, stream)
+        if blocks is None:
+            self.ctx = cc3_ctx_create(self.no, self.nv, src["eps_o"], src["eps_v"], src["t2"],
+                                      src["g_vvvo"], src["g_ooov"], src["g_ovov"], src["F_ov"],
+                                      src.get("chol_L"), naux, flags, stream)
+        else:
+            self.ctx = cc3_ctx_create_general(self.no, self.nv, src["eps_o"], src["eps_v"],
+                                              src["t2"], src["g_vvvo"], src["g_oovo"],
+                                              src["g_ooov"], src["g_ovov"], src["g_vvov"],
+                                              src["F_ov"], flags, stream)
         if device:
             import torch
             torch.cuda.synchronize()
@@ -410,6 +452,15 @@ class Context:
         o1, o2, e = out
         cc3_omega_triples(self.ctx, prec, o1, o2, e, self.stream)
         return o1, o2, e
+
+    def left_jacobian(self, L1, L2, omega, prec=CC3_FP64):
+        """Left (transpose) transformation; returns (sigma1, sigma2)."""
+        no, nv = self.no, self.nv
+        nvec = int(L1.shape[0])
+        s1 = self._new((nvec, no, nv))
+        s2 = self._new((nvec, no, no, nv, nv))
+        cc3_left_jacobian_triples(self.ctx, prec, nvec, omega, L1, L2, s1, s2, self.stream)
+        return s1, s2
 
     def jacobian(self, R1, R2, omega, prec=CC3_FP64):
         no, nv = self.no, self.nv

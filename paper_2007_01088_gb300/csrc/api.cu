@@ -98,6 +98,7 @@ void fill_ptrs(cc3_ctx *c, PtrTable *pt) {
   pt->p[B_OMT] = c->omt;
   pt->p[B_OM1] = c->om1;
   pt->p[B_SCRATCH] = c->omt;
+  pt->p[B_VVOV] = c->vvov;
   pt->fx[B_OMT] = c->omt_fx;  // null unless CC3_DETERMINISTIC
   pt->fx[B_OM1] = c->om1_fx;
 }
@@ -120,10 +121,13 @@ int build_omega_plans(cc3_ctx *c, cudaStream_t s) {
       const double e = eo[ijk[0]] + eo[ijk[1]] + eo[ijk[2]];
       plan_w_build(pab, no, nv, ijk, slot, B_WS_W, &set, 1, 0.0, e, 0);
       plan_w_build(pc, no, nv, ijk, slot, B_WS_W, &set, 1, 0.0, e, 1);
+      // vvov: its own block for general integrals, else a view of vvvo
       plan_omega_contractions(pom, no, nv, ijk, slot, B_WS_TT, B_OVOV, B_FOV,
-                              B_OOOV, true, B_VVVO, B_OMT, B_OM1, 2, 1);
+                              B_OOOV, !c->general, c->general ? B_VVOV : B_VVVO, B_OMT,
+                              B_OM1, 2, 1);
       plan_omega_contractions(pth, no, nv, ijk, slot, B_WS_TT, B_OVOV, B_FOV,
-                              B_OOOV, true, B_VVVO, B_OMT, B_OM1, 1, 2);
+                              B_OOOV, !c->general, c->general ? B_VVOV : B_VVVO, B_OMT,
+                              B_OM1, 1, 2);
     }
     executed += plan_flops(pab) + plan_flops(pc) + plan_flops(pom) + plan_flops(pth);
     DevPlan d;
@@ -343,7 +347,7 @@ void cc3_ctx_destroy(cc3_ctx *c) {
   jacobian_destroy(c);
   for (int k = 0; k < TR_NCLASS; ++k)
     for (cudaEvent_t e : c->trace.ev[k]) cudaEventDestroy(e);
-  double *bufs[] = {c->eps_o, c->eps_v, c->t2, c->vvvo, c->oovo, c->ooov,
+  double *bufs[] = {c->eps_o, c->eps_v, c->t2, c->vvvo, c->vvov, c->oovo, c->ooov,
                     c->ovov, c->F_ov, c->chol, c->vvoo, c->oooo, c->ws_w,
                     c->ws_tt, c->ws_tt2, c->omt, c->om1, c->Zv, c->Zo, c->R2,
                     c->hvvvo, c->hoovo, c->hF, c->rhot, c->rho1};
@@ -355,16 +359,22 @@ void cc3_ctx_destroy(cc3_ctx *c) {
   delete c;
 }
 
-int cc3_ctx_create(cc3_ctx **out, int no, int nv, const double *eps_o,
-                   const double *eps_v, const double *t2, const double *g_vvvo,
-                   const double *g_ooov, const double *g_ovov,
-                   const double *F_ov, const double *chol_L, int naux,
-                   unsigned flags, void *cuda_stream) {
+}  // extern "C"
+
+// Context creation shared by the symmetric and the general entry points:
+// g_oovo and g_vvov are null for symmetric integrals (oovo is then the
+// transpose of ooov and the contractions read vvov through vvvo).
+static int ctx_create_impl(cc3_ctx **out, int no, int nv, const double *eps_o,
+                           const double *eps_v, const double *t2, const double *g_vvvo,
+                           const double *g_oovo, const double *g_ooov, const double *g_ovov,
+                           const double *g_vvov, const double *F_ov, const double *chol_L,
+                           int naux, unsigned flags, void *cuda_stream) {
   if (!out) return CC3_ERR_ARG;
   *out = nullptr;
   if (no < 1 || nv < 1 || nv > 1024 || no > 256) return CC3_ERR_ARG;
   if (!eps_o || !eps_v || !t2 || !g_vvvo || !g_ooov || !g_ovov || !F_ov)
     return CC3_ERR_ARG;
+  if ((g_oovo == nullptr) != (g_vvov == nullptr)) return CC3_ERR_ARG;
   if (naux < 0 || (naux > 0 && !chol_L)) return CC3_ERR_ARG;
   if (flags & ~(CC3_DEVICE_PTRS | CC3_DETERMINISTIC)) return CC3_ERR_ARG;
   cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -394,14 +404,21 @@ int cc3_ctx_create(cc3_ctx **out, int no, int nv, const double *eps_o,
   ALLOC_COPY(vvvo, g_vvvo, nvvvo);
   ALLOC_COPY(ooov, g_ooov, nooov);
   ALLOC_COPY(ovov, g_ovov, novov);
+  if (g_vvov) {
+    c->general = true;
+    ALLOC_COPY(vvov, g_vvov, nvvvo);
+    ALLOC_COPY(oovo, g_oovo, nooov);
+  }
   ALLOC_COPY(F_ov, F_ov, (size_t)no * nv);
   if (c->naux > 0) {
     const size_t n = (size_t)no + nv;
     ALLOC_COPY(chol, chol_L, (size_t)naux * n * n);
   }
 #undef ALLOC_COPY
-  if ((rc = dalloc(&c->oovo, nooov)) != CC3_OK) goto fail;
-  if ((rc = launch_transpose_ooov_to_oovo(c->ooov, c->oovo, no, nv, s)) != CC3_OK) goto fail;
+  if (!c->general) {
+    if ((rc = dalloc(&c->oovo, nooov)) != CC3_OK) goto fail;
+    if ((rc = launch_transpose_ooov_to_oovo(c->ooov, c->oovo, no, nv, s)) != CC3_OK) goto fail;
+  }
   if ((rc = dalloc(&c->omt, nt2)) != CC3_OK) goto fail;
   if ((rc = dalloc(&c->om1, (size_t)no * nv)) != CC3_OK) goto fail;
   if (flags & CC3_DETERMINISTIC) {
@@ -436,6 +453,27 @@ fail:
   cudaGetLastError();
   cc3_ctx_destroy(c);
   return rc;
+}
+
+extern "C" {
+
+int cc3_ctx_create(cc3_ctx **out, int no, int nv, const double *eps_o,
+                   const double *eps_v, const double *t2, const double *g_vvvo,
+                   const double *g_ooov, const double *g_ovov,
+                   const double *F_ov, const double *chol_L, int naux,
+                   unsigned flags, void *cuda_stream) {
+  return ctx_create_impl(out, no, nv, eps_o, eps_v, t2, g_vvvo, nullptr, g_ooov, g_ovov,
+                         nullptr, F_ov, chol_L, naux, flags, cuda_stream);
+}
+
+int cc3_ctx_create_general(cc3_ctx **out, int no, int nv, const double *eps_o,
+                           const double *eps_v, const double *t2, const double *g_vvvo,
+                           const double *g_oovo, const double *g_ooov, const double *g_ovov,
+                           const double *g_vvov, const double *F_ov, unsigned flags,
+                           void *cuda_stream) {
+  if (!g_oovo || !g_vvov) return CC3_ERR_ARG;
+  return ctx_create_impl(out, no, nv, eps_o, eps_v, t2, g_vvvo, g_oovo, g_ooov, g_ovov, g_vvov,
+                         F_ov, nullptr, 0, flags, cuda_stream);
 }
 
 int cc3_ctx_set_triples(cc3_ctx *c, int ntri, const int *ijk) {

@@ -65,9 +65,13 @@ enum BufId {
   B_WS_W, B_WS_TT, B_OMT, B_OM1,
   B_R2, B_HVVVO, B_HOOVO, B_HF, B_ZV, B_ZO, B_VVOO, B_OOOO,
   B_RHOT, B_RHO1, B_TT_TAU, B_SCRATCH, B_SLOTEXP,
-  B_WS_WR, B_WS_TTR, B_MJ, B_CHOL, B_R1, B_WS_W3,
-  B_COUNT
+  B_WS_WR, B_WS_TTR, B_MJ, B_CHOL, B_R1, B_WS_W3, B_VVOV,
+  B_COUNT,
+  // the left transformation (left.cu) reuses slots the right one does not
+  // touch there: Lt2, sigma1, sigma2 (before symmetrising), G, H, Q
+  B_LT = B_R2, B_S1 = B_RHO1, B_S2 = B_RHOT, B_G = B_HVVVO, B_H = B_HOOVO, B_Q = B_HF
 };
+static_assert(B_COUNT <= MAX_BUFS, "pointer table");
 
 struct Plan {  // a host-built list of jobs for one launch
   std::vector<Job> jobs;
@@ -108,6 +112,11 @@ struct cc3_ctx {
   double *eps_o = nullptr, *eps_v = nullptr, *t2 = nullptr, *vvvo = nullptr,
          *oovo = nullptr, *ooov = nullptr, *ovov = nullptr, *F_ov = nullptr,
          *chol = nullptr, *vvoo = nullptr, *oooo = nullptr;
+  // general (T1-transformed) integrals: vvov[d][b][k][c] = g_dbkc and oovo
+  // given on their own instead of derived from vvvo and ooov by the 8-fold
+  // symmetry (cc3_ctx_create_general); vvov is null for symmetric contexts
+  double *vvov = nullptr;
+  bool general = false;
   // host copies of the orbital energies (denominator checks, plan epilogues)
   std::vector<double> eo_h, ev_h;
   // triple list (device and host), weights
@@ -196,6 +205,10 @@ int jac_z_buffers(cc3_ctx *c, double **Zv, double **Zo, bool zero, cudaStream_t 
 void jac_set_prep(cc3_ctx *c, int prec);  // the cached Z~ are valid, built in prec
 int jac_prep_prec(cc3_ctx *c);            // -1 if the cache is not valid
 int jac_z_terms(cc3_ctx *c, const double *R1v, double *rtv, cudaStream_t s);
+int jac_prep_fp64(cc3_ctx *c, cudaStream_t s);           // cached FP64 Z~v, Z~o
+int jac_tau_batch(cc3_ctx *c, int t0, int t1, cudaStream_t s);  // tau~ -> ws_tt
+void jac_fill_ptrs(cc3_ctx *c, PtrTable *pt);
+int jac_run_plan(cc3_ctx *c, const Plan &p, int kind, const PtrTable &pt, cudaStream_t s);
 
 // smallest |w - eps^{abc}_{ijk}| over every (a, b, c) and the ntri triples
 // ijk (host arrays; ntri = 0: the full loop); api.cu

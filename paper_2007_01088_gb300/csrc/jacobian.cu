@@ -331,6 +331,30 @@ int dress(cc3_ctx *c, const PtrTable &pt, cudaStream_t s, bool chol = true) {
 
 }  // namespace
 
+// FP64 Algorithm 2 intermediates (cached), tau and tau~ of a batch, and the
+// base pointer table: shared with the left transformation (left.cu)
+int jac_prep_fp64(cc3_ctx *c, cudaStream_t s) {
+  JacState *J = jst(c);
+  if (!J) return CC3_ERR_OOM;
+  TRY(ensure_blocks(c, J, s));
+  return ensure_prep(c, J, c->eo_h, s);
+}
+int jac_tau_batch(cc3_ctx *c, int t0, int t1, cudaStream_t s) {
+  JacState *J = jst(c);
+  if (!J) return CC3_ERR_OOM;
+  PtrTable pt;
+  fill_base(c, J, &pt);
+  return tau_batch(c, pt, t0, t1, c->eo_h, s);
+}
+void jac_fill_ptrs(cc3_ctx *c, PtrTable *pt) {
+  JacState *J = jst(c);
+  if (J) fill_base(c, J, pt);
+}
+// Upload, launch, free (FP64 engine), counted in the context's counters.
+int jac_run_plan(cc3_ctx *c, const Plan &p, int kind, const PtrTable &pt, cudaStream_t s) {
+  return run_plan(c, p, kind, pt, s);
+}
+
 int jac_blocks(cc3_ctx *c, cudaStream_t s) {
   JacState *J = jst(c);
   if (!J) return CC3_ERR_OOM;
@@ -545,6 +569,8 @@ extern "C" int cc3_jacobian_triples(cc3_ctx *c, cc3_prec prec, int nvec, const d
                                     double *rho2, void *cuda_stream) {
   using namespace cc3;
   if (!c || nvec < 1 || !omega || !R1 || !R2 || !rho1 || !rho2) return CC3_ERR_ARG;
+  if (c->general)
+    return CC3_FAIL(CC3_ERR_UNSUPPORTED, "the Jacobian needs symmetric integrals");
   if (c->naux < 1 || !c->chol)
     return CC3_FAIL(CC3_ERR_ARG, "the Jacobian needs the Cholesky vectors (chol_L)");
   if (prec == CC3_SPLIT_INT8) return CC3_ERR_UNSUPPORTED;

@@ -171,7 +171,9 @@ void plan_w_build(Plan &P, int no, int nv, const int ijk[3], int slot,
 
 // --- residual contractions ----------------------------------------------------
 // which: bit 0 = vvov + singles job (64x64 tiles), bit 1 = ooov + F job (thin),
-//        bit 2 = F-only job (thin; Jacobian tau~ . F^ term).
+//        bit 2 = F-only job (thin; Jacobian tau~ . F^ term), bit 3 = leave out
+//        the singles and F tail columns of the first two (the left
+//        transformation's sigma2 contractions).
 void plan_omega_contractions(Plan &P, int no, int nv, const int ijk[3],
                              int slot, int buf_tt, int buf_ovov, int buf_fov,
                              int buf_ooov, bool vvov_from_vvvo, int buf_vvov,
@@ -198,7 +200,7 @@ void plan_omega_contractions(Plan &P, int no, int nv, const int ijk[3],
     if (which & 1) {
       // Omega~^{ad}_{pq} += sum_{yz} V[x][y][z] vvov[d][y][r][z]   (N = nv)
       // Omega1^x_p       += sum_{yz} V[x][y][z] ovov[q][y][r][z]   (tail col)
-      int jb = new_job(P, 0, nv, nv + 1, nv, 1, ksplit, EPI_ATOMIC);
+      int jb = new_job(P, 0, nv, (which & 8) ? nv : nv + 1, nv, 1, ksplit, EPI_ATOMIC);
       Opnd A = with_k2(op(buf_tt, tt0, st[m[0]], st[m[2]]), nv, st[m[1]]);
       Opnd B;
       if (vvov_from_vvvo)  // vvov[d][y][r][z] = vvvo[y][d][z][r]
@@ -215,7 +217,7 @@ void plan_omega_contractions(Plan &P, int no, int nv, const int ijk[3],
     if (which & 2) {
       // Omega~^{xy}_{pl} -= sum_z V[x][y][z] ooov[q][l][r][z]     (N = no)
       // Omega~^{xy}_{pq} += sum_z V[x][y][z] F[r][z]              (tail col)
-      int jb = new_job(P, 1, (int)nv2, no + 1, no, 1, 1, EPI_ATOMIC);
+      int jb = new_job(P, 1, (int)nv2, (which & 8) ? no : no + 1, no, 1, 1, EPI_ATOMIC);
       Opnd A = with_m2(op(buf_tt, tt0, st[m[1]], st[m[2]]), nv, st[m[0]]);
       Opnd B = op(buf_ooov, (long long)q * no * no * nv + (long long)r * nv,
                   (long long)no * nv, 1, 0, 1);

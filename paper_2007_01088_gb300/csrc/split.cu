@@ -182,6 +182,10 @@ int stage(cc3_ctx *c, SplitState *S, cudaStream_t st) {
   TRY(launch_maxabs(c->t2, (long long)no * no * nv2, mx + 0, st));
   TRY(launch_maxabs(c->vvvo, nv2 * nv * no, mx + 1, st));
   TRY(launch_maxabs(c->ooov, (long long)no * no * no * nv, mx + 2, st));
+  if (c->general) {  // the blocks the symmetric case derives from vvvo and ooov
+    TRY(launch_maxabs(c->oovo, (long long)no * no * no * nv, mx + 2, st));
+    TRY(launch_maxabs(c->vvov, nv2 * nv * no, mx + 1, st));
+  }
   TRY(launch_maxabs(c->ovov, (long long)no * no * nv2, mx + 3, st));
   TRY(launch_maxabs(c->F_ov, (long long)no * nv, mx + 4, st));
   unsigned long long h[8];
@@ -219,11 +223,21 @@ int stage(cc3_ctx *c, SplitState *S, cudaStream_t st) {
   // OS[(q,r)][z][l] = oovo[l][q][z][r]
   g = {0, (long long)nv * no, 1, no, 0, (long long)no * nv * no, no, nv, op, no, 1};
   TRY(slab(&S->OS, c->oovo, (long long)no * no * nv, op, S->Eg, g, nv));
-  // Zg[r][d][(u,w)] = vvvo[u][d][w][r];  Zh[r][d][(u,w)] = vvvo[w][d][u][r]
-  g = {0, 0, 1, (long long)nv * no, nv2 * no, no, no, nv, nv, nv, nv, 1};
-  TRY(slab(&S->Zg, c->vvvo, (long long)no * nv, nv * vp, S->Eg, g, nv));
-  g = {0, 0, 1, (long long)nv * no, no, nv2 * no, no, nv, nv, nv, nv, 1};
-  TRY(slab(&S->Zh, c->vvvo, (long long)no * nv, nv * vp, S->Eg, g, nv));
+  // Zg[r][d][(u,w)] = g_durw, Zh[r][d][(u,w)] = g_dwru: from vvov[d][b][k][c]
+  // for general integrals, else through the symmetry g_durw = vvvo[u][d][w][r]
+  // (Zg) and g_dwru = vvvo[w][d][u][r] (Zh)
+  if (c->general) {
+    const long long sd = (long long)nv * no * nv, sb = (long long)no * nv;
+    g = {0, 0, nv, sd, sb, 1, no, nv, nv, nv, nv, 1};
+    TRY(slab(&S->Zg, c->vvov, (long long)no * nv, nv * vp, S->Eg, g, nv));
+    g = {0, 0, nv, sd, 1, sb, no, nv, nv, nv, nv, 1};
+    TRY(slab(&S->Zh, c->vvov, (long long)no * nv, nv * vp, S->Eg, g, nv));
+  } else {
+    g = {0, 0, 1, (long long)nv * no, nv2 * no, no, no, nv, nv, nv, nv, 1};
+    TRY(slab(&S->Zg, c->vvvo, (long long)no * nv, nv * vp, S->Eg, g, nv));
+    g = {0, 0, 1, (long long)nv * no, no, nv2 * no, no, nv, nv, nv, nv, 1};
+    TRY(slab(&S->Zh, c->vvvo, (long long)no * nv, nv * vp, S->Eg, g, nv));
+  }
   // OO[(q,r)][l'][z]
   {
     double *oo = nullptr;
