@@ -40,8 +40,9 @@ def test_t1_transformed_blocks_are_not_symmetric():
 @pytest.mark.parametrize("no,nv", [(5, 30), (4, 70), (2, 9), (3, 136)])
 def test_general_residual_matches_oracle(no, nv):
     import paper_2007_01088_gb300 as g
+    from oracle import matrix_form as MF
     inp, b = _t1_blocks(no, nv, seed=no * nv)
-    ref = oracle.omega(no, nv, inp.eps_o, inp.eps_v, inp.t2, b)
+    ref = MF.omega(no, nv, inp.eps_o, inp.eps_v, inp.t2, b)
     ctx = g.Context(inp, blocks=b)
     o1, o2, e = ctx.omega(g.CC3_FP64)
     s = max(np.abs(ref["omega2"]).max(), 1e-300)
