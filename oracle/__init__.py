@@ -239,11 +239,11 @@ def t1_transform_complex(inp, t1):
     t1m[no:, :no] = t1.T          # t1m[a][i] = t^a_i
     X = np.eye(n) - t1m
     Y = np.eye(n) + t1m.T
-    Lt = np.einsum("pt,Jtu,qu->Jpq", X, L, Y)
+    Lt = np.einsum("pt,Jtu,qu->Jpq", X, L, Y, optimize=True)
     o, v = slice(0, no), slice(no, n)
 
     def blk(Lx, p, q, r, s):
-        return np.einsum("Jpq,Jrs->pqrs", Lx[:, p, q], Lx[:, r, s])
+        return np.einsum("Jpq,Jrs->pqrs", Lx[:, p, q], Lx[:, r, s], optimize=True)
 
     out = dict(vvvo=blk(Lt, v, v, v, o), oovo=blk(Lt, o, o, v, o),
                ooov=blk(Lt, o, o, o, v), ovov=blk(Lt, o, v, o, v),
