@@ -450,13 +450,17 @@ int jacobian_fp64(cc3_ctx *c, int nvec, const double *w, const double *R1d, cons
   std::vector<double> eo(no);
   CU(cudaMemcpyAsync(eo.data(), c->eps_o, sizeof(double) * no, cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
-  if (J->wsb != c->batch) {
+  // R3 slots: the bj triples of a batch for every vector (slot v * bj + t)
+  const int bj = std::max(1, std::min(c->batch, c->batch / nvec));
+  const int nslot = bj * nvec;
+  if (J->wsb != nslot) {
     if (J->wsWR) cudaFree(J->wsWR);
     if (J->wsTTR) cudaFree(J->wsTTR);
     J->wsWR = J->wsTTR = nullptr;
-    TRY(dalloc(&J->wsWR, (size_t)nv3 * c->batch));
-    TRY(dalloc(&J->wsTTR, (size_t)nv3 * c->batch));
-    J->wsb = c->batch;
+    J->wsb = 0;
+    TRY(dalloc(&J->wsWR, (size_t)nv3 * nslot));
+    TRY(dalloc(&J->wsTTR, (size_t)nv3 * nslot));
+    J->wsb = nslot;
   }
   TRY(ensure_prep(c, J, eo, s));
   // per-vector buffers
@@ -492,38 +496,65 @@ int jacobian_fp64(cc3_ctx *c, int nvec, const double *w, const double *R1d, cons
     return pt;
   };
   for (int v = 0; v < nvec; ++v) TRY(dress(c, vec_ptrs(v), s));
-  const TermSet sets[2] = {{B_R2, B_VVVO, B_OOVO}, {B_T2, B_HVVVO, B_HOOVO}};
-  for (int t0 = 0; t0 < c->ntri; t0 += c->batch) {
-    const int t1 = std::min(c->ntri, t0 + c->batch);
-    TRY(tau_batch(c, base, t0, t1, eo, s));
-    Plan pF, pab, pom, pth;
-    for (int t = t0; t < t1; ++t) {
-      const int *ijk = &c->tri_host[3 * t];
-      plan_omega_contractions(pF, no, nv, ijk, t - t0, B_WS_TT, B_OVOV, B_HF, B_OOOV, true,
-                              B_VVVO, B_RHOT, B_RHO1, 1, 4);
-      plan_w_build(pab, no, nv, ijk, t - t0, B_WS_WR, sets, 2, 0.0, 0.0, 0);
-      plan_omega_contractions(pom, no, nv, ijk, t - t0, B_WS_TTR, B_OVOV, B_FOV, B_OOOV, true,
-                              B_VVVO, B_RHOT, B_RHO1, 2, 1);
-      plan_omega_contractions(pth, no, nv, ijk, t - t0, B_WS_TTR, B_OVOV, B_FOV, B_OOOV, true,
-                              B_VVVO, B_RHOT, B_RHO1, 1, 2);
+  // one launch per phase for all vectors: the vector's part of each per-vector
+  // buffer is an offset added to the jobs planned for it (buffers of vector 0
+  // in the pointer table)
+  const PtrTable all = vec_ptrs(0);
+  auto shift = [&](Plan &P, size_t j0, size_t k0, int v) {
+    long long off[B_COUNT] = {0};
+    off[B_R2] = v * nt2;
+    off[B_HVVVO] = v * nvvvo;
+    off[B_HOOVO] = v * noovo;
+    off[B_HF] = v * n1;
+    off[B_RHOT] = v * nt2;
+    off[B_RHO1] = v * n1;
+    for (size_t j = j0; j < P.jobs.size(); ++j) {
+      P.jobs[j].C.off += off[P.jobs[j].C.buf];
+      P.jobs[j].Ct.off += off[P.jobs[j].Ct.buf];
     }
-    for (int v = 0; v < nvec; ++v) {
-      const PtrTable pt = vec_ptrs(v);
-      TRY(run_plan(c, pF, 1, pt, s));
-      Plan pc;
+    for (size_t k = k0; k < P.terms.size(); ++k) {
+      P.terms[k].A.off += off[P.terms[k].A.buf];
+      P.terms[k].B.off += off[P.terms[k].B.buf];
+      P.terms[k].Bt.off += off[P.terms[k].Bt.buf];
+    }
+  };
+  const TermSet sets[2] = {{B_R2, B_VVVO, B_OOVO}, {B_T2, B_HVVVO, B_HOOVO}};
+  for (int t0 = 0; t0 < c->ntri; t0 += bj) {
+    const int t1 = std::min(c->ntri, t0 + bj);
+    TRY(tau_batch(c, base, t0, t1, eo, s));
+    Plan pF, pab, pc, pom, pth;
+    for (int v = 0; v < nvec; ++v)
       for (int t = t0; t < t1; ++t) {
         const int *ijk = &c->tri_host[3 * t];
+        const int u = v * bj + (t - t0);
         const double e = eo[ijk[0]] + eo[ijk[1]] + eo[ijk[2]];
-        plan_w_build(pc, no, nv, ijk, t - t0, B_WS_WR, sets, 2, w[v], e, 1);
+        size_t j0 = pF.jobs.size(), k0 = pF.terms.size();
+        plan_omega_contractions(pF, no, nv, ijk, t - t0, B_WS_TT, B_OVOV, B_HF, B_OOOV, true,
+                                B_VVVO, B_RHOT, B_RHO1, 1, 4);
+        shift(pF, j0, k0, v);
+        j0 = pab.jobs.size(), k0 = pab.terms.size();
+        plan_w_build(pab, no, nv, ijk, u, B_WS_WR, sets, 2, 0.0, 0.0, 0);
+        shift(pab, j0, k0, v);
+        j0 = pc.jobs.size(), k0 = pc.terms.size();
+        plan_w_build(pc, no, nv, ijk, u, B_WS_WR, sets, 2, w[v], e, 1);
+        shift(pc, j0, k0, v);
+        j0 = pom.jobs.size(), k0 = pom.terms.size();
+        plan_omega_contractions(pom, no, nv, ijk, u, B_WS_TTR, B_OVOV, B_FOV, B_OOOV, true,
+                                B_VVVO, B_RHOT, B_RHO1, 2, 1);
+        shift(pom, j0, k0, v);
+        j0 = pth.jobs.size(), k0 = pth.terms.size();
+        plan_omega_contractions(pth, no, nv, ijk, u, B_WS_TTR, B_OVOV, B_FOV, B_OOOV, true,
+                                B_VVVO, B_RHOT, B_RHO1, 1, 2);
+        shift(pth, j0, k0, v);
       }
-      TRY(run_plan(c, pab, 0, pt, s));
-      TRY(run_plan(c, pc, 0, pt, s));
-      trace_begin(c, TR_FP64_ELEM, s);
-      TRY(launch_contravariant(J->wsWR, J->wsTTR, nv, t1 - t0, s));
-      trace_end(c, TR_FP64_ELEM, s, 0.0, 0.0);
-      TRY(run_plan(c, pom, 0, pt, s));
-      TRY(run_plan(c, pth, 1, pt, s));
-    }
+    TRY(run_plan(c, pF, 1, all, s));
+    TRY(run_plan(c, pab, 0, all, s));
+    TRY(run_plan(c, pc, 0, all, s));
+    trace_begin(c, TR_FP64_ELEM, s);
+    TRY(launch_contravariant(J->wsWR, J->wsTTR, nv, nslot, s));
+    trace_end(c, TR_FP64_ELEM, s, 0.0, 0.0);
+    TRY(run_plan(c, pom, 0, all, s));
+    TRY(run_plan(c, pth, 1, all, s));
   }
   // Z~v . R1 and Z~o . R1 (outside the triple loop), back-transform
   for (int v = 0; v < nvec; ++v) {
@@ -544,7 +575,7 @@ size_t jacobian_footprint(int no, int nv, int naux, int nvec, int ntri, bool hos
                n1 = (size_t)no * nv, o4 = (size_t)no * no * no * no;
   size_t d = o4 + nt2;                               // oooo, oovv
   d += nv3 * no + (size_t)nv * no * no * no;         // Zv, Zo
-  d += 2 * nv3 * batch_for(nv, ntri);                // R3 workspace
+  d += 2 * nv3 * std::max(nvec, batch_for(nv, ntri));  // R3 workspace (all vectors' slots)
   d += (size_t)nvec * (nv3 * no + (size_t)no * no * nv * no + n1 + nt2 + n1);  // per vector
   d += (size_t)naux * nv * no;                       // M^J_ck
   if (host_io) d += (size_t)nvec * 2 * (n1 + nt2);   // staging of R and rho

@@ -395,8 +395,12 @@ void add_sterm(SPlan &P, int job, SOpnd A, SOpnd B, int K, int negA, double &exe
 
 // Slice arrays that play t2 and the (vvvo, oovo) integrals in the W build
 // (the same descriptor serves as A or B operand).
+// The slab offsets select one trial vector's part of an array that holds the
+// slices of every vector back to back (the Jacobian's R2 and g^ arrays): t2
+// roles (S, C, R layouts) and integral roles (XS, YS, OS layouts).
 struct WMaps {
   int aT2S, bT2S, aT2C, bT2C, aT2R, bT2R, aXS, bXS, aYS, bYS, aOS, bOS;
+  int oS = 0, oC = 0, oR = 0, oXS = 0, oYS = 0, oOS = 0;
 };
 const WMaps kStdMaps = {MA_T2S, MB_T2S, MA_T2C, MB_T2C, MA_T2R, MB_T2R,
                         MA_XS,  MB_XS,  MA_YS,  MB_YS,  MA_OS,  MB_OS};
@@ -434,8 +438,8 @@ int w_job(SPlan &P, int nv, int rows, int Nt, int phase, int slot, int E, double
 }
 // A: slabs (x, 0..nv-1) of map `am` flattened; B: slab `bslab` of map `bm`
 void w_term(SPlan &P, int jb, int am, int x, int bm, int bslab, int K, int neg, int nv,
-            int rows, double &ex, int s) {
-  add_sterm(P, jb, opd(am, x * nv), opd(bm, bslab), K, neg, ex, s);
+            int rows, double &ex, int s, int aoff = 0, int boff = 0) {
+  add_sterm(P, jb, opd(am, aoff + x * nv), opd(bm, boff + bslab), K, neg, ex, s);
   P.terms.back().aflat = nv * rows;
 }
 // phase 1, rows (c, a), columns b:
@@ -444,32 +448,32 @@ void w_term(SPlan &P, int jb, int am, int x, int bm, int bslab, int K, int neg, 
 void w_terms_1(SPlan &P, int jb, const WMaps &m, int no, int nv, int rows, int vp, int op,
                const int ijk[3], double &ex, int s) {
   const int i = ijk[0], j = ijk[1], k = ijk[2];
-  w_term(P, jb, m.aXS, k, m.bT2S, j * no + i, vp, 0, nv, rows, ex, s);
-  w_term(P, jb, m.aYS, i, m.bT2S, j * no + k, vp, 0, nv, rows, ex, s);
-  w_term(P, jb, m.aT2R, k, m.bOS, i * no + j, op, 1, nv, rows, ex, s);
-  w_term(P, jb, m.aT2C, i, m.bOS, k * no + j, op, 1, nv, rows, ex, s);
+  w_term(P, jb, m.aXS, k, m.bT2S, j * no + i, vp, 0, nv, rows, ex, s, m.oXS, m.oS);
+  w_term(P, jb, m.aYS, i, m.bT2S, j * no + k, vp, 0, nv, rows, ex, s, m.oYS, m.oS);
+  w_term(P, jb, m.aT2R, k, m.bOS, i * no + j, op, 1, nv, rows, ex, s, m.oR, m.oOS);
+  w_term(P, jb, m.aT2C, i, m.bOS, k * no + j, op, 1, nv, rows, ex, s, m.oC, m.oOS);
 }
 // phase 2, rows (c, b), columns a: the terms whose t2 / oovo factor carries a
 void w_terms_2(SPlan &P, int jb, const WMaps &m, int no, int nv, int rows, int vp, int op,
                const int ijk[3], double &ex, int s) {
   const int i = ijk[0], j = ijk[1], k = ijk[2];
-  w_term(P, jb, m.aXS, k, m.bT2S, i * no + j, vp, 0, nv, rows, ex, s);
-  w_term(P, jb, m.aYS, j, m.bT2S, i * no + k, vp, 0, nv, rows, ex, s);
-  w_term(P, jb, m.aT2C, j, m.bOS, k * no + i, op, 1, nv, rows, ex, s);
-  w_term(P, jb, m.aT2R, k, m.bOS, j * no + i, op, 1, nv, rows, ex, s);
+  w_term(P, jb, m.aXS, k, m.bT2S, i * no + j, vp, 0, nv, rows, ex, s, m.oXS, m.oS);
+  w_term(P, jb, m.aYS, j, m.bT2S, i * no + k, vp, 0, nv, rows, ex, s, m.oYS, m.oS);
+  w_term(P, jb, m.aT2C, j, m.bOS, k * no + i, op, 1, nv, rows, ex, s, m.oC, m.oOS);
+  w_term(P, jb, m.aT2R, k, m.bOS, j * no + i, op, 1, nv, rows, ex, s, m.oR, m.oOS);
 }
 // phase 3, rows (a, b), columns c: the terms whose t2 / oovo factor carries c
 void w_terms_3(SPlan &P, int jc, const WMaps &m, int no, int nv, int rows, int vp, int op,
                const int ijk[3], double &ex, int s) {
   const int i = ijk[0], j = ijk[1], k = ijk[2];
   // (k,i,j): sum_d t_ki[c][d] (ad|bj) -> YS slabs (j, a) rows b
-  w_term(P, jc, m.aYS, j, m.bT2S, k * no + i, vp, 0, nv, rows, ex, s);
+  w_term(P, jc, m.aYS, j, m.bT2S, k * no + i, vp, 0, nv, rows, ex, s, m.oYS, m.oS);
   // (k,j,i): sum_d t_kj[c][d] (bd|ai) -> XS slabs (i, a) rows b
-  w_term(P, jc, m.aXS, i, m.bT2S, k * no + j, vp, 0, nv, rows, ex, s);
+  w_term(P, jc, m.aXS, i, m.bT2S, k * no + j, vp, 0, nv, rows, ex, s, m.oXS, m.oS);
   // (i,j,k) occupied: - sum_l (lj|ck) t^{ab}_{il} -> T2R slabs (i, a) rows b
-  w_term(P, jc, m.aT2R, i, m.bOS, j * no + k, op, 1, nv, rows, ex, s);
+  w_term(P, jc, m.aT2R, i, m.bOS, j * no + k, op, 1, nv, rows, ex, s, m.oR, m.oOS);
   // (j,i,k) occupied: - sum_l (li|ck) t^{ba}_{jl} -> T2C slabs (j, a) rows b
-  w_term(P, jc, m.aT2C, j, m.bOS, i * no + k, op, 1, nv, rows, ex, s);
+  w_term(P, jc, m.aT2C, j, m.bOS, i * no + k, op, 1, nv, rows, ex, s, m.oC, m.oOS);
 }
 
 // the three W build phases of one triple (one launch)
@@ -611,6 +615,7 @@ void plan_omega_split(SPlan &P, SplitState *S, int no, int nv, const int ijk[3],
 // output / integral indices.
 struct VvovPerm {
   int slot, L, yz, p, q, r;
+  long long omt_off = 0, om1_off = 0;  // output base of this permutation's vector
 };
 
 void collect_vvov_perms(std::vector<VvovPerm> &out, const int ijk[3], int slot) {
@@ -630,7 +635,14 @@ void collect_vvov_perms(std::vector<VvovPerm> &out, const int ijk[3], int slot) 
     seen[nseen][2] = r;
     ++nseen;
     const int L = m[0];
-    out.push_back(VvovPerm{slot, L, m[1] == (L + 1) % 3 ? 1 : 0, p, q, r});
+    VvovPerm v;
+    v.slot = slot;
+    v.L = L;
+    v.yz = m[1] == (L + 1) % 3 ? 1 : 0;
+    v.p = p;
+    v.q = q;
+    v.r = r;
+    out.push_back(v);
   }
 }
 
@@ -667,8 +679,8 @@ void plan_vvov_stacked(SPlan &P, SplitState *S, int no, int nv, std::vector<Vvov
       J.expo_slot = u.slot;
       J.Nm = nv;
       J.n_valid = nv;
-      J.C = outd(B_OMT, (((long long)u.p * no + u.q) * nv + x0) * nv, nv, 1);
-      J.Ct = outd(B_OM1, (long long)u.p * nv + x0, 1, 0);
+      J.C = outd(B_OMT, u.omt_off + (((long long)u.p * no + u.q) * nv + x0) * nv, nv, 1);
+      J.Ct = outd(B_OM1, u.om1_off + (long long)u.p * nv + x0, 1, 0);
       const SOpnd tail = opd(MB_OV, u.yz ? u.q * no + u.r : u.r * no + u.q);
       add_sterm(P, jb, opd(MA_V0 + u.L, u.slot, 0, x0, 0), opd(u.yz ? MB_ZG : MB_ZH, u.r), nv * vp,
                 0, ex, s, &tail, nv);
@@ -677,8 +689,8 @@ void plan_vvov_stacked(SPlan &P, SplitState *S, int no, int nv, std::vector<Vvov
         J.msplit = rows0;
         J.Nm2 = nv + 8;
         J.expo_slot2 = w.slot;
-        J.C2 = outd(B_OMT, ((long long)w.p * no + w.q) * nv2, nv, 1);
-        J.Ct2 = outd(B_OM1, (long long)w.p * nv, 1, 0);
+        J.C2 = outd(B_OMT, w.omt_off + ((long long)w.p * no + w.q) * nv2, nv, 1);
+        J.Ct2 = outd(B_OM1, w.om1_off + (long long)w.p * nv, 1, 0);
         STerm &T = P.terms.back();
         T.A2 = opd(MA_V0 + w.L, w.slot);
         T.asplit = rows0;
@@ -1257,126 +1269,205 @@ int split_jacobian(cc3_ctx *c, int nvec, const double *w, const double *R1d, con
   }
   if (Ec < -50000) Ec = S->Et + S->Eg;  // R2 = 0 and R1 = 0: the result is 0
   const int ER = Ec - S->Eg, EH = Ec - S->Et, EF = ex_of(2 * nvec, 0);
-  // slices of R2 (t2 layouts), g^ (vvvo / oovo layouts) and F^
-  std::vector<SArrTable> arrs(nvec, S->arrs);
+  // slices of R2 (t2 layouts), g^ (vvvo / oovo layouts) and F^; each kind holds
+  // the slices of every vector back to back (vector v's slabs follow v - 1's)
+  const long long oo = (long long)no * no, onv = (long long)no * nv;
+  struct Kind {
+    int map;
+    long long K, rps, slabs;  // K, rows per slab, slabs per vector
+    __nv_bfloat16 *base;
+  };
+  Kind kinds[6] = {{MJ_R2S, vp, nv, oo, nullptr},  {MJ_R2C, op, nv, onv, nullptr},
+                   {MJ_R2R, op, nv, onv, nullptr}, {MJ_XH, vp, nv, onv, nullptr},
+                   {MJ_YH, vp, nv, onv, nullptr},  {MJ_OH, op, nv, oo, nullptr}};
+  SArrTable jr = S->arrs;  // the R3 part: combined vector arrays, R3 slot arrays
+  for (Kind &k : kinds) {
+    const size_t per = arr_elems(k.K, k.rps, k.slabs, s);
+    TRY(B.get(&k.base, per * nvec));
+    CU(cudaMemsetAsync(k.base, 0, per * nvec * sizeof(__nv_bfloat16), st));
+    jr.a[k.map] = make_arr(k.base, k.K, k.rps, k.slabs * nvec, s);
+  }
   for (int v = 0; v < nvec; ++v) {
-    __nv_bfloat16 *a = nullptr;
     const double *r2 = R2d + v * nt2, *gv = hv + v * nvvvo, *go = ho + v * noovo;
+    auto dst = [&](int i) {
+      return kinds[i].base + (size_t)v * arr_elems(kinds[i].K, kinds[i].rps, kinds[i].slabs, s);
+    };
     Gather g;
-    SArr *M = arrs[v].a;
     g = {0, (long long)no * nv2, nv2, nv, 0, 1, no, nv, vp, nv, 1};
-    TRY(slice_array(S, &a, r2, (long long)no * no * nv, vp, ER, g, nv, st));
-    B.p.push_back(a);
-    M[MJ_R2S] = make_arr(a, vp, nv, (long long)no * no, s);
+    TRY(launch_slice_gather(r2, dst(0), s, ER, g, oo * nv, vp, nv, st));
     g = {0, (long long)no * nv2, 1, nv, 0, nv2, nv, nv, op, no, 1};
-    TRY(slice_array(S, &a, r2, (long long)no * nv * nv, op, ER, g, nv, st));
-    B.p.push_back(a);
-    M[MJ_R2C] = make_arr(a, op, nv, (long long)no * nv, s);
+    TRY(launch_slice_gather(r2, dst(1), s, ER, g, onv * nv, op, nv, st));
     g = {0, (long long)no * nv2, nv, 1, 0, nv2, nv, nv, op, no, 1};
-    TRY(slice_array(S, &a, r2, (long long)no * nv * nv, op, ER, g, nv, st));
-    B.p.push_back(a);
-    M[MJ_R2R] = make_arr(a, op, nv, (long long)no * nv, s);
+    TRY(launch_slice_gather(r2, dst(2), s, ER, g, onv * nv, op, nv, st));
     g = {0, 1, no, nv2 * no, 0, nvo, nv, nv, vp, nv, 1};
-    TRY(slice_array(S, &a, gv, (long long)no * nv * nv, vp, EH, g, nv, st));
-    B.p.push_back(a);
-    M[MJ_XH] = make_arr(a, vp, nv, (long long)no * nv, s);
+    TRY(launch_slice_gather(gv, dst(3), s, EH, g, onv * nv, vp, nv, st));
     g = {0, 1, nv2 * no, no, 0, nvo, nv, nv, vp, nv, 1};
-    TRY(slice_array(S, &a, gv, (long long)no * nv * nv, vp, EH, g, nv, st));
-    B.p.push_back(a);
-    M[MJ_YH] = make_arr(a, vp, nv, (long long)no * nv, s);
+    TRY(launch_slice_gather(gv, dst(4), s, EH, g, onv * nv, vp, nv, st));
     g = {0, nvo, 1, no, 0, (long long)no * nv * no, no, nv, op, no, 1};
-    TRY(slice_array(S, &a, go, (long long)no * no * nv, op, EH, g, nv, st));
-    B.p.push_back(a);
-    M[MJ_OH] = make_arr(a, op, nv, (long long)no * no, s);
+    TRY(launch_slice_gather(go, dst(5), s, EH, g, oo * nv, op, nv, st));
   }
   {
     __nv_bfloat16 *a = nullptr;
     Gather g = {0, 0, nv, nvo, 0, 1, no, nvec, vp, nv, 1};
     TRY(slice_array(S, &a, hf, (long long)no * nvec, vp, EF, g, nvec, st));
     B.p.push_back(a);
-    for (int v = 0; v < nvec; ++v) arrs[v].a[MJ_FH] = make_arr(a, vp, nvec, no, s);
-    S->arrs.a[MJ_FH] = arrs[0].a[MJ_FH];
+    S->arrs.a[MJ_FH] = jr.a[MJ_FH] = make_arr(a, vp, nvec, no, s);
   }
-  // plans per batch: the R3 W build (one plan, run with each vector's slice
-  // arrays; the frequency enters in the element-wise step), the tau~ . F^
-  // jobs and, when the cache is cold, Z~v, Z~o
+  // Batches: bj triples share tau~3 (the residual's workspace); the R3 of all
+  // vectors for those triples fill nvec * bj slots of a workspace of their
+  // own, slot u = v * bj + t, so that each phase is one launch per batch
+  // whatever the number of vectors.
+  const double per_slot = (double)nv2 * nv * 24.0 + 3.0 * s * nv2 * vp * 2.0;
+  const int bj = std::max(1, std::min(S->batch, (int)(12.0e9 / (per_slot * nvec))));
+  const int nslot = nvec * bj;
+  float2 *Wj = nullptr, *TTj = nullptr, *W3j = nullptr, *eoj = nullptr;
+  __nv_bfloat16 *Vj[3] = {nullptr, nullptr, nullptr};
+  __nv_bfloat16 **vptrj = nullptr;
+  unsigned int *maxj = nullptr;
+  int *exj = nullptr;
+  TRY(B.get(&Wj, (size_t)nslot * nv2 * nv));
+  TRY(B.get(&TTj, (size_t)nslot * nv2 * nv));
+  TRY(B.get(&W3j, (size_t)nslot * nv2 * nv));
+  TRY(B.get(&eoj, (size_t)nslot));
+  TRY(B.get(&maxj, (size_t)nslot));
+  TRY(B.get(&exj, (size_t)nslot));
+  TRY(B.get(&vptrj, 3));
+  const long long nv8 = (nv + 7) / 8 * 8;
+  for (int L = 0; L < 3; ++L) {
+    const size_t n4 = arr_elems((long long)nv * vp, nv, nslot, s);
+    TRY(B.get(&Vj[L], n4));
+    CU(cudaMemsetAsync(Vj[L], 0, n4 * sizeof(__nv_bfloat16), st));
+    jr.a[MA_V0 + L] = make_arr(Vj[L], (long long)nv * vp, nv, nslot, s);
+    jr.a[MA_V0K + L] = make_arr(Vj[L], vp, (long long)nv * nv8, nslot, s);
+  }
+  CU(cudaMemcpyAsync(vptrj, Vj, sizeof(Vj), cudaMemcpyHostToDevice, st));
+  // plans per batch: tau3's W build, the tau~ . F^ jobs and, when the cache is
+  // cold, Z~v, Z~o (slots t); the R3 W build and contractions of all vectors
+  // (slots u, outputs offset to each vector's rho~)
   const bool prep = jac_prep_prec(c) < 0;
   double *Zv = nullptr, *Zo = nullptr;
   TRY(jac_z_buffers(c, &Zv, &Zo, prep, st));
   const int rows = (nv + 7) / 8 * 8;
-  const WMaps set1 = {MJ_R2S, MJ_R2S, MJ_R2C, MJ_R2C, MJ_R2R, MJ_R2R,
-                      MA_XS,  MB_XS,  MA_YS,  MB_YS,  MA_OS,  MB_OS};
-  const WMaps set2 = {MA_T2S, MB_T2S, MA_T2C, MB_T2C, MA_T2R, MB_T2R,
-                      MJ_XH,  MJ_XH,  MJ_YH,  MJ_YH,  MJ_OH,  MJ_OH};
-  const int nb = (int)S->ab.size();
-  JacPlans pAB, pF, pZ;
+  const int ks4 = S->ks4;
+  const bool stack = S->stack_vvov && nv >= S_BM && nv % 8 == 0 && nv % S_BM != 0;
+  const int nb = (c->ntri + bj - 1) / bj;
+  JacPlans pT, pAB, pF, pZ, pO;
+  pT.v.resize(nb);
   pAB.v.resize(nb);
   pF.v.resize(nb);
   pZ.v.resize(nb);
-  double ex = 0.0;
-  for (int b = 0, t0 = 0; b < nb; ++b) {
-    const int t1 = t0 + S->nslot[b];
-    SPlan ab, f, z;
+  pO.v.resize(nb);
+  std::vector<float2> eoh((size_t)nslot * nb);
+  double ex = 0.0, ex_tau = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    const int t0 = b * bj, t1 = std::min(c->ntri, t0 + bj);
+    SPlan tb, ab, f, z, om, om3;
+    std::vector<VvovPerm> vperms;
     for (int t = t0; t < t1; ++t) {
       const int *ijk = &c->tri_host[3 * t];
-      const int j1 = w_job(ab, nv, rows, S->Nab, 1, t - t0, Ec - 14, ex, s);
-      w_terms_1(ab, j1, set1, no, nv, rows, vp, op, ijk, ex, s);
-      w_terms_1(ab, j1, set2, no, nv, rows, vp, op, ijk, ex, s);
-      const int j2 = w_job(ab, nv, rows, S->Nab, 2, t - t0, Ec - 14, ex, s);
-      w_terms_2(ab, j2, set1, no, nv, rows, vp, op, ijk, ex, s);
-      w_terms_2(ab, j2, set2, no, nv, rows, vp, op, ijk, ex, s);
-      const int j3 = w_job(ab, nv, rows, S->Nab, 3, t - t0, Ec - 14, ex, s);
-      w_terms_3(ab, j3, set1, no, nv, rows, vp, op, ijk, ex, s);
-      w_terms_3(ab, j3, set2, no, nv, rows, vp, op, ijk, ex, s);
+      plan_w_split(tb, S, no, nv, ijk, t - t0, ex_tau);
       plan_jac_tau(&f, prep ? &z : nullptr, S, no, nv, nvec, EF, ijk, t - t0, ex);
+      const double eo_sum = c->eo_h[ijk[0]] + c->eo_h[ijk[1]] + c->eo_h[ijk[2]];
+      for (int v = 0; v < nvec; ++v) {
+        const int u = v * bj + (t - t0);
+        // the element-wise step divides by (0 - (e_a+e_b+e_c - eo)): with
+        // eo = e_i + e_j + e_k + w that is (w - eps)
+        const dd::df e = dd::from_double_host(eo_sum + w[v]);
+        eoh[(size_t)b * nslot + u] = make_float2(e.hi, e.lo);
+        WMaps set1 = {MJ_R2S, MJ_R2S, MJ_R2C, MJ_R2C, MJ_R2R, MJ_R2R,
+                      MA_XS,  MB_XS,  MA_YS,  MB_YS,  MA_OS,  MB_OS};
+        set1.oS = (int)(v * oo);
+        set1.oC = set1.oR = (int)(v * onv);
+        WMaps set2 = {MA_T2S, MB_T2S, MA_T2C, MB_T2C, MA_T2R, MB_T2R,
+                      MJ_XH,  MJ_XH,  MJ_YH,  MJ_YH,  MJ_OH,  MJ_OH};
+        set2.oXS = set2.oYS = (int)(v * onv);
+        set2.oOS = (int)(v * oo);
+        const int j1 = w_job(ab, nv, rows, S->Nab, 1, u, Ec - 14, ex, s);
+        w_terms_1(ab, j1, set1, no, nv, rows, vp, op, ijk, ex, s);
+        w_terms_1(ab, j1, set2, no, nv, rows, vp, op, ijk, ex, s);
+        const int j2 = w_job(ab, nv, rows, S->Nab, 2, u, Ec - 14, ex, s);
+        w_terms_2(ab, j2, set1, no, nv, rows, vp, op, ijk, ex, s);
+        w_terms_2(ab, j2, set2, no, nv, rows, vp, op, ijk, ex, s);
+        const int j3 = w_job(ab, nv, rows, S->Nab, 3, u, Ec - 14, ex, s);
+        w_terms_3(ab, j3, set1, no, nv, rows, vp, op, ijk, ex, s);
+        w_terms_3(ab, j3, set2, no, nv, rows, vp, op, ijk, ex, s);
+        // the contractions of R~3 into vector v's rho~ and rho1
+        const size_t first = om3.jobs.size();
+        if (stack) {
+          const size_t f0 = vperms.size();
+          collect_vvov_perms(vperms, ijk, u);
+          for (size_t k = f0; k < vperms.size(); ++k) {
+            vperms[k].omt_off = (long long)v * nt2;
+            vperms[k].om1_off = (long long)v * n1;
+          }
+        } else {
+          plan_omega_split(om3, S, no, nv, ijk, u, ks4, ex, 1);
+        }
+        plan_omega_split(om3, S, no, nv, ijk, u, ks4, ex, 2);
+        for (size_t jx = first; jx < om3.jobs.size(); ++jx) {
+          SJob &J = om3.jobs[jx];
+          for (OutD *o : {&J.C, &J.Ct, &J.C2, &J.Ct2}) {
+            if (o->buf == B_OMT) o->off += (long long)v * nt2;
+            else if (o->buf == B_OM1) o->off += (long long)v * n1;
+          }
+        }
+      }
     }
+    if (stack) plan_vvov_stacked(om, S, no, nv, vperms, ks4, ex);
+    append_plan(om, om3);  // the long-K vvov tiles first
+    TRY(s_upload_plan(tb, &pT.v[b], st));
     TRY(s_upload_plan(ab, &pAB.v[b], st));
     TRY(s_upload_plan(f, &pF.v[b], st));
     if (prep) TRY(s_upload_plan(z, &pZ.v[b], st));
-    t0 = t1;
+    TRY(s_upload_plan(om, &pO.v[b], st));
   }
-  // the loop: tau~ once per batch, then R3 and its contractions per vector
+  float2 *eoj_all = nullptr;
+  TRY(B.get(&eoj_all, eoh.size()));
+  CU(cudaMemcpyAsync(eoj_all, eoh.data(), sizeof(float2) * eoh.size(), cudaMemcpyHostToDevice,
+                     st));
+  // the loop: per batch, tau~3 and its jobs, then the R3 of every vector
   VPtrTable P;
   fill_vptrs(c, S, &P);
   P.p[B_ZV] = Zv;
   P.p[B_ZO] = Zo;
+  P.p[B_OMT] = rt;
+  P.p[B_OM1] = r1a;
+  VPtrTable PR = P;
+  PR.p[B_WS_W] = Wj;
+  PR.p[B_WS_TT] = TTj;
+  PR.p[B_WS_W3] = W3j;
+  PR.p[B_SLOTEXP] = exj;
   const int kd = S_DRAIN_STEPS;
   long long *L = &c->counters.launches;
-  // tau at frequency wv from the W build's partial sums, tau~ and its slices
-  auto elem = [&](int ns, int t0, double wv) -> int {
-    trace_begin(c, TR_SPLIT_ELEM, st);
-    CU(cudaMemsetAsync(S->maxbits, 0, sizeof(unsigned int) * ns, st));
-    const dd::df wd = dd::from_double_host(wv);
-    TRY(launch_tau_contravariant_dd(S->Wdd, S->TTdd, S->W3dd, S->TTdd, S->evdd, S->eo_tri + t0,
-                                    wd.hi, wd.lo, nv, ns, S->maxbits, st));
-    TRY(launch_slot_exponent(S->maxbits, S->slot_ex, ns, st));
-    TRY(launch_slice_tt(S->TTdd, S->vptr, nv, vp, s, S->slot_ex, ns, S->batch, st));
-    trace_end(c, TR_SPLIT_ELEM, st, 0.0, 0.0);
-    *L += 3;
-    return CC3_OK;
-  };
   auto run = [&](const SDevPlan &d, const SArrTable &a, const VPtrTable &pt, int cls) -> int {
     trace_begin(c, cls, st);
     TRY(s_launch_plan(d, a, pt, s, kd, S->status, st, L));
     trace_end(c, cls, st, d.flop, d.slice_flop);
     return CC3_OK;
   };
-  for (int b = 0, t0 = 0; b < nb; t0 += S->nslot[b], ++b) {
-    const int ns = S->nslot[b];
-    P.p[B_OMT] = rt;
-    P.p[B_OM1] = r1a;
-    TRY(run(S->ab[b], S->arrs, P, TR_SPLIT_W));
-    TRY(elem(ns, t0, 0.0));
+  // tau (or R3) and tau~ from the W build's partial sums, slot exponents and
+  // the slices of the contravariant amplitudes
+  auto elem = [&](float2 *W1, float2 *W2, float2 *W3, const float2 *eo, int ns,
+                  unsigned int *mb, int *exs, __nv_bfloat16 **vp_dev, int nalloc) -> int {
+    trace_begin(c, TR_SPLIT_ELEM, st);
+    CU(cudaMemsetAsync(mb, 0, sizeof(unsigned int) * ns, st));
+    TRY(launch_tau_contravariant_dd(W1, W2, W3, W2, S->evdd, eo, 0.f, 0.f, nv, ns, mb, st));
+    TRY(launch_slot_exponent(mb, exs, ns, st));
+    TRY(launch_slice_tt(W2, vp_dev, nv, vp, s, exs, ns, nalloc, st));
+    trace_end(c, TR_SPLIT_ELEM, st, 0.0, 0.0);
+    *L += 3;
+    return CC3_OK;
+  };
+  for (int b = 0; b < nb; ++b) {
+    const int t0 = b * bj, ns = std::min(c->ntri, t0 + bj) - t0;
+    TRY(run(pT.v[b], S->arrs, P, TR_SPLIT_W));
+    TRY(elem(S->Wdd, S->TTdd, S->W3dd, S->eo_tri + t0, ns, S->maxbits, S->slot_ex, S->vptr,
+             S->batch));
     if (prep) TRY(run(pZ.v[b], S->arrs, P, TR_SPLIT_OMEGA));
     TRY(run(pF.v[b], S->arrs, P, TR_SPLIT_OMEGA));
-    for (int v = 0; v < nvec; ++v) {
-      TRY(run(pAB.v[b], arrs[v], P, TR_SPLIT_W));
-      TRY(elem(ns, t0, w[v]));
-      VPtrTable Pv = P;
-      Pv.p[B_OMT] = rt + v * nt2;
-      Pv.p[B_OM1] = r1a + v * n1;
-      TRY(run(S->om[b], S->arrs, Pv, TR_SPLIT_OMEGA));
-    }
+    TRY(run(pAB.v[b], jr, PR, TR_SPLIT_W));
+    TRY(elem(Wj, TTj, W3j, eoj_all + (size_t)b * nslot, nslot, maxj, exj, vptrj, nslot));
+    TRY(run(pO.v[b], jr, PR, TR_SPLIT_OMEGA));
   }
   int hs = 0;
   CU(cudaMemcpyAsync(&hs, S->status, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1395,7 +1486,7 @@ int split_jacobian(cc3_ctx *c, int nvec, const double *w, const double *R1d, con
                        cudaMemcpyDeviceToDevice, st));
   }
   CU(cudaStreamSynchronize(st));
-  c->counters.executed_flop = ex + (double)nvec * S->executed;
+  c->counters.executed_flop = ex + ex_tau;
   c->counters.slices = s;
   return CC3_OK;
 }
@@ -1412,6 +1503,13 @@ size_t split_jacobian_footprint(int no, int nv, int s, int nvec) {
   size_t per = sl((long long)no * no * nv, vp, nv) + 2 * sl((long long)no * nv * nv, op, nv) +
                2 * sl((long long)no * nv * nv, vp, nv) + sl((long long)no * no * nv, op, nv);
   b += (size_t)nvec * per + sl((long long)no * nvec, vp, nvec);
+  // the R3 slots of all vectors (the same arithmetic as split_jacobian)
+  const long long nv2 = (long long)nv * nv;
+  const double per_slot = (double)nv2 * nv * 24.0 + 3.0 * s * nv2 * vp * 2.0;
+  const int batch = (int)std::max(1.0, std::min(16.0, 6.0e9 / per_slot));
+  const int bj = std::max(1, std::min(batch, (int)(12.0e9 / (per_slot * nvec))));
+  b += (size_t)(nvec * bj) * (size_t)(3 * nv2 * nv * sizeof(float2) + 16) +
+       3 * arr_elems((long long)nv * vp, nv, (long long)nvec * bj, s) * sizeof(__nv_bfloat16);
   return b + 65536;
 }
 

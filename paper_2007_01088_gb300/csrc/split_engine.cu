@@ -109,6 +109,26 @@ __device__ __forceinline__ void issue_products_all(uint32_t tmem, uint64_t dA, u
       issue_one<S>(tmem, dA, dB, a16, b16, Nt, idesc, fresh, p, q, q, S - p);
 }
 
+// The slice products of two consecutive K steps with their A-slice runs
+// interleaved (run p of step 0, run p of step 1, run p + 1 of step 0, ...):
+// the first products that read a newly landed stage then overlap the other
+// step's products instead of waiting alone.  Each run keeps its A slice in
+// the collector buffer, as in issue_products_all.
+template <int S>
+__device__ __forceinline__ void issue_products_pair(uint32_t tmem, uint64_t dA0, uint64_t dB0,
+                                                    uint32_t id0, uint64_t dA1, uint64_t dB1,
+                                                    uint32_t id1, uint32_t Nt, uint32_t &fresh) {
+#pragma unroll
+  for (int p = 0; p < S; ++p) {
+#pragma unroll
+    for (int q = 0; q < S - p; ++q)
+      issue_one<S>(tmem, dA0, dB0, 16u, 16u, Nt, id0, fresh, p, q, q, S - p);
+#pragma unroll
+    for (int q = 0; q < S - p; ++q)
+      issue_one<S>(tmem, dA1, dB1, 16u, 16u, Nt, id1, fresh, p, q, q, S - p);
+  }
+}
+
 // Kept out of line: inlined into the unrolled output loop it would make the
 // kernel large enough for instruction-cache misses to stall the MMA warp.
 __device__ __noinline__ void fx_add_call(unsigned long long *slot, double v) { fx_add(slot, v); }
@@ -418,29 +438,48 @@ split_engine_kernel(const SJob *__restrict__ jobs, int njobs, const STerm *__res
         uint32_t fresh = (1u << S_NACC) - 1;
         int since = 0;
         bool pending = false;
-        for (int g = ti.g0; g < ti.g1; ++g, ++it) {
-          const int st = it % S_STAGES, ph = (it / S_STAGES) & 1;
-          if (!mbar_wait(&full[st], ph, &err)) { ok = false; break; }
+        // K steps two at a time (drains come every kdrain_steps, an even
+        // number, so a pair never straddles one); a lone last step of a tile
+        // goes alone
+        for (int g = ti.g0; g < ti.g1;) {
+          const bool two = g + 1 < ti.g1;
+          const int st0 = it % S_STAGES, ph0 = (it / S_STAGES) & 1;
+          const int st1 = (it + 1) % S_STAGES, ph1 = ((it + 1) / S_STAGES) & 1;
+          if (!mbar_wait(&full[st0], ph0, &err)) { ok = false; break; }
+          if (two && !mbar_wait(&full[st1], ph1, &err)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t idesc = sneg[st] ? id_neg : id_pos;
-          const uint32_t sa = smem_u32(smem + (size_t)st * ((size_t)s * (a_bytes + S_NT_MAX * 32)));
+          const uint32_t id0 = sneg[st0] ? id_neg : id_pos, id1 = sneg[st1] ? id_neg : id_pos;
+          const size_t stage_bytes = (size_t)s * (a_bytes + S_NT_MAX * 32);
+          const uint32_t sa0 = smem_u32(smem + (size_t)st0 * stage_bytes),
+                         sa1 = smem_u32(smem + (size_t)st1 * stage_bytes);
           // slice p of a tile starts 256 p bytes in; row groups are 256 s bytes apart
-          const uint64_t dA = smem_desc_kmajor(sa, 256u * s),
-                         dB = smem_desc_kmajor(sa + (uint32_t)s * a_bytes, 256u * s);
+          const uint64_t dA0 = smem_desc_kmajor(sa0, 256u * s),
+                         dB0 = smem_desc_kmajor(sa0 + (uint32_t)s * a_bytes, 256u * s),
+                         dA1 = smem_desc_kmajor(sa1, 256u * s),
+                         dB1 = smem_desc_kmajor(sa1 + (uint32_t)s * a_bytes, 256u * s);
           if (pending) {
             // levels >= 4 first (they never wait for a drain), then levels 0..3
-            issue_products<S, true>(tmem, dA, dB, 16u, 16u, (uint32_t)Nt, idesc, fresh);
+            issue_products<S, true>(tmem, dA0, dB0, 16u, 16u, (uint32_t)Nt, id0, fresh);
+            if (two) issue_products<S, true>(tmem, dA1, dB1, 16u, 16u, (uint32_t)Nt, id1, fresh);
             if (!mbar_wait(&drainempty, nd & 1, &err)) { ok = false; break; }
             tc_fence_after();
             ++nd;
             pending = false;
             fresh |= 0xFu;
-            issue_products<S, false>(tmem, dA, dB, 16u, 16u, (uint32_t)Nt, idesc, fresh);
+            issue_products<S, false>(tmem, dA0, dB0, 16u, 16u, (uint32_t)Nt, id0, fresh);
+            if (two) issue_products<S, false>(tmem, dA1, dB1, 16u, 16u, (uint32_t)Nt, id1, fresh);
+          } else if (two) {
+            issue_products_pair<S>(tmem, dA0, dB0, id0, dA1, dB1, id1, (uint32_t)Nt, fresh);
           } else {
-            issue_products_all<S>(tmem, dA, dB, 16u, 16u, (uint32_t)Nt, idesc, fresh);
+            issue_products_all<S>(tmem, dA0, dB0, 16u, 16u, (uint32_t)Nt, id0, fresh);
           }
-          umma_commit(&empty[st]);
-          if (++since == kdrain_steps && g + 1 < ti.g1) {
+          umma_commit(&empty[st0]);
+          if (two) umma_commit(&empty[st1]);
+          const int n = two ? 2 : 1;
+          g += n;
+          it += n;
+          since += n;
+          if (since >= kdrain_steps && g < ti.g1) {
             umma_commit(&drainfull);
             pending = true;
             since = 0;
@@ -667,6 +706,11 @@ int s_launch_plan(const SDevPlan &d, const SArrTable &arrs, const VPtrTable &ptr
   if (d.njobs == 0 || d.tiles == 0) return CC3_OK;
   if (d.tiles > 0x7fffffffLL) return CC3_ERR_ARG;
   if (slices < 3 || slices > S_MAX_SLICES) return CC3_ERR_ARG;
+  // the issuer takes K steps in pairs, so the exact accumulators are drained
+  // after an even number of steps: the interval must be even (and at most 16,
+  // the bound that keeps them exact)
+  if (kdrain_steps < 2 || kdrain_steps > 16 || (kdrain_steps & 1))
+    return CC3_FAIL(CC3_ERR_ARG, "drain interval");
   // at least 120 KB so that one CTA (and one 512-column TMEM allocation) per SM
   const size_t smem = std::max<size_t>(s_smem_bytes(slices, S_NT_MAX), 120 * 1024);
   // per device, once; several host threads (serving slots) may get here at once

@@ -161,3 +161,24 @@ def test_jacobian_batched_shape_both_paths(g):
     for n in range(8):
         assert split_close(s1[n], f1[n]), (n, split_err(s1[n], f1[n]))
         assert split_close(s2[n], f2[n]), (n, split_err(s2[n], f2[n]))
+
+
+def test_split_jacobian_launches_per_batch_do_not_grow_with_vectors(g):
+    # every phase of a batch of triples is one launch for all trial vectors:
+    # the launches that grow with nvec are the per-vector set-up (dressing,
+    # slicing, the Z~ . R1 terms), the same for any number of triples
+    no, nv = 6, 20
+    inp = make_inputs(no, nv, seed=61)
+    tr = [t[:3] for t in unique_triples(no)]
+    counts = {}
+    for ntri in (4, len(tr)):
+        for nvec in (1, 4):
+            R1, R2 = make_trial_vectors(no, nv, nvec, seed=nvec)
+            ctx = g.Context(inp)
+            ctx.set_triples(tr[:ntri])
+            ctx.jacobian(R1, R2, [0.2] * nvec, g.CC3_SPLIT_BF16)  # fills the Z~ cache
+            ctx.jacobian(R1, R2, [0.2] * nvec, g.CC3_SPLIT_BF16)
+            counts[(ntri, nvec)] = ctx.counters()["launches"]
+            ctx.close()
+    assert counts[(4, 4)] - counts[(4, 1)] == counts[(len(tr), 4)] - counts[(len(tr), 1)]
+    assert counts[(len(tr), 1)] > counts[(4, 1)]
