@@ -7,14 +7,15 @@ seeded input generator in ``cc3_inputs``.
 
 Two independent forms of the same result (Paul, Myhre, Koch, arXiv 2007.01088):
 
-* ``omega`` / ``prep`` / ``jacobian`` / ``left_jacobian``: the restricted-loop
-  algorithms written out in plain C (``cc3_oracle.c``; Algorithm 1,
-  Algorithm 2, the right Jacobian transformation reconstructed from eq. "jcc3"
-  and its transpose).
+* ``omega`` / ``prep`` / ``jacobian`` / ``left_jacobian`` / ``density``: the
+  restricted-loop algorithms written out in plain C (``cc3_oracle.c``;
+  Algorithm 1, Algorithm 2, the right Jacobian transformation reconstructed
+  from eq. "jcc3", its transpose, and Algorithm 3's densities).
 * ``matrix_form``: the same restricted loops with numpy matrix products as
   steps, for test shapes where the C loops are too slow.
-* ``definition.omega_full``: the plain definition over the full
-  nv^3 no^3 tensor (every ordered i,j,k), numpy, tiny sizes only.
+* ``definition.omega_full`` / ``definition.density_full``: the plain
+  definitions over the full nv^3 no^3 tensor (every ordered i,j,k), numpy,
+  tiny sizes only.
 
 ``t1_transform`` gives T1-transformed integral blocks, used to pin the Jacobian
 as the derivative of the residual (finite differences).
@@ -66,6 +67,9 @@ def _load():
             lib.oracle_left_jacobian.argtypes = ([I, I] + [P] * 9 + [P, I, I, P, P, P]
                                                  + [I, P, P, P, P, I])
             lib.oracle_left_jacobian.restype = I
+            lib.oracle_density.argtypes = ([I, I] + [P] * 9 + [ctypes.c_double, P, P]
+                                           + [P, P, P, P, I])
+            lib.oracle_density.restype = I
             lib.oracle_dressed_blocks.argtypes = [I, I, P, I, P, P, P, P, P, P]
             lib.oracle_dressed_blocks.restype = None
             _lib = lib
@@ -204,6 +208,32 @@ def left_jacobian(inp, L1, L2, w, triples=None, nthreads=0):
     if used < 0:
         raise MemoryError("oracle_left_jacobian failed")
     return dict(sigma1=s1, sigma2=s2, flops=fl.value, threads=used)
+
+
+def density(no, nv, eps_o, eps_v, t2, blocks, w, L1, L2, nthreads=0):
+    """Algorithm 3 on the general blocks: the triples contributions to the
+    one-electron density D^{m,0} of the left state (L1[i][a], L2[i][j][a][b])
+    at frequency w (w = 0 with ground-state multipliers: D^{0,0}).  Returns
+    dict(Doo[no][no], Dov[no][nv], Dvv[nv][nv], flops, threads); the vo block
+    has no triples term."""
+    lib = _load()
+    b = {k: _c(v) for k, v in blocks.items()}
+    L1, L2 = _c(L1).reshape(no, nv), _c(L2).reshape(no, no, nv, nv)
+    doo, dov, dvv = np.zeros((no, no)), np.zeros((no, nv)), np.zeros((nv, nv))
+    fl = ctypes.c_longlong(0)
+    used = lib.oracle_density(no, nv, _p(_c(eps_o)), _p(_c(eps_v)), _p(_c(t2)),
+                              _p(b["vvvo"]), _p(b["oovo"]), _p(b["ooov"]), _p(b["ovov"]),
+                              _p(b["vvov"]), _p(b["F_ov"]), float(w), _p(L1), _p(L2),
+                              _p(doo), _p(dov), _p(dvv), ctypes.byref(fl), int(nthreads))
+    if used < 0:
+        raise MemoryError("oracle_density failed")
+    return dict(Doo=doo, Dov=dov, Dvv=dvv, flops=fl.value, threads=used)
+
+
+def density_inputs(inp, w, L1, L2, nthreads=0):
+    """``density`` on the symmetric (T1 = 0) inputs of ``cc3_inputs``."""
+    return density(inp.no, inp.nv, inp.eps_o, inp.eps_v, inp.t2, symmetric_blocks(inp),
+                   w, L1, L2, nthreads)
 
 
 def dressed_blocks(inp, R1):

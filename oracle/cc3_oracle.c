@@ -1017,6 +1017,257 @@ int oracle_left_jacobian(int no, int nv, const double *eps_o, const double *eps_
   return used;
 }
 
+/* ------------------------------------------------------------------------
+ * Algorithm 3: the triples contributions to the one-electron density
+ * D^{m,0}_{pq} = <m|E_pq|CC> of a left state (L1, L2) at frequency w; with
+ * w = 0 and the ground-state multipliers in place of (L1, L2) the same steps
+ * give D^{0,0} (the paragraph after Algorithm 3).
+ *
+ * The L3 amplitudes are the covariant triples of the left state exactly as
+ * the left transformation above builds them: X from L1 and Lt2 (the
+ * back-transformed L2), L3 = P X / (w - eps), L~3 = contravariant(L3).  The
+ * doubles of the left state enter the ov block through Lt2 as well: that
+ * term is the derivative of sum L.Omega with respect to F_kc.
+ *
+ * Occupied loop, triples i >= j >= k, every distinct permutation (p,q,r) of a
+ * triple (V_X = the view of X_{ijk} with the virtual slots permuted alike):
+ *   tau = W / (0 - eps) (Algorithm 1),  tau~ = contravariant(tau)
+ *   Y[c][l][p][r] += sum_ab V_L~[a][b][c] t[l][q][a][b]
+ *   Dvv[c][d]     += 1/2 sum_ab V_L~[a][b][c] V_tau[a][b][d]
+ *   Dov[r][c]     += sum_ab Lt2[p][q][a][b] V_tau~[a][b][c]
+ * after it  Dov[l][d] -= sum_cik Y[c][l][i][k] t[k][i][c][d].
+ * Virtual loop, a >= b >= c, every distinct ordering (x,y,z) of the virtual
+ * triple and every ordered occupied triple (i,j,k): tau^{xyz}_{ijk} and
+ * L3^{xyz}_{ijk} from the same formulas, and
+ *   Doo[l][k]     -= 1/2 sum_ij L~^{xyz}_{ijk} tau^{xyz}_{ijl}.
+ * The vo block has no triples term.  tau and L3 take the formula's values at
+ * every index (also i = j = k and a = b = c), as the two loops build them.
+ * Cost: 6 nv^4 per distinct permutation (tau3, X, Dvv) plus 4 nv^4 no^3 for
+ * the virtual loop (tau3 and X again): 10 nv^4 no^3 in all.
+ * ---------------------------------------------------------------------- */
+
+/* B^{xyz}_{pqr} and X^{xyz}_{pqr} of one element (the tau3 bracket and the L3
+ * numerator of one ordered triple pair) */
+static double elem_B(const blocks_t *B, int x, int y, int z, int p, int q, int r) {
+  int no = B->no, nv = B->nv;
+  double s = 0.0;
+  for (int d = 0; d < nv; ++d) s += T2(B, p, q, x, d) * VVVO(B, y, d, z, r);
+  for (int l = 0; l < no; ++l) s -= T2(B, p, l, x, y) * OOVO(B, l, q, z, r);
+  return s;
+}
+
+static double elem_X(const blocks_t *B, const double *l1, const double *lt2, int x, int y,
+                     int z, int p, int q, int r) {
+  int no = B->no, nv = B->nv;
+#define LT(i, j, a, b) lt2[(((size_t)(i) * no + (j)) * nv + (a)) * nv + (b)]
+  double s = l1[(size_t)p * nv + x] * OVOV(B, q, y, r, z) + LT(p, q, x, y) * B->F_ov[(size_t)r * nv + z];
+  for (int d = 0; d < nv; ++d) s += LT(p, q, x, d) * VVOV(B, d, y, r, z);
+  for (int l = 0; l < no; ++l) s -= LT(p, l, x, y) * OOOV(B, q, l, r, z);
+#undef LT
+  return s;
+}
+
+/* index in PERM6 of the slot map m */
+static int perm_index(const int m[3]) {
+  for (int s = 0; s < 6; ++s)
+    if (PERM6[s][0] == m[0] && PERM6[s][1] == m[1] && PERM6[s][2] == m[2]) return s;
+  return -1;
+}
+
+int oracle_density(int no, int nv, const double *eps_o, const double *eps_v,
+                   const double *t2, const double *vvvo, const double *oovo,
+                   const double *ooov, const double *ovov, const double *vvov,
+                   const double *F_ov, double w, const double *L1, const double *L2,
+                   double *Doo, double *Dov, double *Dvv, long long *flops, int nthreads) {
+  size_t nv2 = (size_t)nv * nv, nv3 = nv2 * nv, n1 = (size_t)no * nv,
+         n2 = (size_t)no * no * nv * nv, no3 = (size_t)no * no * no;
+  size_t ny = (size_t)nv * no * no * no;
+  int *T = NULL;
+  int nt = list_triples(no, 0, NULL, &T);
+  if (nt < 0) return -1;
+  int used = set_threads(nthreads);
+  blocks_t B = {no, nv, eps_o, eps_v, t2, vvvo, oovo, ooov, ovov, vvov, F_ov};
+  double *lt2 = (double *)malloc(n2 * sizeof(double) + 8);
+  back_transform(no, nv, L2, lt2);
+  double *Y = (double *)calloc(ny + 1, sizeof(double));
+  double *dvv = (double *)calloc(nv2 + 1, sizeof(double));
+  double *dov = (double *)calloc(n1 + 1, sizeof(double));
+  double *doo = (double *)calloc((size_t)no * no + 1, sizeof(double));
+  long long fl = 0;
+  /* occupied loop */
+#pragma omp parallel if (nt >= used) reduction(+ : fl)
+  {
+    double *W = (double *)malloc(nv3 * sizeof(double) + 8);
+    double *S = (double *)malloc(nv3 * sizeof(double) + 8);
+    double *tau = (double *)malloc(nv3 * sizeof(double) + 8);
+    double *tt = (double *)malloc(nv3 * sizeof(double) + 8);
+    double *l3 = (double *)malloc(nv3 * sizeof(double) + 8);
+    double *lt = (double *)malloc(nv3 * sizeof(double) + 8);
+    double *VL = (double *)malloc(nv3 * sizeof(double) + 8);
+    double *Vt = (double *)malloc(nv3 * sizeof(double) + 8);
+    double *Vtt = (double *)malloc(nv3 * sizeof(double) + 8);
+    double *y = (double *)calloc(ny + 1, sizeof(double));
+    double *mvv = (double *)calloc(nv2 + 1, sizeof(double));
+    double *mov = (double *)calloc(n1 + 1, sizeof(double));
+#pragma omp for schedule(dynamic, 1)
+    for (int t = 0; t < nt; ++t) {
+      const int *ijk = T + 3 * t;
+      int maps[6][3];
+      int np = distinct_perms(ijk, maps);
+      if (np == 0) continue;
+      build_W(no, nv, t2, vvvo, oovo, ijk, W, S, &fl);
+      divide_denominator(&B, ijk, 0.0, W, tau);
+      contravariant(nv, tau, tt);
+      build_PX(&B, L1, lt2, ijk, W, S, &fl);
+      divide_denominator(&B, ijk, w, W, l3);
+      contravariant(nv, l3, lt);
+      for (int u = 0; u < np; ++u) {
+        int p = ijk[maps[u][0]], q = ijk[maps[u][1]], r = ijk[maps[u][2]];
+        permuted_view(nv, lt, maps[u], VL);
+        permuted_view(nv, tau, maps[u], Vt);
+        permuted_view(nv, tt, maps[u], Vtt);
+        ORACLE_INNER_FOR
+        for (int c = 0; c < nv; ++c) {
+          for (int l = 0; l < no; ++l) {   /* Y[c][l][p][r] */
+            double s = 0.0;
+            for (int a = 0; a < nv; ++a)
+              for (int b = 0; b < nv; ++b)
+                s += VL[(size_t)a * nv2 + (size_t)b * nv + c] * T2(&B, l, q, a, b);
+            y[(((size_t)c * no + l) * no + p) * no + r] += s;
+          }
+          for (int d = 0; d < nv; ++d) {   /* Dvv[c][d] */
+            double s = 0.0;
+            for (int a = 0; a < nv; ++a)
+              for (int b = 0; b < nv; ++b)
+                s += VL[(size_t)a * nv2 + (size_t)b * nv + c] * Vt[(size_t)a * nv2 + (size_t)b * nv + d];
+            mvv[(size_t)c * nv + d] += 0.5 * s;
+          }
+          double s = 0.0;                  /* Dov[r][c] */
+          for (int a = 0; a < nv; ++a)
+            for (int b = 0; b < nv; ++b)
+              s += lt2[(((size_t)p * no + q) * nv + a) * nv + b] * Vtt[(size_t)a * nv2 + (size_t)b * nv + c];
+          mov[(size_t)r * nv + c] += s;
+        }
+        fl += 2LL * nv * nv * nv * nv;
+      }
+    }
+#pragma omp critical
+    {
+      for (size_t x = 0; x < ny; ++x) Y[x] += y[x];
+      for (size_t x = 0; x < nv2; ++x) dvv[x] += mvv[x];
+      for (size_t x = 0; x < n1; ++x) dov[x] += mov[x];
+    }
+    free(W); free(S); free(tau); free(tt); free(l3); free(lt); free(VL); free(Vt); free(Vtt);
+    free(y); free(mvv); free(mov);
+  }
+  /* Dov[l][d] -= sum_{c,i,k} Y[c][l][i][k] t[k][i][c][d] */
+  for (int l = 0; l < no; ++l)
+    for (int d = 0; d < nv; ++d) {
+      double s = 0.0;
+      for (int c = 0; c < nv; ++c)
+        for (int i = 0; i < no; ++i)
+          for (int k = 0; k < no; ++k)
+            s += Y[(((size_t)c * no + l) * no + i) * no + k] * T2(&B, k, i, c, d);
+      dov[(size_t)l * nv + d] -= s;
+    }
+  /* virtual loop over a >= b >= c */
+  int nvt = 0;
+  int *V3 = (int *)malloc(sizeof(int) * 3 * ((size_t)nv * nv * nv + 1));
+  for (int a = 0; a < nv; ++a)
+    for (int b = 0; b <= a; ++b)
+      for (int c = 0; c <= b; ++c) {
+        if (a == b && b == c) continue;
+        V3[3 * nvt] = a;
+        V3[3 * nvt + 1] = b;
+        V3[3 * nvt + 2] = c;
+        ++nvt;
+      }
+  /* the composed slot maps pi o m and the contravariant partners, as PERM6
+   * indices */
+  int comp[6][6];
+  for (int s = 0; s < 6; ++s)
+    for (int u = 0; u < 6; ++u) {
+      int m[3] = {PERM6[s][PERM6[u][0]], PERM6[s][PERM6[u][1]], PERM6[s][PERM6[u][2]]};
+      comp[s][u] = perm_index(m);
+    }
+  /* contravariant partners: orderings (x,z,y), (z,y,x), (y,x,z), (y,z,x),
+   * (z,x,y) of an ordering (x,y,z), i.e. the slot maps PERM6[3], [2], [1],
+   * [4], [5] composed after it */
+#pragma omp parallel reduction(+ : fl)
+  {
+    double *Bt = (double *)malloc(6 * no3 * sizeof(double) + 8);
+    double *Bx = (double *)malloc(6 * no3 * sizeof(double) + 8);
+    double *tv = (double *)malloc(6 * no3 * sizeof(double) + 8);
+    double *lv = (double *)malloc(6 * no3 * sizeof(double) + 8);
+    double *ltv = (double *)malloc(no3 * sizeof(double) + 8);
+    double *moo = (double *)calloc((size_t)no * no + 1, sizeof(double));
+#pragma omp for schedule(dynamic, 4)
+    for (int t = 0; t < nvt; ++t) {
+      const int *v = V3 + 3 * t;
+      for (int s = 0; s < 6; ++s) {
+        int x = v[PERM6[s][0]], yy = v[PERM6[s][1]], z = v[PERM6[s][2]];
+        for (int p = 0; p < no; ++p)
+          for (int q = 0; q < no; ++q)
+            for (int r = 0; r < no; ++r) {
+              size_t o = ((size_t)p * no + q) * no + r;
+              Bt[s * no3 + o] = elem_B(&B, x, yy, z, p, q, r);
+              Bx[s * no3 + o] = elem_X(&B, L1, lt2, x, yy, z, p, q, r);
+            }
+        fl += 4LL * nv * (long long)no3;
+      }
+      /* tau and L3 at every ordering pi: P sums term u = B^{ordering pi o m_u}
+       * at the occupied triple (o_{m0}, o_{m1}, o_{m2}), m_u = PERM6[u] */
+      const double e = eps_v[v[0]] + eps_v[v[1]] + eps_v[v[2]];
+      for (int s = 0; s < 6; ++s)
+        for (int i = 0; i < no; ++i)
+          for (int j = 0; j < no; ++j)
+            for (int k = 0; k < no; ++k) {
+              const int o[3] = {i, j, k};
+              double wt = 0.0, wx = 0.0;
+              for (int u = 0; u < 6; ++u) {
+                size_t src = ((size_t)o[PERM6[u][0]] * no + o[PERM6[u][1]]) * no + o[PERM6[u][2]];
+                wt += Bt[comp[s][u] * no3 + src];
+                wx += Bx[comp[s][u] * no3 + src];
+              }
+              const double den = e - eps_o[i] - eps_o[j] - eps_o[k];
+              size_t x = ((size_t)i * no + j) * no + k;
+              tv[s * no3 + x] = wt / (0.0 - den);
+              lv[s * no3 + x] = wx / (w - den);
+            }
+      int maps[6][3];
+      int nd = distinct_perms(v, maps);
+      for (int u = 0; u < nd; ++u) {
+        const int s = perm_index(maps[u]);
+        /* L~ at ordering s: 4 L^{xyz} - 2 L^{xzy} - 2 L^{zyx} - 2 L^{yxz}
+         * + L^{yzx} + L^{zxy} */
+        for (size_t x = 0; x < no3; ++x)
+          ltv[x] = 4.0 * lv[s * no3 + x] - 2.0 * lv[comp[s][3] * no3 + x] -
+                   2.0 * lv[comp[s][2] * no3 + x] - 2.0 * lv[comp[s][1] * no3 + x] +
+                   lv[comp[s][4] * no3 + x] + lv[comp[s][5] * no3 + x];
+        for (int l = 0; l < no; ++l)
+          for (int k = 0; k < no; ++k) {
+            double acc = 0.0;
+            for (int i = 0; i < no; ++i)
+              for (int j = 0; j < no; ++j)
+                acc += ltv[((size_t)i * no + j) * no + k] * tv[s * no3 + ((size_t)i * no + j) * no + l];
+            moo[(size_t)l * no + k] -= 0.5 * acc;
+          }
+      }
+    }
+#pragma omp critical
+    {
+      for (size_t x = 0; x < (size_t)no * no; ++x) doo[x] += moo[x];
+    }
+    free(Bt); free(Bx); free(tv); free(lv); free(ltv); free(moo);
+  }
+  memcpy(Doo, doo, (size_t)no * no * sizeof(double));
+  memcpy(Dov, dov, n1 * sizeof(double));
+  memcpy(Dvv, dvv, nv2 * sizeof(double));
+  if (flops) *flops = fl;
+  free(V3); free(T); free(lt2); free(Y); free(dvv); free(dov); free(doo);
+  return used;
+}
+
 /* Only the dressed blocks (for tests that pin them on their own). */
 void oracle_dressed_blocks(int no, int nv, const double *chol_L, int naux,
                            const double *R1, double *hvvvo, double *hoovo,

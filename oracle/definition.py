@@ -99,3 +99,40 @@ def jacobian_full(inp, R1, R2, w, blocks, dblocks):
     hb["ovov"] = np.zeros_like(blocks["ovov"])
     o1b, otb = contractions(tt, hb)
     return dict(rho1=o1a + o1b, rho2=back_transform(ota + otb))
+
+
+def P6(B):
+    """The permutation operator P^{abc}_{ijk} of eq. "permutation" (six terms)."""
+    return (B + E("jikbac->ijkabc", B) + E("kjicba->ijkabc", B)
+            + E("ikjacb->ijkabc", B) + E("jkibca->ijkabc", B)
+            + E("kijcab->ijkabc", B))
+
+
+def L3_full(L1, Lt2, blocks, eps_o, eps_v, w):
+    """Covariant L3 of a left state over every ordered i,j,k:
+    X^{abc}_{ijk} = L^a_i g_{jbkc} + Lt^{ab}_{ij} F_kc + sum_d Lt^{ad}_{ij} g_{dbkc}
+    - sum_l Lt^{ab}_{il} g_{jlkc} (the transposed contractions of Algorithm 1),
+    L3 = P X / (w - eps)."""
+    X = (E("ia,jbkc->ijkabc", L1, blocks["ovov"]) + E("ijab,kc->ijkabc", Lt2, blocks["F_ov"])
+         + E("ijad,dbkc->ijkabc", Lt2, blocks["vvov"])
+         - E("ilab,jlkc->ijkabc", Lt2, blocks["ooov"]))
+    return P6(X) / (w - denominators(eps_o, eps_v))
+
+
+def density_full(eps_o, eps_v, t2, blocks, w, L1, L2):
+    """Triples contributions of Algorithm 3 by their plain full-tensor sums:
+      Dvv_cd =  1/2 sum_{ijkab} L~^{abc}_{ijk} tau^{abd}_{ijk}
+      Doo_lk = -1/2 sum_{ijabc} L~^{abc}_{ijk} tau^{abc}_{ijl}
+      Dov_kc =  sum_{ijab} Lt^{ab}_{ij} tau~^{abc}_{ijk} - sum_{cik} Y_clik t^{cd}_{ki}
+                (the second term at [l][d]), Y_clik = sum_{jab} L~^{abc}_{ijk} t^{ab}_{lj}
+    with tau = W / (0 - eps), Lt = the back-transformed L2.  Returns
+    dict(Doo, Dov, Dvv, Y, tau, L3)."""
+    Lt2 = back_transform(L2)
+    tau = W_full(t2, blocks["vvvo"], blocks["oovo"]) / (0.0 - denominators(eps_o, eps_v))
+    L3 = L3_full(L1, Lt2, blocks, eps_o, eps_v, w)
+    Lc, tc = contravariant(L3), contravariant(tau)
+    Y = E("ijkabc,ljab->clik", Lc, t2)
+    Dvv = 0.5 * E("ijkabc,ijkabd->cd", Lc, tau)
+    Doo = -0.5 * E("ijkabc,ijlabc->lk", Lc, tau)
+    Dov = E("ijab,ijkabc->kc", Lt2, tc) - E("clik,kicd->ld", Y, t2)
+    return dict(Doo=Doo, Dov=Dov, Dvv=Dvv, Y=Y, tau=tau, L3=L3)

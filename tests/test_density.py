@@ -1,0 +1,198 @@
+"""Algorithm 3: the triples contributions to the one-electron density of a
+left state.
+
+CPU part (pins of the oracle, nothing here touches the GPU):
+- the restricted loops (occupied i >= j >= k, virtual a >= b >= c) equal the
+  plain full-tensor sums;
+- the vv and oo blocks at w = 0 are the derivatives of sum L.Omega with
+  respect to a one-electron perturbation of the virtual-virtual or
+  occupied-occupied Fock block inside the triples equations (complex step
+  through a direct solve of the perturbed triples equations);
+- the L2 part of the ov block is the derivative of sum L.Omega with respect
+  to F_kc (Omega is linear in F_ov);
+- tr Dvv + tr Doo = 0 (the two loops, different index restrictions);
+- no = 1 and nv = 1 give zero; linearity in the left state; the FLOP count.
+
+GPU part (marked gpu): the library's FP64 density through the C ABI against
+the oracle, 1e-11 relative to the largest element of each block.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import definition as D
+from cc3_inputs import make_inputs
+
+
+def _left(no, nv, seed):
+    rng = np.random.default_rng(seed)
+    L2 = rng.normal(size=(no, no, nv, nv))
+    return rng.normal(size=(no, nv)), 0.5 * (L2 + np.transpose(L2, (1, 0, 3, 2)))
+
+
+def _rel(x, ref):
+    return np.abs(np.asarray(x) - ref).max() / max(np.abs(ref).max(), 1e-300)
+
+
+def _density(inp, w, L1, L2):
+    return oracle.density_inputs(inp, w, L1, L2)
+
+
+def _pairing(inp, blocks, L1, L2, tau):
+    """sum L1.Omega1 + sum L2.Omega2 for the residual built from tau."""
+    om1, omt = D.contractions(D.contravariant(tau), blocks)
+    return np.sum(L1 * om1) + np.sum(L2 * D.back_transform(omt))
+
+
+@pytest.mark.parametrize("no,nv", [(2, 3), (3, 4), (4, 3), (3, 5)])
+def test_restricted_loops_equal_full_sums(no, nv):
+    inp = make_inputs(no, nv, seed=10 * no + nv)
+    L1, L2 = _left(no, nv, seed=no * nv)
+    b = oracle.symmetric_blocks(inp)
+    for w in (0.0, 0.41):
+        r = _density(inp, w, L1, L2)
+        d = D.density_full(inp.eps_o, inp.eps_v, inp.t2, b, w, L1, L2)
+        for k in ("Doo", "Dov", "Dvv"):
+            assert _rel(r[k], d[k]) < 1e-13, k
+
+
+def test_restricted_loops_general_blocks():
+    """Non-symmetric (T1-transformed) blocks: the loops still equal the sums."""
+    no, nv = 3, 4
+    inp = make_inputs(no, nv, seed=5, naux=20)
+    rng = np.random.default_rng(8)
+    b = oracle.t1_transform(inp, 0.1 * rng.normal(size=(no, nv)))
+    L1, L2 = _left(no, nv, seed=9)
+    r = oracle.density(no, nv, inp.eps_o, inp.eps_v, inp.t2, b, 0.2, L1, L2)
+    d = D.density_full(inp.eps_o, inp.eps_v, inp.t2, b, 0.2, L1, L2)
+    for k in ("Doo", "Dov", "Dvv"):
+        assert _rel(r[k], d[k]) < 1e-13, k
+
+
+def _perturbed_tau(inp, blocks, block, p, q, h):
+    """tau solving the triples equations with the one-electron operator
+    F0 + h E_pq (F0 = the orbital energies): (eps + h K) tau = -W, with K the
+    action of [E_pq, .] on the virtual (block 'vv') or occupied ('oo') indices
+    of a triples tensor, solved directly for every fixed index set."""
+    no, nv = inp.no, inp.nv
+    W = D.W_full(inp.t2, blocks["vvvo"], blocks["oovo"])
+    eps = D.denominators(inp.eps_o, inp.eps_v)
+    tau = np.zeros(W.shape, dtype=complex)
+    if block == "vv":
+        f = np.zeros((nv, nv))
+        f[p, q] = 1.0
+        I = np.eye(nv)
+        K = np.kron(np.kron(f, I), I) + np.kron(np.kron(I, f), I) + np.kron(np.kron(I, I), f)
+        for i in range(no):
+            for j in range(no):
+                for k in range(no):
+                    A = np.diag(eps[i, j, k].reshape(-1)) + h * K
+                    tau[i, j, k] = np.linalg.solve(A, -W[i, j, k].reshape(-1)).reshape(nv, nv, nv)
+    else:
+        # [E_pq, E_ai] = -delta_pi E_aq: amplitude at occupied q receives -h tau(at p)
+        g = np.zeros((no, no))
+        g[q, p] = -1.0
+        I = np.eye(no)
+        K = np.kron(np.kron(g, I), I) + np.kron(np.kron(I, g), I) + np.kron(np.kron(I, I), g)
+        Wt = np.moveaxis(W, (3, 4, 5), (0, 1, 2))
+        et = np.moveaxis(eps, (3, 4, 5), (0, 1, 2))
+        tt = np.zeros(Wt.shape, dtype=complex)
+        for a in range(nv):
+            for bb in range(nv):
+                for c in range(nv):
+                    A = np.diag(et[a, bb, c].reshape(-1)) + h * K
+                    tt[a, bb, c] = np.linalg.solve(A, -Wt[a, bb, c].reshape(-1)).reshape(no, no, no)
+        tau = np.moveaxis(tt, (0, 1, 2), (3, 4, 5))
+    return tau
+
+
+@pytest.mark.parametrize("no,nv", [(2, 3), (3, 3)])
+def test_vv_and_oo_blocks_are_fock_derivatives(no, nv):
+    inp = make_inputs(no, nv, seed=77 + no)
+    L1, L2 = _left(no, nv, seed=3)
+    b = oracle.symmetric_blocks(inp)
+    r = _density(inp, 0.0, L1, L2)
+    h = 1e-20
+    dvv = np.zeros((nv, nv))
+    for c in range(nv):
+        for d in range(nv):
+            tau = _perturbed_tau(inp, b, "vv", c, d, 1j * h)
+            dvv[c, d] = np.imag(_pairing(inp, b, L1, L2, tau)) / h
+    doo = np.zeros((no, no))
+    for l in range(no):
+        for k in range(no):
+            tau = _perturbed_tau(inp, b, "oo", l, k, 1j * h)
+            doo[l, k] = np.imag(_pairing(inp, b, L1, L2, tau)) / h
+    assert _rel(r["Dvv"], dvv) < 1e-11
+    assert _rel(r["Doo"], doo) < 1e-11
+
+
+def test_ov_block_l2_part_is_the_F_derivative():
+    no, nv = 3, 4
+    inp = make_inputs(no, nv, seed=21)
+    L1, L2 = _left(no, nv, seed=22)
+    b = oracle.symmetric_blocks(inp)
+    r = _density(inp, 0.3, L1, L2)
+    d = D.density_full(inp.eps_o, inp.eps_v, inp.t2, b, 0.3, L1, L2)
+    y_part = -np.einsum("clik,kicd->ld", d["Y"], inp.t2)
+
+    def pairing(F):
+        bb = dict(b)
+        bb["F_ov"] = F
+        o = oracle.omega(no, nv, inp.eps_o, inp.eps_v, inp.t2, bb)
+        return np.sum(L1 * o["omega1"]) + np.sum(L2 * o["omega2"])
+
+    base = pairing(np.zeros((no, nv)))
+    dF = np.zeros((no, nv))
+    for k in range(no):
+        for c in range(nv):
+            F = np.zeros((no, nv))
+            F[k, c] = 1.0
+            dF[k, c] = pairing(F) - base
+    assert _rel(r["Dov"] - y_part, dF) < 1e-11
+    assert np.abs(y_part).max() > 1e-3 * np.abs(dF).max()  # both parts present
+
+
+@pytest.mark.parametrize("no,nv", [(4, 7), (5, 6)])
+def test_trace_of_the_two_loops_cancels(no, nv):
+    inp = make_inputs(no, nv, seed=no + nv)
+    L1, L2 = _left(no, nv, seed=1)
+    r = _density(inp, 0.15, L1, L2)
+    tv, to = np.trace(r["Dvv"]), np.trace(r["Doo"])
+    assert abs(tv) > 0 and abs(tv + to) <= 1e-12 * abs(tv)
+
+
+def test_degenerate_sizes_give_zero():
+    """no = 1: only i = j = k, where L~3 and tau~3 vanish; nv = 1: the same for
+    a = b = c.  What is left is the rounding of sums that cancel exactly (the
+    six terms of P in different orders): ~1e-38 here, against densities of
+    ~1e-5 at the sizes above."""
+    for no, nv in [(1, 5), (4, 1)]:
+        inp = make_inputs(no, nv, seed=2)
+        L1, L2 = _left(no, nv, seed=2)
+        r = _density(inp, 0.1, L1, L2)
+        for k in ("Doo", "Dov", "Dvv"):
+            assert np.abs(r[k]).max() < 1e-30, (no, nv, k)
+
+
+def test_linear_in_the_left_state():
+    no, nv = 3, 5
+    inp = make_inputs(no, nv, seed=4)
+    A1, A2 = _left(no, nv, seed=5)
+    B1, B2 = _left(no, nv, seed=6)
+    ra, rb = _density(inp, 0.2, A1, A2), _density(inp, 0.2, B1, B2)
+    rs = _density(inp, 0.2, 2.0 * A1 - B1, 2.0 * A2 - B2)
+    for k in ("Doo", "Dov", "Dvv"):
+        assert _rel(rs[k], 2.0 * ra[k] - rb[k]) < 1e-12
+
+
+def test_flop_count():
+    """6 nv^4 per distinct occupied permutation (tau3, X, Dvv) plus 24 nv no^3
+    per virtual triple a >= b >= c (not all equal): 10 nv^4 no^3 to leading
+    order."""
+    no, nv = 4, 5
+    inp = make_inputs(no, nv, seed=1)
+    L1, L2 = _left(no, nv, seed=1)
+    r = _density(inp, 0.0, L1, L2)
+    nvt = nv * (nv + 1) * (nv + 2) // 6 - nv
+    assert r["flops"] == 6 * nv ** 4 * (no ** 3 - no) + 24 * nv * no ** 3 * nvt
