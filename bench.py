@@ -61,12 +61,13 @@ WORKLOADS = {
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
-# the dominant kernel; None where no capture of the current kernel exists.
-# no=16 nv=160: from a capture of the no=6 nv=160 launches, whose W build
-# launches are the same size; contraction launches scaled by the distinct
-# permutations per batch (81.6 against 67.2).
-TRAFFIC = {}
-TRAFFIC_NOTE = {}
+# the dominant kernel, averaged over the 668 engine launches of one residual
+# evaluation of the benchmark workload (one-pass capture of the full
+# workload); None where no capture of the current kernel exists.
+TRAFFIC = {("split_engine_kernel", 22, 250): 15.562e9}
+TRAFFIC_NOTE = {("split_engine_kernel", 22, 250):
+                "mean of 334 W-build launches (8.00 GB read, 2.23 GB written) and 334 "
+                "contraction launches (20.56 GB read, 0.34 GB written), 6 triples per batch"}
 
 
 def peaks():
@@ -556,6 +557,87 @@ def jacobian_measure(args, local):
     return out
 
 
+def density_measure(args, local):
+    """Triples contributions of Algorithm 3 to the one-electron density of a
+    left state (FP64 path; the split path does not cover it): no=12, nv=120,
+    a seeded left vector at w = 0.25, one warm-up call, `--dsteps` timed calls
+    with inputs and outputs resident on the device."""
+    import torch
+    import paper_2007_01088_gb300 as g
+    from cc3_inputs import make_inputs
+    dev = torch.device("cuda", local)
+    no, nv = args.density_no, args.density_nv
+    inp = make_inputs(no, nv, seed=5)
+    rng = np.random.default_rng(6)
+    L2 = rng.normal(size=(no, no, nv, nv))
+    L2 = 0.5 * (L2 + np.transpose(L2, (1, 0, 3, 2)))
+    L1 = rng.normal(size=(no, nv))
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        ctx = g.Context(inp, device=True, stream=stream)
+        l1 = torch.from_numpy(L1).to(dev)
+        l2 = torch.from_numpy(L2).to(dev)
+        ctx.set_tracing(True)
+        ctx.density(l1, l2, 0.25)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        traces, launches = {}, 0
+        for _ in range(args.dsteps):
+            doo, dov, dvv = ctx.density(l1, l2, 0.25)
+            launches += ctx.counters()["launches"]
+            for k, v in ctx.trace().items():
+                a = traces.setdefault(k, dict(launches=0, ms=0.0, flop=0.0, slice_flop=0.0))
+                for f in a:
+                    a[f] += v[f]
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.dsteps
+    cnt = ctx.counters()
+    ctx.close()
+    pk, src = peaks()
+    fp64_peak = pk["bf16_tflops_sustained"] * 1.25 / 2250.0
+    kern = per_kernel(traces)
+    eng = kern.get("fp64_engine_kernel", dict(ms=0.0, flop=0.0, launches=0))
+    value = cnt["nominal_flop"] / (ms * 1e-3) / 1e12
+    return {"workload": f"triples density of a left state (Algorithm 3), no={no} nv={nv}, "
+                        "w=0.25, FP64 path, seeded synthetic inputs and left vector",
+            "value": value, "unit": "TFLOP/s", "ms_per_step": ms, "steps": args.dsteps,
+            "nominal_flop_per_step": cnt["nominal_flop"],
+            "executed_flop_per_step": cnt["executed_flop"],
+            "launches_per_step": launches / args.dsteps,
+            "fp64_engine": {"ms_per_step": eng["ms"] / args.dsteps,
+                            "achieved_tflops": eng["flop"] / (eng["ms"] * 1e-3) / 1e12
+                            if eng["ms"] else None,
+                            "peak_tflops": fp64_peak,
+                            "peak_source": f"{src} bf16 sustained x nominal FP64/BF16 (1.25/2250)"},
+            "kernels": {k: {"ms_per_step": v["ms"] / args.dsteps,
+                            "launches_per_step": v["launches"] / args.dsteps}
+                        for k, v in kern.items() if v["launches"]},
+            "trace_D_vv_plus_trace_D_oo": float(np.trace(dvv.cpu().numpy())
+                                                + np.trace(doo.cpu().numpy())),
+            "trace_D_vv": float(np.trace(dvv.cpu().numpy()))}
+
+
+def run_density(args):
+    """--workload density: the Algorithm 3 densities alone, as their own line."""
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    clocks = ClockSampler(local)
+    clocks.start()
+    r = density_measure(args, local)
+    clk = clocks.stop()
+    line = {"metric": "CC3 triples density TFLOP/s (Algorithm 3 FLOP per left state)",
+            "value": r["value"], "unit": "TFLOP/s", "n_gpus": 1, "steps": r["steps"],
+            "warmup": 1, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": r["workload"]}, "density": r, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_jacobian(args):
     """--workload jacobian: the batched Jacobian alone, as its own line."""
     import torch
@@ -591,9 +673,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-jacobian", action="store_true", help="skip the batched-Jacobian leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-density", action="store_true", help="skip the density leg")
+    ap.add_argument("--density-no", type=int, default=12, help="density: occupied orbitals")
+    ap.add_argument("--density-nv", type=int, default=120, help="density: virtual orbitals")
+    ap.add_argument("--dsteps", type=int, default=1, help="density: timed calls")
     ap.add_argument("--compare-triples", type=int, default=24,
                     help="seeded triple sample of the split-vs-FP64 comparison")
-    ap.add_argument("--workload", default="omega", choices=["omega", "serve", "jacobian"])
+    ap.add_argument("--workload", default="omega",
+                    choices=["omega", "serve", "jacobian", "density"])
     ap.add_argument("--nvec", type=int, default=8, help="jacobian: trial vectors")
     ap.add_argument("--sample", type=float, default=1.0,
                     help="jacobian: fraction of the triples of the split measurement")
@@ -621,6 +708,8 @@ def main():
         return run_serve(args)
     if args.workload == "jacobian":
         return run_jacobian(args)
+    if args.workload == "density":
+        return run_density(args)
     return run_omega(args)
 
 
@@ -773,6 +862,9 @@ def run_omega(args):
         line["e2e"] = end_to_end(g, inp, prec, stream, args.steps, ws, dev)
     if one and not args.no_jacobian:
         line["jacobian"] = jacobian_measure(args, local)
+        torch.cuda.empty_cache()
+    if one and not args.no_density:
+        line["density"] = density_measure(args, local)
         torch.cuda.empty_cache()
     if one and not args.no_serve:
         line["serving"] = serving(args, local, args.prec)

@@ -195,6 +195,34 @@ int cc3_left_jacobian_triples(cc3_ctx *ctx, cc3_prec prec, int nvec, const doubl
                               const double *L1, const double *L2, double *sigma1,
                               double *sigma2, void *cuda_stream);
 
+/* Triples contributions to the one-electron density of a left state
+ * (paper, "Implementation", Algorithm 3): for the left state (L1, L2) at
+ * frequency omega,
+ *   D_vv[c][d] =  1/2 sum_{ijkab} L3~^{abc}_{ijk} tau^{abd}_{ijk}
+ *   D_oo[l][k] = -1/2 sum_{ijabc} L3~^{abc}_{ijk} tau^{abc}_{ijl}
+ *   D_ov[k][c] =  sum_{ijab} L2~^{ab}_{ij} tau~^{abc}_{ijk}
+ *                - sum_{cik} Y^o_{clik} t^{cd}_{ki}  (at [l][d]),
+ *   Y^o_{clik} = sum_{jab} L3~^{abc}_{ijk} t^{ab}_{lj},
+ * with tau = -W / eps (Algorithm 1), L3 the covariant amplitudes of
+ * cc3_left_jacobian_triples, L3~ their contravariant form and L2~ the
+ * back-transform applied to L2; the vo block has no triples term.  The
+ * occupied loop runs over the triples i >= j >= k, the D_oo term over
+ * Algorithm 3's virtual loop a >= b >= c.  With omega = 0 and the
+ * ground-state multipliers in place of (L1, L2) the call gives D^{0,0}.
+ * L1[no][nv], L2[no][no][nv][nv] (host, or device with CC3_DEVICE_PTRS);
+ * outputs D_oo[no][no], D_ov[no][nv], D_vv[nv][nv], overwritten.  Before any
+ * device work: CC3_ERR_ARG for a null pointer or a non-finite omega,
+ * CC3_ERR_DENOM if omega comes within CC3_DENOM_MIN of any eps^{abc}_{ijk}
+ * (i >= j >= k, i = j = k included: the virtual loop divides there too),
+ * CC3_ERR_UNSUPPORTED for a context with general (T1-transformed) integrals,
+ * a restricted triples list, more than 24 occupied orbitals, deterministic
+ * mode or a split precision (FP64 path only).  Cost 10 nv^4 no^3 FLOP to
+ * leading order (6 nv^4 per distinct permutation in the occupied loop, 4 nv^4
+ * no^3 in the virtual loop). */
+int cc3_density_triples(cc3_ctx *ctx, cc3_prec prec, double omega, const double *L1,
+                        const double *L2, double *D_oo, double *D_ov, double *D_vv,
+                        void *cuda_stream);
+
 /* Smallest |w - eps^{abc}_{ijk}| over every virtual triple (a, b, c) and the
  * occupied triples of a loop, eps^{abc}_{ijk} = e_a + e_b + e_c - e_i - e_j -
  * e_k (the R3 denominator of eq. "jcc3" at frequency w; at w = 0 the tau

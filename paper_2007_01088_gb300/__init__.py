@@ -23,7 +23,7 @@ __all__ = ["CC3_FP64", "CC3_SPLIT_BF16", "CC3_SPLIT_INT8", "CC3_DEVICE_PTRS",
            "cc3_ctx_destroy", "cc3_ctx_set_triples", "cc3_omega_triples",
            "cc3_jacobian_triples", "cc3_ctx_counters", "cc3_ctx_set_slices",
            "cc3_strerror", "cc3_cvs_triples", "cc3_denominator_gap", "CC3_DENOM_MIN",
-           "Context", "EXPORTED"]
+           "cc3_left_jacobian_triples", "cc3_density_triples", "Context", "EXPORTED"]
 
 CC3_FP64, CC3_SPLIT_BF16, CC3_SPLIT_INT8 = 0, 1, 2
 CC3_DEVICE_PTRS, CC3_DETERMINISTIC = 1, 2
@@ -41,7 +41,7 @@ EXPORTED = ["cc3_ctx_create", "cc3_ctx_destroy", "cc3_ctx_set_triples",
             "cc3_ctx_trace", "cc3_omega_triples_noalloc", "cc3_serve_footprint",
             "cc3_ctx_autotune", "cc3_ctx_get_tuning", "cc3_cvs_triples",
             "cc3_denominator_gap", "cc3_debug_wait_timeout", "cc3_ctx_create_general",
-            "cc3_left_jacobian_triples"]
+            "cc3_left_jacobian_triples", "cc3_density_triples"]
 
 
 class CC3Error(RuntimeError):
@@ -110,6 +110,8 @@ def _load():
     L.cc3_jacobian_triples.restype = I
     L.cc3_left_jacobian_triples.argtypes = [P, I, I, P, P, P, P, P, P]
     L.cc3_left_jacobian_triples.restype = I
+    L.cc3_density_triples.argtypes = [P, I, ctypes.c_double, P, P, P, P, P, P]
+    L.cc3_density_triples.restype = I
     L.cc3_ctx_counters.argtypes = [P, ctypes.POINTER(Counters)]
     L.cc3_ctx_counters.restype = I
     L.cc3_ctx_set_slices.argtypes = [P, I]
@@ -280,6 +282,12 @@ def cc3_left_jacobian_triples(ctx, prec, nvec, omega, L1, L2, sigma1, sigma2, st
                                          w.ctypes.data_as(ctypes.c_void_p), _ptr(L1), _ptr(L2),
                                          _ptr(sigma1), _ptr(sigma2), _stream(stream)),
            "cc3_left_jacobian_triples")
+
+
+def cc3_density_triples(ctx, prec, omega, L1, L2, D_oo, D_ov, D_vv, stream=None):
+    _check(lib.cc3_density_triples(ctx, int(prec), float(omega), _ptr(L1), _ptr(L2), _ptr(D_oo),
+                                   _ptr(D_ov), _ptr(D_vv), _stream(stream)),
+           "cc3_density_triples")
 
 
 def cc3_ctx_counters(ctx):
@@ -461,6 +469,14 @@ class Context:
         s2 = self._new((nvec, no, no, nv, nv))
         cc3_left_jacobian_triples(self.ctx, prec, nvec, omega, L1, L2, s1, s2, self.stream)
         return s1, s2
+
+    def density(self, L1, L2, omega, prec=CC3_FP64):
+        """Triples contributions of Algorithm 3 to the one-electron density of
+        the left state (L1, L2) at frequency omega; returns (D_oo, D_ov, D_vv)."""
+        no, nv = self.no, self.nv
+        doo, dov, dvv = self._new((no, no)), self._new((no, nv)), self._new((nv, nv))
+        cc3_density_triples(self.ctx, prec, omega, L1, L2, doo, dov, dvv, self.stream)
+        return doo, dov, dvv
 
     def jacobian(self, R1, R2, omega, prec=CC3_FP64):
         no, nv = self.no, self.nv

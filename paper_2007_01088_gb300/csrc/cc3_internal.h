@@ -69,9 +69,12 @@ enum BufId {
   B_COUNT,
   // the left transformation (left.cu) reuses slots the right one does not
   // touch there: Lt2, sigma1, sigma2 (before symmetrising), G, H, Q
-  B_LT = B_R2, B_S1 = B_RHO1, B_S2 = B_RHOT, B_G = B_HVVVO, B_H = B_HOOVO, B_Q = B_HF
+  B_LT = B_R2, B_S1 = B_RHO1, B_S2 = B_RHOT, B_G = B_HVVVO, B_H = B_HOOVO, B_Q = B_HF,
+  // the densities (density.cu) reuse Lt2 and Q (= Dov) as above, and take
+  // Y, Dvv and the virtual loop's two bracket buffers from unused slots
+  B_DY = B_ZV, B_DVV = B_ZO, B_DOV = B_Q, B_VBT = B_VVOO, B_VBX = B_OOOO
 };
-static_assert(B_COUNT <= MAX_BUFS, "pointer table");
+static_assert((int)B_COUNT <= (int)MAX_BUFS, "pointer table");
 
 struct Plan {  // a host-built list of jobs for one launch
   std::vector<Job> jobs;
@@ -209,6 +212,12 @@ int jac_prep_fp64(cc3_ctx *c, cudaStream_t s);           // cached FP64 Z~v, Z~o
 int jac_tau_batch(cc3_ctx *c, int t0, int t1, cudaStream_t s);  // tau~ -> ws_tt
 void jac_fill_ptrs(cc3_ctx *c, PtrTable *pt);
 int jac_run_plan(cc3_ctx *c, const Plan &p, int kind, const PtrTable &pt, cudaStream_t s);
+// pieces of the left transformation shared with the densities (left.cu):
+// Q[r][z] += sum_xy Lt2[p][q][x][y] tau~[x][y][z] jobs of one triple, and the
+// covariant L3 (wsW, [c][a][b] per slot) with its contravariant form (wsT)
+void plan_left_q(Plan &P, int no, int nv, const int ijk[3], int slot);
+int left_l3_batch(cc3_ctx *c, const PtrTable &pt, int t0, int t1, double w, const double *L1d,
+                  const double *ltd, int *tri, double *wsW, double *wsT, cudaStream_t s);
 
 // smallest |w - eps^{abc}_{ijk}| over every (a, b, c) and the ntri triples
 // ijk (host arrays; ntri = 0: the full loop); api.cu

@@ -348,7 +348,10 @@ int jac_tau_batch(cc3_ctx *c, int t0, int t1, cudaStream_t s) {
 }
 void jac_fill_ptrs(cc3_ctx *c, PtrTable *pt) {
   JacState *J = jst(c);
-  if (J) fill_base(c, J, pt);
+  if (J)
+    fill_base(c, J, pt);
+  else
+    std::memset(pt, 0, sizeof(*pt));
 }
 // Upload, launch, free (FP64 engine), counted in the context's counters.
 int jac_run_plan(cc3_ctx *c, const Plan &p, int kind, const PtrTable &pt, cudaStream_t s) {

@@ -151,6 +151,8 @@ void plan_left_gh(Plan &pg, Plan &ph, int no, int nv, const int ijk[3], int slot
   }
 }
 
+}  // namespace
+
 // Q[r][z] += sum_xy Lt2[p][q][x][y] V[x][y][z] for every distinct permutation
 // (V: tau~3 in slot `slot` of B_WS_TT)
 void plan_left_q(Plan &P, int no, int nv, const int ijk[3], int slot) {
@@ -177,6 +179,38 @@ void plan_left_q(Plan &P, int no, int nv, const int ijk[3], int slot) {
     P.jobs[jb].Ct = o;
   }
 }
+
+// Covariant L3 = P X / (w - eps) of the triples [t0, t1) into wsW (slot layout
+// [c][a][b], as the W build writes it) and its contravariant form into wsT
+// ([a][b][c]).  pt: B_LT = ltd (the back-transformed L2), B_WS_WR = wsW;
+// tri: device room for 3 (t1 - t0) ints.
+int left_l3_batch(cc3_ctx *c, const PtrTable &pt, int t0, int t1, double w, const double *L1d,
+                  const double *ltd, int *tri, double *wsW, double *wsT, cudaStream_t s) {
+  const int no = c->no, nv = c->nv, ns = t1 - t0;
+  const long long nv3 = (long long)nv * nv * nv;
+  const TermSet set{B_LT, B_VVVO, B_OOVO};
+  Plan pab, pc;
+  for (int t = t0; t < t1; ++t) {
+    const int *ijk = &c->tri_host[3 * t];
+    const double e = c->eo_h[ijk[0]] + c->eo_h[ijk[1]] + c->eo_h[ijk[2]];
+    plan_w_build(pab, no, nv, ijk, t - t0, B_WS_WR, &set, 1, 0.0, 0.0, 0);
+    plan_w_build(pc, no, nv, ijk, t - t0, B_WS_WR, &set, 1, w, e, 1);
+  }
+  CU(cudaMemcpyAsync(tri, &c->tri_host[3 * t0], sizeof(int) * 3 * ns, cudaMemcpyHostToDevice, s));
+  TRY(jac_run_plan(c, pab, 0, pt, s));
+  left_outer_kernel<<<dim3(grid_for(nv3 / 4), ns), 256, 0, s>>>(wsW, tri, L1d, ltd, c->ovov,
+                                                                 c->F_ov, no, nv);
+  CU(cudaGetLastError());
+  c->counters.launches++;
+  TRY(jac_run_plan(c, pc, 0, pt, s));
+  trace_begin(c, TR_FP64_ELEM, s);
+  TRY(launch_contravariant(wsW, wsT, nv, ns, s));
+  trace_end(c, TR_FP64_ELEM, s, 0.0, 0.0);
+  c->counters.launches++;
+  return CC3_OK;
+}
+
+namespace {
 
 // sigma1 terms outside the loops (rows and columns as in the header)
 int left_singles(cc3_ctx *c, const PtrTable &pt, cudaStream_t s) {
@@ -311,7 +345,6 @@ int left_fp64(cc3_ctx *c, int nvec, const double *w, const double *L1d, const do
     for (int v = 0; v < nvec; ++v) TRY(jac_run_plan(c, pq, 1, vec_ptrs(v), s));
   }
   // loop 2, vector by vector: L3, its contravariant form, its contractions
-  const TermSet set{B_LT, B_VVVO, B_OOVO};
   for (int v = 0; v < nvec; ++v) {
     const PtrTable pt = vec_ptrs(v);
     TRY(launch_zero(s1d + v * n1, n1, s));
@@ -320,13 +353,9 @@ int left_fp64(cc3_ctx *c, int nvec, const double *w, const double *L1d, const do
     TRY(launch_zero(H, (size_t)no * no * nv * no, s));
     for (int t0 = 0; t0 < c->ntri; t0 += c->batch) {
       const int t1 = std::min(c->ntri, t0 + c->batch);
-      const int ns = t1 - t0;
-      Plan pab, pc, pom, pth, pg, ph;
+      Plan pom, pth, pg, ph;
       for (int t = t0; t < t1; ++t) {
         const int *ijk = &c->tri_host[3 * t];
-        const double e = c->eo_h[ijk[0]] + c->eo_h[ijk[1]] + c->eo_h[ijk[2]];
-        plan_w_build(pab, no, nv, ijk, t - t0, B_WS_WR, &set, 1, 0.0, 0.0, 0);
-        plan_w_build(pc, no, nv, ijk, t - t0, B_WS_WR, &set, 1, w[v], e, 1);
         // sigma2: the residual's vvov and ooov contractions, no tail columns
         plan_omega_contractions(pom, no, nv, ijk, t - t0, B_WS_TTR, B_OVOV, B_FOV, B_OOOV, true,
                                 B_VVVO, B_S2, B_S1, 1, 1 | 8);
@@ -334,18 +363,7 @@ int left_fp64(cc3_ctx *c, int nvec, const double *w, const double *L1d, const do
                                 B_VVVO, B_S2, B_S1, 1, 2 | 8);
         plan_left_gh(pg, ph, no, nv, ijk, t - t0);
       }
-      CU(cudaMemcpyAsync(tri, &c->tri_host[3 * t0], sizeof(int) * 3 * ns, cudaMemcpyHostToDevice,
-                         s));
-      TRY(jac_run_plan(c, pab, 0, pt, s));
-      left_outer_kernel<<<dim3(grid_for(nv3 / 4), ns), 256, 0, s>>>(
-          wsW, tri, L1d + v * n1, lt + v * nt2, c->ovov, c->F_ov, no, nv);
-      CU(cudaGetLastError());
-      c->counters.launches++;
-      TRY(jac_run_plan(c, pc, 0, pt, s));
-      trace_begin(c, TR_FP64_ELEM, s);
-      TRY(launch_contravariant(wsW, wsT, nv, ns, s));
-      trace_end(c, TR_FP64_ELEM, s, 0.0, 0.0);
-      c->counters.launches++;
+      TRY(left_l3_batch(c, pt, t0, t1, w[v], L1d + v * n1, lt + v * nt2, tri, wsW, wsT, s));
       TRY(jac_run_plan(c, pom, 0, pt, s));
       TRY(jac_run_plan(c, pth, 1, pt, s));
       TRY(jac_run_plan(c, pg, 0, pt, s));

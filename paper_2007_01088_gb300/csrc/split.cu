@@ -87,7 +87,7 @@ enum MapId {
   MJ_R2S, MJ_R2C, MJ_R2R, MJ_XH, MJ_YH, MJ_OH, MJ_FH, MJ_OVD, MJ_OVZA, MJ_OVZB,
   MAP_COUNT
 };
-static_assert(MAP_COUNT <= SMAX_MAPS, "map table");
+static_assert((int)MAP_COUNT <= (int)SMAX_MAPS, "map table");
 
 struct SplitState {
   int s = 0, vp = 0, op = 0, Et = 0, Eg = 0;

@@ -196,3 +196,75 @@ def test_flop_count():
     r = _density(inp, 0.0, L1, L2)
     nvt = nv * (nv + 1) * (nv + 2) // 6 - nv
     assert r["flops"] == 6 * nv ** 4 * (no ** 3 - no) + 24 * nv * no ** 3 * nvt
+
+
+# ---- GPU: the library's FP64 density against the oracle -------------------------------------
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_2007_01088_gb300 as g
+    return g
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("no,nv", [(3, 9), (4, 20), (2, 17), (5, 33), (6, 24)])
+def test_density_matches_oracle(g, no, nv):
+    inp = make_inputs(no, nv, seed=300 + no * nv)
+    L1, L2 = _left(no, nv, seed=no + 2 * nv)
+    ctx = g.Context(inp)
+    for w in (0.25, 0.0):
+        ref = _density(inp, w, L1, L2)
+        doo, dov, dvv = ctx.density(L1, L2, w)
+        assert _rel(doo, ref["Doo"]) < 1e-11, ("Doo", w)
+        assert _rel(dov, ref["Dov"]) < 1e-11, ("Dov", w)
+        assert _rel(dvv, ref["Dvv"]) < 1e-11, ("Dvv", w)
+    c = ctx.counters()
+    nvt = nv * (nv + 1) * (nv + 2) // 6 - nv
+    assert c["nominal_flop"] == 6 * nv ** 4 * (no ** 3 - no) + 24 * nv * no ** 3 * nvt
+    assert c["launches"] > 0
+
+
+@pytest.mark.gpu
+def test_density_larger_shape(g):
+    """Several W-build batches, multi-slab and single-slab virtual groups."""
+    no, nv = 8, 64
+    inp = make_inputs(no, nv, seed=11)
+    L1, L2 = _left(no, nv, seed=12)
+    ref = _density(inp, 0.1, L1, L2)
+    doo, dov, dvv = g.Context(inp).density(L1, L2, 0.1)
+    for x, k in ((doo, "Doo"), (dov, "Dov"), (dvv, "Dvv")):
+        assert _rel(x, ref[k]) < 1e-11, k
+
+
+@pytest.mark.gpu
+def test_density_device_pointers(g):
+    torch = pytest.importorskip("torch")
+    no, nv = 4, 16
+    inp = make_inputs(no, nv, seed=13)
+    L1, L2 = _left(no, nv, seed=14)
+    ref = _density(inp, 0.2, L1, L2)
+    ctx = g.Context(inp, device=True)
+    doo, dov, dvv = ctx.density(torch.from_numpy(L1).cuda(), torch.from_numpy(L2).cuda(), 0.2)
+    for x, k in ((doo, "Doo"), (dov, "Dov"), (dvv, "Dvv")):
+        assert _rel(x.cpu().numpy(), ref[k]) < 1e-11, k
+
+
+@pytest.mark.gpu
+def test_density_refusals(g):
+    no, nv = 3, 8
+    inp = make_inputs(no, nv, seed=15)
+    L1, L2 = _left(no, nv, seed=16)
+    ctx = g.Context(inp)
+
+    def status(fn):
+        with pytest.raises(g.CC3Error) as e:
+            fn()
+        return str(e.value)
+
+    assert "(-7)" in status(lambda: ctx.density(L1, L2, 0.1, prec=g.CC3_SPLIT_BF16))
+    # a frequency on a triples denominator (i = j = k included)
+    eps = inp.eps_v[0] * 3 - inp.eps_o[0] * 3
+    assert "(-5)" in status(lambda: ctx.density(L1, L2, float(eps)))
+    assert "(-1)" in status(lambda: ctx.density(L1, L2, float("nan")))
+    ctx.set_triples([[2, 1, 0]])
+    assert "(-7)" in status(lambda: ctx.density(L1, L2, 0.1))
