@@ -620,6 +620,101 @@ def density_measure(args, local):
             "trace_D_vv": float(np.trace(dvv.cpu().numpy()))}
 
 
+def _timed_calls(stream, fn, steps):
+    """CUDA-event time of `steps` calls of fn on `stream` (ms per call)."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, out
+
+
+def widening_measure(args, local):
+    """The NEXT rows besides the densities, each on one seeded problem with
+    inputs resident on the device, one warm-up and one timed call:
+    - the left (transpose) Jacobian, FP64 path, no=12 nv=120, 2 left vectors;
+    - the core-valence separation filter: the batched Jacobian workload
+      (no=20, nv=200, 8 vectors) restricted to the triples that contain
+      occupied orbital 0, split path;
+    - general (non-symmetric) five-block integrals: the residual on seeded
+      symmetric blocks plus a seeded non-symmetric perturbation of 1e-3 of
+      each block's scale, split path, no=16 nv=160."""
+    import torch
+    import paper_2007_01088_gb300 as g
+    from cc3_inputs import config_inputs, make_inputs, make_trial_vectors
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    out = {}
+    with torch.cuda.stream(stream):
+        # left Jacobian
+        no, nv, nvec = 12, 120, 2
+        inp = make_inputs(no, nv, seed=21)
+        rng = np.random.default_rng(22)
+        L2 = rng.normal(size=(nvec, no, no, nv, nv))
+        L2 = 0.5 * (L2 + np.transpose(L2, (0, 2, 1, 4, 3)))
+        l1 = torch.from_numpy(rng.normal(size=(nvec, no, nv))).to(dev)
+        l2 = torch.from_numpy(L2).to(dev)
+        w = [0.25, 0.1]
+        ctx = g.Context(inp, device=True, stream=stream)
+        ctx.left_jacobian(l1, l2, w)
+        ms, _ = _timed_calls(stream, lambda: ctx.left_jacobian(l1, l2, w), 1)
+        flop = ctx.counters()["nominal_flop"]
+        ctx.close()
+        out["left_jacobian"] = {
+            "workload": f"left (transpose) Jacobian, no={no} nv={nv} naux={inp.naux}, {nvec} "
+                        "left vectors at w=0.25, 0.1, FP64 path",
+            "value": flop / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
+            "nominal_flop_per_step": flop}
+        # CVS filter
+        inp = config_inputs("cfg4_jacobian_no20_nv200")
+        no, nv, nvec = inp.no, inp.nv, 8
+        R1, R2 = make_trial_vectors(no, nv, nvec, seed=1)
+        r1, r2 = torch.from_numpy(R1).to(dev), torch.from_numpy(R2).to(dev)
+        wv = np.full(nvec, 0.25)
+        ctx = g.Context(inp, device=True, stream=stream)
+        tr = ctx.set_cvs([0])
+        ctx.jacobian(r1, r2, wv, g.CC3_SPLIT_BF16)
+        ms, _ = _timed_calls(stream, lambda: ctx.jacobian(r1, r2, wv, g.CC3_SPLIT_BF16), 1)
+        flop = ctx.counters()["nominal_flop"]
+        ctx.close()
+        out["cvs"] = {
+            "workload": f"core-valence separation: the batched Jacobian (no={no}, nv={nv}, "
+                        f"{nvec} vectors at w=0.25) on the {len(tr)} triples that contain "
+                        "occupied orbital 0, split path",
+            "value": flop / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
+            "nominal_flop_per_step": flop, "triples": len(tr)}
+        torch.cuda.empty_cache()
+        # general integrals
+        no, nv = 16, 160
+        inp = make_inputs(no, nv, seed=31)
+        rng = np.random.default_rng(32)
+        # the five blocks of the symmetric problem (oovo = (lj|kc) reordered,
+        # vvov = (bd|ck) reordered), then perturbed out of symmetry
+        blocks = {"vvvo": inp.g_vvvo, "oovo": np.transpose(inp.g_ooov, (0, 1, 3, 2)),
+                  "ooov": inp.g_ooov, "ovov": inp.g_ovov,
+                  "vvov": np.transpose(inp.g_vvvo, (1, 0, 3, 2)), "F_ov": inp.F_ov}
+        for k in ("vvvo", "oovo", "ooov", "ovov", "vvov"):
+            x = blocks[k]
+            blocks[k] = np.ascontiguousarray(x + 1e-3 * np.abs(x).max() * rng.normal(size=x.shape))
+        ctx = g.Context(inp, device=True, stream=stream, blocks=blocks)
+        ctx.omega(g.CC3_SPLIT_BF16)
+        ms, _ = _timed_calls(stream, lambda: ctx.omega(g.CC3_SPLIT_BF16), 3)
+        flop = ctx.counters()["nominal_flop"]
+        ctx.close()
+        out["general_integrals"] = {
+            "workload": f"residual on general (non-symmetric) five-block integrals, no={no} "
+                        f"nv={nv}, split path",
+            "value": flop / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
+            "nominal_flop_per_step": flop}
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_density(args):
     """--workload density: the Algorithm 3 densities alone, as their own line."""
     import torch
@@ -674,6 +769,8 @@ def main():
     ap.add_argument("--no-jacobian", action="store_true", help="skip the batched-Jacobian leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-density", action="store_true", help="skip the density leg")
+    ap.add_argument("--no-widening", action="store_true",
+                    help="skip the left-Jacobian, CVS and general-integral legs")
     ap.add_argument("--density-no", type=int, default=12, help="density: occupied orbitals")
     ap.add_argument("--density-nv", type=int, default=120, help="density: virtual orbitals")
     ap.add_argument("--dsteps", type=int, default=1, help="density: timed calls")
@@ -866,6 +963,8 @@ def run_omega(args):
     if one and not args.no_density:
         line["density"] = density_measure(args, local)
         torch.cuda.empty_cache()
+    if one and not args.no_widening:
+        line.update(widening_measure(args, local))
     if one and not args.no_serve:
         line["serving"] = serving(args, local, args.prec)
         s = line["serving"]

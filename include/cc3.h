@@ -265,7 +265,9 @@ int cc3_ctx_counters(const cc3_ctx *ctx, cc3_counters *out);
  * could be <= 0 (3 min eps_v <= 3 max eps_o), as cc3_ctx_create does.  It
  * synchronises cuda_stream twice (after reading the orbital energies and after
  * uploading its tables into the array) and returns after enqueuing its kernels
- * on cuda_stream. */
+ * on cuda_stream.  Because it reads back and synchronises, the call cannot be
+ * recorded into a CUDA graph, and it must not run while another thread
+ * captures a stream in cudaStreamCaptureModeGlobal. */
 int cc3_omega_triples_noalloc(int no, int nv, const double *eps_o, const double *eps_v,
                               const double *t2, const double *g_vvvo,
                               const double *g_ooov, const double *g_ovov,

@@ -4,9 +4,10 @@
 //
 // Who needs this: code that runs inside a host framework which owns the GPU
 // memory pool and forbids other allocations (a fixed-budget embedding, a
-// process whose allocator is locked while a CUDA graph is being recorded
-// elsewhere, a plugin with a pre-reserved heap) can still call the triples
-// residual as long as it passes its own input and output buffers.
+// plugin with a pre-reserved heap) can still call the triples residual as long
+// as it passes its own input and output buffers.  The call reads the orbital
+// energies back and synchronises its stream, so it is not capturable into a
+// CUDA graph and must not overlap a global-mode capture on another thread.
 //
 // The scratch array below is part of the library image: every GPU that loads
 // libcc3 holds it (16 MiB) until the process exits.  Its device address is
