@@ -637,7 +637,8 @@ def _timed_calls(stream, fn, steps):
 def widening_measure(args, local):
     """The NEXT rows besides the densities, each on one seeded problem with
     inputs resident on the device, one warm-up and one timed call:
-    - the left (transpose) Jacobian, FP64 path, no=12 nv=120, 2 left vectors;
+    - the left (transpose) Jacobian: FP64 path at no=12 nv=120 with 2 left
+      vectors, split path on the batched-Jacobian workload with 8;
     - the core-valence separation filter: the batched Jacobian workload
       (no=20, nv=200, 8 vectors) restricted to the triples that contain
       occupied orbital 0, split path;
@@ -670,6 +671,23 @@ def widening_measure(args, local):
                         "left vectors at w=0.25, 0.1, FP64 path",
             "value": flop / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
             "nominal_flop_per_step": flop}
+        # the split path on the batched-Jacobian workload, 8 left vectors
+        inp = config_inputs("cfg4_jacobian_no20_nv200")
+        no, nv, nvec = inp.no, inp.nv, 8
+        A1, A2 = make_trial_vectors(no, nv, nvec, seed=23)
+        a1, a2 = torch.from_numpy(A1).to(dev), torch.from_numpy(A2).to(dev)
+        wv = np.full(nvec, 0.25)
+        ctx = g.Context(inp, device=True, stream=stream)
+        ctx.left_jacobian(a1, a2, wv, g.CC3_SPLIT_BF16)
+        ms, _ = _timed_calls(stream, lambda: ctx.left_jacobian(a1, a2, wv, g.CC3_SPLIT_BF16), 1)
+        flop = ctx.counters()["nominal_flop"]
+        ctx.close()
+        out["left_jacobian"]["split"] = {
+            "workload": f"left (transpose) Jacobian, no={no} nv={nv} naux={inp.naux}, {nvec} "
+                        "left vectors at w=0.25, the whole triple loop, split path",
+            "value": flop / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
+            "nominal_flop_per_step": flop}
+        torch.cuda.empty_cache()
         # CVS filter
         inp = config_inputs("cfg4_jacobian_no20_nv200")
         no, nv, nvec = inp.no, inp.nv, 8

@@ -218,6 +218,8 @@ int jac_run_plan(cc3_ctx *c, const Plan &p, int kind, const PtrTable &pt, cudaSt
 void plan_left_q(Plan &P, int no, int nv, const int ijk[3], int slot);
 int left_l3_batch(cc3_ctx *c, const PtrTable &pt, int t0, int t1, double w, const double *L1d,
                   const double *ltd, int *tri, double *wsW, double *wsT, cudaStream_t s);
+int left_finish(cc3_ctx *c, const PtrTable &pt, const double *s2raw, double *s2d,
+                cudaStream_t s);
 
 // smallest |w - eps^{abc}_{ijk}| over every (a, b, c) and the ntri triples
 // ijk (host arrays; ntri = 0: the full loop); api.cu

@@ -30,6 +30,7 @@
 #include <vector>
 
 #include "cc3_internal.h"
+#include "split.h"
 
 namespace cc3 {
 namespace {
@@ -379,6 +380,19 @@ int left_fp64(cc3_ctx *c, int nvec, const double *w, const double *L1d, const do
 }
 
 }  // namespace
+
+// sigma1 from Q, G, H, Lt2 and the cached Algorithm 2 intermediates (pt's
+// B_Q, B_G, B_H, B_LT, B_ZV, B_ZO; output B_S1), then sigma2 = the pair-
+// symmetric part of s2raw
+int left_finish(cc3_ctx *c, const PtrTable &pt, const double *s2raw, double *s2d,
+                cudaStream_t s) {
+  TRY(left_singles(c, pt, s));
+  const long long nt2 = (long long)c->no * c->no * c->nv * c->nv;
+  pair_symmetrize_kernel<<<grid_for(nt2), 256, 0, s>>>(s2raw, s2d, c->no, c->nv);
+  CU(cudaGetLastError());
+  c->counters.launches++;
+  return CC3_OK;
+}
 }  // namespace cc3
 
 extern "C" int cc3_left_jacobian_triples(cc3_ctx *c, cc3_prec prec, int nvec,
@@ -391,11 +405,11 @@ extern "C" int cc3_left_jacobian_triples(cc3_ctx *c, cc3_prec prec, int nvec,
     return CC3_FAIL(CC3_ERR_UNSUPPORTED, "the Jacobian needs symmetric integrals");
   if (c->naux < 1 || !c->chol)
     return CC3_FAIL(CC3_ERR_ARG, "the Jacobian needs the Cholesky vectors (chol_L)");
-  if (prec == CC3_SPLIT_INT8 || prec == CC3_SPLIT_BF16)
-    return CC3_FAIL(CC3_ERR_UNSUPPORTED, "the left transformation runs on the FP64 path");
+  if (prec == CC3_SPLIT_INT8)
+    return CC3_FAIL(CC3_ERR_UNSUPPORTED, "no INT8 slice path");
   if (c->flags & CC3_DETERMINISTIC)
     return CC3_FAIL(CC3_ERR_UNSUPPORTED, "deterministic reductions cover the residual only");
-  if (prec != CC3_FP64) return CC3_ERR_ARG;
+  if (prec != CC3_FP64 && prec != CC3_SPLIT_BF16) return CC3_ERR_ARG;
   std::lock_guard<std::mutex> lk(c->mu);
   for (int v = 0; v < nvec; ++v) {
     if (!std::isfinite(omega[v])) return CC3_FAIL(CC3_ERR_ARG, "non-finite frequency");
@@ -446,6 +460,8 @@ extern "C" int cc3_left_jacobian_triples(cc3_ctx *c, cc3_prec prec, int nvec,
     if (c->ntri == 0) {
       rc = launch_zero(ds1, n1 * nvec, s);
       if (rc == CC3_OK) rc = launch_zero(ds2, nt2 * nvec, s);
+    } else if (prec == CC3_SPLIT_BF16) {
+      rc = split_left_jacobian(c, nvec, omega, dL1, dL2, ds1, ds2, s);
     } else {
       rc = left_fp64(c, nvec, omega, dL1, dL2, ds1, ds2, s);
     }

@@ -85,6 +85,9 @@ enum MapId {
   // Jacobian: per trial vector (R2 in the t2 layouts, g^ in the integral
   // layouts), F^ of all vectors, and ovov in the layouts of Algorithm 2
   MJ_R2S, MJ_R2C, MJ_R2R, MJ_XH, MJ_YH, MJ_OH, MJ_FH, MJ_OVD, MJ_OVZA, MJ_OVZB,
+  // left transformation: t2 as [(p,q)][d][x] (G), as [p][l][(u,w)] in both K
+  // orders (H), and Lt2 of every vector as [(p,q)][v][(u,w)] in both orders (Q)
+  ML_T2T, ML_T2ZA, ML_T2ZB, ML_LQA, ML_LQB,
   MAP_COUNT
 };
 static_assert((int)MAP_COUNT <= (int)SMAX_MAPS, "map table");
@@ -503,7 +506,9 @@ void append_plan(SPlan &dst, const SPlan &src) {
 }
 
 // residual contractions of one triple (every distinct permutation); which:
-// bit 0 the vvov + singles jobs (long K), bit 1 the ooov + F jobs (short K)
+// bit 0 the vvov + singles jobs (long K), bit 1 the ooov + F jobs (short K),
+// bit 3 leave out the singles and F columns (the left transformation's sigma2
+// contractions)
 void plan_omega_split(SPlan &P, SplitState *S, int no, int nv, const int ijk[3], int slot,
                       int ksplit4, double &ex, int which = 3) {
   static const int PERM6[6][3] = {{0, 1, 2}, {1, 0, 2}, {2, 1, 0},
@@ -528,7 +533,13 @@ void plan_omega_split(SPlan &P, SplitState *S, int no, int nv, const int ijk[3],
     // layout with x slot outermost: K order (slot m0+1, slot m0+2)
     const int L = m[0];
     const bool yz = (m[1] == (L + 1) % 3);
-    if (which & 1) {  // Omega~^{ad}_{pq} += sum_{yz} V[x][y][z] (dy|rz)   columns d < nv
+    if ((which & 1) && (which & 8)) {  // the vvov contraction alone
+      int jb = new_sjob(P, nv, nv, ntile_for(nv), 1, ksplit4, SEPI_F64_ATOMIC, E, ex, s);
+      P.jobs[jb].expo_slot = slot;
+      P.jobs[jb].C = outd(B_OMT, ((long long)p * no + q) * nv2, nv, 1);
+      P.jobs[jb].Ct = P.jobs[jb].C;
+      add_sterm(P, jb, opd(MA_V0 + L, slot), opd(yz ? MB_ZG : MB_ZH, r), nv * vp, 0, ex, s);
+    } else if (which & 1) {  // Omega~^{ad}_{pq} += sum_{yz} V[x][y][z] (dy|rz)   columns d < nv
        // Omega1^x_p       += sum_{yz} V[x][y][z] (qy|rz)   tail column nv8
       const int nv8 = (nv + 7) / 8 * 8;
       int jb = new_sjob(P, nv, nv8 + 1, ntile_for(nv8 + 1), 1, ksplit4, SEPI_F64_ATOMIC, E, ex, s);
@@ -578,8 +589,11 @@ void plan_omega_split(SPlan &P, SplitState *S, int no, int nv, const int ijk[3],
         break;
       }
     const int Lz = ooov[a][3];
+    const bool notail = (which & 8) != 0;
     if (b < 0) {
-      int jb = new_sjob(P, nv * nv8, no + 1, S->N3, 1, 1, SEPI_F64_ATOMIC, E, ex, s);
+      // without the F column the job stops at the last ooov row of OO
+      int jb = new_sjob(P, nv * nv8, notail ? no : no + 1, S->N3, 1, 1, SEPI_F64_ATOMIC, E, ex,
+                        s);
       SJob &J = P.jobs[jb];
       J.expo_slot = slot;
       J.Nm = no;
@@ -599,7 +613,7 @@ void plan_omega_split(SPlan &P, SplitState *S, int no, int nv, const int ijk[3],
     J.n_valid = N;
     J.route = 1;  // columns [0, cs): first permutation, [cs, N): second
     J.Nm2 = cs;
-    J.tw = 1;
+    J.tw = notail ? 0 : 1;  // tw = 0: the F columns are computed and dropped
     J.m_pad = nv8;
     J.m_valid = nv;
     ooov_out(ooov[a][0], ooov[a][4], ooov[a][1], &J.C, &J.Ct);
@@ -1487,6 +1501,355 @@ int split_jacobian(cc3_ctx *c, int nvec, const double *w, const double *R1d, con
   }
   CU(cudaStreamSynchronize(st));
   c->counters.executed_flop = ex + ex_tau;
+  c->counters.slices = s;
+  return CC3_OK;
+}
+
+// ---- left (transpose) Jacobian transformation -----------------------------------
+namespace {
+
+// Jobs of the left transformation for one triple (every distinct permutation
+// (p,q,r) = (ijk[m0], ijk[m1], ijk[m2]); layouts as in plan_jac_tau):
+//   pgh, on L~3 in slot u (G and H at the vector's offsets goff, hoff):
+//     G[y][d][z][r] += sum_x L~[x][y][z] t[p][q][x][d]   rows (y_L, x_L) of layout (m0+1)%3, K = x
+//     H[l][q][z][r] += sum_xy L~[x][y][z] t[p][l][x][y]  rows z of layout m2, K = (zb, u, zz)
+//   pq, on tau~3 in slot u (all vectors at once, column v):
+//     Q[v][r][z]    += sum_xy Lt2_v[p][q][x][y] tau~[x][y][z]
+void plan_left_split(SPlan *pgh, SPlan *pq, SplitState *S, int no, int nv, int ELt, int nvec,
+                     const int ijk[3], int u, long long goff, long long hoff, double &ex) {
+  static const int PERM6[6][3] = {{0, 1, 2}, {1, 0, 2}, {2, 1, 0},
+                                  {0, 2, 1}, {1, 2, 0}, {2, 0, 1}};
+  const int s = S->s, vp = S->vp, nv8 = (nv + 7) / 8 * 8;
+  const long long nv2 = (long long)nv * nv, nvo = (long long)nv * no, n1 = nvo;
+  int seen[6][3], nseen = 0;
+  if (ijk[0] == ijk[1] && ijk[1] == ijk[2]) return;
+  for (int w = 0; w < 6; ++w) {
+    const int *m = PERM6[w];
+    const int p = ijk[m[0]], q = ijk[m[1]], r = ijk[m[2]];
+    bool dup = false;
+    for (int x = 0; x < nseen; ++x)
+      if (seen[x][0] == p && seen[x][1] == q && seen[x][2] == r) dup = true;
+    if (dup) continue;
+    seen[nseen][0] = p;
+    seen[nseen][1] = q;
+    seen[nseen][2] = r;
+    ++nseen;
+    const int Lz = m[2];                          // rows z, K over the other two slots
+    const bool yz = (m[0] == (Lz + 1) % 3);       // K = (zb over y, x, zz) or (.., y, ..)
+    if (pgh) {
+      const int L = (m[0] + 1) % 3;  // K = slot L+2 = x; rows (slot L+1, slot L)
+      const bool xl_y = (L == m[1]);
+      int jb = new_sjob(*pgh, nv * nv8, nv, ntile_for(nv), 1, 1, SEPI_F64_ATOMIC, S->Et - 14,
+                        ex, s);
+      SJob &J = pgh->jobs[jb];
+      J.expo_slot = u;
+      J.m_pad = nv8;
+      J.m_valid = nv;
+      OutD c = outd(B_G, goff + r, xl_y ? nv2 * no : no, nvo);
+      c.m_in = nv8;
+      c.sm1 = xl_y ? no : nv2 * no;
+      J.C = c;
+      J.Ct = c;
+      add_sterm(*pgh, jb, opd(MA_V0K + L, u), opd(ML_T2T, p * no + q), vp, 0, ex, s);
+      jb = new_sjob(*pgh, nv, no, ntile_for(no), 1, S->ks4, SEPI_F64_ATOMIC, S->Et - 14, ex, s);
+      SJob &K = pgh->jobs[jb];
+      K.expo_slot = u;
+      K.C = outd(B_H, hoff + (long long)q * nvo + r, no, (long long)no * nvo);
+      K.Ct = K.C;
+      add_sterm(*pgh, jb, opd(MA_V0 + Lz, u), opd(yz ? ML_T2ZA : ML_T2ZB, p), nv * vp, 0, ex, s);
+    }
+    if (pq) {
+      int jb = new_sjob(*pq, nv, nvec, ntile_for(nvec), 1, S->ks4, SEPI_F64_ATOMIC, ELt - 14,
+                        ex, s);
+      SJob &J = pq->jobs[jb];
+      J.expo_slot = u;
+      J.C = outd(B_Q, (long long)r * nv, 1, n1);
+      J.Ct = J.C;
+      add_sterm(*pq, jb, opd(MA_V0 + Lz, u), opd(yz ? ML_LQA : ML_LQB, p * no + q), nv * vp, 0,
+                ex, s);
+    }
+  }
+}
+
+}  // namespace
+
+// The left transformation on the tensor cores.  Per batch of triples: tau3
+// (the residual's W build and element-wise step) with the Algorithm 2 jobs
+// when the cache is cold and the Q jobs of every vector; then the L3 of every
+// vector (slots u = v * bj + t): the W-build bracket of Lt2 on the engine, the
+// outer products L1 (x) g_ovov + Lt2 (x) F in double-float, the element-wise
+// step with (w - eps), and the contractions of L~3 (the residual's vvov and
+// ooov ones without the singles and F columns into sigma2, and G, H).  sigma1
+// then follows in FP64 from Q, G, H, Lt2 and the Algorithm 2 intermediates,
+// as on the FP64 path.
+int split_left_jacobian(cc3_ctx *c, int nvec, const double *w, const double *L1d,
+                        const double *L2d, double *s1d, double *s2d, cudaStream_t st) {
+  SplitState *S = nullptr;
+  TRY(split_ready(c, &S, st));
+  TRY(jac_blocks(c, st));
+  TRY(stage_jac_static(c, S, st));
+  const int no = c->no, nv = c->nv, s = S->s, vp = S->vp, op = S->op;
+  const long long nv2 = (long long)nv * nv, nvo = (long long)nv * no, oo = (long long)no * no;
+  const long long onv = (long long)no * nv;
+  const size_t n1 = (size_t)no * nv, nt2 = n1 * no * nv, ng = (size_t)nv2 * nv * no,
+               nh = (size_t)no * no * nv * no;
+  JacBufs B;
+  double *lt = nullptr, *s2raw = nullptr, *Q = nullptr, *G = nullptr, *H = nullptr,
+         *N = nullptr;
+  float2 *l1dd = nullptr, *ltdd = nullptr, *ovdd = nullptr, *fdd = nullptr;
+  int *tri_all = nullptr;
+  TRY(B.get(&lt, nt2 * nvec));
+  TRY(B.get(&s2raw, nt2 * nvec));
+  TRY(B.get(&Q, n1 * nvec));
+  TRY(B.get(&G, ng * nvec));
+  TRY(B.get(&H, nh * nvec));
+  TRY(B.get(&N, (size_t)c->naux * nv * no));
+  TRY(B.get(&l1dd, n1 * nvec));
+  TRY(B.get(&ltdd, nt2 * nvec));
+  TRY(B.get(&ovdd, (size_t)(oo * nv2)));
+  TRY(B.get(&fdd, n1));
+  TRY(B.get(&tri_all, 3 * (size_t)c->ntri));
+  CU(cudaMemcpyAsync(tri_all, c->tri_host.data(), sizeof(int) * 3 * c->ntri,
+                     cudaMemcpyHostToDevice, st));
+  TRY(launch_zero(s2raw, nt2 * nvec, st));
+  TRY(launch_zero(Q, n1 * nvec, st));
+  TRY(launch_zero(G, ng * nvec, st));
+  TRY(launch_zero(H, nh * nvec, st));
+  for (int v = 0; v < nvec; ++v)
+    TRY(launch_back_transform(L2d + v * nt2, lt + v * nt2, no, nv, st));
+  TRY(launch_to_dd(L1d, l1dd, (long long)(n1 * nvec), st));
+  TRY(launch_to_dd(lt, ltdd, (long long)(nt2 * nvec), st));
+  TRY(launch_to_dd(c->ovov, ovdd, oo * nv2, st));
+  TRY(launch_to_dd(c->F_ov, fdd, (long long)n1, st));
+  // one exponent for the slices of Lt2 (all vectors)
+  int ELt = 0;
+  {
+    unsigned long long *mx = nullptr;
+    TRY(B.get(&mx, 1));
+    CU(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), st));
+    TRY(launch_maxabs(lt, (long long)(nt2 * nvec), mx, st));
+    unsigned long long hb = 0;
+    CU(cudaMemcpyAsync(&hb, mx, sizeof(hb), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    double x;
+    std::memcpy(&x, &hb, 8);
+    ELt = x > 0.0 ? exponent_of(x) : 0;
+  }
+  auto sliced = [&](__nv_bfloat16 **dst, const double *src, long long rows, int Kp, int E,
+                    const Gather &g, int rps) -> int {
+    const size_t n = arr_elems(Kp, rps, rows / rps, s);
+    TRY(B.get(dst, n));
+    CU(cudaMemsetAsync(*dst, 0, n * sizeof(__nv_bfloat16), st));
+    return launch_slice_gather(src, *dst, s, E, g, rows, Kp, rps, st);
+  };
+  SArrTable jr = S->arrs;  // the L3 part
+  SArrTable aq = S->arrs;  // the tau3 part (Q jobs)
+  {
+    // t2 for G: [(p,q)][d][x];  for H: [p][l][(u,w)], (u,w) = (x,y) or (y,x)
+    __nv_bfloat16 *t2t = nullptr, *tza = nullptr, *tzb = nullptr, *lqa = nullptr, *lqb = nullptr;
+    Gather g;
+    g = {0, (long long)no * nv2, nv2, 1, 0, nv, no, nv, vp, nv, 1, 0};
+    TRY(sliced(&t2t, c->t2, oo * nv, vp, S->Et, g, nv));
+    g = {0, 0, (long long)no * nv2, nv2, nv, 1, no, no, nv, nv, nv, 1};
+    TRY(sliced(&tza, c->t2, oo, nv * vp, S->Et, g, no));
+    g = {0, 0, (long long)no * nv2, nv2, 1, nv, no, no, nv, nv, nv, 1};
+    TRY(sliced(&tzb, c->t2, oo, nv * vp, S->Et, g, no));
+    // Lt2 of every vector: rows v of slab (p,q)
+    g = {0, nv2, 0, (long long)nt2, nv, 1, 1, nvec, nv, nv, nv, 1};
+    TRY(sliced(&lqa, lt, oo * nvec, nv * vp, ELt, g, nvec));
+    g = {0, nv2, 0, (long long)nt2, 1, nv, 1, nvec, nv, nv, nv, 1};
+    TRY(sliced(&lqb, lt, oo * nvec, nv * vp, ELt, g, nvec));
+    jr.a[ML_T2T] = make_arr(t2t, vp, nv, oo, s);
+    jr.a[ML_T2ZA] = make_arr(tza, (long long)nv * vp, no, no, s);
+    jr.a[ML_T2ZB] = make_arr(tzb, (long long)nv * vp, no, no, s);
+    aq.a[ML_LQA] = make_arr(lqa, (long long)nv * vp, nvec, oo, s);
+    aq.a[ML_LQB] = make_arr(lqb, (long long)nv * vp, nvec, oo, s);
+  }
+  // Lt2 in the t2 roles of the W build (every vector back to back)
+  struct Kind {
+    int map;
+    long long K, rps, slabs;
+    __nv_bfloat16 *base;
+  };
+  Kind kinds[3] = {{MJ_R2S, vp, nv, oo, nullptr}, {MJ_R2C, op, nv, onv, nullptr},
+                   {MJ_R2R, op, nv, onv, nullptr}};
+  for (Kind &k : kinds) {
+    const size_t per = arr_elems(k.K, k.rps, k.slabs, s);
+    TRY(B.get(&k.base, per * nvec));
+    CU(cudaMemsetAsync(k.base, 0, per * nvec * sizeof(__nv_bfloat16), st));
+    jr.a[k.map] = make_arr(k.base, k.K, k.rps, k.slabs * nvec, s);
+  }
+  for (int v = 0; v < nvec; ++v) {
+    const double *l2 = lt + v * nt2;
+    auto dst = [&](int i) {
+      return kinds[i].base + (size_t)v * arr_elems(kinds[i].K, kinds[i].rps, kinds[i].slabs, s);
+    };
+    Gather g;
+    g = {0, (long long)no * nv2, nv2, nv, 0, 1, no, nv, vp, nv, 1, 0};
+    TRY(launch_slice_gather(l2, dst(0), s, ELt, g, oo * nv, vp, nv, st));
+    g = {0, (long long)no * nv2, 1, nv, 0, nv2, nv, nv, op, no, 1, 0};
+    TRY(launch_slice_gather(l2, dst(1), s, ELt, g, onv * nv, op, nv, st));
+    g = {0, (long long)no * nv2, nv, 1, 0, nv2, nv, nv, op, no, 1, 0};
+    TRY(launch_slice_gather(l2, dst(2), s, ELt, g, onv * nv, op, nv, st));
+  }
+  // L3 slots of all vectors (as the right transformation's R3 slots)
+  const double per_slot = (double)nv2 * nv * 24.0 + 3.0 * s * nv2 * vp * 2.0;
+  const int bj = std::max(1, std::min(S->batch, (int)(12.0e9 / (per_slot * nvec))));
+  const int nslot = nvec * bj;
+  float2 *Wj = nullptr, *TTj = nullptr, *W3j = nullptr;
+  __nv_bfloat16 *Vj[3] = {nullptr, nullptr, nullptr};
+  __nv_bfloat16 **vptrj = nullptr;
+  unsigned int *maxj = nullptr;
+  int *exj = nullptr;
+  TRY(B.get(&Wj, (size_t)nslot * nv2 * nv));
+  TRY(B.get(&TTj, (size_t)nslot * nv2 * nv));
+  TRY(B.get(&W3j, (size_t)nslot * nv2 * nv));
+  TRY(B.get(&maxj, (size_t)nslot));
+  TRY(B.get(&exj, (size_t)nslot));
+  TRY(B.get(&vptrj, 3));
+  const long long nv8 = (nv + 7) / 8 * 8;
+  for (int L = 0; L < 3; ++L) {
+    const size_t n4 = arr_elems((long long)nv * vp, nv, nslot, s);
+    TRY(B.get(&Vj[L], n4));
+    CU(cudaMemsetAsync(Vj[L], 0, n4 * sizeof(__nv_bfloat16), st));
+    jr.a[MA_V0 + L] = make_arr(Vj[L], (long long)nv * vp, nv, nslot, s);
+    jr.a[MA_V0K + L] = make_arr(Vj[L], vp, (long long)nv * nv8, nslot, s);
+  }
+  CU(cudaMemcpyAsync(vptrj, Vj, sizeof(Vj), cudaMemcpyHostToDevice, st));
+  const bool prep = jac_prep_prec(c) < 0;
+  double *Zv = nullptr, *Zo = nullptr;
+  TRY(jac_z_buffers(c, &Zv, &Zo, prep, st));
+  const int rows = (nv + 7) / 8 * 8;
+  const int ks4 = S->ks4;
+  const int Ec = ELt + S->Eg;
+  const int nb = (c->ntri + bj - 1) / bj;
+  JacPlans pT, pZ, pQ, pAB, pO;
+  pT.v.resize(nb);
+  pZ.v.resize(nb);
+  pQ.v.resize(nb);
+  pAB.v.resize(nb);
+  pO.v.resize(nb);
+  std::vector<float2> eoh((size_t)nslot * nb);
+  double ex = 0.0, ex_tau = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    const int t0 = b * bj, t1 = std::min(c->ntri, t0 + bj);
+    SPlan tb, z, qp, ab, om;
+    for (int t = t0; t < t1; ++t) {
+      const int *ijk = &c->tri_host[3 * t];
+      plan_w_split(tb, S, no, nv, ijk, t - t0, ex_tau);
+      if (prep) plan_jac_tau(nullptr, &z, S, no, nv, nvec, 0, ijk, t - t0, ex);
+      plan_left_split(nullptr, &qp, S, no, nv, ELt, nvec, ijk, t - t0, 0, 0, ex);
+      const double eo_sum = c->eo_h[ijk[0]] + c->eo_h[ijk[1]] + c->eo_h[ijk[2]];
+      for (int v = 0; v < nvec; ++v) {
+        const int u = v * bj + (t - t0);
+        const dd::df e = dd::from_double_host(eo_sum + w[v]);
+        eoh[(size_t)b * nslot + u] = make_float2(e.hi, e.lo);
+        WMaps set1 = {MJ_R2S, MJ_R2S, MJ_R2C, MJ_R2C, MJ_R2R, MJ_R2R,
+                      MA_XS,  MB_XS,  MA_YS,  MB_YS,  MA_OS,  MB_OS};
+        set1.oS = (int)(v * oo);
+        set1.oC = set1.oR = (int)(v * onv);
+        const int j1 = w_job(ab, nv, rows, S->Nab, 1, u, Ec - 14, ex, s);
+        w_terms_1(ab, j1, set1, no, nv, rows, vp, op, ijk, ex, s);
+        const int j2 = w_job(ab, nv, rows, S->Nab, 2, u, Ec - 14, ex, s);
+        w_terms_2(ab, j2, set1, no, nv, rows, vp, op, ijk, ex, s);
+        const int j3 = w_job(ab, nv, rows, S->Nab, 3, u, Ec - 14, ex, s);
+        w_terms_3(ab, j3, set1, no, nv, rows, vp, op, ijk, ex, s);
+        // sigma2 (the residual's vvov and ooov contractions, no singles or F
+        // columns), G and H of vector v
+        const size_t first = om.jobs.size();
+        plan_omega_split(om, S, no, nv, ijk, u, ks4, ex, 1 | 8);
+        plan_omega_split(om, S, no, nv, ijk, u, ks4, ex, 2 | 8);
+        for (size_t jx = first; jx < om.jobs.size(); ++jx) {
+          SJob &J = om.jobs[jx];
+          for (OutD *o : {&J.C, &J.Ct, &J.C2, &J.Ct2})
+            if (o->buf == B_OMT) o->off += (long long)v * nt2;
+        }
+        plan_left_split(&om, nullptr, S, no, nv, ELt, nvec, ijk, u, (long long)v * ng,
+                        (long long)v * nh, ex);
+      }
+    }
+    TRY(s_upload_plan(tb, &pT.v[b], st));
+    if (prep) TRY(s_upload_plan(z, &pZ.v[b], st));
+    TRY(s_upload_plan(qp, &pQ.v[b], st));
+    TRY(s_upload_plan(ab, &pAB.v[b], st));
+    TRY(s_upload_plan(om, &pO.v[b], st));
+  }
+  float2 *eoj_all = nullptr;
+  TRY(B.get(&eoj_all, eoh.size()));
+  CU(cudaMemcpyAsync(eoj_all, eoh.data(), sizeof(float2) * eoh.size(), cudaMemcpyHostToDevice,
+                     st));
+  VPtrTable P;
+  fill_vptrs(c, S, &P);
+  P.p[B_ZV] = Zv;
+  P.p[B_ZO] = Zo;
+  P.p[B_Q] = Q;
+  VPtrTable PR = P;
+  PR.p[B_WS_W] = Wj;
+  PR.p[B_WS_TT] = TTj;
+  PR.p[B_WS_W3] = W3j;
+  PR.p[B_SLOTEXP] = exj;
+  PR.p[B_OMT] = s2raw;
+  PR.p[B_G] = G;
+  PR.p[B_H] = H;
+  const int kd = S_DRAIN_STEPS;
+  long long *L = &c->counters.launches;
+  auto run = [&](const SDevPlan &d, const SArrTable &a, const VPtrTable &pt, int cls) -> int {
+    trace_begin(c, cls, st);
+    TRY(s_launch_plan(d, a, pt, s, kd, S->status, st, L));
+    trace_end(c, cls, st, d.flop, d.slice_flop);
+    return CC3_OK;
+  };
+  auto elem = [&](float2 *W1, float2 *W2, float2 *W3, const float2 *eo, int ns, unsigned int *mb,
+                  int *exs, __nv_bfloat16 **vp_dev, int nalloc) -> int {
+    trace_begin(c, TR_SPLIT_ELEM, st);
+    CU(cudaMemsetAsync(mb, 0, sizeof(unsigned int) * ns, st));
+    TRY(launch_tau_contravariant_dd(W1, W2, W3, W2, S->evdd, eo, 0.f, 0.f, nv, ns, mb, st));
+    TRY(launch_slot_exponent(mb, exs, ns, st));
+    TRY(launch_slice_tt(W2, vp_dev, nv, vp, s, exs, ns, nalloc, st));
+    trace_end(c, TR_SPLIT_ELEM, st, 0.0, 0.0);
+    *L += 3;
+    return CC3_OK;
+  };
+  for (int b = 0; b < nb; ++b) {
+    const int t0 = b * bj, ns = std::min(c->ntri, t0 + bj) - t0;
+    TRY(run(pT.v[b], S->arrs, P, TR_SPLIT_W));
+    TRY(elem(S->Wdd, S->TTdd, S->W3dd, S->eo_tri + t0, ns, S->maxbits, S->slot_ex, S->vptr,
+             S->batch));
+    if (prep) TRY(run(pZ.v[b], S->arrs, P, TR_SPLIT_OMEGA));
+    TRY(run(pQ.v[b], aq, P, TR_SPLIT_OMEGA));
+    TRY(run(pAB.v[b], jr, PR, TR_SPLIT_W));
+    trace_begin(c, TR_SPLIT_ELEM, st);
+    TRY(launch_left_outer_dd(Wj, tri_all + 3 * t0, bj, ns, nslot, l1dd, ltdd, ovdd, fdd, no, nv,
+                             st));
+    trace_end(c, TR_SPLIT_ELEM, st, 0.0, 0.0);
+    *L += 1;
+    TRY(elem(Wj, TTj, W3j, eoj_all + (size_t)b * nslot, nslot, maxj, exj, vptrj, nslot));
+    TRY(run(pO.v[b], jr, PR, TR_SPLIT_OMEGA));
+  }
+  int hs = 0;
+  CU(cudaMemcpyAsync(&hs, S->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  if (hs != 0) {
+    cudaMemsetAsync(S->status, 0, sizeof(int), st);
+    return hs == 2 ? CC3_FAIL(CC3_ERR_ARG, "a left-Jacobian plan addressed outside a slice array")
+                   : CC3_FAIL(CC3_ERR_TIMEOUT, "split engine wait gave up");
+  }
+  if (prep) jac_set_prep(c, CC3_SPLIT_BF16);
+  // sigma1 (FP64, from Q, G, H, Lt2 and Z~) and the pair-symmetric sigma2
+  PtrTable pt;
+  jac_fill_ptrs(c, &pt);
+  pt.p[B_MJ] = N;
+  for (int v = 0; v < nvec; ++v) {
+    pt.p[B_LT] = lt + v * nt2;
+    pt.p[B_Q] = Q + v * n1;
+    pt.p[B_G] = G + v * ng;
+    pt.p[B_H] = H + v * nh;
+    pt.p[B_S1] = s1d + v * n1;
+    TRY(launch_zero(s1d + v * n1, n1, st));
+    TRY(left_finish(c, pt, s2raw + v * nt2, s2d + v * nt2, st));
+  }
+  CU(cudaStreamSynchronize(st));
+  c->counters.executed_flop += ex + ex_tau;
   c->counters.slices = s;
   return CC3_OK;
 }

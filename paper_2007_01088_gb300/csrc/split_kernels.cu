@@ -191,18 +191,24 @@ tau_contravariant_dd_kernel(const float2 *__restrict__ W1, const float2 *W2,
       if (slot[q] == q && cx[u] == cx[q] && cy[u] == cy[q] && cz[u] == cz[q]) slot[q] = u;
   }
   const int t = threadIdx.x;
-  // the denominators' (x, y) parts of every staged cube, w + e_ijk - e_x - e_y
-  __shared__ float2 dxy[6][64];
-  for (int u = t; u < 6 * 64; u += 256) {
-    const int q = u >> 6, x = (u >> 3) & 7, y = u & 7;
-    const int gx = cx[q] * 8 + x, gy = cy[q] * 8 + y;
-    if (slot[q] != q || gx >= nv || gy >= nv) continue;
-    const float2 ex = ev[gx], ey = ev[gy];
-    const dd::df d = dd::add(dd::add(wo, dd::df{-ex.x, -ex.y}), dd::df{-ey.x, -ey.y});
-    dxy[q][u & 63] = make_float2(d.hi, d.lo);
+  // 1 / (w + e_ijk - e_a - e_b - e_c) at every point (a, b, c) of cube (A, B, C):
+  // the six permuted points of the orbit share it, so each is formed once
+  // (one dd division per orbit point instead of one per staged element)
+  __shared__ float2 rcp[512];
+  for (int u = t; u < 512; u += 256) {
+    const int a = u >> 6, b = (u >> 3) & 7, c = u & 7;
+    const int ga = A * 8 + a, gb = B * 8 + b, gc = C * 8 + c;
+    if (ga >= nv || gb >= nv || gc >= nv) continue;
+    const float2 ea = ev[ga], eb = ev[gb], ec = ev[gc];
+    const dd::df d = dd::add(dd::add(dd::add(wo, dd::df{-ea.x, -ea.y}), dd::df{-eb.x, -eb.y}),
+                             dd::df{-ec.x, -ec.y});
+    const dd::df r = dd::div(dd::df{1.f, 0.f}, d);
+    rcp[u] = make_float2(r.hi, r.lo);
   }
   __syncthreads();
-  // stage tau^{xyz} of cube (X, Y, Z) at [z][x][y] (y contiguous in memory)
+  // stage tau^{xyz} of cube (X, Y, Z) at [z][x][y] (y contiguous in memory);
+  // its point (x, y, z) is the point (a, b, c) of cube (A, B, C) with each
+  // index moved to the slot of its cube index
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
     if (slot[q] != q) continue;
@@ -216,9 +222,11 @@ tau_contravariant_dd_kernel(const float2 *__restrict__ W1, const float2 *W2,
         const float2 a1 = W1[i], a2 = W2[i], a3 = W3[i];
         const dd::df sum =
             dd::add(dd::add(dd::df{a1.x, a1.y}, dd::df{a2.x, a2.y}), dd::df{a3.x, a3.y});
-        const float2 dq = dxy[q][x * 8 + y], ez = ev[gz];
-        const dd::df den = dd::add(dd::df{dq.x, dq.y}, dd::df{-ez.x, -ez.y});
-        const dd::df tau = dd::div(sum, den);
+        // (a, b, c) of this point: abc, acb, cba, bac, bca, cab orders of q
+        const int pa[6] = {x, x, z, y, z, y}, pb[6] = {y, z, y, x, x, z},
+                  pc[6] = {z, y, x, z, y, x};
+        const float2 r = rcp[pa[q] * 64 + pb[q] * 8 + pc[q]];
+        const dd::df tau = dd::mul(sum, dd::df{r.x, r.y});
         v = make_float2(tau.hi, tau.lo);
       }
       sm[q][z * CV_SZ + x * CV_SX + y] = v;
@@ -398,6 +406,57 @@ slice_tt_kernel(const float2 *__restrict__ tt, __nv_bfloat16 *const *__restrict_
   }
 }
 
+// y = x as double-float pairs (hi = x rounded to FP32, lo = the rest)
+__global__ void to_dd_kernel(const double *__restrict__ x, float2 *__restrict__ y, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double v = x[e];
+    const float h = (float)v;
+    y[e] = make_float2(h, (float)(v - (double)h));
+  }
+}
+
+// The outer products of the left transformation's L3 numerator, added to the
+// W build's first partial sum W1[u][c][a][b] (double-float) of slot u = v * bj
+// + t (vector v, triple t of the batch; slots with t >= ns are idle):
+//   sum over the six terms of P of L1[o0][x] (o1 y|o2 z) + Lt2[o0][o1][x][y] F[o2][z],
+// (o0,o1,o2) = (ijk[s0], ijk[s1], ijk[s2]), (x,y,z) = (v[s0], v[s1], v[s2]),
+// v = (a, b, c).  All factors come as double-float pairs.
+__global__ void __launch_bounds__(256)
+left_outer_dd_kernel(float2 *__restrict__ W1, const int *__restrict__ tri, int bj, int ns,
+                     const float2 *__restrict__ L1, const float2 *__restrict__ Lt,
+                     const float2 *__restrict__ ovov, const float2 *__restrict__ F, int no,
+                     int nv) {
+  constexpr int P6[6][3] = {{0, 1, 2}, {1, 0, 2}, {2, 1, 0}, {0, 2, 1}, {1, 2, 0}, {2, 0, 1}};
+  const int u = blockIdx.y, vec = u / bj, t = u % bj;
+  if (t >= ns) return;
+  const int ijk[3] = {tri[3 * t], tri[3 * t + 1], tri[3 * t + 2]};
+  const long long nv2 = (long long)nv * nv, nv3 = nv2 * nv;
+  const long long n1 = (long long)no * nv, nt2 = n1 * no * nv;
+  const float2 *l1 = L1 + vec * n1, *lt = Lt + vec * nt2;
+  float2 *W = W1 + (long long)u * nv3;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nv3;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(e % nv), a = (int)((e / nv) % nv), c = (int)(e / nv2);
+    const int v[3] = {a, b, c};
+    dd::df sum = {0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const int o0 = ijk[P6[q][0]], o1 = ijk[P6[q][1]], o2 = ijk[P6[q][2]];
+      const int x = v[P6[q][0]], y = v[P6[q][1]], z = v[P6[q][2]];
+      const float2 f1 = l1[(long long)o0 * nv + x];
+      const float2 g1 = ovov[(((long long)o1 * nv + y) * no + o2) * nv + z];
+      const float2 f2 = lt[(((long long)o0 * no + o1) * nv + x) * nv + y];
+      const float2 g2 = F[(long long)o2 * nv + z];
+      sum = dd::add(sum, dd::add(dd::mul(dd::df{f1.x, f1.y}, dd::df{g1.x, g1.y}),
+                                 dd::mul(dd::df{f2.x, f2.y}, dd::df{g2.x, g2.y})));
+    }
+    const float2 w0 = W[e];
+    const dd::df r = dd::add(dd::df{w0.x, w0.y}, sum);
+    W[e] = make_float2(r.hi, r.lo);
+  }
+}
+
 // ---- launchers ----------------------------------------------------------------
 static int grid_for(long long n) {
   long long b = (n + 255) / 256;
@@ -426,6 +485,23 @@ int launch_tau_contravariant_dd(const float2 *W1, const float2 *W2, const float2
   tau_contravariant_dd_kernel<<<dim3((unsigned)ncube, nslot), 256, 0, st>>>(
       W1, W2, W3, tt, ev, eo, w_hi, w_lo, nv, maxbits);
   return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_FAIL(CC3_ERR_CUDA, "split element-wise kernel launch");
+}
+int launch_to_dd(const double *x, float2 *y, long long n, cudaStream_t st) {
+  if (n <= 0) return CC3_OK;
+  to_dd_kernel<<<grid_for(n), 256, 0, st>>>(x, y, n);
+  return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_FAIL(CC3_ERR_CUDA, "to_dd launch");
+}
+int launch_left_outer_dd(float2 *W1, const int *tri, int bj, int ns, int nslot, const float2 *L1,
+                         const float2 *Lt, const float2 *ovov, const float2 *F, int no, int nv,
+                         cudaStream_t st) {
+  if (nslot <= 0) return CC3_OK;
+  if (nslot > 65535) return CC3_FAIL(CC3_ERR_ARG, "left outer products: slots");
+  const long long nv3 = (long long)nv * nv * nv;
+  const int blocks = (int)std::min<long long>((nv3 + 255) / 256, 2048);
+  left_outer_dd_kernel<<<dim3(blocks, nslot), 256, 0, st>>>(W1, tri, bj, ns, L1, Lt, ovov, F, no,
+                                                            nv);
+  return cudaGetLastError() == cudaSuccess ? CC3_OK
+                                           : CC3_FAIL(CC3_ERR_CUDA, "left outer products launch");
 }
 int launch_slot_exponent(const unsigned int *maxbits, int *ex, int nslot, cudaStream_t st) {
   slot_exponent_kernel<<<(nslot + 127) / 128, 128, 0, st>>>(maxbits, ex, nslot);

@@ -35,6 +35,15 @@ int launch_tau_contravariant_dd(const float2 *W1, const float2 *W2, const float2
                                 float w_lo, int nv, int nslot, unsigned int *maxbits,
                                 cudaStream_t st);
 int launch_slot_exponent(const unsigned int *maxbits, int *ex, int nslot, cudaStream_t st);
+// y[e] = x[e] as a double-float pair
+int launch_to_dd(const double *x, float2 *y, long long n, cudaStream_t st);
+// the left transformation's outer products L1 (x) g_ovov + Lt2 (x) F of the L3
+// numerator (six terms of P) added to W1[u][c][a][b] (dd) of the nslot slots
+// u = v * bj + t of a batch of ns triples (tri: 3 ints per triple); all
+// factors as dd pairs (L1[v][i][a], Lt[v][i][j][a][b], ovov, F_ov)
+int launch_left_outer_dd(float2 *W1, const int *tri, int bj, int ns, int nslot, const float2 *L1,
+                         const float2 *Lt, const float2 *ovov, const float2 *F, int no, int nv,
+                         cudaStream_t st);
 // v: device array of 3 pointers (one per cyclic layout)
 int launch_slice_tt(const float2 *tt, __nv_bfloat16 *const *v, int nv, int vp, int s,
                     const int *ex, int nslot, int nslot_alloc, cudaStream_t st);

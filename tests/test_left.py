@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 from cc3_inputs import config_inputs, make_inputs, make_trial_vectors, unique_triples
+from split_tol import split_close, split_err
 
 pytestmark = pytest.mark.gpu
 
@@ -85,7 +86,7 @@ def test_left_jacobian_refusals(g):
     L1, L2 = _left_vectors(no, nv, 1, seed=1)
     ctx = g.Context(inp)
     with pytest.raises(g.CC3Error) as e:
-        ctx.left_jacobian(L1, L2, [0.0], g.CC3_SPLIT_BF16)
+        ctx.left_jacobian(L1, L2, [0.0], g.CC3_SPLIT_INT8)
     assert e.value.status == g.CC3_ERR_UNSUPPORTED
     w_bad = inp.eps_v[0] + inp.eps_v[1] + inp.eps_v[2] - inp.eps_o.sum() + 1e-8
     with pytest.raises(g.CC3Error) as e:
@@ -108,3 +109,58 @@ def test_left_jacobian_batched_shape(g):
     s1, s2 = ctx.left_jacobian(L1, L2, w)
     assert _close(s1, ref["sigma1"], 1e-11)
     assert _close(s2, ref["sigma2"], 1e-11)
+
+
+# ---- split (BF16 slice) path -------------------------------------------------------------
+# Left vectors normalised like the trial vectors, so that the absolute targets
+# of the split path apply as for rho.
+
+@pytest.mark.parametrize("no,nv", [(3, 9), (4, 20), (2, 17), (5, 33)])
+def test_split_left_jacobian_matches_oracle(g, no, nv):
+    inp = make_inputs(no, nv, seed=500 + no * nv)
+    L1, L2 = make_trial_vectors(no, nv, 2, seed=no + 3 * nv)
+    w = [0.25, 0.0]
+    ref = oracle.left_jacobian(inp, L1, L2, w)
+    ctx = g.Context(inp)
+    s1, s2 = ctx.left_jacobian(L1, L2, w, g.CC3_SPLIT_BF16)
+    assert split_close(s1, ref["sigma1"]), split_err(s1, ref["sigma1"])
+    assert split_close(s2, ref["sigma2"]), split_err(s2, ref["sigma2"])
+    c = ctx.counters()
+    assert c["slices"] == 6 and c["launches"] > 0
+    # FP64 after split on the same context (shared Algorithm 2 cache)
+    f1, f2 = ctx.left_jacobian(L1, L2, w)
+    assert _close(f1, ref["sigma1"], 1e-11) and _close(f2, ref["sigma2"], 1e-11)
+
+
+def test_split_left_and_right_are_transposes(g):
+    no, nv = 4, 24
+    inp = make_inputs(no, nv, seed=35)
+    R1, R2 = make_trial_vectors(no, nv, 2, seed=4)
+    L1, L2 = make_trial_vectors(no, nv, 2, seed=6)
+    ctx = g.Context(inp)
+    r1, r2 = ctx.jacobian(R1, R2, [0.3, 0.3], g.CC3_SPLIT_BF16)
+    s1, s2 = ctx.left_jacobian(L1, L2, [0.3, 0.3], g.CC3_SPLIT_BF16)
+    for n in range(2):
+        for m in range(2):
+            a = np.sum(L1[n] * r1[m]) + np.sum(L2[n] * r2[m])
+            b = np.sum(s1[n] * R1[m]) + np.sum(s2[n] * R2[m])
+            assert abs(a - b) <= 1e-9
+
+
+def test_split_left_jacobian_batched_shape(g):
+    """The batched-Jacobian shape (no=20, nv=200, 96- and 48-column N tiles,
+    several K splits) on a triple subset against the matrix-product oracle."""
+    from oracle import matrix_form as MF
+    inp = config_inputs("cfg4_jacobian_no20_nv200")
+    no, nv = inp.no, inp.nv
+    L1, L2 = make_trial_vectors(no, nv, 3, seed=13)
+    w = [0.25, 0.0, -0.1]
+    tr = [t[:3] for t in unique_triples(no)]
+    rng = np.random.default_rng(10)
+    sel = [tr[i] for i in sorted(rng.choice(len(tr), size=2, replace=False))] + [(18, 18, 3)]
+    ref = MF.left_jacobian(inp, L1, L2, w, triples=sel)
+    ctx = g.Context(inp)
+    ctx.set_triples(sel)
+    s1, s2 = ctx.left_jacobian(L1, L2, w, g.CC3_SPLIT_BF16)
+    assert split_close(s1, ref["sigma1"]), split_err(s1, ref["sigma1"])
+    assert split_close(s2, ref["sigma2"]), split_err(s2, ref["sigma2"])
