@@ -30,9 +30,10 @@ def test_reference_arm_prints_one_contract_line():
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
-    baseline = json.load(open(os.path.join(ROOT, "BASELINE.json")))
+    sys.path.insert(0, ROOT)
+    import bench
     assert d["impl"] == "reference"
-    assert d["metric"] == baseline["metric"]
+    assert d["metric"] == bench.METRIC  # the same metric as the native arm
     assert d["unit"] == "TFLOP/s" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["steps"] == 1 and d["warmup"] == 3 and d["n_gpus"] == 1
     cb = d["cpu_baseline"]
