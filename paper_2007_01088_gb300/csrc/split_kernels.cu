@@ -191,6 +191,28 @@ tau_contravariant_dd_kernel(const float2 *__restrict__ W1, const float2 *W2,
       if (slot[q] == q && cx[u] == cx[q] && cy[u] == cy[q] && cz[u] == cz[q]) slot[q] = u;
   }
   const int t = threadIdx.x;
+  // The partial sums of two cubes at a time are loaded into registers before
+  // any of them is used (12 loads in flight per thread); the first two cubes'
+  // loads are issued before the reciprocals below are formed.
+  float2 la[2][2][3];
+  auto issue = [&](int q0) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int q = q0 + k;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int e = t + 256 * h, y = e & 7, x = (e >> 3) & 7, z = e >> 6;
+        const int gx = cx[q] * 8 + x, gy = cy[q] * 8 + y, gz = cz[q] * 8 + z;
+        if (slot[q] == q && gx < nv && gy < nv && gz < nv) {
+          const long long i = sbase + (long long)gz * nv2 + (long long)gx * nv + gy;
+          la[k][h][0] = W1[i];
+          la[k][h][1] = W2[i];
+          la[k][h][2] = W3[i];
+        }
+      }
+    }
+  };
+  issue(0);
   // 1 / (w + e_ijk - e_a - e_b - e_c) at every point (a, b, c) of cube (A, B, C):
   // the six permuted points of the orbit share it, so each is formed once
   // (one dd division per orbit point instead of one per staged element)
@@ -209,29 +231,36 @@ tau_contravariant_dd_kernel(const float2 *__restrict__ W1, const float2 *W2,
   // stage tau^{xyz} of cube (X, Y, Z) at [z][x][y] (y contiguous in memory);
   // its point (x, y, z) is the point (a, b, c) of cube (A, B, C) with each
   // index moved to the slot of its cube index
+  auto stage = [&](int q0) {
 #pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    if (slot[q] != q) continue;
+    for (int k = 0; k < 2; ++k) {
+      const int q = q0 + k;
+      if (slot[q] != q) continue;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int e = t + 256 * h, y = e & 7, x = (e >> 3) & 7, z = e >> 6;
-      const int gx = cx[q] * 8 + x, gy = cy[q] * 8 + y, gz = cz[q] * 8 + z;
-      float2 v = make_float2(0.f, 0.f);
-      if (gx < nv && gy < nv && gz < nv) {
-        const long long i = sbase + (long long)gz * nv2 + (long long)gx * nv + gy;
-        const float2 a1 = W1[i], a2 = W2[i], a3 = W3[i];
-        const dd::df sum =
-            dd::add(dd::add(dd::df{a1.x, a1.y}, dd::df{a2.x, a2.y}), dd::df{a3.x, a3.y});
-        // (a, b, c) of this point: abc, acb, cba, bac, bca, cab orders of q
-        const int pa[6] = {x, x, z, y, z, y}, pb[6] = {y, z, y, x, x, z},
-                  pc[6] = {z, y, x, z, y, x};
-        const float2 r = rcp[pa[q] * 64 + pb[q] * 8 + pc[q]];
-        const dd::df tau = dd::mul(sum, dd::df{r.x, r.y});
-        v = make_float2(tau.hi, tau.lo);
+      for (int h = 0; h < 2; ++h) {
+        const int e = t + 256 * h, y = e & 7, x = (e >> 3) & 7, z = e >> 6;
+        const int gx = cx[q] * 8 + x, gy = cy[q] * 8 + y, gz = cz[q] * 8 + z;
+        float2 v = make_float2(0.f, 0.f);
+        if (gx < nv && gy < nv && gz < nv) {
+          const float2 a1 = la[k][h][0], a2 = la[k][h][1], a3 = la[k][h][2];
+          const dd::df sum =
+              dd::add(dd::add(dd::df{a1.x, a1.y}, dd::df{a2.x, a2.y}), dd::df{a3.x, a3.y});
+          // (a, b, c) of this point: abc, acb, cba, bac, bca, cab orders of q
+          const int pa[6] = {x, x, z, y, z, y}, pb[6] = {y, z, y, x, x, z},
+                    pc[6] = {z, y, x, z, y, x};
+          const float2 r = rcp[pa[q] * 64 + pb[q] * 8 + pc[q]];
+          const dd::df tau = dd::mul(sum, dd::df{r.x, r.y});
+          v = make_float2(tau.hi, tau.lo);
+        }
+        sm[q][z * CV_SZ + x * CV_SX + y] = v;
       }
-      sm[q][z * CV_SZ + x * CV_SX + y] = v;
     }
-  }
+  };
+  stage(0);
+  issue(2);
+  stage(2);
+  issue(4);
+  stage(4);
   __syncthreads();
   dd::df v[2][6];
   bool own[2];
