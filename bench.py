@@ -681,12 +681,17 @@ def widening_measure(args, local):
         ctx.left_jacobian(a1, a2, wv, g.CC3_SPLIT_BF16)
         ms, _ = _timed_calls(stream, lambda: ctx.left_jacobian(a1, a2, wv, g.CC3_SPLIT_BF16), 1)
         flop = ctx.counters()["nominal_flop"]
+        # one traced call: device time per kernel class (the timed call above is untraced)
+        ctx.set_tracing(True)
+        ctx.left_jacobian(a1, a2, wv, g.CC3_SPLIT_BF16)
+        phases = {k: {"ms": v["ms"], "launches": v["launches"]} for k, v in ctx.trace().items()
+                  if v["launches"]}
         ctx.close()
         out["left_jacobian"]["split"] = {
             "workload": f"left (transpose) Jacobian, no={no} nv={nv} naux={inp.naux}, {nvec} "
                         "left vectors at w=0.25, the whole triple loop, split path",
             "value": flop / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
-            "nominal_flop_per_step": flop}
+            "nominal_flop_per_step": flop, "phases_traced_call": phases}
         torch.cuda.empty_cache()
         # CVS filter
         inp = config_inputs("cfg4_jacobian_no20_nv200")
