@@ -361,6 +361,8 @@ slice_tt_kernel(const float2 *__restrict__ tt, __nv_bfloat16 *const *__restrict_
   const float2 *T = tt + (long long)slot * nv2 * nv;
   const int sh = 7 + 8 * (s - 1) - ex[slot];
   const int plane = TT_PLANE;
+  // 2^sh and 2^(sh-24) as floats (the 32-bit digit path of s = 6)
+  const float s0 = ldexpf(1.f, sh), s24 = ldexpf(1.f, sh - 24);
   // 16 elements per thread, loaded 8 at a time before any is converted (the
   // loads of a batch are in flight together)
 #pragma unroll 1
@@ -378,18 +380,46 @@ slice_tt_kernel(const float2 *__restrict__ tt, __nv_bfloat16 *const *__restrict_
     for (int u = 0; u < 8; ++u) {
       const int e = threadIdx.x + 256 * (i0 + u);
       const int c = e & 15, b = (e >> 4) & 15, a = e >> 8;
-      long long Tt = fixed_from_float(tv[u].x, sh) + fixed_from_float(tv[u].y, sh);
-      // balanced base-256 digits, slice p stores d_p 2^(-8p)
+      // balanced base-256 digits of the fixed-point value T, slice p stores d_p 2^(-8p)
       float d[S_MAX_SLICES_K];
+      if (s == 6 && sh >= 24 && sh <= 120) {  // 2^sh and 2^(sh-24) are normal floats
+        // |T| < 2^47: T = th 2^24 + tl with 0 <= tl < 2^24, both in 32-bit
+        // integers.  hi 2^(sh-24) = Hi + f (Hi = its floor, exact; f in [0, 1)),
+        // so round(hi 2^sh) = Hi 2^24 + round(f 2^24); |lo| <= ulp(hi) / 2 keeps
+        // round(lo 2^sh) below 2^23.  (Power-of-two scalings are exact.)
+        const float H = tv[u].x * s24;
+        const float Hi = floorf(H);
+        int th = __float2int_rn(Hi);
+        int tl = __float2int_rn((H - Hi) * 16777216.f) + __float2int_rn(tv[u].y * s0);
+        const int cy = tl >> 24;  // floor(tl / 2^24)
+        th += cy;
+        tl -= cy * 16777216;
 #pragma unroll
-      for (int p = S_MAX_SLICES_K - 1; p >= 0; --p) {
-        if (p < s) {
-          if (p > 0) {
-            const long long r = ((Tt + 128) & 255) - 128;
-            d[p] = (float)(int)r;
-            Tt = (Tt - r) >> 8;
-          } else {
-            d[0] = (float)(int)Tt;  // |d_0| <= 128 by the bound on Tt
+        for (int p = 5; p >= 3; --p) {  // the three low digits from tl
+          const int r = ((tl + 128) & 255) - 128;
+          d[p] = (float)r;
+          tl = (tl - r) >> 8;
+        }
+        th += tl;  // the carry out of the low digits (0 or 1)
+#pragma unroll
+        for (int p = 2; p >= 1; --p) {
+          const int r = ((th + 128) & 255) - 128;
+          d[p] = (float)r;
+          th = (th - r) >> 8;
+        }
+        d[0] = (float)th;  // |d_0| <= 128 by the bound on T
+      } else {
+        long long Tt = fixed_from_float(tv[u].x, sh) + fixed_from_float(tv[u].y, sh);
+#pragma unroll
+        for (int p = S_MAX_SLICES_K - 1; p >= 0; --p) {
+          if (p < s) {
+            if (p > 0) {
+              const long long r = ((Tt + 128) & 255) - 128;
+              d[p] = (float)(int)r;
+              Tt = (Tt - r) >> 8;
+            } else {
+              d[0] = (float)(int)Tt;  // |d_0| <= 128 by the bound on Tt
+            }
           }
         }
       }
