@@ -268,3 +268,16 @@ def test_density_refusals(g):
     assert "(-1)" in status(lambda: ctx.density(L1, L2, float("nan")))
     ctx.set_triples([[2, 1, 0]])
     assert "(-7)" in status(lambda: ctx.density(L1, L2, 0.1))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("no,nv", [(2, 5), (7, 16)])
+def test_density_small_and_ragged(g, no, nv):
+    """no = 2 (two triples, each with one pair of equal indices) and a ragged shape
+    with several occupied batches and 16 virtual slabs."""
+    inp = make_inputs(no, nv, seed=no * 100 + nv)
+    L1, L2 = _left(no, nv, seed=nv)
+    ref = _density(inp, -0.15, L1, L2)
+    doo, dov, dvv = g.Context(inp).density(L1, L2, -0.15)
+    for x, k in ((doo, "Doo"), (dov, "Dov"), (dvv, "Dvv")):
+        assert _rel(x, ref[k]) < 1e-11, k

@@ -164,3 +164,20 @@ def test_split_left_jacobian_batched_shape(g):
     s1, s2 = ctx.left_jacobian(L1, L2, w, g.CC3_SPLIT_BF16)
     assert split_close(s1, ref["sigma1"]), split_err(s1, ref["sigma1"])
     assert split_close(s2, ref["sigma2"]), split_err(s2, ref["sigma2"])
+
+
+def test_split_left_jacobian_device_pointers_and_cvs_subset(g):
+    """Device pointers and a core-valence-separation triple list on the split path,
+    against the oracle restricted to the same triples."""
+    import torch
+    no, nv = 5, 24
+    inp = make_inputs(no, nv, seed=44)
+    L1, L2 = make_trial_vectors(no, nv, 2, seed=7)
+    ctx = g.Context(inp, device=True)
+    tri = ctx.set_cvs([0, 1])
+    ref = oracle.left_jacobian(inp, L1, L2, [0.2, -0.05], triples=[t[:3] for t in tri])
+    s1, s2 = ctx.left_jacobian(torch.from_numpy(L1).cuda(), torch.from_numpy(L2).cuda(),
+                               [0.2, -0.05], g.CC3_SPLIT_BF16)
+    torch.cuda.synchronize()
+    assert split_close(s1.cpu().numpy(), ref["sigma1"]), split_err(s1.cpu().numpy(), ref["sigma1"])
+    assert split_close(s2.cpu().numpy(), ref["sigma2"]), split_err(s2.cpu().numpy(), ref["sigma2"])
