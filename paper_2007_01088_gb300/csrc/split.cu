@@ -1508,19 +1508,25 @@ int split_jacobian(cc3_ctx *c, int nvec, const double *w, const double *R1d, con
 // ---- left (transpose) Jacobian transformation -----------------------------------
 namespace {
 
+// One permutation's term of the G contraction (see plan_left_g).
+struct GTerm {
+  int v, r, mi, u, p, q;
+};
+
 // Jobs of the left transformation for one triple (every distinct permutation
 // (p,q,r) = (ijk[m0], ijk[m1], ijk[m2]); layouts as in plan_jac_tau):
-//   pgh, on L~3 in slot u (G and H at the vector's offsets goff, hoff):
-//     G[y][d][z][r] += sum_x L~[x][y][z] t[p][q][x][d]   rows (y_L, x_L) of layout (m0+1)%3, K = x
+//   pgh, on L~3 in slot u of vector v (H at the vector's offset hoff; the G
+//   terms go to gterms, made into jobs by plan_left_g):
 //     H[l][q][z][r] += sum_xy L~[x][y][z] t[p][l][x][y]  rows z of layout m2, K = (zb, u, zz)
 //   pq, on tau~3 in slot u (all vectors at once, column v):
 //     Q[v][r][z]    += sum_xy Lt2_v[p][q][x][y] tau~[x][y][z]
-void plan_left_split(SPlan *pgh, SPlan *pq, SplitState *S, int no, int nv, int ELt, int nvec,
-                     const int ijk[3], int u, long long goff, long long hoff, double &ex) {
+void plan_left_split(SPlan *pgh, SPlan *pq, std::vector<GTerm> *gterms, SplitState *S, int no,
+                     int nv, int ELt, int nvec, const int ijk[3], int u, int v, long long hoff,
+                     double &ex) {
   static const int PERM6[6][3] = {{0, 1, 2}, {1, 0, 2}, {2, 1, 0},
                                   {0, 2, 1}, {1, 2, 0}, {2, 0, 1}};
-  const int s = S->s, vp = S->vp, nv8 = (nv + 7) / 8 * 8;
-  const long long nv2 = (long long)nv * nv, nvo = (long long)nv * no, n1 = nvo;
+  const int s = S->s, vp = S->vp;
+  const long long nvo = (long long)nv * no, n1 = nvo;
   int seen[6][3], nseen = 0;
   if (ijk[0] == ijk[1] && ijk[1] == ijk[2]) return;
   for (int w = 0; w < 6; ++w) {
@@ -1536,22 +1542,9 @@ void plan_left_split(SPlan *pgh, SPlan *pq, SplitState *S, int no, int nv, int E
     ++nseen;
     const int Lz = m[2];                          // rows z, K over the other two slots
     const bool yz = (m[0] == (Lz + 1) % 3);       // K = (zb over y, x, zz) or (.., y, ..)
+    if (gterms) gterms->push_back(GTerm{v, r, w, u, p, q});
     if (pgh) {
-      const int L = (m[0] + 1) % 3;  // K = slot L+2 = x; rows (slot L+1, slot L)
-      const bool xl_y = (L == m[1]);
-      int jb = new_sjob(*pgh, nv * nv8, nv, ntile_for(nv), 1, 1, SEPI_F64_ATOMIC, S->Et - 14,
-                        ex, s);
-      SJob &J = pgh->jobs[jb];
-      J.expo_slot = u;
-      J.m_pad = nv8;
-      J.m_valid = nv;
-      OutD c = outd(B_G, goff + r, xl_y ? nv2 * no : no, nvo);
-      c.m_in = nv8;
-      c.sm1 = xl_y ? no : nv2 * no;
-      J.C = c;
-      J.Ct = c;
-      add_sterm(*pgh, jb, opd(MA_V0K + L, u), opd(ML_T2T, p * no + q), vp, 0, ex, s);
-      jb = new_sjob(*pgh, nv, no, ntile_for(no), 1, S->ks4, SEPI_F64_ATOMIC, S->Et - 14, ex, s);
+      int jb = new_sjob(*pgh, nv, no, ntile_for(no), 1, S->ks4, SEPI_F64_ATOMIC, S->Et - 14, ex, s);
       SJob &K = pgh->jobs[jb];
       K.expo_slot = u;
       K.C = outd(B_H, hoff + (long long)q * nvo + r, no, (long long)no * nvo);
@@ -1568,6 +1561,49 @@ void plan_left_split(SPlan *pgh, SPlan *pq, SplitState *S, int no, int nv, int E
       add_sterm(*pq, jb, opd(MA_V0 + Lz, u), opd(yz ? ML_LQA : ML_LQB, p * no + q), nv * vp, 0,
                 ex, s);
     }
+  }
+}
+
+// The G contraction of a batch, G[y][d][z][r] += sum_x L~[x][y][z] t[p][q][x][d],
+// rows (y_L, x_L) of layout (m0+1)%3, K = x: the permutations of the batch with the
+// same vector, output index r and slot map m write the same output rows in the
+// same order, so they become the terms of one job (K = their number times nv).
+// All L3 slots of a batch share one exponent, so the job's scale is that of any.
+void plan_left_g(SPlan &P, SplitState *S, int no, int nv, std::vector<GTerm> terms,
+                 size_t ng, double &ex) {
+  static const int PERM6[6][3] = {{0, 1, 2}, {1, 0, 2}, {2, 1, 0},
+                                  {0, 2, 1}, {1, 2, 0}, {2, 0, 1}};
+  const int s = S->s, vp = S->vp, nv8 = (nv + 7) / 8 * 8;
+  const long long nv2 = (long long)nv * nv, nvo = (long long)nv * no;
+  std::stable_sort(terms.begin(), terms.end(), [](const GTerm &a, const GTerm &b) {
+    return a.v != b.v ? a.v < b.v : (a.r != b.r ? a.r < b.r : a.mi < b.mi);
+  });
+  for (size_t g0 = 0; g0 < terms.size();) {
+    size_t g1 = g0 + 1;
+    while (g1 < terms.size() && terms[g1].v == terms[g0].v && terms[g1].r == terms[g0].r &&
+           terms[g1].mi == terms[g0].mi)
+      ++g1;
+    const GTerm &f = terms[g0];
+    const int *m = PERM6[f.mi];
+    const int L = (m[0] + 1) % 3;  // K = slot L+2 = x; rows (slot L+1, slot L)
+    const bool xl_y = (L == m[1]);
+    const int ksteps = (int)(g1 - g0) * (vp / 16);
+    const int ksplit = std::max(1, std::min(8, ksteps / 192));
+    int jb = new_sjob(P, nv * nv8, nv, ntile_for(nv), 1, ksplit, SEPI_F64_ATOMIC, S->Et - 14,
+                      ex, s);
+    SJob &J = P.jobs[jb];
+    J.expo_slot = f.u;
+    J.m_pad = nv8;
+    J.m_valid = nv;
+    OutD c = outd(B_G, (long long)f.v * (long long)ng + f.r, xl_y ? nv2 * no : no, nvo);
+    c.m_in = nv8;
+    c.sm1 = xl_y ? no : nv2 * no;
+    J.C = c;
+    J.Ct = c;
+    for (size_t k = g0; k < g1; ++k)
+      add_sterm(P, jb, opd(MA_V0K + L, terms[k].u), opd(ML_T2T, terms[k].p * no + terms[k].q),
+                vp, 0, ex, s);
+    g0 = g1;
   }
 }
 
@@ -1589,7 +1625,7 @@ int split_left_jacobian(cc3_ctx *c, int nvec, const double *w, const double *L1d
   TRY(jac_blocks(c, st));
   TRY(stage_jac_static(c, S, st));
   const int no = c->no, nv = c->nv, s = S->s, vp = S->vp, op = S->op;
-  const long long nv2 = (long long)nv * nv, nvo = (long long)nv * no, oo = (long long)no * no;
+  const long long nv2 = (long long)nv * nv, oo = (long long)no * no;
   const long long onv = (long long)no * nv;
   const size_t n1 = (size_t)no * nv, nt2 = n1 * no * nv, ng = (size_t)nv2 * nv * no,
                nh = (size_t)no * no * nv * no;
@@ -1692,9 +1728,14 @@ int split_left_jacobian(cc3_ctx *c, int nvec, const double *w, const double *L1d
     g = {0, (long long)no * nv2, nv, 1, 0, nv2, nv, nv, op, no, 1, 0};
     TRY(launch_slice_gather(l2, dst(2), s, ELt, g, onv * nv, op, nv, st));
   }
-  // L3 slots of all vectors (as the right transformation's R3 slots)
+  // L3 slots of all vectors (as the right transformation's R3 slots); larger
+  // batches than the right transformation's (up to 40 GB, at most 40 % of the free
+  // memory) give the grouped G jobs more terms
   const double per_slot = (double)nv2 * nv * 24.0 + 3.0 * s * nv2 * vp * 2.0;
-  const int bj = std::max(1, std::min(S->batch, (int)(12.0e9 / (per_slot * nvec))));
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  const double slot_budget = std::min(40.0e9, 0.4 * (double)free_b);
+  const int bj = std::max(1, std::min(S->batch, (int)(slot_budget / (per_slot * nvec))));
   const int nslot = nvec * bj;
   float2 *Wj = nullptr, *TTj = nullptr, *W3j = nullptr;
   __nv_bfloat16 *Vj[3] = {nullptr, nullptr, nullptr};
@@ -1734,11 +1775,12 @@ int split_left_jacobian(cc3_ctx *c, int nvec, const double *w, const double *L1d
   for (int b = 0; b < nb; ++b) {
     const int t0 = b * bj, t1 = std::min(c->ntri, t0 + bj);
     SPlan tb, z, qp, ab, om;
+    std::vector<GTerm> gterms;
     for (int t = t0; t < t1; ++t) {
       const int *ijk = &c->tri_host[3 * t];
       plan_w_split(tb, S, no, nv, ijk, t - t0, ex_tau);
       if (prep) plan_jac_tau(nullptr, &z, S, no, nv, nvec, 0, ijk, t - t0, ex);
-      plan_left_split(nullptr, &qp, S, no, nv, ELt, nvec, ijk, t - t0, 0, 0, ex);
+      plan_left_split(nullptr, &qp, nullptr, S, no, nv, ELt, nvec, ijk, t - t0, 0, 0, ex);
       const double eo_sum = c->eo_h[ijk[0]] + c->eo_h[ijk[1]] + c->eo_h[ijk[2]];
       for (int v = 0; v < nvec; ++v) {
         const int u = v * bj + (t - t0);
@@ -1764,10 +1806,11 @@ int split_left_jacobian(cc3_ctx *c, int nvec, const double *w, const double *L1d
           for (OutD *o : {&J.C, &J.Ct, &J.C2, &J.Ct2})
             if (o->buf == B_OMT) o->off += (long long)v * nt2;
         }
-        plan_left_split(&om, nullptr, S, no, nv, ELt, nvec, ijk, u, (long long)v * ng,
+        plan_left_split(&om, nullptr, &gterms, S, no, nv, ELt, nvec, ijk, u, v,
                         (long long)v * nh, ex);
       }
     }
+    plan_left_g(om, S, no, nv, gterms, ng, ex);
     TRY(s_upload_plan(tb, &pT.v[b], st));
     if (prep) TRY(s_upload_plan(z, &pZ.v[b], st));
     TRY(s_upload_plan(qp, &pQ.v[b], st));
@@ -1823,7 +1866,15 @@ int split_left_jacobian(cc3_ctx *c, int nvec, const double *w, const double *L1d
                              st));
     trace_end(c, TR_SPLIT_ELEM, st, 0.0, 0.0);
     *L += 1;
-    TRY(elem(Wj, TTj, W3j, eoj_all + (size_t)b * nslot, nslot, maxj, exj, vptrj, nslot));
+    // L3 of the batch: one exponent for all its slots (the grouped G jobs)
+    trace_begin(c, TR_SPLIT_ELEM, st);
+    CU(cudaMemsetAsync(maxj, 0, sizeof(unsigned int) * nslot, st));
+    TRY(launch_tau_contravariant_dd(Wj, TTj, W3j, TTj, S->evdd, eoj_all + (size_t)b * nslot, 0.f,
+                                    0.f, nv, nslot, maxj, st));
+    TRY(launch_common_exponent(maxj, exj, nslot, bj, ns, st));
+    TRY(launch_slice_tt(TTj, vptrj, nv, vp, s, exj, nslot, nslot, st));
+    trace_end(c, TR_SPLIT_ELEM, st, 0.0, 0.0);
+    *L += 3;
     TRY(run(pO.v[b], jr, PR, TR_SPLIT_OMEGA));
   }
   int hs = 0;

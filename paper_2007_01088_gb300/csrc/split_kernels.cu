@@ -330,6 +330,27 @@ __global__ void slot_exponent_kernel(const unsigned int *__restrict__ maxbits, i
   ex[i] = e;
 }
 
+// One exponent for every active slot of a batch (slot u active when u % bj <
+// ns): the largest of their maxima, so that the slices of all slots share a
+// scale and contractions over several slots can run as one job.
+__global__ void common_exponent_kernel(const unsigned int *__restrict__ maxbits,
+                                       int *__restrict__ ex, int nslot, int bj, int ns) {
+  __shared__ unsigned int red[256];
+  unsigned int m = 0;
+  for (int i = threadIdx.x; i < nslot; i += blockDim.x)
+    if (i % bj < ns) m = max(m, maxbits[i]);  // non-negative floats order as their bits
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  const float mf = __uint_as_float(red[0]) * (1.0f + 1e-6f);
+  int e = 0;
+  if (mf > 0.f) frexpf(mf, &e);
+  for (int i = threadIdx.x; i < nslot; i += blockDim.x) ex[i] = e;
+}
+
 // Slices of tau~ in the three cyclic layouts used by the residual
 // contractions.  Layout L puts slot L outermost (rows x), then slot L+1 (y),
 // then slot L+2 (z, padded to vp):
@@ -564,6 +585,12 @@ int launch_left_outer_dd(float2 *W1, const int *tri, int bj, int ns, int nslot, 
 }
 int launch_slot_exponent(const unsigned int *maxbits, int *ex, int nslot, cudaStream_t st) {
   slot_exponent_kernel<<<(nslot + 127) / 128, 128, 0, st>>>(maxbits, ex, nslot);
+  return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_FAIL(CC3_ERR_CUDA, "split element-wise kernel launch");
+}
+int launch_common_exponent(const unsigned int *maxbits, int *ex, int nslot, int bj, int ns,
+                           cudaStream_t st) {
+  if (nslot <= 0 || bj < 1) return CC3_OK;
+  common_exponent_kernel<<<1, 256, 0, st>>>(maxbits, ex, nslot, bj, ns);
   return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_FAIL(CC3_ERR_CUDA, "split element-wise kernel launch");
 }
 int launch_slice_tt(const float2 *tt, __nv_bfloat16 *const *v, int nv, int vp, int s,

@@ -35,6 +35,9 @@ int launch_tau_contravariant_dd(const float2 *W1, const float2 *W2, const float2
                                 float w_lo, int nv, int nslot, unsigned int *maxbits,
                                 cudaStream_t st);
 int launch_slot_exponent(const unsigned int *maxbits, int *ex, int nslot, cudaStream_t st);
+// one exponent (that of the largest maximum) for every active slot u (u % bj < ns)
+int launch_common_exponent(const unsigned int *maxbits, int *ex, int nslot, int bj, int ns,
+                           cudaStream_t st);
 // y[e] = x[e] as a double-float pair
 int launch_to_dd(const double *x, float2 *y, long long n, cudaStream_t st);
 // the left transformation's outer products L1 (x) g_ovov + Lt2 (x) F of the L3
