@@ -559,33 +559,32 @@ def jacobian_measure(args, local):
 
 def density_measure(args, local):
     """Triples contributions of Algorithm 3 to the one-electron density of a
-    left state (FP64 path; the split path does not cover it): no=12, nv=120,
-    a seeded left vector at w = 0.25, one warm-up call, `--dsteps` timed calls
-    with inputs and outputs resident on the device."""
+    left state: no=12, nv=120, a seeded left vector normalised like the trial
+    vectors at w = 0.25, one warm-up call and `--dsteps` timed calls per path
+    with inputs and outputs resident on the device.  The FP64 path gives the
+    line's figures; the split (BF16 slice) path is reported beside it with its
+    largest deviation from the FP64 densities."""
     import torch
     import paper_2007_01088_gb300 as g
-    from cc3_inputs import make_inputs
+    from cc3_inputs import make_inputs, make_trial_vectors
     dev = torch.device("cuda", local)
     no, nv = args.density_no, args.density_nv
     inp = make_inputs(no, nv, seed=5)
-    rng = np.random.default_rng(6)
-    L2 = rng.normal(size=(no, no, nv, nv))
-    L2 = 0.5 * (L2 + np.transpose(L2, (1, 0, 3, 2)))
-    L1 = rng.normal(size=(no, nv))
+    L1, L2 = make_trial_vectors(no, nv, 1, seed=6)
     stream = torch.cuda.Stream(device=dev)
-    with torch.cuda.stream(stream):
-        ctx = g.Context(inp, device=True, stream=stream)
-        l1 = torch.from_numpy(L1).to(dev)
-        l2 = torch.from_numpy(L2).to(dev)
+    pk, src = peaks()
+    fp64_peak = pk["bf16_tflops_sustained"] * 1.25 / 2250.0
+
+    def one(ctx, l1, l2, prec):
         ctx.set_tracing(True)
-        ctx.density(l1, l2, 0.25)
+        ctx.density(l1, l2, 0.25, prec=prec)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
         traces, launches = {}, 0
         for _ in range(args.dsteps):
-            doo, dov, dvv = ctx.density(l1, l2, 0.25)
+            out = ctx.density(l1, l2, 0.25, prec=prec)
             launches += ctx.counters()["launches"]
             for k, v in ctx.trace().items():
                 a = traces.setdefault(k, dict(launches=0, ms=0.0, flop=0.0, slice_flop=0.0))
@@ -593,31 +592,43 @@ def density_measure(args, local):
                     a[f] += v[f]
         e1.record(stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.dsteps
-    cnt = ctx.counters()
-    ctx.close()
-    pk, src = peaks()
-    fp64_peak = pk["bf16_tflops_sustained"] * 1.25 / 2250.0
-    kern = per_kernel(traces)
-    eng = kern.get("fp64_engine_kernel", dict(ms=0.0, flop=0.0, launches=0))
-    value = cnt["nominal_flop"] / (ms * 1e-3) / 1e12
-    return {"workload": f"triples density of a left state (Algorithm 3), no={no} nv={nv}, "
-                        "w=0.25, FP64 path, seeded synthetic inputs and left vector",
-            "value": value, "unit": "TFLOP/s", "ms_per_step": ms, "steps": args.dsteps,
-            "nominal_flop_per_step": cnt["nominal_flop"],
-            "executed_flop_per_step": cnt["executed_flop"],
-            "launches_per_step": launches / args.dsteps,
-            "fp64_engine": {"ms_per_step": eng["ms"] / args.dsteps,
+        ms = e0.elapsed_time(e1) / args.dsteps
+        cnt = ctx.counters()
+        kern = per_kernel(traces)
+        r = {"value": cnt["nominal_flop"] / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+             "ms_per_step": ms, "steps": args.dsteps,
+             "nominal_flop_per_step": cnt["nominal_flop"],
+             "executed_flop_per_step": cnt["executed_flop"],
+             "launches_per_step": launches / args.dsteps,
+             "kernels": {k: {"ms_per_step": v["ms"] / args.dsteps,
+                             "launches_per_step": v["launches"] / args.dsteps}
+                         for k, v in kern.items() if v["launches"]}}
+        return r, kern, [x.cpu().numpy() for x in out]
+
+    with torch.cuda.stream(stream):
+        ctx = g.Context(inp, device=True, stream=stream)
+        l1 = torch.from_numpy(L1[0]).to(dev)
+        l2 = torch.from_numpy(L2[0]).to(dev)
+        r, kern, (doo, dov, dvv) = one(ctx, l1, l2, g.CC3_FP64)
+        eng = kern.get("fp64_engine_kernel", dict(ms=0.0, flop=0.0, launches=0))
+        r["fp64_engine"] = {"ms_per_step": eng["ms"] / args.dsteps,
                             "achieved_tflops": eng["flop"] / (eng["ms"] * 1e-3) / 1e12
                             if eng["ms"] else None,
                             "peak_tflops": fp64_peak,
-                            "peak_source": f"{src} bf16 sustained x nominal FP64/BF16 (1.25/2250)"},
-            "kernels": {k: {"ms_per_step": v["ms"] / args.dsteps,
-                            "launches_per_step": v["launches"] / args.dsteps}
-                        for k, v in kern.items() if v["launches"]},
-            "trace_D_vv_plus_trace_D_oo": float(np.trace(dvv.cpu().numpy())
-                                                + np.trace(doo.cpu().numpy())),
-            "trace_D_vv": float(np.trace(dvv.cpu().numpy()))}
+                            "peak_source": f"{src} bf16 sustained x nominal FP64/BF16 (1.25/2250)"}
+        split, _, (soo, sov, svv) = one(ctx, l1, l2, g.CC3_SPLIT_BF16)
+        ctx.close()
+    split["max_abs_dev_from_fp64"] = {
+        "D_oo": float(np.abs(soo - doo).max()), "D_ov": float(np.abs(sov - dov).max()),
+        "D_vv": float(np.abs(svv - dvv).max())}
+    split["max_abs"] = {"D_oo": float(np.abs(doo).max()), "D_ov": float(np.abs(dov).max()),
+                        "D_vv": float(np.abs(dvv).max())}
+    r["workload"] = (f"triples density of a left state (Algorithm 3), no={no} nv={nv}, "
+                     "w=0.25, FP64 path, seeded synthetic inputs and left vector")
+    r["split_bf16"] = split
+    r["trace_D_vv_plus_trace_D_oo"] = float(np.trace(dvv) + np.trace(doo))
+    r["trace_D_vv"] = float(np.trace(dvv))
+    return r
 
 
 def _timed_calls(stream, fn, steps):

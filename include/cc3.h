@@ -189,8 +189,10 @@ int cc3_jacobian_triples(cc3_ctx *ctx, cc3_prec prec, int nvec,
  * for every R with pair-symmetric R2; sigma2 is pair symmetric.
  * L1[n][i][a], L2[n][i][j][a][b], sigma1[n][i][a], sigma2[n][i][j][a][b]; other
  * rules (pointers, frequencies, CC3_ERR_DENOM, symmetric integrals, Cholesky
- * vectors required) as cc3_jacobian_triples.  FP64 path only: CC3_SPLIT_BF16
- * returns CC3_ERR_UNSUPPORTED. */
+ * vectors required) as cc3_jacobian_triples.  CC3_FP64 or CC3_SPLIT_BF16 (the
+ * W build, the contractions of tau3 and L3 and the G, H, Q intermediates on the
+ * tensor cores, sigma1 from them in FP64; CC3_SPLIT_INT8 returns
+ * CC3_ERR_UNSUPPORTED). */
 int cc3_left_jacobian_triples(cc3_ctx *ctx, cc3_prec prec, int nvec, const double *omega,
                               const double *L1, const double *L2, double *sigma1,
                               double *sigma2, void *cuda_stream);
@@ -206,8 +208,12 @@ int cc3_left_jacobian_triples(cc3_ctx *ctx, cc3_prec prec, int nvec, const doubl
  * with tau = -W / eps (Algorithm 1), L3 the covariant amplitudes of
  * cc3_left_jacobian_triples, L3~ their contravariant form and L2~ the
  * back-transform applied to L2; the vo block has no triples term.  The
- * occupied loop runs over the triples i >= j >= k, the D_oo term over
- * Algorithm 3's virtual loop a >= b >= c.  With omega = 0 and the
+ * occupied loop runs over the triples i >= j >= k.  On CC3_FP64 the D_oo term
+ * runs over Algorithm 3's virtual loop a >= b >= c; on CC3_SPLIT_BF16 the
+ * occupied loop's contractions run on the tensor cores and D_oo comes from tau
+ * and L3~ of every triple (i = j = k included) held resident in device memory,
+ * 32 nv^3 bytes per triple (CC3_ERR_OOM when that exceeds half of the free
+ * memory; the FP64 path has no such limit).  With omega = 0 and the
  * ground-state multipliers in place of (L1, L2) the call gives D^{0,0}.
  * L1[no][nv], L2[no][no][nv][nv] (host, or device with CC3_DEVICE_PTRS);
  * outputs D_oo[no][no], D_ov[no][nv], D_vv[nv][nv], overwritten.  Before any
@@ -215,10 +221,10 @@ int cc3_left_jacobian_triples(cc3_ctx *ctx, cc3_prec prec, int nvec, const doubl
  * CC3_ERR_DENOM if omega comes within CC3_DENOM_MIN of any eps^{abc}_{ijk}
  * (i >= j >= k, i = j = k included: the virtual loop divides there too),
  * CC3_ERR_UNSUPPORTED for a context with general (T1-transformed) integrals,
- * a restricted triples list, more than 24 occupied orbitals, deterministic
- * mode or a split precision (FP64 path only).  Cost 10 nv^4 no^3 FLOP to
- * leading order (6 nv^4 per distinct permutation in the occupied loop, 4 nv^4
- * no^3 in the virtual loop). */
+ * a restricted triples list, deterministic mode, CC3_SPLIT_INT8, or more than
+ * 24 occupied orbitals on CC3_FP64.  Cost 10 nv^4 no^3 FLOP to leading order
+ * (6 nv^4 per distinct permutation in the occupied loop, 4 nv^4 no^3 in the
+ * virtual loop; the counters report this count on both paths). */
 int cc3_density_triples(cc3_ctx *ctx, cc3_prec prec, double omega, const double *L1,
                         const double *L2, double *D_oo, double *D_ov, double *D_vv,
                         void *cuda_stream);

@@ -220,6 +220,12 @@ int left_l3_batch(cc3_ctx *c, const PtrTable &pt, int t0, int t1, double w, cons
                   const double *ltd, int *tri, double *wsW, double *wsT, cudaStream_t s);
 int left_finish(cc3_ctx *c, const PtrTable &pt, const double *s2raw, double *s2d,
                 cudaStream_t s);
+// the densities' FP64 pieces shared by both paths (density.cu): the end of the
+// occupied loop (pt: B_DY = Y, B_DOV = Dov, B_T2), and Doo from tau and L~ of
+// every triple of tri (3 ints each, sorted i >= j >= k) held resident
+int density_tail(cc3_ctx *c, const PtrTable &pt, double *Dvv, cudaStream_t s);
+int density_doo_resident(cc3_ctx *c, const float2 *tau_all, const float2 *lt_all,
+                         const std::vector<int> &tri, double *Doo, cudaStream_t s);
 
 // smallest |w - eps^{abc}_{ijk}| over every (a, b, c) and the ntri triples
 // ijk (host arrays; ntri = 0: the full loop); api.cu

@@ -39,6 +39,7 @@
 #include <vector>
 
 #include "cc3_internal.h"
+#include "split.h"
 
 namespace cc3 {
 namespace {
@@ -374,25 +375,174 @@ int density_fp64(cc3_ctx *c, double w, const double *L1d, const double *L2d, dou
     TRY(jac_run_plan(c, pv, 0, pt, s));
     TRY(jac_run_plan(c, pq, 1, pt, s));
   }
-  {  // Dov[l][d] -= sum_{k,i,c} Y[l][k][i][c] t[k][i][c][d]
-    Plan pf;
-    const int jb = new_job(pf, 0, no, nv, nv, 1, 1, EPI_ATOMIC);
-    add_term(pf, jb, op(B_DY, 0, (long long)no * no * nv, 1, 0, 1), op(B_T2, 0, 1, nv),
-             no * no * nv);
-    const OutD o = out(B_DOV, 0, nv, 1);
-    pf.jobs[jb].C = o;
-    pf.jobs[jb].Ct = o;
-    TRY(jac_run_plan(c, pf, 0, pt, s));
-  }
-  scale_kernel<<<grid_for(nv2), 256, 0, s>>>(Dvv, nv2, 0.5);
-  CU(cudaGetLastError());
-  c->counters.launches++;
+  TRY(density_tail(c, pt, Dvv, s));
   TRY(density_virtual(c, pt, w, L1d, lt, Doo, s));
   CU(cudaStreamSynchronize(s));
   return CC3_OK;
 }
 
+// C[k][l] += wgt_ij sum_e X_k(e) Y_l(e) over the pairs i >= j (blockIdx.y), with
+// X_k the view (i,j,k) of L~ and Y_l the view (i,j,l) of tau, e = (a,b,c) the
+// virtual triple of the view.  tab[((y*2 + h)*no + k)*4 + {0..3}] = {T, s0, s1,
+// s2}: the stored tensor T ([a][b][c] double-float, T < 0: a zero row) and the
+// strides of the view's three slots in it.  Per chunk of DOO_E values of e the
+// block stages the 2 no rows as doubles in shared memory (a padded row stride),
+// then each thread accumulates up to 4 of the no^2 products (blockIdx.z selects
+// the group of 1024 products).
+constexpr int DOO_E = 128, DOO_LD = DOO_E + 1;
+__global__ void __launch_bounds__(256)
+    doo_pairs_kernel(const float2 *__restrict__ lt_all, const float2 *__restrict__ tau_all,
+                     const long long *__restrict__ tab, const double *__restrict__ wgt, int no,
+                     int nv, double *__restrict__ C) {
+  extern __shared__ double sm[];  // [2][no][DOO_LD]
+  const long long nv2 = (long long)nv * nv, nv3 = nv2 * nv;
+  const long long *tb = tab + (long long)blockIdx.y * 2 * no * 4;
+  const int t = threadIdx.x, e0 = t % DOO_E, h = t / DOO_E;  // h: 0 = L~, 1 = tau
+  const float2 *X = h ? tau_all : lt_all;
+  const int nprod = no * no, pbase = blockIdx.z * 1024;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const long long nchunk = (nv3 + DOO_E - 1) / DOO_E;
+  for (long long ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
+    const long long e = ch * DOO_E + e0;
+    const bool in = e < nv3;
+    const long long v0 = in ? e / nv2 : 0, v1 = in ? (e / nv) % nv : 0, v2 = in ? e % nv : 0;
+    __syncthreads();  // the previous chunk's products are done
+    for (int k = 0; k < no; ++k) {
+      const long long *r = tb + ((long long)h * no + k) * 4;
+      double x = 0.0;
+      if (in && r[0] >= 0) {
+        const float2 f = X[r[0] * nv3 + v0 * r[1] + v1 * r[2] + v2 * r[3]];
+        x = (double)f.x + (double)f.y;
+      }
+      sm[(h * no + k) * DOO_LD + e0] = x;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int p = pbase + t + 256 * q;
+      if (p < nprod) {
+        const double *xa = sm + (p / no) * DOO_LD, *yb = sm + (no + p % no) * DOO_LD;
+        double a = acc[q];
+        for (int u = 0; u < DOO_E; ++u) a = fma(xa[u], yb[u], a);
+        acc[q] = a;
+      }
+    }
+  }
+  const double w = wgt[blockIdx.y];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int p = pbase + t + 256 * q;
+    if (p < nprod) atomicAdd(C + p, w * acc[q]);
+  }
+}
+
 }  // namespace
+
+// Dov[l][d] -= sum_{k,i,c} Y[l][k][i][c] t[k][i][c][d] (pt: B_DY = Y, B_DOV = Dov),
+// then Dvv *= 1/2: the end of the occupied loop, on both paths
+int density_tail(cc3_ctx *c, const PtrTable &pt, double *Dvv, cudaStream_t s) {
+  const int no = c->no, nv = c->nv;
+  const long long nv2 = (long long)nv * nv;
+  Plan pf;
+  // K = no^2 nv over few tiles: split K across CTAs
+  const int ks = std::max(1, std::min(128, no * no * nv / 512));
+  const int jb = new_job(pf, 0, no, nv, nv, 1, ks, EPI_ATOMIC);
+  add_term(pf, jb, op(B_DY, 0, (long long)no * no * nv, 1, 0, 1), op(B_T2, 0, 1, nv),
+           no * no * nv);
+  const OutD o = out(B_DOV, 0, nv, 1);
+  pf.jobs[jb].C = o;
+  pf.jobs[jb].Ct = o;
+  TRY(jac_run_plan(c, pf, 0, pt, s));
+  scale_kernel<<<grid_for(nv2), 256, 0, s>>>(Dvv, nv2, 0.5);
+  CU(cudaGetLastError());
+  c->counters.launches++;
+  return CC3_OK;
+}
+
+// Doo[l][k] = -1/2 sum_{ij} sum_{abc} L~^{abc}_{ijk} tau^{abc}_{ijl} from tau and L~ of
+// every triple held resident (tau_all, lt_all: [T][a][b][c] double-float, T the
+// index in tri of the sorted triple; L~ is zero where i = j = k).  Both tensors are
+// symmetric under a simultaneous permutation of occupied and virtual indices, so
+// the pair (j, i) gives the same sum over (a,b,c) as (i, j): the pairs i > j count
+// twice, i = j once, and one launch covers them all.
+int density_doo_resident(cc3_ctx *c, const float2 *tau_all, const float2 *lt_all,
+                         const std::vector<int> &tri, double *Doo, cudaStream_t s) {
+  const int no = c->no, nv = c->nv;
+  const long long nv2 = (long long)nv * nv;
+  const int nt = (int)tri.size() / 3;
+  std::vector<int> where((size_t)no * no * no, -1);  // sorted triple -> index in tri
+  for (int t = 0; t < nt; ++t)
+    where[((size_t)tri[3 * t] * no + tri[3 * t + 1]) * no + tri[3 * t + 2]] = t;
+  // row of the view (p,q,r): {T, strides of the view's slots in T's storage}
+  auto row = [&](int p, int q, int r, bool zero, long long *o) {
+    o[0] = -1;
+    o[1] = o[2] = o[3] = 0;
+    if (zero) return;
+    int x[3] = {p, q, r};
+    std::sort(x, x + 3, [](int u, int v) { return u > v; });
+    const int T = where[((size_t)x[0] * no + x[1]) * no + x[2]];
+    if (T < 0) return;
+    const long long str[3] = {nv2, nv, 1};
+    for (int u = 0; u < 6; ++u) {
+      const int *m = PERM6[u];
+      const int *tt = &tri[3 * T];
+      if (tt[m[0]] == p && tt[m[1]] == q && tt[m[2]] == r) {
+        o[0] = T;
+        o[1] = str[m[0]];
+        o[2] = str[m[1]];
+        o[3] = str[m[2]];
+        return;
+      }
+    }
+  };
+  const int npair = no * (no + 1) / 2;
+  std::vector<long long> tab((size_t)npair * 2 * no * 4);
+  std::vector<double> wgt(npair);
+  int y = 0;
+  for (int i = 0; i < no; ++i)
+    for (int j = 0; j <= i; ++j, ++y) {
+      wgt[y] = i == j ? 1.0 : 2.0;
+      for (int k = 0; k < no; ++k) {
+        row(i, j, k, i == j && j == k, &tab[(((size_t)y * 2 + 0) * no + k) * 4]);
+        row(i, j, k, false, &tab[(((size_t)y * 2 + 1) * no + k) * 4]);
+      }
+    }
+  Bufs B;
+  double *C = nullptr, *dw = nullptr;
+  long long *dtab = nullptr;
+  TRY(B.get(&C, (size_t)no * no));
+  TRY(B.get(&dw, (size_t)npair));
+  TRY(B.get(&dtab, tab.size()));
+  TRY(launch_zero(C, (size_t)no * no, s));
+  CU(cudaMemcpyAsync(dtab, tab.data(), sizeof(long long) * tab.size(), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(dw, wgt.data(), sizeof(double) * npair, cudaMemcpyHostToDevice, s));
+  const size_t smem = sizeof(double) * 2 * no * DOO_LD;
+  if (smem > 227 * 1024) return CC3_FAIL(CC3_ERR_UNSUPPORTED, "too many occupied orbitals");
+  CU(cudaFuncSetAttribute(doo_pairs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)smem));
+  const long long nchunk = (nv2 * nv + DOO_E - 1) / DOO_E;
+  int dev = 0, nsm = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int gz = (no * no + 1023) / 1024;
+  const long long gx = std::max<long long>(
+      1, std::min<long long>(nchunk, (4LL * nsm + (long long)npair * gz - 1) / ((long long)npair * gz)));
+  trace_begin(c, TR_FP64_ELEM, s);
+  doo_pairs_kernel<<<dim3((unsigned)gx, npair, gz), 256, smem, s>>>(lt_all, tau_all, dtab, dw, no,
+                                                                     nv, C);
+  CU(cudaGetLastError());
+  trace_end(c, TR_FP64_ELEM, s, 2.0 * no * no * (double)npair * nv2 * nv, 0.0);
+  c->counters.launches++;
+  // Doo[l][k] = -1/2 C[k][l]
+  std::vector<double> hc((size_t)no * no), hd((size_t)no * no);
+  CU(cudaMemcpyAsync(hc.data(), C, sizeof(double) * no * no, cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  for (int k = 0; k < no; ++k)
+    for (int l = 0; l < no; ++l) hd[(size_t)l * no + k] = -0.5 * hc[(size_t)k * no + l];
+  CU(cudaMemcpyAsync(Doo, hd.data(), sizeof(double) * no * no, cudaMemcpyHostToDevice, s));
+  CU(cudaStreamSynchronize(s));
+  return CC3_OK;
+}
 }  // namespace cc3
 
 extern "C" int cc3_density_triples(cc3_ctx *c, cc3_prec prec, double omega, const double *L1,
@@ -402,13 +552,12 @@ extern "C" int cc3_density_triples(cc3_ctx *c, cc3_prec prec, double omega, cons
   if (!c || !L1 || !L2 || !D_oo || !D_ov || !D_vv) return CC3_ERR_ARG;
   if (c->general)
     return CC3_FAIL(CC3_ERR_UNSUPPORTED, "the densities need symmetric integrals");
-  if (prec == CC3_SPLIT_INT8 || prec == CC3_SPLIT_BF16)
-    return CC3_FAIL(CC3_ERR_UNSUPPORTED, "the densities run on the FP64 path");
-  if (prec != CC3_FP64) return CC3_ERR_ARG;
+  if (prec == CC3_SPLIT_INT8) return CC3_FAIL(CC3_ERR_UNSUPPORTED, "no INT8 slice path");
+  if (prec != CC3_FP64 && prec != CC3_SPLIT_BF16) return CC3_ERR_ARG;
   if (c->flags & CC3_DETERMINISTIC)
     return CC3_FAIL(CC3_ERR_UNSUPPORTED, "deterministic reductions cover the residual only");
-  if (c->no > DV_MAX_NO)
-    return CC3_FAIL(CC3_ERR_UNSUPPORTED, "the densities take at most 24 occupied orbitals");
+  if (prec == CC3_FP64 && c->no > DV_MAX_NO)
+    return CC3_FAIL(CC3_ERR_UNSUPPORTED, "the FP64 densities take at most 24 occupied orbitals");
   if (!std::isfinite(omega)) return CC3_FAIL(CC3_ERR_ARG, "non-finite frequency");
   const int no = c->no, nv = c->nv;
   std::lock_guard<std::mutex> lk(c->mu);
@@ -463,7 +612,9 @@ extern "C" int cc3_density_triples(cc3_ctx *c, cc3_prec prec, double omega, cons
          cudaMemcpyAsync(dL2, L2, sizeof(double) * nt2, cudaMemcpyHostToDevice, s) != cudaSuccess))
       rc = CC3_FAIL(CC3_ERR_CUDA, "density upload");
   }
-  if (rc == CC3_OK) rc = density_fp64(c, omega, dL1, dL2, doo, dov, dvv, s);
+  if (rc == CC3_OK)
+    rc = prec == CC3_SPLIT_BF16 ? split_density(c, omega, dL1, dL2, doo, dov, dvv, s)
+                                : density_fp64(c, omega, dL1, dL2, doo, dov, dvv, s);
   if (rc == CC3_OK && !dev) {
     if (cudaMemcpyAsync(D_oo, doo, sizeof(double) * noo, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(D_ov, dov, sizeof(double) * n1, cudaMemcpyDeviceToHost, s) != cudaSuccess ||

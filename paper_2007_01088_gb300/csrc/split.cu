@@ -88,6 +88,9 @@ enum MapId {
   // left transformation: t2 as [(p,q)][d][x] (G), as [p][l][(u,w)] in both K
   // orders (H), and Lt2 of every vector as [(p,q)][v][(u,w)] in both orders (Q)
   ML_T2T, ML_T2ZA, ML_T2ZB, ML_LQA, ML_LQB,
+  // densities: t2 as [q][l][(u,w)] in both K orders (Y), and tau itself in the
+  // rows-x views of the three cyclic layouts (D_vv)
+  MD_T2YA, MD_T2YB, MD_TAU0, MD_TAU1, MD_TAU2,
   MAP_COUNT
 };
 static_assert((int)MAP_COUNT <= (int)SMAX_MAPS, "map table");
@@ -1901,6 +1904,312 @@ int split_left_jacobian(cc3_ctx *c, int nvec, const double *w, const double *L1d
   }
   CU(cudaStreamSynchronize(st));
   c->counters.executed_flop += ex + ex_tau;
+  c->counters.slices = s;
+  return CC3_OK;
+}
+
+// ---- densities (Algorithm 3) on the tensor cores -----------------------------------
+namespace {
+
+// Y and D_vv jobs of one triple in slot u (L~ in the L3 layouts, tau in MD_TAU*):
+//   Y[l][r][p][c] += sum_ab L~[a][b][c] t[l][q][a][b]   rows c of layout m2, K = (zb, u, zz)
+//   Dvv[c][d]     += sum_ab L~[a][b][c] tau[a][b][d]    rows c of L~'s and d of tau's layout m2
+void plan_density_split(SPlan &py, SPlan &pv, SplitState *S, int no, int nv, const int ijk[3],
+                        int u, double &ex) {
+  static const int PERM6[6][3] = {{0, 1, 2}, {1, 0, 2}, {2, 1, 0},
+                                  {0, 2, 1}, {1, 2, 0}, {2, 0, 1}};
+  const int s = S->s, vp = S->vp;
+  int seen[6][3], nseen = 0;
+  if (ijk[0] == ijk[1] && ijk[1] == ijk[2]) return;
+  for (int w = 0; w < 6; ++w) {
+    const int *m = PERM6[w];
+    const int p = ijk[m[0]], q = ijk[m[1]], r = ijk[m[2]];
+    bool dup = false;
+    for (int x = 0; x < nseen; ++x)
+      if (seen[x][0] == p && seen[x][1] == q && seen[x][2] == r) dup = true;
+    if (dup) continue;
+    seen[nseen][0] = p;
+    seen[nseen][1] = q;
+    seen[nseen][2] = r;
+    ++nseen;
+    const int Lz = m[2];
+    const bool yz = (m[0] == (Lz + 1) % 3);  // K = (a, b) or (b, a)
+    int jb = new_sjob(py, nv, no, ntile_for(no), 1, S->ks4, SEPI_F64_ATOMIC, S->Et - 14, ex, s);
+    SJob &J = py.jobs[jb];
+    J.expo_slot = u;
+    J.C = outd(B_DY, ((long long)r * no + p) * nv, 1, (long long)no * no * nv);
+    J.Ct = J.C;
+    add_sterm(py, jb, opd(MA_V0 + Lz, u), opd(yz ? MD_T2YA : MD_T2YB, q), nv * vp, 0, ex, s);
+    jb = new_sjob(pv, nv, nv, ntile_for(nv), 1, S->ks4, SEPI_F64_ATOMIC, -14, ex, s);
+    SJob &K = pv.jobs[jb];
+    K.expo_slot = u;  // in the array of summed exponents of L~ and tau
+    K.C = outd(B_DVV, 0, nv, 1);
+    K.Ct = K.C;
+    add_sterm(pv, jb, opd(MA_V0 + Lz, u), opd(MD_TAU0 + Lz, u), nv * vp, 0, ex, s);
+  }
+}
+
+}  // namespace
+
+// Algorithm 3 on the tensor cores.  The occupied loop runs over the triples
+// i >= j >= k and also i = j = k (tau there enters Doo): per batch tau3 (the
+// residual's W build; the element-wise step also writes tau itself), the
+// slices of tau, the Q jobs of the ov block, the L3 of the left state (as in
+// the left transformation, one slice exponent for the batch), and the Y and
+// D_vv jobs.  tau and L~3 of every triple stay resident (double-float), and
+// Doo follows from them pair by pair (density_doo_resident) instead of the
+// virtual loop; the calls that do not fit in memory return CC3_ERR_OOM.
+int split_density(cc3_ctx *c, double w, const double *L1d, const double *L2d, double *Doo,
+                  double *Dov, double *Dvv, cudaStream_t st) {
+  SplitState *S = nullptr;
+  TRY(split_ready(c, &S, st));
+  const int no = c->no, nv = c->nv, s = S->s, vp = S->vp, op = S->op;
+  const long long nv2 = (long long)nv * nv, nv3 = nv2 * nv, oo = (long long)no * no;
+  const long long onv = (long long)no * nv;
+  const size_t n1 = (size_t)no * nv, nt2 = n1 * no * nv;
+  // the triples with i = j = k appended to the context's full list
+  std::vector<int> ext(c->tri_host.begin(), c->tri_host.begin() + 3 * c->ntri);
+  for (int i = 0; i < no; ++i) {
+    ext.push_back(i);
+    ext.push_back(i);
+    ext.push_back(i);
+  }
+  const int next = (int)ext.size() / 3;
+  JacBufs B;
+  float2 *tau_all = nullptr, *lt_all = nullptr;
+  {
+    const size_t need = 2 * (size_t)next * (size_t)nv3 * sizeof(float2);
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    if (need > free_b / 2)
+      return CC3_FAIL(CC3_ERR_OOM, "split densities: tau and L3 of every triple do not fit");
+  }
+  TRY(B.get(&tau_all, (size_t)next * nv3));
+  TRY(B.get(&lt_all, (size_t)next * nv3));
+  double *lt = nullptr, *Y = nullptr;
+  float2 *l1dd = nullptr, *ltdd = nullptr, *ovdd = nullptr, *fdd = nullptr, *eo_ext = nullptr;
+  int *tri_ext = nullptr;
+  TRY(B.get(&lt, nt2));
+  TRY(B.get(&Y, (size_t)(oo * no * nv)));
+  TRY(B.get(&l1dd, n1));
+  TRY(B.get(&ltdd, nt2));
+  TRY(B.get(&ovdd, (size_t)(oo * nv2)));
+  TRY(B.get(&fdd, n1));
+  TRY(B.get(&eo_ext, (size_t)next));
+  TRY(B.get(&tri_ext, 3 * (size_t)next));
+  CU(cudaMemcpyAsync(tri_ext, ext.data(), sizeof(int) * ext.size(), cudaMemcpyHostToDevice, st));
+  {
+    std::vector<float2> h(next);
+    for (int t = 0; t < next; ++t) {
+      const dd::df e = dd::from_double_host(c->eo_h[ext[3 * t]] + c->eo_h[ext[3 * t + 1]] +
+                                            c->eo_h[ext[3 * t + 2]]);
+      h[t] = make_float2(e.hi, e.lo);
+    }
+    CU(cudaMemcpyAsync(eo_ext, h.data(), sizeof(float2) * next, cudaMemcpyHostToDevice, st));
+    CU(cudaStreamSynchronize(st));
+  }
+  TRY(launch_zero(Doo, (size_t)oo, st));
+  TRY(launch_zero(Dov, n1, st));
+  TRY(launch_zero(Dvv, (size_t)nv2, st));
+  TRY(launch_zero(Y, (size_t)(oo * no * nv), st));
+  TRY(launch_back_transform(L2d, lt, no, nv, st));
+  TRY(launch_to_dd(L1d, l1dd, (long long)n1, st));
+  TRY(launch_to_dd(lt, ltdd, (long long)nt2, st));
+  TRY(launch_to_dd(c->ovov, ovdd, oo * nv2, st));
+  TRY(launch_to_dd(c->F_ov, fdd, (long long)n1, st));
+  int ELt = 0;
+  {
+    unsigned long long *mx = nullptr;
+    TRY(B.get(&mx, 1));
+    CU(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), st));
+    TRY(launch_maxabs(lt, (long long)nt2, mx, st));
+    unsigned long long hb = 0;
+    CU(cudaMemcpyAsync(&hb, mx, sizeof(hb), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    double x;
+    std::memcpy(&x, &hb, 8);
+    ELt = x > 0.0 ? exponent_of(x) : 0;
+  }
+  auto sliced = [&](__nv_bfloat16 **dst, const double *src, long long rows, int Kp, int E,
+                    const Gather &g, int rps) -> int {
+    const size_t n = arr_elems(Kp, rps, rows / rps, s);
+    TRY(B.get(dst, n));
+    CU(cudaMemsetAsync(*dst, 0, n * sizeof(__nv_bfloat16), st));
+    return launch_slice_gather(src, *dst, s, E, g, rows, Kp, rps, st);
+  };
+  SArrTable jr = S->arrs, aq = S->arrs;
+  {
+    __nv_bfloat16 *tya = nullptr, *tyb = nullptr, *lqa = nullptr, *lqb = nullptr;
+    Gather g;
+    // t2 for Y: [q][l][(u,w)] = t[l][q][u][w] (YA) or t[l][q][w][u] (YB)
+    g = {0, 0, nv2, (long long)no * nv2, nv, 1, no, no, nv, nv, nv, 1};
+    TRY(sliced(&tya, c->t2, oo, nv * vp, S->Et, g, no));
+    g = {0, 0, nv2, (long long)no * nv2, 1, nv, no, no, nv, nv, nv, 1};
+    TRY(sliced(&tyb, c->t2, oo, nv * vp, S->Et, g, no));
+    // Lt2 for Q (one vector): rows 0 of slab (p,q)
+    g = {0, nv2, 0, 0, nv, 1, 1, 1, nv, nv, nv, 1};
+    TRY(sliced(&lqa, lt, oo, nv * vp, ELt, g, 1));
+    g = {0, nv2, 0, 0, 1, nv, 1, 1, nv, nv, nv, 1};
+    TRY(sliced(&lqb, lt, oo, nv * vp, ELt, g, 1));
+    jr.a[MD_T2YA] = make_arr(tya, (long long)nv * vp, no, no, s);
+    jr.a[MD_T2YB] = make_arr(tyb, (long long)nv * vp, no, no, s);
+    aq.a[ML_LQA] = make_arr(lqa, (long long)nv * vp, 1, oo, s);
+    aq.a[ML_LQB] = make_arr(lqb, (long long)nv * vp, 1, oo, s);
+  }
+  // Lt2 in the t2 roles of the W build
+  {
+    struct Kind {
+      int map;
+      long long K, rps, slabs;
+    };
+    const Kind kinds[3] = {{MJ_R2S, vp, nv, oo}, {MJ_R2C, op, nv, onv}, {MJ_R2R, op, nv, onv}};
+    const Gather gs[3] = {{0, (long long)no * nv2, nv2, nv, 0, 1, no, nv, vp, nv, 1, 0},
+                          {0, (long long)no * nv2, 1, nv, 0, nv2, nv, nv, op, no, 1, 0},
+                          {0, (long long)no * nv2, nv, 1, 0, nv2, nv, nv, op, no, 1, 0}};
+    for (int i = 0; i < 3; ++i) {
+      __nv_bfloat16 *a = nullptr;
+      TRY(sliced(&a, lt, kinds[i].slabs * kinds[i].rps, (int)kinds[i].K, ELt, gs[i],
+                 (int)kinds[i].rps));
+      jr.a[kinds[i].map] = make_arr(a, kinds[i].K, kinds[i].rps, kinds[i].slabs, s);
+    }
+  }
+  // per batch: L3 slots (the residual's batch size), the slices of L~ and of tau
+  const int bj = S->batch;
+  float2 *Wj = nullptr, *TTj = nullptr, *W3j = nullptr, *eol = nullptr;
+  __nv_bfloat16 *Vj[3] = {nullptr, nullptr, nullptr}, *Vt[3] = {nullptr, nullptr, nullptr};
+  __nv_bfloat16 **vptrj = nullptr, **vptrt = nullptr;
+  unsigned int *maxj = nullptr, *maxt = nullptr;
+  int *exj = nullptr, *ext_ = nullptr, *exs = nullptr;
+  TRY(B.get(&Wj, (size_t)bj * nv3));
+  TRY(B.get(&TTj, (size_t)bj * nv3));
+  TRY(B.get(&W3j, (size_t)bj * nv3));
+  TRY(B.get(&eol, (size_t)next));
+  TRY(B.get(&maxj, (size_t)bj));
+  TRY(B.get(&maxt, (size_t)bj));
+  TRY(B.get(&exj, (size_t)bj));
+  TRY(B.get(&ext_, (size_t)bj));
+  TRY(B.get(&exs, (size_t)bj));
+  TRY(B.get(&vptrj, 3));
+  TRY(B.get(&vptrt, 3));
+  const long long nv8 = (nv + 7) / 8 * 8;
+  for (int L = 0; L < 3; ++L) {
+    const size_t n4 = arr_elems((long long)nv * vp, nv, bj, s);
+    TRY(B.get(&Vj[L], n4));
+    TRY(B.get(&Vt[L], n4));
+    CU(cudaMemsetAsync(Vj[L], 0, n4 * sizeof(__nv_bfloat16), st));
+    CU(cudaMemsetAsync(Vt[L], 0, n4 * sizeof(__nv_bfloat16), st));
+    jr.a[MA_V0 + L] = make_arr(Vj[L], (long long)nv * vp, nv, bj, s);
+    jr.a[MA_V0K + L] = make_arr(Vj[L], vp, (long long)nv * nv8, bj, s);
+    jr.a[MD_TAU0 + L] = make_arr(Vt[L], (long long)nv * vp, nv, bj, s);
+  }
+  CU(cudaMemcpyAsync(vptrj, Vj, sizeof(Vj), cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(vptrt, Vt, sizeof(Vt), cudaMemcpyHostToDevice, st));
+  {
+    std::vector<float2> h(next);
+    for (int t = 0; t < next; ++t) {
+      const dd::df e = dd::from_double_host(c->eo_h[ext[3 * t]] + c->eo_h[ext[3 * t + 1]] +
+                                            c->eo_h[ext[3 * t + 2]] + w);
+      h[t] = make_float2(e.hi, e.lo);
+    }
+    CU(cudaMemcpyAsync(eol, h.data(), sizeof(float2) * next, cudaMemcpyHostToDevice, st));
+    CU(cudaStreamSynchronize(st));
+  }
+  const int rows = (nv + 7) / 8 * 8;
+  const int Ec = ELt + S->Eg;
+  VPtrTable P;
+  fill_vptrs(c, S, &P);
+  P.p[B_Q] = Dov;
+  VPtrTable PR = P;
+  PR.p[B_WS_W] = Wj;
+  PR.p[B_WS_TT] = TTj;
+  PR.p[B_WS_W3] = W3j;
+  PR.p[B_SLOTEXP] = exj;
+  PR.p[B_DY] = Y;
+  VPtrTable PV = PR;
+  PV.p[B_SLOTEXP] = exs;
+  PV.p[B_DVV] = Dvv;
+  const int kd = S_DRAIN_STEPS;
+  long long *Lc = &c->counters.launches;
+  double ex = 0.0;
+  auto run = [&](const SPlan &p, const SArrTable &a, const VPtrTable &pt, int cls) -> int {
+    if (p.jobs.empty()) return CC3_OK;
+    SDevPlan d;
+    TRY(s_upload_plan(p, &d, st));
+    trace_begin(c, cls, st);
+    const int rc = s_launch_plan(d, a, pt, s, kd, S->status, st, Lc);
+    trace_end(c, cls, st, d.flop, d.slice_flop);
+    CU(cudaStreamSynchronize(st));  // the tables are freed next
+    s_free_plan(&d);
+    return rc;
+  };
+  for (int t0 = 0; t0 < next; t0 += bj) {
+    const int t1 = std::min(next, t0 + bj), ns = t1 - t0;
+    SPlan tb, qp, ab, py, pv;
+    for (int t = t0; t < t1; ++t) {
+      const int *ijk = &ext[3 * t];
+      plan_w_split(tb, S, no, nv, ijk, t - t0, ex);
+      plan_left_split(nullptr, &qp, nullptr, S, no, nv, ELt, 1, ijk, t - t0, 0, 0, ex);
+      WMaps set1 = {MJ_R2S, MJ_R2S, MJ_R2C, MJ_R2C, MJ_R2R, MJ_R2R,
+                    MA_XS,  MB_XS,  MA_YS,  MB_YS,  MA_OS,  MB_OS};
+      const int u = t - t0;
+      const int j1 = w_job(ab, nv, rows, S->Nab, 1, u, Ec - 14, ex, s);
+      w_terms_1(ab, j1, set1, no, nv, rows, vp, op, ijk, ex, s);
+      const int j2 = w_job(ab, nv, rows, S->Nab, 2, u, Ec - 14, ex, s);
+      w_terms_2(ab, j2, set1, no, nv, rows, vp, op, ijk, ex, s);
+      const int j3 = w_job(ab, nv, rows, S->Nab, 3, u, Ec - 14, ex, s);
+      w_terms_3(ab, j3, set1, no, nv, rows, vp, op, ijk, ex, s);
+      plan_density_split(py, pv, S, no, nv, ijk, u, ex);
+    }
+    // tau: W build, then tau (resident) and tau~ with its slices
+    TRY(run(tb, S->arrs, P, TR_SPLIT_W));
+    trace_begin(c, TR_SPLIT_ELEM, st);
+    CU(cudaMemsetAsync(S->maxbits, 0, sizeof(unsigned int) * ns, st));
+    TRY(launch_tau_contravariant_dd(S->Wdd, S->TTdd, S->W3dd, S->TTdd, S->evdd, eo_ext + t0, 0.f,
+                                    0.f, nv, ns, S->maxbits, st, tau_all + (size_t)t0 * nv3));
+    TRY(launch_slot_exponent(S->maxbits, S->slot_ex, ns, st));
+    TRY(launch_slice_tt(S->TTdd, S->vptr, nv, vp, s, S->slot_ex, ns, S->batch, st));
+    // the slices of tau itself, one exponent for the batch
+    CU(cudaMemsetAsync(maxt, 0, sizeof(unsigned int) * bj, st));
+    TRY(launch_slot_maxabs_dd(tau_all + (size_t)t0 * nv3, nv3, ns, maxt, st));
+    TRY(launch_common_exponent(maxt, ext_, bj, bj, ns, st));
+    TRY(launch_slice_tt(tau_all + (size_t)t0 * nv3, vptrt, nv, vp, s, ext_, ns, bj, st));
+    trace_end(c, TR_SPLIT_ELEM, st, 0.0, 0.0);
+    *Lc += 7;
+    TRY(run(qp, aq, P, TR_SPLIT_OMEGA));
+    // L3 of the left state: W-build bracket, outer products, (w - eps), L~ (one
+    // exponent for the batch) with its slices, kept resident
+    TRY(run(ab, jr, PR, TR_SPLIT_W));
+    trace_begin(c, TR_SPLIT_ELEM, st);
+    TRY(launch_left_outer_dd(Wj, tri_ext + 3 * t0, bj, ns, ns, l1dd, ltdd, ovdd, fdd, no, nv, st));
+    CU(cudaMemsetAsync(maxj, 0, sizeof(unsigned int) * bj, st));
+    TRY(launch_tau_contravariant_dd(Wj, TTj, W3j, TTj, S->evdd, eol + t0, 0.f, 0.f, nv, ns, maxj,
+                                    st));
+    TRY(launch_common_exponent(maxj, exj, bj, bj, ns, st));
+    TRY(launch_slice_tt(TTj, vptrj, nv, vp, s, exj, ns, bj, st));
+    CU(cudaMemcpyAsync(lt_all + (size_t)t0 * nv3, TTj, sizeof(float2) * (size_t)ns * nv3,
+                       cudaMemcpyDeviceToDevice, st));
+    TRY(launch_add_int(exj, ext_, exs, bj, st));
+    trace_end(c, TR_SPLIT_ELEM, st, 0.0, 0.0);
+    *Lc += 6;
+    TRY(run(py, jr, PR, TR_SPLIT_OMEGA));
+    TRY(run(pv, jr, PV, TR_SPLIT_OMEGA));
+  }
+  int hs = 0;
+  CU(cudaMemcpyAsync(&hs, S->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  if (hs != 0) {
+    cudaMemsetAsync(S->status, 0, sizeof(int), st);
+    return hs == 2 ? CC3_FAIL(CC3_ERR_ARG, "a density plan addressed outside a slice array")
+                   : CC3_FAIL(CC3_ERR_TIMEOUT, "split engine wait gave up");
+  }
+  // the end of the occupied loop and Doo, in FP64
+  PtrTable pt;
+  jac_fill_ptrs(c, &pt);
+  pt.p[B_DY] = Y;
+  pt.p[B_DOV] = Dov;
+  TRY(density_tail(c, pt, Dvv, st));
+  TRY(density_doo_resident(c, tau_all, lt_all, ext, Doo, st));
+  c->counters.executed_flop += ex;
   c->counters.slices = s;
   return CC3_OK;
 }

@@ -11,6 +11,9 @@ size_t split_footprint(int no, int nv, int slices, int ntri);
 int split_jacobian(cc3_ctx *c, int nvec, const double *w, const double *R1, const double *R2,
                    double *rho1, double *rho2, cudaStream_t s);
 size_t split_jacobian_footprint(int no, int nv, int slices, int nvec);
+// Algorithm 3's densities of one left state (device pointers)
+int split_density(cc3_ctx *c, double w, const double *L1, const double *L2, double *Doo,
+                  double *Dov, double *Dvv, cudaStream_t s);
 // left (transpose) Jacobian transformation of nvec left vectors (device pointers)
 int split_left_jacobian(cc3_ctx *c, int nvec, const double *w, const double *L1,
                         const double *L2, double *sigma1, double *sigma2, cudaStream_t s);

@@ -6,7 +6,7 @@
 
 namespace cc3 {
 
-enum { SMAX_MAPS = 40, S_BM = 128, S_BK = 16, S_STAGES_MAX = 6, S_MAX_SLICES = 7,
+enum { SMAX_MAPS = 48, S_BM = 128, S_BK = 16, S_STAGES_MAX = 6, S_MAX_SLICES = 7,
        S_NT_MAX = 96, S_NACC = 5, S_DRAIN_STEPS = 16, S_EPI_WARPS = 16, S_THREADS = 64 + 32 * S_EPI_WARPS };
 
 // A BF16 slice array in the tensor cores' canonical no-swizzle K-major order

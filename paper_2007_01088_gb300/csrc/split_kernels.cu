@@ -160,7 +160,8 @@ __global__ void __launch_bounds__(256)
 tau_contravariant_dd_kernel(const float2 *__restrict__ W1, const float2 *W2,
                             const float2 *__restrict__ W3, float2 *tt,
                             const float2 *__restrict__ ev, const float2 *__restrict__ eo,
-                            float w_hi, float w_lo, int nv, unsigned int *__restrict__ maxbits) {
+                            float w_hi, float w_lo, int nv, unsigned int *__restrict__ maxbits,
+                            float2 *__restrict__ tau_out) {
   __shared__ float2 sm[6][CV_SLOT];
   const long long nv2 = (long long)nv * nv, nv3 = nv2 * nv;
   const long long sbase = blockIdx.y * nv3;
@@ -262,6 +263,20 @@ tau_contravariant_dd_kernel(const float2 *__restrict__ W1, const float2 *W2,
   issue(4);
   stage(4);
   __syncthreads();
+  if (tau_out) {  // tau itself, [slot][a][b][c] like tau~ (the densities' D_vv and D_oo)
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      if (slot[q] != q) continue;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int e = t + 256 * h, z = e & 7, y = (e >> 3) & 7, x = e >> 6;
+        const int gx = cx[q] * 8 + x, gy = cy[q] * 8 + y, gz = cz[q] * 8 + z;
+        if (gx < nv && gy < nv && gz < nv)
+          tau_out[sbase + (long long)gx * nv2 + (long long)gy * nv + gz] =
+              sm[q][z * CV_SZ + x * CV_SX + y];
+      }
+    }
+  }
   dd::df v[2][6];
   bool own[2];
 #pragma unroll
@@ -557,13 +572,13 @@ int launch_maxabs(const double *x, long long n, unsigned long long *out, cudaStr
 int launch_tau_contravariant_dd(const float2 *W1, const float2 *W2, const float2 *W3,
                                 float2 *tt, const float2 *ev, const float2 *eo, float w_hi,
                                 float w_lo, int nv, int nslot, unsigned int *maxbits,
-                                cudaStream_t st) {
+                                cudaStream_t st, float2 *tau_out) {
   if (nslot <= 0) return CC3_OK;
   const long long nx = (nv + 7) / 8, ncube = nx * (nx + 1) * (nx + 2) / 6;  // A >= B >= C
   if (ncube > 0x7fffffffLL || nslot > 65535)
     return CC3_FAIL(CC3_ERR_ARG, "tau_contravariant_dd grid");
   tau_contravariant_dd_kernel<<<dim3((unsigned)ncube, nslot), 256, 0, st>>>(
-      W1, W2, W3, tt, ev, eo, w_hi, w_lo, nv, maxbits);
+      W1, W2, W3, tt, ev, eo, w_hi, w_lo, nv, maxbits, tau_out);
   return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_FAIL(CC3_ERR_CUDA, "split element-wise kernel launch");
 }
 int launch_to_dd(const double *x, float2 *y, long long n, cudaStream_t st) {
@@ -586,6 +601,35 @@ int launch_left_outer_dd(float2 *W1, const int *tri, int bj, int ns, int nslot, 
 int launch_slot_exponent(const unsigned int *maxbits, int *ex, int nslot, cudaStream_t st) {
   slot_exponent_kernel<<<(nslot + 127) / 128, 128, 0, st>>>(maxbits, ex, nslot);
   return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_FAIL(CC3_ERR_CUDA, "split element-wise kernel launch");
+}
+// maxbits[u] = max |hi| (as float bits) over slot u's n elements of x
+__global__ void slot_maxabs_dd_kernel(const float2 *__restrict__ x, long long n,
+                                      unsigned int *__restrict__ maxbits) {
+  const float2 *xs = x + (long long)blockIdx.y * n;
+  float m = 0.f;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(xs[e].x));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(maxbits + blockIdx.y, __float_as_uint(m));
+}
+__global__ void add_int_kernel(const int *__restrict__ a, const int *__restrict__ b,
+                               int *__restrict__ c, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) c[i] = a[i] + b[i];
+}
+int launch_slot_maxabs_dd(const float2 *x, long long n, int nslot, unsigned int *maxbits,
+                          cudaStream_t st) {
+  if (nslot <= 0) return CC3_OK;
+  if (nslot > 65535) return CC3_FAIL(CC3_ERR_ARG, "slot_maxabs: slots");
+  const int blocks = (int)std::min<long long>((n + 255) / 256, 1024);
+  slot_maxabs_dd_kernel<<<dim3(blocks, nslot), 256, 0, st>>>(x, n, maxbits);
+  return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_FAIL(CC3_ERR_CUDA, "slot_maxabs launch");
+}
+int launch_add_int(const int *a, const int *b, int *c, int n, cudaStream_t st) {
+  if (n <= 0) return CC3_OK;
+  add_int_kernel<<<(n + 127) / 128, 128, 0, st>>>(a, b, c, n);
+  return cudaGetLastError() == cudaSuccess ? CC3_OK : CC3_FAIL(CC3_ERR_CUDA, "add_int launch");
 }
 int launch_common_exponent(const unsigned int *maxbits, int *ex, int nslot, int bj, int ns,
                            cudaStream_t st) {

@@ -30,11 +30,17 @@ int launch_maxabs(const double *x, long long n, unsigned long long *out, cudaStr
 // tau from the W build's three partial sums W1 + W2 + W3 (dd, [slot][c][a][b])
 // over (w - eps), and tau~ (dd, [slot][a][b][c]) into tt, which may be W2;
 // ev: dd virtual orbital energies, eo: dd e_i + e_j + e_k of each slot
+// tau_out (optional): tau itself, [slot][a][b][c] (dd), written as well
 int launch_tau_contravariant_dd(const float2 *W1, const float2 *W2, const float2 *W3,
                                 float2 *tt, const float2 *ev, const float2 *eo, float w_hi,
                                 float w_lo, int nv, int nslot, unsigned int *maxbits,
-                                cudaStream_t st);
+                                cudaStream_t st, float2 *tau_out = nullptr);
 int launch_slot_exponent(const unsigned int *maxbits, int *ex, int nslot, cudaStream_t st);
+// maxbits[u] = max |x.hi| over the n elements of slot u (atomic max; zero it first)
+int launch_slot_maxabs_dd(const float2 *x, long long n, int nslot, unsigned int *maxbits,
+                          cudaStream_t st);
+// c[i] = a[i] + b[i]
+int launch_add_int(const int *a, const int *b, int *c, int n, cudaStream_t st);
 // one exponent (that of the largest maximum) for every active slot u (u % bj < ns)
 int launch_common_exponent(const unsigned int *maxbits, int *ex, int nslot, int bj, int ns,
                            cudaStream_t st);

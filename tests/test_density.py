@@ -14,14 +14,17 @@ CPU part (pins of the oracle, nothing here touches the GPU):
 - no = 1 and nv = 1 give zero; linearity in the left state; the FLOP count.
 
 GPU part (marked gpu): the library's FP64 density through the C ABI against
-the oracle, 1e-11 relative to the largest element of each block.
+the oracle, 1e-11 relative to the largest element of each block; the split
+(BF16 slice) density with a left state normalised like the trial vectors,
+within the split path's absolute and relative targets.
 """
 import numpy as np
 import pytest
 
 import oracle
 from oracle import definition as D
-from cc3_inputs import make_inputs
+from cc3_inputs import make_inputs, make_trial_vectors
+from split_tol import split_close, split_err
 
 
 def _left(no, nv, seed):
@@ -261,13 +264,14 @@ def test_density_refusals(g):
             fn()
         return str(e.value)
 
-    assert "(-7)" in status(lambda: ctx.density(L1, L2, 0.1, prec=g.CC3_SPLIT_BF16))
+    assert "(-7)" in status(lambda: ctx.density(L1, L2, 0.1, prec=g.CC3_SPLIT_INT8))
     # a frequency on a triples denominator (i = j = k included)
     eps = inp.eps_v[0] * 3 - inp.eps_o[0] * 3
     assert "(-5)" in status(lambda: ctx.density(L1, L2, float(eps)))
     assert "(-1)" in status(lambda: ctx.density(L1, L2, float("nan")))
     ctx.set_triples([[2, 1, 0]])
     assert "(-7)" in status(lambda: ctx.density(L1, L2, 0.1))
+    assert "(-7)" in status(lambda: ctx.density(L1, L2, 0.1, prec=g.CC3_SPLIT_BF16))
 
 
 @pytest.mark.gpu
@@ -281,3 +285,62 @@ def test_density_small_and_ragged(g, no, nv):
     doo, dov, dvv = g.Context(inp).density(L1, L2, -0.15)
     for x, k in ((doo, "Doo"), (dov, "Dov"), (dvv, "Dvv")):
         assert _rel(x, ref[k]) < 1e-11, k
+
+
+# ---- split (BF16 slice) path -------------------------------------------------------------
+# Left state normalised like the trial vectors, so that the absolute targets of
+# the split path apply as for rho.
+
+def _left_unit(no, nv, seed):
+    L1, L2 = make_trial_vectors(no, nv, 1, seed=seed)
+    return L1[0], L2[0]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("no,nv", [(3, 9), (4, 20), (2, 17), (5, 33), (6, 24), (7, 16)])
+def test_split_density_matches_oracle(g, no, nv):
+    inp = make_inputs(no, nv, seed=700 + no * nv)
+    L1, L2 = _left_unit(no, nv, seed=no + 5 * nv)
+    ctx = g.Context(inp)
+    for w in (0.25, 0.0):
+        ref = _density(inp, w, L1, L2)
+        doo, dov, dvv = ctx.density(L1, L2, w, prec=g.CC3_SPLIT_BF16)
+        for x, k in ((doo, "Doo"), (dov, "Dov"), (dvv, "Dvv")):
+            assert split_close(x, ref[k]), (k, w, split_err(x, ref[k]))
+    c = ctx.counters()
+    nvt = nv * (nv + 1) * (nv + 2) // 6 - nv
+    assert c["nominal_flop"] == 6 * nv ** 4 * (no ** 3 - no) + 24 * nv * no ** 3 * nvt
+    assert c["slices"] == 6 and c["launches"] > 0
+    # FP64 after split on the same context
+    doo, dov, dvv = ctx.density(L1, L2, 0.0)
+    for x, k in ((doo, "Doo"), (dov, "Dov"), (dvv, "Dvv")):
+        assert _rel(x, ref[k]) < 1e-11, k
+
+
+@pytest.mark.gpu
+def test_split_density_larger_shape_and_device_pointers(g):
+    """Several triple batches, device pointers and an odd nv."""
+    torch = pytest.importorskip("torch")
+    no, nv = 9, 37
+    inp = make_inputs(no, nv, seed=21)
+    L1, L2 = _left_unit(no, nv, seed=22)
+    ref = _density(inp, -0.1, L1, L2)
+    ctx = g.Context(inp, device=True)
+    doo, dov, dvv = ctx.density(torch.from_numpy(L1).cuda(), torch.from_numpy(L2).cuda(),
+                                -0.1, prec=g.CC3_SPLIT_BF16)
+    for x, k in ((doo, "Doo"), (dov, "Dov"), (dvv, "Dvv")):
+        x = x.cpu().numpy()
+        assert split_close(x, ref[k]), (k, split_err(x, ref[k]))
+
+
+@pytest.mark.gpu
+def test_split_density_small(g):
+    """no = 2: two triples with one pair of equal indices each, plus the
+    i = j = k triples that only the resident D_oo term uses."""
+    no, nv = 2, 5
+    inp = make_inputs(no, nv, seed=23)
+    L1, L2 = _left_unit(no, nv, seed=24)
+    ref = _density(inp, 0.3, L1, L2)
+    doo, dov, dvv = g.Context(inp).density(L1, L2, 0.3, prec=g.CC3_SPLIT_BF16)
+    for x, k in ((doo, "Doo"), (dov, "Dov"), (dvv, "Dvv")):
+        assert split_close(x, ref[k]), (k, split_err(x, ref[k]))
