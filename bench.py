@@ -177,6 +177,39 @@ def oracle_sample(inp, seconds_target=15.0, nthreads=0, n=None, seed=11):
                        f"{r['threads']} OpenMP threads")
 
 
+def blas_sample(inp, seconds_target=15.0, seed=12):
+    """Time the BLAS-backed restatement of Algorithm 1 (the oracle's matrix
+    form: one numpy matrix product per contraction, numpy's BLAS threads on
+    the host cores) on a bounded, seeded sample of triples, sized from a
+    calibration run on one triple.  The reordered integral copies are made
+    before the timed region."""
+    import oracle
+    from oracle import matrix_form as MF
+    from cc3_inputs import unique_triples
+    tr = unique_triples(inp.no)
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(len(tr))
+    blocks = MF.Blocks(oracle.symmetric_blocks(inp))
+
+    def run(sel):
+        t0 = time.perf_counter()
+        MF.omega(inp.no, inp.nv, inp.eps_o, inp.eps_v, inp.t2, blocks, triples=sel)
+        return time.perf_counter() - t0
+
+    dt1 = run([tr[order[0]][:3]])
+    n = int(max(1, min(len(tr), seconds_target / max(dt1, 1e-3))))
+    sel = [tuple(int(x) for x in tr[k][:3]) for k in order[:n]]
+    w = sum(tr[k][3] for k in order[:n])
+    dt = run(sel)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return dict(value=4.0 * inp.nv ** 4 * w / dt / 1e12, unit="TFLOP/s", cores=cores,
+                kind="blas restatement of Algorithm 1 (numpy matrix products)",
+                seconds=dt, cpu=cpu_model(),
+                sample=f"{n} of {len(tr)} triples (weight {w} of {inp.no**3 - inp.no}) of "
+                       f"the no={inp.no} nv={inp.nv} residual; numpy BLAS threads on "
+                       f"{cores} host cores (transposes single-threaded)")
+
+
 def workload_inputs(args, rank=0):
     """The bench's problem: a named workload of the input generator (default:
     the L-proline-sized residual) or --no/--nv."""
@@ -981,6 +1014,9 @@ def run_omega(args):
         sample = oracle_sample(inp)
         line["cpu_baseline"] = {k: v for k, v in sample.items()
                                 if k in ("value", "unit", "cores", "kind", "sample", "cpu")}
+        blas = blas_sample(inp)
+        line["cpu_baseline"]["blas"] = {k: v for k, v in blas.items()
+                                        if k in ("value", "unit", "cores", "kind", "sample")}
     # the split path against the FP64 path (seeded triple sample) and both
     # against the oracle (the cpu_baseline sample)
     if one and prec == g.CC3_SPLIT_BF16 and not args.no_fp64_compare:

@@ -129,7 +129,7 @@ def omega(no, nv, eps_o, eps_v, t2, blocks, triples=None):
     vvov, F_ov).  Returns dict(omega1, omega2, omega2_tilde, E_T)."""
     triples = all_triples(no) if triples is None else [tuple(int(x) for x in t) for t in triples]
     eo = np.asarray(eps_o)
-    blocks = Blocks(blocks)
+    blocks = blocks if isinstance(blocks, Blocks) else Blocks(blocks)
     om1 = np.zeros((no, nv))
     omt = np.zeros((no, no, nv, nv))
 

@@ -86,3 +86,14 @@ def test_serving_stream_is_the_mixed_workload():
     assert all(1 <= q["nvec"] <= 6 for q in plan)
     rate = len(plan) / plan[-1]["t"]
     assert 3.0 < rate < 5.0
+
+
+def test_blas_baseline_times_a_bounded_sample():
+    """The BLAS-backed CPU baseline times the oracle's matrix form on a seeded
+    sample; at a size where the sample is the whole loop its rate is positive."""
+    import bench
+    from cc3_inputs import make_inputs
+    inp = make_inputs(3, 8, seed=2)
+    r = bench.blas_sample(inp, seconds_target=30.0)
+    assert r["value"] > 0 and r["cores"] >= 1 and r["unit"] == "TFLOP/s"
+    assert r["sample"].startswith("7 of 7 triples (weight 24 of 24)")
