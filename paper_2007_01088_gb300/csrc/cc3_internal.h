@@ -219,7 +219,7 @@ void plan_left_q(Plan &P, int no, int nv, const int ijk[3], int slot);
 int left_l3_batch(cc3_ctx *c, const PtrTable &pt, int t0, int t1, double w, const double *L1d,
                   const double *ltd, int *tri, double *wsW, double *wsT, cudaStream_t s);
 int left_finish(cc3_ctx *c, const PtrTable &pt, const double *s2raw, double *s2d,
-                cudaStream_t s);
+                cudaStream_t s, bool chol_done = false);
 // the densities' FP64 pieces shared by both paths (density.cu): the end of the
 // occupied loop (pt: B_DY = Y, B_DOV = Dov, B_T2), and Doo from tau and L~ of
 // every triple of tri (3 ints each, sorted i >= j >= k) held resident

@@ -213,8 +213,9 @@ int left_l3_batch(cc3_ctx *c, const PtrTable &pt, int t0, int t1, double w, cons
 
 namespace {
 
-// sigma1 terms outside the loops (rows and columns as in the header)
-int left_singles(cc3_ctx *c, const PtrTable &pt, cudaStream_t s) {
+// sigma1 terms outside the loops (rows and columns as in the header); with
+// chol_done the Cholesky product N = L . G is already in B_MJ
+int left_singles(cc3_ctx *c, const PtrTable &pt, cudaStream_t s, bool chol_done = false) {
   const int no = c->no, nv = c->nv, n = no + nv, naux = c->naux;
   const long long nv2 = (long long)nv * nv, nvo = (long long)nv * no, n2 = (long long)n * n;
   const long long ovl = (long long)nv * no * nv;  // stride of the first ovov index
@@ -296,7 +297,7 @@ int left_singles(cc3_ctx *c, const PtrTable &pt, cudaStream_t s) {
   chol1.jobs[jb].C = s1;
   chol1.jobs[jb].Ct = s1;
   TRY(jac_run_plan(c, thin, 1, pt, s));
-  TRY(jac_run_plan(c, wide, 0, pt, s));
+  if (!chol_done) TRY(jac_run_plan(c, wide, 0, pt, s));
   TRY(jac_run_plan(c, chol1, 1, pt, s));
   return CC3_OK;
 }
@@ -383,10 +384,11 @@ int left_fp64(cc3_ctx *c, int nvec, const double *w, const double *L1d, const do
 
 // sigma1 from Q, G, H, Lt2 and the cached Algorithm 2 intermediates (pt's
 // B_Q, B_G, B_H, B_LT, B_ZV, B_ZO; output B_S1), then sigma2 = the pair-
-// symmetric part of s2raw
+// symmetric part of s2raw.  chol_done: B_MJ already holds N[J][(c,k)] =
+// sum_bd L^J_bd G[b][d][c][k].
 int left_finish(cc3_ctx *c, const PtrTable &pt, const double *s2raw, double *s2d,
-                cudaStream_t s) {
-  TRY(left_singles(c, pt, s));
+                cudaStream_t s, bool chol_done) {
+  TRY(left_singles(c, pt, s, chol_done));
   const long long nt2 = (long long)c->no * c->no * c->nv * c->nv;
   pair_symmetrize_kernel<<<grid_for(nt2), 256, 0, s>>>(s2raw, s2d, c->no, c->nv);
   CU(cudaGetLastError());

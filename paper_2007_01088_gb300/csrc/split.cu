@@ -91,6 +91,9 @@ enum MapId {
   // densities: t2 as [q][l][(u,w)] in both K orders (Y), and tau itself in the
   // rows-x views of the three cyclic layouts (D_vv)
   MD_T2YA, MD_T2YB, MD_TAU0, MD_TAU1, MD_TAU2,
+  // the left transformation's Cholesky product: L^J_bd as [J][(b,d)] and one
+  // vector's G as [(c,k)][(b,d)]
+  ML_CHA, ML_GB,
   MAP_COUNT
 };
 static_assert((int)MAP_COUNT <= (int)SMAX_MAPS, "map table");
@@ -1889,18 +1892,91 @@ int split_left_jacobian(cc3_ctx *c, int nvec, const double *w, const double *L1d
                    : CC3_FAIL(CC3_ERR_TIMEOUT, "split engine wait gave up");
   }
   if (prep) jac_set_prep(c, CC3_SPLIT_BF16);
-  // sigma1 (FP64, from Q, G, H, Lt2 and Z~) and the pair-symmetric sigma2
+  // The Cholesky product of sigma1, N[J][(c,k)] = sum_bd L^J_bd G[b][d][c][k]
+  // (M = naux, N = nv no, K = nv^2), on the tensor cores: the slices of L^J_bd
+  // once, those of each vector's G (its own exponent) per vector.
+  const int naux = c->naux, n = no + nv;
+  const long long nvo = (long long)nv * no, Kc = (long long)nv * vp;
+  SArrTable ac = S->arrs;
+  int Ech = 0;
+  __nv_bfloat16 *gsl = nullptr;
+  {
+    __nv_bfloat16 *lch = nullptr;
+    unsigned long long *mx = nullptr;
+    TRY(B.get(&mx, 1));
+    CU(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), st));
+    TRY(launch_maxabs(c->chol, (long long)naux * n * n, mx, st));
+    unsigned long long hb = 0;
+    CU(cudaMemcpyAsync(&hb, mx, sizeof(hb), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    double x;
+    std::memcpy(&x, &hb, 8);
+    Ech = exponent_of(x);
+    const Gather g = {(long long)no * n + no, 0, 0, (long long)n * n, n, 1, 1, naux, vp,
+                      nv, nv, 0};
+    TRY(sliced(&lch, c->chol, naux, (int)Kc, Ech, g, naux));
+    const size_t ng_sl = arr_elems(Kc, nvo, 1, s);
+    TRY(B.get(&gsl, ng_sl));
+    CU(cudaMemsetAsync(gsl, 0, ng_sl * sizeof(__nv_bfloat16), st));  // padding rows
+    ac.a[ML_CHA] = make_arr(lch, Kc, naux, 1, s);
+    ac.a[ML_GB] = make_arr(gsl, Kc, nvo, 1, s);
+  }
+  const int kspl = std::max(1, (int)((Kc / S_BK + S->ks_target - 1) / std::max(16, S->ks_target)));
+  // sigma1 (FP64, from Q, G, H, N, Lt2 and Z~) and the pair-symmetric sigma2
   PtrTable pt;
   jac_fill_ptrs(c, &pt);
   pt.p[B_MJ] = N;
+  VPtrTable PC = P;
+  PC.p[B_MJ] = N;
   for (int v = 0; v < nvec; ++v) {
+    double *Gv = G + v * ng;
+    TRY(launch_zero(N, (size_t)naux * nvo, st));
+    unsigned long long *mx = nullptr;
+    TRY(B.get(&mx, 1));
+    CU(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), st));
+    TRY(launch_maxabs(Gv, (long long)ng, mx, st));
+    unsigned long long hb = 0;
+    CU(cudaMemcpyAsync(&hb, mx, sizeof(hb), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    double x;
+    std::memcpy(&x, &hb, 8);
+    if (x > 0.0) {
+      const int EG = exponent_of(x);
+      const Gather g = {0, 0, 0, 1, (long long)nv * nvo, nvo, 1, (int)nvo, vp, nv, nv, 0};
+      trace_begin(c, TR_SPLIT_ELEM, st);
+      TRY(launch_slice_gather(Gv, gsl, s, EG, g, nvo, (int)Kc, (int)nvo, st));
+      trace_end(c, TR_SPLIT_ELEM, st, 0.0, 0.0);
+      *L += 1;
+      SPlan pc;
+      const int jb = new_sjob(pc, naux, (int)nvo, ntile_for((int)nvo), 1, kspl, SEPI_F64_ATOMIC,
+                              Ech + EG - 14, ex, s);
+      pc.jobs[jb].C = outd(B_MJ, 0, nvo, 1);
+      pc.jobs[jb].Ct = pc.jobs[jb].C;
+      add_sterm(pc, jb, opd(ML_CHA, 0), opd(ML_GB, 0), (int)Kc, 0, ex, s);
+      SDevPlan d;
+      TRY(s_upload_plan(pc, &d, st));
+      const int rc = run(d, ac, PC, TR_SPLIT_OMEGA);
+      CU(cudaStreamSynchronize(st));  // the plan's tables are freed next
+      s_free_plan(&d);
+      TRY(rc);
+    }
     pt.p[B_LT] = lt + v * nt2;
     pt.p[B_Q] = Q + v * n1;
-    pt.p[B_G] = G + v * ng;
+    pt.p[B_G] = Gv;
     pt.p[B_H] = H + v * nh;
     pt.p[B_S1] = s1d + v * n1;
     TRY(launch_zero(s1d + v * n1, n1, st));
-    TRY(left_finish(c, pt, s2raw + v * nt2, s2d + v * nt2, st));
+    TRY(left_finish(c, pt, s2raw + v * nt2, s2d + v * nt2, st, true));
+  }
+  {
+    int hs2 = 0;
+    CU(cudaMemcpyAsync(&hs2, S->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (hs2 != 0) {
+      cudaMemsetAsync(S->status, 0, sizeof(int), st);
+      return hs2 == 2 ? CC3_FAIL(CC3_ERR_ARG, "a left-Jacobian plan addressed outside a slice array")
+                      : CC3_FAIL(CC3_ERR_TIMEOUT, "split engine wait gave up");
+    }
   }
   CU(cudaStreamSynchronize(st));
   c->counters.executed_flop += ex + ex_tau;
