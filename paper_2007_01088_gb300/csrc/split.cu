@@ -1735,12 +1735,12 @@ int split_left_jacobian(cc3_ctx *c, int nvec, const double *w, const double *L1d
     TRY(launch_slice_gather(l2, dst(2), s, ELt, g, onv * nv, op, nv, st));
   }
   // L3 slots of all vectors (as the right transformation's R3 slots); larger
-  // batches than the right transformation's (up to 40 GB, at most 40 % of the free
+  // batches than the right transformation's (up to 120 GB, at most 40 % of the free
   // memory) give the grouped G jobs more terms
   const double per_slot = (double)nv2 * nv * 24.0 + 3.0 * s * nv2 * vp * 2.0;
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
-  const double slot_budget = std::min(40.0e9, 0.4 * (double)free_b);
+  const double slot_budget = std::min(120.0e9, 0.4 * (double)free_b);
   const int bj = std::max(1, std::min(S->batch, (int)(slot_budget / (per_slot * nvec))));
   const int nslot = nvec * bj;
   float2 *Wj = nullptr, *TTj = nullptr, *W3j = nullptr;
