@@ -594,9 +594,9 @@ def density_measure(args, local):
     """Triples contributions of Algorithm 3 to the one-electron density of a
     left state: no=12, nv=120, a seeded left vector normalised like the trial
     vectors at w = 0.25, one warm-up call and `--dsteps` timed calls per path
-    with inputs and outputs resident on the device.  The FP64 path gives the
-    line's figures; the split (BF16 slice) path is reported beside it with its
-    largest deviation from the FP64 densities."""
+    with inputs and outputs resident on the device.  The split (BF16 slice)
+    path gives the figures, with its largest deviation from the FP64
+    densities; the FP64 path is reported beside it (`fp64`)."""
     import torch
     import paper_2007_01088_gb300 as g
     from cc3_inputs import make_inputs, make_trial_vectors
@@ -656,12 +656,13 @@ def density_measure(args, local):
         "D_vv": float(np.abs(svv - dvv).max())}
     split["max_abs"] = {"D_oo": float(np.abs(doo).max()), "D_ov": float(np.abs(dov).max()),
                         "D_vv": float(np.abs(dvv).max())}
-    r["workload"] = (f"triples density of a left state (Algorithm 3), no={no} nv={nv}, "
-                     "w=0.25, FP64 path, seeded synthetic inputs and left vector")
-    r["split_bf16"] = split
+    split["workload"] = (f"triples density of a left state (Algorithm 3), no={no} nv={nv}, "
+                         "w=0.25, split (BF16 slice) path, seeded synthetic inputs and a "
+                         "normalised left vector")
     r["trace_D_vv_plus_trace_D_oo"] = float(np.trace(dvv) + np.trace(doo))
     r["trace_D_vv"] = float(np.trace(dvv))
-    return r
+    split["fp64"] = r
+    return split
 
 
 def _timed_calls(stream, fn, steps):
@@ -794,7 +795,7 @@ def run_density(args):
     line = {"metric": "CC3 triples density TFLOP/s (Algorithm 3 FLOP per left state)",
             "value": r["value"], "unit": "TFLOP/s", "n_gpus": 1, "steps": r["steps"],
             "warmup": 1, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": r["workload"]}, "density": r, "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
