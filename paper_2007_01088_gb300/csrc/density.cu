@@ -386,15 +386,19 @@ int density_fp64(cc3_ctx *c, double w, const double *L1d, const double *L2d, dou
 // virtual triple of the view.  tab[((y*2 + h)*no + k)*4 + {0..3}] = {T, s0, s1,
 // s2}: the stored tensor T ([a][b][c] double-float, T < 0: a zero row) and the
 // strides of the view's three slots in it.  Per chunk of DOO_E values of e the
-// block stages the 2 no rows as doubles in shared memory (a padded row stride),
-// then each thread accumulates up to 4 of the no^2 products (blockIdx.z selects
-// the group of 1024 products).
+// block stages the 2 no rows (double-float) in shared memory (a padded row
+// stride), then each thread accumulates up to 4 of the no^2 products
+// (blockIdx.z selects the group of 1024 products) in FP32 arithmetic: each
+// double-float product as a rounded high part plus its error and cross terms
+// (FMA), the high parts summed with their rounding errors (two-sum), the low
+// parts plainly; each chunk's sum then adds into an FP64 accumulator.  The
+// terms keep ~2^-44 of their size, well inside the FP64 path's agreement.
 constexpr int DOO_E = 128, DOO_LD = DOO_E + 1;
 __global__ void __launch_bounds__(256)
     doo_pairs_kernel(const float2 *__restrict__ lt_all, const float2 *__restrict__ tau_all,
                      const long long *__restrict__ tab, const double *__restrict__ wgt, int no,
                      int nv, double *__restrict__ C) {
-  extern __shared__ double sm[];  // [2][no][DOO_LD]
+  extern __shared__ float2 sm2[];  // [2][no][DOO_LD]
   const long long nv2 = (long long)nv * nv, nv3 = nv2 * nv;
   const long long *tb = tab + (long long)blockIdx.y * 2 * no * 4;
   const int t = threadIdx.x, e0 = t % DOO_E, h = t / DOO_E;  // h: 0 = L~, 1 = tau
@@ -409,22 +413,31 @@ __global__ void __launch_bounds__(256)
     __syncthreads();  // the previous chunk's products are done
     for (int k = 0; k < no; ++k) {
       const long long *r = tb + ((long long)h * no + k) * 4;
-      double x = 0.0;
-      if (in && r[0] >= 0) {
-        const float2 f = X[r[0] * nv3 + v0 * r[1] + v1 * r[2] + v2 * r[3]];
-        x = (double)f.x + (double)f.y;
-      }
-      sm[(h * no + k) * DOO_LD + e0] = x;
+      float2 x = make_float2(0.f, 0.f);
+      if (in && r[0] >= 0) x = X[r[0] * nv3 + v0 * r[1] + v1 * r[2] + v2 * r[3]];
+      sm2[(h * no + k) * DOO_LD + e0] = x;
     }
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int p = pbase + t + 256 * q;
       if (p < nprod) {
-        const double *xa = sm + (p / no) * DOO_LD, *yb = sm + (no + p % no) * DOO_LD;
-        double a = acc[q];
-        for (int u = 0; u < DOO_E; ++u) a = fma(xa[u], yb[u], a);
-        acc[q] = a;
+        const float2 *xa = sm2 + (p / no) * DOO_LD, *yb = sm2 + (no + p % no) * DOO_LD;
+        float shi = 0.f, slo = 0.f;
+#pragma unroll 4
+        for (int u = 0; u < DOO_E; ++u) {
+          const float2 x = xa[u], y = yb[u];
+          const float ph = __fmul_rn(x.x, y.x);
+          float pl = __fmaf_rn(x.x, y.x, -ph);
+          pl = __fmaf_rn(x.x, y.y, pl);
+          pl = __fmaf_rn(x.y, y.x, pl);
+          const float sn = __fadd_rn(shi, ph);
+          const float bb = __fsub_rn(sn, shi);
+          const float er = __fadd_rn(__fsub_rn(shi, __fsub_rn(sn, bb)), __fsub_rn(ph, bb));
+          shi = sn;
+          slo = __fadd_rn(slo, __fadd_rn(er, pl));
+        }
+        acc[q] += (double)shi + (double)slo;
       }
     }
   }
@@ -516,7 +529,7 @@ int density_doo_resident(cc3_ctx *c, const float2 *tau_all, const float2 *lt_all
   TRY(launch_zero(C, (size_t)no * no, s));
   CU(cudaMemcpyAsync(dtab, tab.data(), sizeof(long long) * tab.size(), cudaMemcpyHostToDevice, s));
   CU(cudaMemcpyAsync(dw, wgt.data(), sizeof(double) * npair, cudaMemcpyHostToDevice, s));
-  const size_t smem = sizeof(double) * 2 * no * DOO_LD;
+  const size_t smem = sizeof(float2) * 2 * no * DOO_LD;
   if (smem > 227 * 1024) return CC3_FAIL(CC3_ERR_UNSUPPORTED, "too many occupied orbitals");
   CU(cudaFuncSetAttribute(doo_pairs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)smem));
