@@ -516,7 +516,11 @@ __global__ void to_dd_kernel(const double *__restrict__ x, float2 *__restrict__ 
 // + t (vector v, triple t of the batch; slots with t >= ns are idle):
 //   sum over the six terms of P of L1[o0][x] (o1 y|o2 z) + Lt2[o0][o1][x][y] F[o2][z],
 // (o0,o1,o2) = (ijk[s0], ijk[s1], ijk[s2]), (x,y,z) = (v[s0], v[s1], v[s2]),
-// v = (a, b, c).  All factors come as double-float pairs.
+// v = (a, b, c).  All factors come as double-float pairs.  Consecutive threads
+// take consecutive b; where b is y, the ovov factor is read as (o2 z|o1 y) and
+// where b is x, the Lt2 factor as Lt2[o1][o0][y][x] (the integrals' pair symmetry
+// and Lt2's pair symmetry), so that every factor that varies along b is read
+// contiguously.
 __global__ void __launch_bounds__(256)
 left_outer_dd_kernel(float2 *__restrict__ W1, const int *__restrict__ tri, int bj, int ns,
                      const float2 *__restrict__ L1, const float2 *__restrict__ Lt,
@@ -540,8 +544,10 @@ left_outer_dd_kernel(float2 *__restrict__ W1, const int *__restrict__ tri, int b
       const int o0 = ijk[P6[q][0]], o1 = ijk[P6[q][1]], o2 = ijk[P6[q][2]];
       const int x = v[P6[q][0]], y = v[P6[q][1]], z = v[P6[q][2]];
       const float2 f1 = l1[(long long)o0 * nv + x];
-      const float2 g1 = ovov[(((long long)o1 * nv + y) * no + o2) * nv + z];
-      const float2 f2 = lt[(((long long)o0 * no + o1) * nv + x) * nv + y];
+      const float2 g1 = P6[q][1] == 1 ? ovov[(((long long)o2 * nv + z) * no + o1) * nv + y]
+                                      : ovov[(((long long)o1 * nv + y) * no + o2) * nv + z];
+      const float2 f2 = P6[q][0] == 1 ? lt[(((long long)o1 * no + o0) * nv + y) * nv + x]
+                                      : lt[(((long long)o0 * no + o1) * nv + x) * nv + y];
       const float2 g2 = F[(long long)o2 * nv + z];
       sum = dd::add(sum, dd::add(dd::mul(dd::df{f1.x, f1.y}, dd::df{g1.x, g1.y}),
                                  dd::mul(dd::df{f2.x, f2.y}, dd::df{g2.x, g2.y})));
