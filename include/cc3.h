@@ -212,7 +212,7 @@ int cc3_left_jacobian_triples(cc3_ctx *ctx, cc3_prec prec, int nvec, const doubl
  * runs over Algorithm 3's virtual loop a >= b >= c; on CC3_SPLIT_BF16 the
  * occupied loop's contractions run on the tensor cores and D_oo comes from tau
  * and L3~ of every triple (i = j = k included) held resident in device memory,
- * 32 nv^3 bytes per triple (CC3_ERR_OOM when that exceeds half of the free
+ * 16 nv^3 bytes per triple (CC3_ERR_OOM when that exceeds half of the free
  * memory; the FP64 path has no such limit).  With omega = 0 and the
  * ground-state multipliers in place of (L1, L2) the call gives D^{0,0}.
  * L1[no][nv], L2[no][no][nv][nv] (host, or device with CC3_DEVICE_PTRS);
