@@ -344,3 +344,17 @@ def test_split_density_small(g):
     doo, dov, dvv = g.Context(inp).density(L1, L2, 0.3, prec=g.CC3_SPLIT_BF16)
     for x, k in ((doo, "Doo"), (dov, "Dov"), (dvv, "Dvv")):
         assert split_close(x, ref[k]), (k, split_err(x, ref[k]))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("no,nv", [(18, 10), (34, 6)])
+def test_split_density_many_occupied(g, no, nv):
+    """More than 16 occupied orbitals: each thread of the D_oo pair kernel sums
+    several of the no^2 products, and at no = 34 a second group of 1024 products
+    runs (the FP64 path stops at 24 occupied orbitals)."""
+    inp = make_inputs(no, nv, seed=40 + no)
+    L1, L2 = _left_unit(no, nv, seed=41 + no)
+    ref = _density(inp, 0.2, L1, L2)
+    doo, dov, dvv = g.Context(inp).density(L1, L2, 0.2, prec=g.CC3_SPLIT_BF16)
+    for x, k in ((doo, "Doo"), (dov, "Dov"), (dvv, "Dvv")):
+        assert split_close(x, ref[k]), (k, split_err(x, ref[k]))

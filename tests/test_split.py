@@ -57,6 +57,27 @@ def test_omega_split_matches_oracle(g, no, nv):
     assert c["slices"] == 6 and c["executed_flop"] > c["nominal_flop"]
 
 
+def test_omega_split_wide_dynamic_range(g):
+    # each tensor is sliced with one power-of-two scale, so its small elements
+    # keep fewer bits: t2 pair blocks and an occupied slab of the vvvo integrals
+    # scaled down by 1e-3 to 1e-6 make the operands span up to six more orders of
+    # magnitude, and the result must still meet the absolute and relative gates
+    import dataclasses
+    base = make_inputs(4, 40, seed=77)
+    t2 = base.t2.copy()
+    t2[1, 1] *= 1.0e-6
+    t2[2, 0] *= 1.0e-3
+    t2[0, 2] *= 1.0e-3  # keeps t2[i][j][a][b] = t2[j][i][b][a]
+    vvvo = base.g_vvvo.copy()
+    vvvo[:, :, :, 2] *= 1.0e-4
+    inp = dataclasses.replace(base, t2=t2, g_vvvo=vvvo)
+    ref = oracle.omega_inputs(inp)
+    o1, o2, e = g.Context(inp).omega(g.CC3_SPLIT_BF16)
+    assert split_close(o1, ref["omega1"]), split_err(o1, ref["omega1"])
+    assert split_close(o2, ref["omega2"]), split_err(o2, ref["omega2"])
+    assert energy_close(e[0], ref["E_T"]), (e[0], ref["E_T"])
+
+
 def test_autotune_keeps_parity_and_is_shared(g):
     inp = make_inputs(6, 40, seed=12)
     ref = oracle.omega_inputs(inp)
