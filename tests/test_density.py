@@ -358,3 +358,16 @@ def test_split_density_many_occupied(g, no, nv):
     doo, dov, dvv = g.Context(inp).density(L1, L2, 0.2, prec=g.CC3_SPLIT_BF16)
     for x, k in ((doo, "Doo"), (dov, "Dov"), (dvv, "Dvv")):
         assert split_close(x, ref[k]), (k, split_err(x, ref[k]))
+
+
+@pytest.mark.gpu
+def test_density_single_occupied_is_zero(g):
+    """no = 1: every occupied triple has i = j = k, so tau~ and L3~ vanish and
+    all three blocks are zero on both paths (the split path still builds tau3
+    and L3 of the one triple for its D_oo pairs)."""
+    inp = make_inputs(1, 7, seed=5)
+    L1, L2 = _left_unit(1, 7, seed=6)
+    ctx = g.Context(inp)
+    for prec in (g.CC3_FP64, g.CC3_SPLIT_BF16):
+        for x in ctx.density(L1, L2, 0.1, prec=prec):
+            assert np.abs(np.asarray(x)).max() < 1e-30, prec
