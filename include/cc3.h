@@ -190,9 +190,9 @@ int cc3_jacobian_triples(cc3_ctx *ctx, cc3_prec prec, int nvec,
  * L1[n][i][a], L2[n][i][j][a][b], sigma1[n][i][a], sigma2[n][i][j][a][b]; other
  * rules (pointers, frequencies, CC3_ERR_DENOM, symmetric integrals, Cholesky
  * vectors required) as cc3_jacobian_triples.  CC3_FP64 or CC3_SPLIT_BF16 (the
- * W build, the contractions of tau3 and L3 and the G, H, Q intermediates on the
- * tensor cores, sigma1 from them in FP64; CC3_SPLIT_INT8 returns
- * CC3_ERR_UNSUPPORTED). */
+ * W build, the contractions of tau3 and L3, the G, H, Q intermediates and the
+ * Cholesky product of sigma1 on the tensor cores, the rest of sigma1 in FP64;
+ * CC3_SPLIT_INT8 returns CC3_ERR_UNSUPPORTED). */
 int cc3_left_jacobian_triples(cc3_ctx *ctx, cc3_prec prec, int nvec, const double *omega,
                               const double *L1, const double *L2, double *sigma1,
                               double *sigma2, void *cuda_stream);
