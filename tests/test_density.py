@@ -178,6 +178,30 @@ def test_degenerate_sizes_give_zero():
             assert np.abs(r[k]).max() < 1e-30, (no, nv, k)
 
 
+@pytest.mark.parametrize("no,nv", [(4, 5), (3, 6)])
+def test_doo_by_occupied_pairs_equals_the_full_sum(no, nv):
+    """The split path's D_oo reading: D_oo[l][k] = -1/2 sum_{ij} <L3~_{ijk}, tau_{ijl}>
+    over (a,b,c), and because L3~ and tau are unchanged by a simultaneous swap of
+    (i,a) with (j,b), the pair (j,i) repeats the sum of (i,j): the pairs i > j with
+    weight 2 and i = j with weight 1 give the same block.  L3~ vanishes at
+    i = j = k, which the split path uses as zero rows."""
+    inp = make_inputs(no, nv, seed=no * nv)
+    L1, L2 = _left(no, nv, seed=3)
+    full = D.density_full(inp.eps_o, inp.eps_v, inp.t2, oracle.symmetric_blocks(inp), 0.2,
+                          L1, L2)
+    Lc, tau = D.contravariant(full["L3"]), full["tau"]
+    pairs = np.zeros((no, no))
+    for i in range(no):
+        for j in range(i + 1):
+            w = 1.0 if i == j else 2.0
+            pairs += -0.5 * w * np.einsum("kabc,labc->lk", Lc[i, j], tau[i, j])
+    assert _rel(pairs, full["Doo"]) < 1e-13
+    swapped = np.einsum("ijkabc->jikbac", Lc)
+    assert _rel(swapped, Lc) < 1e-13
+    for i in range(no):
+        assert np.abs(Lc[i, i, i]).max() <= 1e-13 * np.abs(Lc).max()
+
+
 def test_linear_in_the_left_state():
     no, nv = 3, 5
     inp = make_inputs(no, nv, seed=4)
