@@ -202,6 +202,19 @@ def test_doo_by_occupied_pairs_equals_the_full_sum(no, nv):
         assert np.abs(Lc[i, i, i]).max() <= 1e-13 * np.abs(Lc).max()
 
 
+def test_symmetries_the_split_outer_products_read():
+    """The split path forms the outer products of L3 (left transformation and
+    densities) reading (o1 y|o2 z) as (o2 z|o1 y) and Lt2[o0][o1][x][y] as
+    Lt2[o1][o0][y][x]: the symmetric integrals have the first symmetry, and the
+    back-transform makes Lt2 pair symmetric for any L2."""
+    inp = make_inputs(4, 9, seed=8)
+    ov = inp.g_ovov
+    assert np.abs(ov - np.transpose(ov, (2, 3, 0, 1))).max() <= 1e-15 * np.abs(ov).max()
+    L2 = np.random.default_rng(9).normal(size=(4, 4, 9, 9))  # not pair symmetric
+    lt = D.back_transform(L2)
+    assert np.abs(lt - np.transpose(lt, (1, 0, 3, 2))).max() <= 1e-15 * np.abs(lt).max()
+
+
 def test_linear_in_the_left_state():
     no, nv = 3, 5
     inp = make_inputs(no, nv, seed=4)
